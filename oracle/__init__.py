@@ -1,0 +1,293 @@
+"""FP64 CPU oracle for the DVGO render step (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs
+of ``bench.py`` may import this package.  The product (the CUDA library and its Python binding)
+never imports it and shares no code with it.
+
+The arithmetic lives in ``dvgo_oracle.c`` (plain C, double precision, one loop per ray); this
+module only compiles it with gcc and marshals numpy arrays through ctypes.  Every function cites
+the passage of the paper (Sun, Sun & Chen, "Direct Voxel Grid Optimization", arXiv 2111.11215)
+that it restates; the C file lists the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dvgo_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libdvgo_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available, no FP contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)  # single-threaded fallback
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.oracle_shift_from_alpha_init.restype = C.c_double
+        _lib.oracle_shift_from_alpha_init.argtypes = [C.c_double, C.c_double]
+        _lib.oracle_lr_decay.restype = C.c_double
+        _lib.oracle_lr_decay.argtypes = [C.c_double, C.c_int, C.c_double]
+        _lib.oracle_alpha_at.restype = C.c_double
+        _lib.oracle_num_threads.restype = C.c_int
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+# ----------------------------------------------------------------------------------------------
+# ctypes mirrors of the C structs
+# ----------------------------------------------------------------------------------------------
+
+_dp = C.POINTER(C.c_double)
+
+
+class _Params(C.Structure):
+    _fields_ = [("mode", C.c_int), ("rgb_act", C.c_int), ("feat_dim", C.c_int), ("n_freq", C.c_int),
+                ("hidden", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("xyz_min", C.c_double * 3), ("xyz_max", C.c_double * 3), ("shift_b", C.c_double),
+                ("delta", C.c_double), ("tau_f", C.c_double), ("t_near", C.c_double),
+                ("t_far", C.c_double), ("bg", C.c_double * 3)]
+
+
+class _Model(C.Structure):
+    _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+class _Grads(C.Structure):
+    _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+class _Prop(C.Structure):
+    _fields_ = [("n_bins", C.c_int), ("n_freq", C.c_int), ("width", C.c_int),
+                ("w", _dp * 4), ("b", _dp * 4)]
+
+
+class _PropGrads(C.Structure):
+    _fields_ = [("w", _dp * 4), ("b", _dp * 4)]
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+@dataclass
+class Params:
+    """Render parameters (Eq. volume_rendering, Eq. density_activation, Sec. 4.2 sampling)."""
+    grid_shape: tuple            # lattice points (nx, ny, nz)
+    xyz_min: tuple = (-1.0, -1.0, -1.0)
+    xyz_max: tuple = (1.0, 1.0, 1.0)
+    shift_b: float = 0.0
+    delta: float = 0.03125
+    tau_f: float = 0.0
+    t_near: float = 0.0
+    t_far: float = 1e30
+    bg: tuple = (1.0, 1.0, 1.0)
+    mode: int = 0                # 0 coarse (colour grid), 1 fine (feature grid + MLP)
+    rgb_act: int = 0
+    feat_dim: int = 3
+    n_freq: int = 4
+    hidden: int = 128
+
+    def _c(self) -> _Params:
+        p = _Params()
+        p.mode, p.rgb_act, p.feat_dim, p.n_freq, p.hidden = self.mode, self.rgb_act, self.feat_dim, self.n_freq, self.hidden
+        p.nx, p.ny, p.nz = (int(v) for v in self.grid_shape)
+        p.xyz_min[:] = [float(v) for v in self.xyz_min]
+        p.xyz_max[:] = [float(v) for v in self.xyz_max]
+        p.shift_b, p.delta, p.tau_f = float(self.shift_b), float(self.delta), float(self.tau_f)
+        p.t_near, p.t_far = float(self.t_near), float(self.t_far)
+        p.bg[:] = [float(v) for v in self.bg]
+        return p
+
+
+@dataclass
+class RenderResult:
+    rgb: np.ndarray
+    tfinal: np.ndarray
+    n_samples: np.ndarray
+    t_enter: np.ndarray
+    t_exit: np.ndarray
+    loss: float | None = None
+    grads: dict = field(default_factory=dict)
+    wbins: np.ndarray | None = None
+
+
+MLP_KEYS = ("w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def shift_from_alpha_init(alpha_init: float, voxel_size: float) -> float:
+    """Sec. 4.1 Eq. low_density_init."""
+    return float(lib().oracle_shift_from_alpha_init(alpha_init, voxel_size))
+
+
+def lr_decay(lr0: float, step: int, decay_steps: float = 20000.0) -> float:
+    """Supp. A: learning rates are scaled by 0.1 at 20k iterations, exponentially."""
+    return float(lib().oracle_lr_decay(lr0, step, decay_steps))
+
+
+def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dict | None = None,
+           target=None, grad_rgb=None, grad_tfinal=None, explicit_t=None, explicit_dt=None,
+           n_bins: int = 0) -> RenderResult:
+    """Render a ray batch forward and, if ``grad_rgb`` is given, backward (Sec. 2-4).
+
+    density: [nx, ny, nz]; cgrid: [nx, ny, nz, C] (coarse colour or fine features);
+    rays_o, rays_d: [R, 3]; jitter: [R] in [0, 1) or None (0.5); mlp: dict of w1..b3 (fine);
+    grad_rgb: [R, 3] upstream dL/dC_hat; grad_tfinal: [R] or None.
+    Returns colours, final transmittances, sample counts, clip bounds, loss and gradients.
+    """
+    P = params._c()
+    density = _f64(density)
+    cgrid = _f64(cgrid)
+    rays_o = _f64(rays_o).reshape(-1, 3)
+    rays_d = _f64(rays_d).reshape(-1, 3)
+    R = rays_o.shape[0]
+    jit = None if jitter is None else _f64(jitter).reshape(R)
+    M = _Model()
+    M.density, M.cgrid = _ptr(density), _ptr(cgrid)
+    mlp_arrs = {}
+    if params.mode == 1:
+        for k in MLP_KEYS:
+            mlp_arrs[k] = _f64(mlp[k])
+            setattr(M, k, _ptr(mlp_arrs[k]))
+    tgt = None if target is None else _f64(target).reshape(R, 3)
+    rgb = np.zeros((R, 3)); tf = np.zeros(R); ns = np.zeros(R, dtype=np.int32)
+    t0 = np.zeros(R); t1 = np.zeros(R); loss = C.c_double(0.0)
+    gC = None if grad_rgb is None else _f64(grad_rgb).reshape(R, 3)
+    gT = None if grad_tfinal is None else _f64(grad_tfinal).reshape(R)
+    G = _Grads()
+    grads = {}
+    if gC is not None:
+        grads["density"] = np.zeros_like(density)
+        grads["cgrid"] = np.zeros_like(cgrid)
+        G.density, G.cgrid = _ptr(grads["density"]), _ptr(grads["cgrid"])
+        if params.mode == 1:
+            for k in MLP_KEYS:
+                grads[k] = np.zeros_like(mlp_arrs[k])
+                setattr(G, k, _ptr(grads[k]))
+    n_expl = 0
+    ts = dts = None
+    if explicit_t is not None:
+        ts = _f64(explicit_t).reshape(R, -1)
+        dts = _f64(explicit_dt).reshape(R, -1)
+        n_expl = ts.shape[1]
+    wb = np.zeros((R, n_bins)) if n_bins > 0 else None
+    lib().oracle_render(C.byref(P), C.byref(M), C.c_int(R), _ptr(rays_o), _ptr(rays_d), _ptr(jit),
+                        C.c_int(n_expl), _ptr(ts), _ptr(dts), _ptr(tgt), _ptr(rgb), _ptr(tf),
+                        ns.ctypes.data_as(C.POINTER(C.c_int)), _ptr(t0), _ptr(t1), C.byref(loss),
+                        _ptr(gC), _ptr(gT), C.byref(G) if gC is not None else None, _ptr(wb),
+                        C.c_int(n_bins))
+    return RenderResult(rgb=rgb, tfinal=tf, n_samples=ns, t_enter=t0, t_exit=t1,
+                        loss=float(loss.value) if tgt is not None else None, grads=grads, wbins=wb)
+
+
+def ray_bounds(params: Params, o, d, p: float = 0.5):
+    """Slab clip and sample count of one ray (Eq. coarse_sample, Sec. 4.2)."""
+    P = params._c()
+    o = _f64(o); d = _f64(d)
+    t0 = C.c_double(); t1 = C.c_double(); n = C.c_int(); dn = np.zeros(3)
+    rc = lib().oracle_ray_bounds(C.byref(P), _ptr(o), _ptr(d), C.c_double(p), C.byref(t0), C.byref(t1),
+                                 _ptr(dn), C.byref(n))
+    return rc, t0.value, t1.value, dn, n.value
+
+
+def interp(params: Params, grid, x):
+    """Sec. 3 Eq. interp: trilinear interpolation of a channel-last grid at one point."""
+    P = params._c()
+    grid = _f64(grid)
+    Cc = 1 if grid.ndim == 3 else grid.shape[-1]
+    out = np.zeros(Cc)
+    lib().oracle_interp(C.byref(P), _ptr(grid), C.c_int(Cc), _ptr(_f64(x)), _ptr(out))
+    return out
+
+
+def alpha_at(params: Params, density, x, delta: float) -> float:
+    """Eq. post_activation: alpha(softplus(interp(x, V) + b), delta) at one point."""
+    P = params._c()
+    lib().oracle_alpha_at.argtypes = [C.POINTER(_Params), _dp, _dp, C.c_double]
+    return float(lib().oracle_alpha_at(C.byref(P), _ptr(_f64(density)), _ptr(_f64(x)), C.c_double(delta)))
+
+
+def mlp_forward(params: Params, mlp: dict, e):
+    """Shallow colour MLP of Sec. 4.2 / Supp. A on a batch of input rows."""
+    P = params._c()
+    e = _f64(e)
+    M = _Model()
+    arrs = {k: _f64(mlp[k]) for k in MLP_KEYS}
+    for k in MLP_KEYS:
+        setattr(M, k, _ptr(arrs[k]))
+    out = np.zeros((e.shape[0], 3))
+    lib().oracle_mlp_forward(C.byref(P), C.byref(M), C.c_int(e.shape[0]), _ptr(e), _ptr(out))
+    return out
+
+
+def adam(param, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None, zero_grad=True):
+    """One Adam step (Kingma & Ba), in place on float64 arrays; lr already decayed."""
+    for a in (param, grad, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().oracle_adam(C.c_long(param.size), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), C.c_double(lr),
+                      C.c_double(beta1), C.c_double(beta2), C.c_double(eps), C.c_int(t),
+                      _ptr(None if lr_scale is None else _f64(lr_scale)), C.c_int(int(zero_grad)))
+
+
+PROP_KEYS = ("w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def proposal(params: Params, prop: dict, n_bins: int, n_freq: int, rays_o, rays_d, labels=None,
+             want_grads: bool = False):
+    """Sample-proposal network: per-ray softmax PDF over n_bins equal bins of [t_enter, t_exit];
+    with labels, the mean cross-entropy loss and (optionally) its gradient."""
+    P = params._c()
+    rays_o = _f64(rays_o).reshape(-1, 3); rays_d = _f64(rays_d).reshape(-1, 3)
+    R = rays_o.shape[0]
+    arrs = {k: _f64(prop[k]) for k in PROP_KEYS}
+    Q = _Prop()
+    Q.n_bins, Q.n_freq, Q.width = n_bins, n_freq, arrs["w1"].shape[0]
+    for i in range(4):
+        Q.w[i] = _ptr(arrs[f"w{i}"]); Q.b[i] = _ptr(arrs[f"b{i}"])
+    probs = np.zeros((R, n_bins))
+    loss = C.c_double(0.0)
+    lab = None if labels is None else _f64(labels).reshape(R, n_bins)
+    grads = None
+    G = None
+    if want_grads:
+        grads = {k: np.zeros_like(arrs[k]) for k in PROP_KEYS}
+        G = _PropGrads()
+        for i in range(4):
+            G.w[i] = _ptr(grads[f"w{i}"]); G.b[i] = _ptr(grads[f"b{i}"])
+    lib().oracle_proposal(C.byref(P), C.byref(Q), C.c_int(R), _ptr(rays_o), _ptr(rays_d), _ptr(lab),
+                          _ptr(probs), C.byref(loss), C.byref(G) if G is not None else None)
+    return probs, (float(loss.value) if lab is not None else None), grads
+
+
+def sample_pdf(probs, t0: float, t1: float, n_samples: int, jit: float = 0.5, eta: float = 1e-3):
+    """Inverse-CDF sampling of sorted samples from a piecewise-constant PDF over equal bins."""
+    probs = _f64(probs)
+    t = np.zeros(n_samples); dt = np.zeros(n_samples)
+    lib().oracle_sample_pdf(C.c_int(probs.size), _ptr(probs), C.c_double(t0), C.c_double(t1),
+                            C.c_int(n_samples), C.c_double(jit), C.c_double(eta), _ptr(t), _ptr(dt))
+    return t, dt
