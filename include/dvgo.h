@@ -1,0 +1,205 @@
+/*
+ * dvgo.h -- C ABI of the GB300 (sm_103a) implementation of the Direct Voxel Grid Optimization
+ * render step: differentiable volume rendering of ray batches through a post-activated density
+ * voxel grid and a colour grid (coarse stage) or a feature grid with a shallow colour MLP (fine
+ * stage), forward, backward and Adam.
+ *
+ * Paper: C. Sun, M. Sun, H.-T. Chen, "Direct Voxel Grid Optimization: Super-fast Convergence for
+ * Radiance Fields Reconstruction", arXiv 2111.11215.  Citations below name its sections and
+ * equations.
+ *
+ * Conventions
+ *   - Every pointer argument named *_out, grad_*, or a grid / ray / weight array is a DEVICE
+ *     pointer; the structs themselves (dvgo_params, dvgo_grid_desc, dvgo_mlp, dvgo_samples) are
+ *     read on the host during the call and may be freed when it returns.
+ *   - The caller owns all device memory and the stream.  Apart from the one entry point that
+ *     says otherwise, the library never allocates: scratch space is a caller-supplied workspace
+ *     of dvgo_workspace_size() bytes (256-byte aligned).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.  Every call
+ *     only enqueues work on that stream and returns; nothing synchronises.
+ *   - Gradients are ACCUMULATED (+=); clear them first (dvgo_adam_step can clear them).
+ *   - Return value: DVGO_OK or a negative dvgo_status.  Argument errors are detected on the host
+ *     before anything is enqueued.  Conditions only visible on the device (a ray with a zero or
+ *     non-finite direction) make that ray sample-free and set a flag in the workspace that
+ *     dvgo_workspace_status() reads back.
+ *   - Grids are channel-last on an align-corners lattice: value (ix, iy, iz, ch) of an
+ *     nx*ny*nz*C grid is at ((ix*ny + iy)*nz + iz)*C + ch; lattice point (ix, iy, iz) sits at
+ *     xyz_min + (ix, iy, iz) * (xyz_max - xyz_min) / (n - 1)   (Sec. 3 Eq. interp).
+ */
+#ifndef DVGO_H
+#define DVGO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DVGO_ABI_VERSION 1
+
+typedef enum {
+    DVGO_OK = 0,
+    DVGO_ERR_INVALID_ARG = -1,   /* null pointer, bad size, inconsistent descriptors          */
+    DVGO_ERR_WORKSPACE = -2,     /* workspace NULL, misaligned or smaller than required       */
+    DVGO_ERR_UNSUPPORTED = -3,   /* a combination this build does not implement               */
+    DVGO_ERR_CUDA = -4,          /* a kernel launch failed (cudaGetLastError)                 */
+    DVGO_ERR_DEVICE = -5         /* device-side flag: a ray had a zero / non-finite direction */
+} dvgo_status;
+
+enum { DVGO_DTYPE_F32 = 0, DVGO_DTYPE_BF16 = 1 };
+enum { DVGO_MODE_COARSE = 0, DVGO_MODE_FINE = 1 };
+enum { DVGO_MLP_FP32 = 0, DVGO_MLP_BF16 = 1 };
+
+/* A voxel grid (Sec. 3 Eq. interp): values on an align-corners lattice spanning the box. */
+typedef struct {
+    int nx, ny, nz;      /* lattice points per axis, each >= 2                                 */
+    int channels;        /* 1 (density), 3 (coarse colour), D (fine features, D <= 16)         */
+    float xyz_min[3];    /* box corners; the density and colour grids must share the box        */
+    float xyz_max[3];
+    int dtype;           /* DVGO_DTYPE_F32, or DVGO_DTYPE_BF16 for the fine feature grid only   */
+} dvgo_grid_desc;
+
+/* Render parameters. */
+typedef struct {
+    int mode;            /* DVGO_MODE_COARSE: colour = interp(x, V_rgb) (Sec. 4.1 Eq. coarse_queries)
+                            DVGO_MODE_FINE: colour = MLP(interp(x, V_feat), PE(d))
+                            (Sec. 4.2 Eq. fine_queries)                                          */
+    int rgb_act;         /* coarse: 0 = identity (the paper states no activation), 1 = sigmoid   */
+    int mlp_prec;        /* fine: DVGO_MLP_FP32 (SIMT FP32) or DVGO_MLP_BF16 (tensor cores,
+                            BF16 operands, FP32 accumulation)                                    */
+    int n_freq_dir;      /* fine: positional-encoding frequencies on d (Supp. A: k_d = 4)        */
+    int hidden;          /* fine: MLP width; this build supports 128 (Supp. A)                   */
+    float step;          /* delta, the sampling step in world units (Supp. A: 0.5 voxel)         */
+    float shift_b;       /* b of Eq. density_activation, e.g. from Eq. low_density_init          */
+    float tau_f;         /* samples with alpha < tau_f are removed (Sec. 4.2 free space skipping) */
+    float t_near, t_far; /* ray clip range before the box intersection                           */
+    float bg[3];         /* c_bg of Eq. volume_rendering                                          */
+} dvgo_params;
+
+/* Colour MLP (fine stage), FP32 row-major [in][out]:
+ *   in = C + 3 + 6*n_freq_dir  ->  hidden  ->  hidden  ->  3
+ *   input row e = [interp(x, V_feat) (C), d (3), sin(2^k d_c) (c-major, k < n_freq_dir),
+ *                  cos(2^k d_c) (c-major)],  ReLU after the hidden layers, sigmoid on the output
+ *   (Sec. 2 Eq. nerf_mlp output activation, Sec. 4.2, Supp. A). */
+typedef struct {
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+} dvgo_mlp;
+
+/* Optional explicit samples (the proposal path): ray r uses n_per_ray samples at distances
+ * t[r*n_per_ray + j] along its normalised direction with step lengths dt[...]; a ray that
+ * misses the box gets none.  NULL selects uniform stepping t_k = t_enter + (k + p) * step. */
+typedef struct {
+    const float *t;
+    const float *dt;
+    int n_per_ray;
+} dvgo_samples;
+
+/* Bytes of workspace that dvgo_render_fwd / dvgo_render_bwd need for n_rays rays.  The bound
+ * covers the longest possible ray: ceil(|xyz_max - xyz_min| / step) + 1 samples. */
+size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
+                           const dvgo_samples *explicit_samples);
+
+/*
+ * Forward render of n_rays rays (Sec. 2 Eq. volume_rendering with the post-activated density
+ * of Sec. 3 Eq. post_activation and the queries of Sec. 4.1 / 4.2):
+ *   1. normalise d and clip the ray to the box and [t_near, t_far] (Sec. 4.2 fine-stage sampling);
+ *   2. sample t_k = t_enter + (k + p) step, k = 0.. while t_k < t_exit (Eq. coarse_sample and the
+ *      jitter p of Supp. A), or use the explicit samples;
+ *   3. sigma_k = softplus(interp(x_k, V_density) + b), alpha_k = 1 - exp(-sigma_k dt_k)
+ *      (Eq. density_activation, Eq. density_2_alpha), dropped when alpha_k < tau_f;
+ *   4. colour c_k from the colour grid (coarse) or the feature grid and the MLP (fine);
+ *   5. C_hat = sum_k T_k alpha_k c_k + T_K bg, T_k = prod_{j<k} (1 - alpha_j).
+ * Inputs: density [nx*ny*nz] FP32; cgrid [nx*ny*nz*C] (FP32, or BF16 for fine features);
+ *   rays_o, rays_d [n_rays*3] FP32; jitter [n_rays] in [0,1) or NULL (p = 0.5);
+ *   target [n_rays*3] or NULL.
+ * Outputs: rgb_out [n_rays*3]; tfinal_out [n_rays] (T_K) or NULL; if target is given,
+ *   loss_out[0] = (1/R) sum_r ||C_hat_r - C_r||^2 (Eq. photo_loss) and dloss_drgb_out
+ *   [n_rays*3] = 2 (C_hat - C) / R, each nullable.
+ * The workspace keeps the per-ray and per-sample state that dvgo_render_bwd consumes; it must
+ * not be modified between the two calls, which must see the same inputs.
+ */
+int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, const float *density,
+                    const dvgo_grid_desc *cgrid_desc, const void *cgrid, const dvgo_mlp *mlp,
+                    int n_rays, const float *rays_o, const float *rays_d, const float *jitter,
+                    const dvgo_samples *explicit_samples, const float *target, float *rgb_out,
+                    float *tfinal_out, float *loss_out, float *dloss_drgb_out, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
+/*
+ * Backward of dvgo_render_fwd: accumulates into the gradients the derivative of
+ *     sum_r ( grad_rgb_r . C_hat_r + grad_tfinal_r * T_K,r )
+ * with respect to the density grid, the colour / feature grid and the MLP parameters.
+ * Compositing state (T_k, the weights and the suffix colour sums) is recomputed from the
+ * per-sample values the forward left in the workspace; the MLP activations are recomputed.
+ * grad_rgb [n_rays*3] (required), grad_tfinal [n_rays] or NULL.
+ * grad_density [nx*ny*nz] FP32; grad_cgrid [nx*ny*nz*C] FP32 (also for a BF16 feature grid);
+ * grad_mlp (fine only) FP32, packed w1 | b1 | w2 | b2 | w3 | b3 in the dvgo_mlp layouts.
+ */
+int dvgo_render_bwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, const float *density,
+                    const dvgo_grid_desc *cgrid_desc, const void *cgrid, const dvgo_mlp *mlp,
+                    int n_rays, const float *rays_o, const float *rays_d, const float *jitter,
+                    const dvgo_samples *explicit_samples, const float *grad_rgb,
+                    const float *grad_tfinal, float *grad_density, float *grad_cgrid,
+                    float *grad_mlp, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Adam hyper-parameters (Kingma & Ba; Sec. 5.2 / Supp. A use Adam with base rates 0.1 for the
+ * grids and 1e-3 for the MLP, decayed by 0.1 over 20k steps). */
+typedef struct {
+    float lr;            /* already-decayed learning rate for this step                        */
+    float beta1, beta2, eps;
+    int step;            /* 1-based step count t (bias correction 1 - beta^t)                  */
+} dvgo_adam_hparams;
+
+/*
+ * One Adam step on n FP32 parameters:  m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
+ *   p -= lr * s_i * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+ * with s_i = lr_scale[i] (nullable; the per-voxel rate of Sec. 4.1 Prior 2) or 1.
+ * param_bf16_out (nullable): also writes the updated parameters rounded to BF16 (the storage
+ * copy of a BF16 feature grid).  zero_grad != 0 clears grad after reading it.
+ * All arrays are device pointers of n elements, 16-byte aligned.
+ */
+int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n,
+                   const dvgo_adam_hparams *h, const float *lr_scale, uint16_t *param_bf16_out,
+                   int zero_grad, void *stream);
+
+/* Learning rate of Supp. A at 0-based step t: lr0 * 0.1^(t / decay_steps). */
+float dvgo_lr_at(float lr0, int step, float decay_steps);
+
+/* Reads (synchronously, on `stream`) the device-side flag word that the last forward left:
+ * returns DVGO_OK or DVGO_ERR_DEVICE when a ray had a zero or non-finite direction. */
+int dvgo_workspace_status(void *workspace, void *stream);
+
+/* Copies the per-ray sample counts that the last forward computed (step 2 of dvgo_render_fwd)
+ * from a workspace into counts_out [n_rays] (device int32), and the batch total into
+ * total_out[0] (device, nullable).  n_rays must be the forward's ray count. */
+int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *total_out, void *stream);
+
+/* Kernel kinds for the optional per-kernel timing below. */
+enum {
+    DVGO_K_RAY_SETUP = 0, DVGO_K_SCAN = 1, DVGO_K_COARSE_FWD = 2, DVGO_K_COARSE_BWD = 3,
+    DVGO_K_FINE_DENSITY = 4, DVGO_K_FINE_COLOUR_FWD = 5, DVGO_K_FINE_COMPOSITE = 6,
+    DVGO_K_FINE_COMP_BWD = 7, DVGO_K_FINE_COLOUR_BWD = 8, DVGO_K_ADAM = 9, DVGO_K_AUX = 10,
+    DVGO_K_COUNT = 11
+};
+
+/* Benchmarking aid.  While enabled (on != 0), every kernel launch of this library is bracketed
+ * by a pair of CUDA events recorded on its stream.  dvgo_profile_read() waits for the recorded
+ * events, returns the summed device time (ms) and the launch count of one kernel kind, and
+ * forgets that kind's records.  Not for use during stream capture.  Host-thread safe. */
+int dvgo_profile_enable(int on);
+int dvgo_profile_read(int kind, double *total_ms, long long *launches);
+
+/* Number of kernels this library has launched in this process (all devices, all streams). */
+long long dvgo_launch_counter(void);
+
+/* Shift b of Sec. 4.1 Eq. low_density_init for alpha_init and voxel size s. */
+float dvgo_shift_from_alpha_init(float alpha_init, float voxel_size);
+
+const char *dvgo_status_string(int status);
+int dvgo_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVGO_H */

@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) implementation of the Direct Voxel Grid Optimization render step.
+
+The compute lives in ``libdvgo.so`` (CUDA, C ABI in ``include/dvgo.h``).  This package only
+marshals torch tensors into that ABI: ``dvgo_*`` functions with the C names, a
+``torch.autograd.Function`` over the forward / backward pair, and a small ``Renderer`` helper
+that owns descriptors and the workspace.  There is no CPU fallback: every call fails loudly when
+the library is missing or a tensor is not on a CUDA device.
+"""
+from .binding import (  # noqa: F401
+    DVGO_DTYPE_BF16, DVGO_DTYPE_F32, DVGO_MLP_BF16, DVGO_MLP_FP32, DVGO_MODE_COARSE, DVGO_MODE_FINE,
+    DVGOError, GridDesc, Params, dvgo_abi_version, dvgo_adam_step, dvgo_lr_at, dvgo_render_bwd,
+    dvgo_render_fwd, dvgo_sample_counts, dvgo_shift_from_alpha_init, dvgo_status_string, dvgo_workspace_size,
+    dvgo_workspace_status, lib, library_path, EXPORTED_SYMBOLS, KERNEL_KINDS, dvgo_profile_enable,
+    dvgo_profile_read, dvgo_launch_counter,
+)
+from .render import Renderer, RenderFunction, FineModel, AdamState, mlp_flat_size  # noqa: F401

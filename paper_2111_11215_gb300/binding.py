@@ -1,0 +1,296 @@
+"""ctypes binding of libdvgo (include/dvgo.h): argument marshalling only.
+
+Each ``dvgo_*`` function here has the name and argument order of the C entry point; tensors are
+passed as device pointers, structs as ctypes mirrors.  A non-zero status raises ``DVGOError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+DVGO_OK = 0
+DVGO_DTYPE_F32, DVGO_DTYPE_BF16 = 0, 1
+DVGO_MODE_COARSE, DVGO_MODE_FINE = 0, 1
+DVGO_MLP_FP32, DVGO_MLP_BF16 = 0, 1
+
+EXPORTED_SYMBOLS = (
+    "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_lr_at",
+    "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
+    "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
+)
+
+KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
+                "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libdvgo.so")
+
+
+class DVGOError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {lib().dvgo_status_string(status).decode()} (status {status})")
+        self.status = status
+
+
+class _GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("channels", C.c_int),
+                ("xyz_min", C.c_float * 3), ("xyz_max", C.c_float * 3), ("dtype", C.c_int)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("mode", C.c_int), ("rgb_act", C.c_int), ("mlp_prec", C.c_int), ("n_freq_dir", C.c_int),
+                ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
+                ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3)]
+
+
+class _Mlp(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+class _Samples(C.Structure):
+    _fields_ = [("t", C.c_void_p), ("dt", C.c_void_p), ("n_per_ray", C.c_int)]
+
+
+class _AdamH(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int)]
+
+
+def lib():
+    """Load libdvgo.so; raise if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "or python paper_2111_11215_gb300/build_lib.py")
+        L = C.CDLL(path)
+        vp, i, sz, f = C.c_void_p, C.c_int, C.c_size_t, C.c_float
+        L.dvgo_workspace_size.restype = sz
+        L.dvgo_workspace_size.argtypes = [vp, vp, i, vp]
+        L.dvgo_render_fwd.restype = i
+        L.dvgo_render_fwd.argtypes = [vp, vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.dvgo_render_bwd.restype = i
+        L.dvgo_render_bwd.argtypes = [vp, vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.dvgo_adam_step.restype = i
+        L.dvgo_adam_step.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp, i, vp]
+        L.dvgo_lr_at.restype = f
+        L.dvgo_lr_at.argtypes = [f, i, f]
+        L.dvgo_workspace_status.restype = i
+        L.dvgo_workspace_status.argtypes = [vp, vp]
+        L.dvgo_sample_counts.restype = i
+        L.dvgo_sample_counts.argtypes = [vp, i, vp, vp, vp]
+        L.dvgo_profile_enable.restype = i
+        L.dvgo_profile_enable.argtypes = [i]
+        L.dvgo_profile_read.restype = i
+        L.dvgo_profile_read.argtypes = [i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.dvgo_launch_counter.restype = C.c_longlong
+        L.dvgo_launch_counter.argtypes = []
+        L.dvgo_shift_from_alpha_init.restype = f
+        L.dvgo_shift_from_alpha_init.argtypes = [f, f]
+        L.dvgo_status_string.restype = C.c_char_p
+        L.dvgo_status_string.argtypes = [i]
+        L.dvgo_abi_version.restype = i
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------------------------
+# Python-side descriptors
+# ----------------------------------------------------------------------------------------------
+
+@dataclass
+class GridDesc:
+    shape: tuple                     # lattice points (nx, ny, nz)
+    channels: int
+    xyz_min: tuple = (-1.0, -1.0, -1.0)
+    xyz_max: tuple = (1.0, 1.0, 1.0)
+    dtype: int = DVGO_DTYPE_F32
+
+    def c(self) -> _GridDesc:
+        g = _GridDesc()
+        g.nx, g.ny, g.nz = (int(v) for v in self.shape)
+        g.channels = int(self.channels)
+        g.xyz_min[:] = [float(v) for v in self.xyz_min]
+        g.xyz_max[:] = [float(v) for v in self.xyz_max]
+        g.dtype = int(self.dtype)
+        return g
+
+
+@dataclass
+class Params:
+    mode: int = DVGO_MODE_COARSE
+    step: float = 0.03125
+    shift_b: float = 0.0
+    tau_f: float = 0.0
+    t_near: float = 0.0
+    t_far: float = 1e30
+    bg: tuple = (1.0, 1.0, 1.0)
+    rgb_act: int = 0
+    mlp_prec: int = DVGO_MLP_FP32
+    n_freq_dir: int = 4
+    hidden: int = 128
+
+    def c(self) -> _Params:
+        p = _Params()
+        p.mode, p.rgb_act, p.mlp_prec = int(self.mode), int(self.rgb_act), int(self.mlp_prec)
+        p.n_freq_dir, p.hidden = int(self.n_freq_dir), int(self.hidden)
+        p.step, p.shift_b, p.tau_f = float(self.step), float(self.shift_b), float(self.tau_f)
+        p.t_near, p.t_far = float(self.t_near), float(self.t_far)
+        p.bg[:] = [float(v) for v in self.bg]
+        return p
+
+
+def _dev(t, name, dtype=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _mlp_struct(mlp):
+    if mlp is None:
+        return None
+    m = _Mlp()
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        setattr(m, k, _dev(mlp[k], f"mlp.{k}", torch.float32))
+    return m
+
+
+def _samples_struct(samples):
+    if samples is None:
+        return None
+    t, dt = samples
+    s = _Samples()
+    s.t = _dev(t, "samples.t", torch.float32)
+    s.dt = _dev(dt, "samples.dt", torch.float32)
+    s.n_per_ray = int(t.shape[-1])
+    return s
+
+
+def _ref(x):
+    return None if x is None else C.byref(x)
+
+
+def _check(status, where):
+    if status != DVGO_OK:
+        raise DVGOError(status, where)
+
+
+# ----------------------------------------------------------------------------------------------
+# Entry points (same names and argument order as include/dvgo.h)
+# ----------------------------------------------------------------------------------------------
+
+def dvgo_abi_version() -> int:
+    return int(lib().dvgo_abi_version())
+
+
+def dvgo_status_string(status: int) -> str:
+    return lib().dvgo_status_string(int(status)).decode()
+
+
+def dvgo_shift_from_alpha_init(alpha_init: float, voxel_size: float) -> float:
+    return float(lib().dvgo_shift_from_alpha_init(alpha_init, voxel_size))
+
+
+def dvgo_lr_at(lr0: float, step: int, decay_steps: float = 20000.0) -> float:
+    return float(lib().dvgo_lr_at(lr0, step, decay_steps))
+
+
+def dvgo_workspace_size(params: Params, density_desc: GridDesc, n_rays: int, samples=None) -> int:
+    p, g = params.c(), density_desc.c()
+    s = _samples_struct(samples) if samples is not None else None
+    return int(lib().dvgo_workspace_size(C.byref(p), C.byref(g), int(n_rays), _ref(s)))
+
+
+def dvgo_render_fwd(params: Params, density_desc: GridDesc, density, cgrid_desc: GridDesc, cgrid, mlp,
+                    rays_o, rays_d, jitter, samples, target, rgb_out, tfinal_out, loss_out, dloss_drgb_out,
+                    workspace, stream=None):
+    p, dd, cd = params.c(), density_desc.c(), cgrid_desc.c()
+    m, s = _mlp_struct(mlp), _samples_struct(samples)
+    R = int(rays_o.shape[0])
+    st = lib().dvgo_render_fwd(
+        C.byref(p), C.byref(dd), _dev(density, "density", torch.float32), C.byref(cd),
+        _dev(cgrid, "cgrid", (torch.float32, torch.bfloat16)), _ref(m), R,
+        _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
+        _dev(jitter, "jitter", torch.float32, True), _ref(s), _dev(target, "target", torch.float32, True),
+        _dev(rgb_out, "rgb_out", torch.float32), _dev(tfinal_out, "tfinal_out", torch.float32, True),
+        _dev(loss_out, "loss_out", torch.float32, True), _dev(dloss_drgb_out, "dloss_drgb_out", torch.float32, True),
+        _dev(workspace, "workspace", torch.uint8), workspace.numel(), _stream(stream))
+    _check(st, "dvgo_render_fwd")
+
+
+def dvgo_render_bwd(params: Params, density_desc: GridDesc, density, cgrid_desc: GridDesc, cgrid, mlp,
+                    rays_o, rays_d, jitter, samples, grad_rgb, grad_tfinal, grad_density, grad_cgrid, grad_mlp,
+                    workspace, stream=None):
+    p, dd, cd = params.c(), density_desc.c(), cgrid_desc.c()
+    m, s = _mlp_struct(mlp), _samples_struct(samples)
+    R = int(rays_o.shape[0])
+    st = lib().dvgo_render_bwd(
+        C.byref(p), C.byref(dd), _dev(density, "density", torch.float32), C.byref(cd),
+        _dev(cgrid, "cgrid", (torch.float32, torch.bfloat16)), _ref(m), R,
+        _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
+        _dev(jitter, "jitter", torch.float32, True), _ref(s), _dev(grad_rgb, "grad_rgb", torch.float32),
+        _dev(grad_tfinal, "grad_tfinal", torch.float32, True), _dev(grad_density, "grad_density", torch.float32),
+        _dev(grad_cgrid, "grad_cgrid", torch.float32), _dev(grad_mlp, "grad_mlp", torch.float32, True),
+        _dev(workspace, "workspace", torch.uint8), workspace.numel(), _stream(stream))
+    _check(st, "dvgo_render_bwd")
+
+
+def dvgo_adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8,
+                   lr_scale=None, param_bf16_out=None, zero_grad=True, stream=None):
+    h = _AdamH()
+    h.lr, h.beta1, h.beta2, h.eps, h.step = float(lr), float(beta1), float(beta2), float(eps), int(step)
+    st = lib().dvgo_adam_step(
+        _dev(param, "param", torch.float32), _dev(grad, "grad", torch.float32), _dev(m, "m", torch.float32),
+        _dev(v, "v", torch.float32), param.numel(), C.byref(h), _dev(lr_scale, "lr_scale", torch.float32, True),
+        _dev(param_bf16_out, "param_bf16_out", torch.bfloat16, True), int(bool(zero_grad)), _stream(stream))
+    _check(st, "dvgo_adam_step")
+
+
+def dvgo_workspace_status(workspace, stream=None) -> int:
+    return int(lib().dvgo_workspace_status(_dev(workspace, "workspace", torch.uint8), _stream(stream)))
+
+
+def dvgo_sample_counts(workspace, n_rays: int, counts_out, total_out=None, stream=None):
+    st = lib().dvgo_sample_counts(_dev(workspace, "workspace", torch.uint8), int(n_rays),
+                                  _dev(counts_out, "counts_out", torch.int32), _dev(total_out, "total_out", torch.int32, True),
+                                  _stream(stream))
+    _check(st, "dvgo_sample_counts")
+
+
+def dvgo_profile_enable(on: bool):
+    _check(lib().dvgo_profile_enable(int(bool(on))), "dvgo_profile_enable")
+
+
+def dvgo_profile_read(kind) -> tuple:
+    """(total device ms, launches) of one kernel kind since the last read; kind is an index or a
+    name from KERNEL_KINDS."""
+    k = KERNEL_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ms, n = C.c_double(0.0), C.c_longlong(0)
+    _check(lib().dvgo_profile_read(k, C.byref(ms), C.byref(n)), "dvgo_profile_read")
+    return ms.value, n.value
+
+
+def dvgo_launch_counter() -> int:
+    return int(lib().dvgo_launch_counter())

@@ -1,0 +1,91 @@
+// adam.cu -- elementwise Adam step (Kingma & Ba) used for the grids and the MLP (Sec. 5.2,
+// Supp. A: Adam, base learning rates 0.1 for the voxel grids and 1e-3 for the MLP, decayed
+// exponentially by 0.1 over 20k iterations; Sec. 4.1 Prior 2: a per-voxel rate scale).
+//
+// HBM-bound: per element it reads p, g, m, v (16 B) and writes p, m, v and, with zero_grad, g
+// (12-16 B), plus 2 B for the optional BF16 copy.  16-byte vector loads/stores, grid-stride
+// loop over a grid sized to fill every SM.
+
+#include "dvgo_internal.cuh"
+
+namespace dvgo {
+
+namespace {
+
+struct AdamK {
+    float lr, b1, b2, eps, inv_bc1, inv_bc2;
+};
+
+__device__ __forceinline__ void adam_one(float &p, float &m, float &v, float g, float s, const AdamK &k) {
+    m = fmaf(k.b1, m, (1.0f - k.b1) * g);
+    v = fmaf(k.b2, v, (1.0f - k.b2) * g * g);
+    float mhat = m * k.inv_bc1, vhat = v * k.inv_bc2;
+    p -= k.lr * s * mhat / (sqrtf(vhat) + k.eps);
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                                                    float *__restrict__ v, size_t n, AdamK k,
+                                                    const float *__restrict__ scale, uint16_t *__restrict__ pb,
+                                                    int zero_grad) {
+    size_t n4 = n / 4;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 P = reinterpret_cast<float4 *>(p)[i];
+        float4 G = reinterpret_cast<const float4 *>(g)[i];
+        float4 M = reinterpret_cast<float4 *>(m)[i];
+        float4 V = reinterpret_cast<float4 *>(v)[i];
+        float4 S = scale ? reinterpret_cast<const float4 *>(scale)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+        adam_one(P.x, M.x, V.x, G.x, S.x, k);
+        adam_one(P.y, M.y, V.y, G.y, S.y, k);
+        adam_one(P.z, M.z, V.z, G.z, S.z, k);
+        adam_one(P.w, M.w, V.w, G.w, S.w, k);
+        reinterpret_cast<float4 *>(p)[i] = P;
+        reinterpret_cast<float4 *>(m)[i] = M;
+        reinterpret_cast<float4 *>(v)[i] = V;
+        if (zero_grad) reinterpret_cast<float4 *>(g)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pb) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
+            uint2 o;
+            o.x = *reinterpret_cast<unsigned *>(&lo);
+            o.y = *reinterpret_cast<unsigned *>(&hi);
+            reinterpret_cast<uint2 *>(pb)[i] = o;
+        }
+    }
+    // scalar tail
+    for (size_t i = n4 * 4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float P = p[i], M = m[i], V = v[i];
+        adam_one(P, M, V, g[i], scale ? scale[i] : 1.0f, k);
+        p[i] = P;
+        m[i] = M;
+        v[i] = V;
+        if (zero_grad) g[i] = 0.0f;
+        if (pb) {
+            __nv_bfloat16 b = __float2bfloat16_rn(P);
+            pb[i] = *reinterpret_cast<uint16_t *>(&b);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
+                 const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s) {
+    AdamK k;
+    k.lr = h.lr;
+    k.b1 = h.beta1;
+    k.b2 = h.beta2;
+    k.eps = h.eps;
+    k.inv_bc1 = (float)(1.0 / (1.0 - pow((double)h.beta1, (double)h.step)));
+    k.inv_bc2 = (float)(1.0 / (1.0 - pow((double)h.beta2, (double)h.step)));
+    size_t n4 = (n + 3) / 4;
+    size_t blocks = (n4 + 255) / 256;
+    size_t cap = (size_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    {
+        ProfScope ps_(DVGO_K_ADAM, s);
+        adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, k, lr_scale, bf16_out, zero_grad);
+    }
+}
+
+}  // namespace dvgo

@@ -1,0 +1,222 @@
+// coarse.cu -- coarse-stage render (Sec. 4.1): density grid + view-invariant colour grid.
+//
+// One warp per ray, 32 consecutive samples per iteration.  Per sample:
+//   sigma_ddot = interp(x, V_density)                      (Eq. coarse_queries_densities)
+//   sigma = softplus(sigma_ddot + b), tau = sigma * dt       (Eq. density_activation, post-activation)
+//   alpha = 1 - exp(-tau); removed when alpha < tau_f        (Eq. density_2_alpha, Sec. 4.2 skipping)
+//   c = interp(x, V_rgb) (optionally sigmoid)                (Eq. coarse_queries)
+// Compositing keeps the optical depth prefix sum: T_k = exp(-sum_{j<k} tau_j), w_k = T_k alpha_k,
+// C_hat = sum w_k c_k + T_K bg (Eq. volume_rendering).  The prefix is a warp scan per chunk plus a
+// running carry, which keeps T exact to FP32 rounding of the sum even over hundreds of samples.
+//
+// Backward (recomputes the forward chunk by chunk, stores nothing per sample):
+//   dC/dc_k = w_k,  dC/dtau_k = T_{k+1} c_k - S_k,  S_k = C_hat - sum_{j<=k} w_j c_j,
+//   dT_K/dtau_k = -T_K,  dtau_k/dsigma_ddot = dt * sigmoid(sigma_ddot + b);
+// gradients are scattered to the 8 lattice corners with weights equal to the trilinear weights,
+// summed first over runs of lanes that hit the same corner.
+
+#include "dvgo_internal.cuh"
+
+namespace dvgo {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct CoarseSample {
+    Cell cell;
+    float z;      // sigma_ddot + b
+    float tau;    // optical depth (0 when removed)
+    float dt;
+    float c[3];   // emitted colour
+    bool kept;
+};
+
+__device__ __forceinline__ CoarseSample coarse_sample(const RenderArgs &A, const RayRec &rr, int ray, int k) {
+    CoarseSample S;
+    double t;
+    sample_t(A, rr, ray, k, t, S.dt);
+    double u[3];
+    lattice_coord(rr, t, u);
+    S.cell = make_cell(u, A.nx, A.ny, A.nz);
+    const float *rgb = static_cast<const float *>(A.cgrid);
+    float s = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        long long idx = corner_index(S.cell, q, A.ny, A.nz);
+        float w = corner_weight(S.cell, q);
+        s = fmaf(w, __ldg(A.density + idx), s);
+        const float *cp = rgb + idx * 3;
+        col[0] = fmaf(w, __ldg(cp + 0), col[0]);
+        col[1] = fmaf(w, __ldg(cp + 1), col[1]);
+        col[2] = fmaf(w, __ldg(cp + 2), col[2]);
+    }
+    S.z = s + A.shift_b;
+    S.tau = softplusf(S.z) * S.dt;
+    float alpha = -expm1f(-S.tau);
+    S.kept = !(alpha < A.tau_f);
+    if (!S.kept) S.tau = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) S.c[ch] = A.rgb_act ? sigmoidf_(col[ch]) : col[ch];
+    return S;
+}
+
+// Block-level loss reduction: every block adds its partial sum; the last block to finish
+// writes loss_out = sum / R.
+__device__ void finish_loss(const RenderArgs &A, float part) {
+    __shared__ float red[32];
+    __shared__ bool last;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    part = warp_sum(part);
+    if (lane == 0) red[wid] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        atomicAdd(&A.hdr->loss_acc, s);
+        __threadfence();
+        unsigned prev = atomicAdd(&A.hdr->done, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0 && A.loss_out) {
+        __threadfence();
+        float tot = atomicAdd(&A.hdr->loss_acc, 0.0f);
+        A.loss_out[0] = A.R > 0 ? tot / (float)A.R : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    float loss_part = 0.0f;
+    for (int r = warp; r < A.R; r += nwarps) {
+        const RayRec rr = A.rays[r];
+        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int base = 0; base < rr.n; base += 32) {
+            int k = base + lane;
+            CoarseSample S;
+            S.tau = 0.0f;
+            S.c[0] = S.c[1] = S.c[2] = 0.0f;
+            if (k < rr.n) S = coarse_sample(A, rr, r, k);
+            float incl = warp_incl_scan(S.tau, lane);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0.0f;
+            float T = expf(-(carry + excl));
+            float w = T * -expm1f(-S.tau);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(w, S.c[ch], acc[ch]);
+            carry += __shfl_sync(FULL, incl, 31);
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) acc[ch] = warp_sum(acc[ch]);
+        if (lane == 0) {
+            float TK = expf(-carry);
+            float rgb[3];
+            for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(TK, A.bg[ch], acc[ch]);
+            for (int ch = 0; ch < 3; ++ch) A.rgb_out[3 * r + ch] = rgb[ch];
+            if (A.tfinal_out) A.tfinal_out[r] = TK;
+            A.rayout[r] = make_float4(rgb[0], rgb[1], rgb[2], TK);
+            if (A.target) {
+                for (int ch = 0; ch < 3; ++ch) {
+                    float e = rgb[ch] - A.target[3 * r + ch];
+                    loss_part = fmaf(e, e, loss_part);
+                    if (A.dloss_out) A.dloss_out[3 * r + ch] = 2.0f * e / (float)A.R;
+                }
+            }
+        }
+    }
+    if (A.target) finish_loss(A, loss_part);
+}
+
+__global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < A.R; r += nwarps) {
+        const RayRec rr = A.rays[r];
+        if (rr.n == 0) continue;
+        const float4 ro = A.rayout[r];
+        const float Chat[3] = {ro.x, ro.y, ro.z};
+        const float TK = ro.w;
+        const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
+        const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
+        float carry = 0.0f, Acarry[3] = {0.0f, 0.0f, 0.0f};
+        for (int base = 0; base < rr.n; base += 32) {
+            int k = base + lane;
+            bool valid = k < rr.n;
+            CoarseSample S;
+            S.tau = 0.0f;
+            S.kept = false;
+            S.z = 0.0f;
+            S.dt = 0.0f;
+            S.c[0] = S.c[1] = S.c[2] = 0.0f;
+            S.cell.i0 = S.cell.j0 = S.cell.k0 = 0;
+            S.cell.fx = S.cell.fy = S.cell.fz = 0.0f;
+            if (valid) S = coarse_sample(A, rr, r, k);
+            float incl = warp_incl_scan(S.tau, lane);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0.0f;
+            float T = expf(-(carry + excl));
+            float T1 = expf(-(carry + incl));
+            float w = T * -expm1f(-S.tau);
+            float Ain[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) Ain[ch] = Acarry[ch] + warp_incl_scan(w * S.c[ch], lane);
+            float dtau = -gT * TK;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], T1 * S.c[ch] - (Chat[ch] - Ain[ch]), dtau);
+            bool act = valid && S.kept;
+            float dz = act ? dtau * S.dt * sigmoidf_(S.z) : 0.0f;
+            float dc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float gc = g[ch] * w;
+                if (A.rgb_act) gc *= S.c[ch] * (1.0f - S.c[ch]);
+                dc[ch] = act ? gc : 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int idx = (int)corner_index(S.cell, q, A.ny, A.nz);
+                float cw = corner_weight(S.cell, q);
+                Seg sg = make_seg(act ? idx : -1 - lane, lane);
+                float v = seg_sum(dz * cw, sg, lane);
+                if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float vc = seg_sum(dc[ch] * cw, sg, lane);
+                    if (act && sg.tail) atomicAdd(A.grad_cgrid + (long long)idx * 3 + ch, vc);
+                }
+            }
+            carry += __shfl_sync(FULL, incl, 31);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) Acarry[ch] = __shfl_sync(FULL, Ain[ch], 31);
+        }
+    }
+}
+
+}  // namespace
+
+static int warp_grid(int R, int warps_per_block) {
+    int want = (R + warps_per_block - 1) / warps_per_block;
+    int cap = num_sms() * 16;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : want;
+}
+
+void launch_coarse_fwd(const RenderArgs &A, cudaStream_t s) {
+    {
+        ProfScope ps_(DVGO_K_COARSE_FWD, s);
+        coarse_fwd_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+    }
+}
+
+void launch_coarse_bwd(const RenderArgs &A, cudaStream_t s) {
+    {
+        ProfScope ps_(DVGO_K_COARSE_BWD, s);
+        coarse_bwd_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+    }
+}
+
+}  // namespace dvgo

@@ -1,0 +1,219 @@
+// dvgo_internal.cuh -- shared device-side definitions of the DVGO render kernels (sm_103a).
+//
+// Data flow of one render (all on the caller's stream, no host synchronisation):
+//   ray_setup        per ray, FP64: normalise d, clip to the box, count samples, store the ray
+//                    in lattice coordinates (Sec. 4.2 fine-stage sampling, Eq. coarse_sample)
+//   scan_counts      exclusive scan of the per-ray counts -> first sample slot of every ray
+//   coarse_fwd/bwd   warp per ray: gather, post-activation, warp-scan compositing (Sec. 2/3/4.1)
+//   fine_density     warp per ray: density gather + post-activation, per-sample optical depth,
+//                    compact list of the kept samples (Sec. 4.2 free space skipping)
+//   fine_colour      persistent CTAs over tiles of kept samples: feature gather + PE + MLP
+//   fine_composite   warp per ray: transmittance scan, C_hat, loss (Eq. volume_rendering)
+//   fine_bwd_*       composite backward + density scatter (warp per ray), then the colour tile
+//                    kernel backward (MLP backward + feature scatter)
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dvgo.h"
+
+namespace dvgo {
+
+constexpr int kWarp = 32;
+constexpr int kMaxFeat = 16;
+
+// Per-ray record written by ray_setup (80 bytes).
+struct RayRec {
+    double uo[3];     // ray origin in lattice coordinates: (o - xyz_min) * (n - 1) / (xyz_max - xyz_min)
+    double e[3];      // normalised direction in lattice coordinates per unit of t
+    double t_enter;   // clipped entry distance
+    float dir[3];     // normalised direction (FP32, positional encoding input)
+    float p;          // jitter in [0, 1)
+    int n;            // number of samples
+    int off;          // first sample slot (exclusive scan of n)
+};
+static_assert(sizeof(RayRec) == 80, "RayRec layout");
+
+// Workspace header (first 256 bytes of the workspace).
+struct WsHeader {
+    int flags;           // bit 0: a ray of the last forward had a zero / non-finite direction
+    int total;           // total samples of the batch (sum of n)
+    int n_kept;          // fine stage: samples kept after the tau_f test
+    unsigned done;       // block-completion counter of the loss reduction
+    float loss_acc;      // sum over rays of ||C_hat - C||^2
+    int pad[59];
+};
+static_assert(sizeof(WsHeader) == 256, "WsHeader size");
+
+// Workspace layout; every block 256-byte aligned.
+struct WsLayout {
+    size_t header, rays, rayout, samp, sgrad, kept, total;
+    long long max_samples;
+};
+
+// Everything a render kernel needs, passed by value.
+struct RenderArgs {
+    int R;
+    int mode, rgb_act, mlp_prec, nfreq, hidden;
+    float step, shift_b, tau_f;
+    float bg[3];
+    int nx, ny, nz, C;
+    int cdtype;                 // dtype of the colour / feature grid
+    const float *density;
+    const void *cgrid;
+    const float *target;        // nullable
+    // explicit samples (nullable)
+    const float *ts, *dts;
+    int n_expl;
+    // workspace views
+    WsHeader *hdr;
+    RayRec *rays;
+    float4 *rayout;             // per ray: C_hat (xyz), T_K (w)
+    float4 *samp;               // per sample slot: (tau, r, g, b)
+    float4 *sgrad;              // per sample slot: (unused, dL/dc)
+    int2 *kept;                 // compact list of kept samples: (slot, ray)
+    long long max_samples;
+    // outputs
+    float *rgb_out, *tfinal_out, *loss_out, *dloss_out;
+    // backward inputs / outputs
+    const float *grad_rgb, *grad_tfinal;
+    float *grad_density, *grad_cgrid, *grad_mlp;
+    // MLP
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+    int in_dim;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float softplusf(float z) {
+    // log(1 + exp(z)) without overflow (Eq. density_activation)
+    return fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Lattice coordinate of sample (ray, t) along one axis, in FP64 (see RayRec).
+__device__ __forceinline__ void lattice_coord(const RayRec &r, double t, double u[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = fma(t, r.e[a], r.uo[a]);
+}
+
+// Base corner (clamped to [0, n-2]) and FP32 fractional offsets of a lattice coordinate.
+struct Cell {
+    int i0, j0, k0;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ Cell make_cell(const double u[3], int nx, int ny, int nz) {
+    Cell c;
+    double fl;
+    fl = floor(u[0]); fl = fmin(fmax(fl, 0.0), (double)(nx - 2)); c.i0 = (int)fl; c.fx = (float)(u[0] - fl);
+    fl = floor(u[1]); fl = fmin(fmax(fl, 0.0), (double)(ny - 2)); c.j0 = (int)fl; c.fy = (float)(u[1] - fl);
+    fl = floor(u[2]); fl = fmin(fmax(fl, 0.0), (double)(nz - 2)); c.k0 = (int)fl; c.fz = (float)(u[2] - fl);
+    return c;
+}
+
+// Corner q (bits x = q>>2, y = (q>>1)&1, z = q&1): flat lattice index and trilinear weight.
+__device__ __forceinline__ long long corner_index(const Cell &c, int q, int ny, int nz) {
+    return ((long long)(c.i0 + ((q >> 2) & 1)) * ny + (c.j0 + ((q >> 1) & 1))) * nz + (c.k0 + (q & 1));
+}
+__device__ __forceinline__ float corner_weight(const Cell &c, int q) {
+    float wx = ((q >> 2) & 1) ? c.fx : 1.0f - c.fx;
+    float wy = ((q >> 1) & 1) ? c.fy : 1.0f - c.fy;
+    float wz = (q & 1) ? c.fz : 1.0f - c.fz;
+    return wx * wy * wz;
+}
+
+// Sample position along a ray: uniform stepping or explicit list.
+__device__ __forceinline__ void sample_t(const RenderArgs &A, const RayRec &r, int ray, int k,
+                                         double &t, float &dt) {
+    if (A.ts) {
+        t = (double)A.ts[(long long)ray * A.n_expl + k];
+        dt = A.dts[(long long)ray * A.n_expl + k];
+    } else {
+        t = fma((double)k + (double)r.p, (double)A.step, r.t_enter);
+        dt = A.step;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_incl_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Warp-level segmented reduction for gradient scatter.  Lanes hold consecutive samples; a
+// segment is a maximal run of adjacent lanes with the same destination index (consecutive
+// samples of one ray share lattice corners).  seg_sum() leaves the run total in the run's last
+// lane, which then issues one atomic for the whole run.  All 32 lanes must participate.
+struct Seg {
+    int first;   // first lane of my run
+    bool tail;   // I am the last lane of my run
+};
+
+__device__ __forceinline__ Seg make_seg(int key, int lane) {
+    int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    int next = __shfl_down_sync(0xffffffffu, key, 1);
+    bool head = (lane == 0) || (prev != key);
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    Seg s;
+    s.first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    s.tail = (lane == 31) || (next != key);
+    return s;
+}
+
+__device__ __forceinline__ float seg_sum(float v, const Seg &s, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane - o >= s.first) v += n;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+
+WsLayout ws_layout(int R, long long max_samples, int mode);
+void launch_ray_setup(const RenderArgs &A, const float *rays_o, const float *rays_d, const float *jitter,
+                      const dvgo_params &p, const dvgo_grid_desc &g, long long cap, cudaStream_t s);
+void launch_coarse_fwd(const RenderArgs &A, cudaStream_t s);
+void launch_coarse_bwd(const RenderArgs &A, cudaStream_t s);
+void launch_fine_density(const RenderArgs &A, cudaStream_t s);
+void launch_fine_colour_fwd(const RenderArgs &A, cudaStream_t s);
+void launch_fine_composite_fwd(const RenderArgs &A, cudaStream_t s);
+void launch_fine_composite_bwd(const RenderArgs &A, cudaStream_t s);
+void launch_fine_colour_bwd(const RenderArgs &A, cudaStream_t s);
+void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
+                 const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s);
+
+int num_sms();
+void ensure_smem(const void *kernel, int bytes);
+
+// Counts a kernel launch and, when timing is enabled, brackets it with two events on its stream.
+class ProfScope {
+  public:
+    ProfScope(int kind, cudaStream_t s);
+    ~ProfScope();
+
+  private:
+    int kind_;
+    cudaStream_t s_;
+    void *a_;
+};
+
+}  // namespace dvgo

@@ -1,0 +1,220 @@
+// fine_ray.cu -- the per-ray kernels of the fine-stage render (Sec. 4.2).
+//
+// fine_density:   warp per ray.  For each sample k of the ray: position, density gather,
+//                 sigma_ddot = interp(x, V_density) (Eq. fine_queries_densities),
+//                 tau_k = softplus(sigma_ddot + b) * dt_k (Eq. density_activation, post-activation),
+//                 removed when alpha_k = 1 - exp(-tau_k) < tau_f (Sec. 4.2 free space skipping).
+//                 Writes tau_k to the sample slot and appends kept samples to a compact list
+//                 (one atomic per warp chunk, lane order kept) for the colour kernel.
+// fine_composite: warp per ray.  T_k = exp(-sum_{j<k} tau_j), w_k = T_k alpha_k,
+//                 C_hat = sum w_k c_k + T_K bg (Eq. volume_rendering), loss (Eq. photo_loss).
+// fine_comp_bwd:  warp per ray.  dC/dc_k = w_k -> stored for the colour backward;
+//                 dC/dtau_k = T_{k+1} c_k - (C_hat - sum_{j<=k} w_j c_j), dT_K/dtau_k = -T_K;
+//                 dtau/dsigma_ddot = dt sigmoid(sigma_ddot + b) = dt (1 - exp(-tau/dt));
+//                 the density gradient is scattered to the 8 corners (runs of lanes that share a
+//                 corner are summed before one atomic).
+
+#include "dvgo_internal.cuh"
+
+namespace dvgo {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < A.R; r += nwarps) {
+        const RayRec rr = A.rays[r];
+        for (int base = 0; base < rr.n; base += 32) {
+            int k = base + lane;
+            bool valid = k < rr.n;
+            float tau = 0.0f;
+            bool kept = false;
+            if (valid) {
+                double t;
+                float dt;
+                sample_t(A, rr, r, k, t, dt);
+                double u[3];
+                lattice_coord(rr, t, u);
+                Cell c = make_cell(u, A.nx, A.ny, A.nz);
+                float s = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
+                tau = softplusf(s + A.shift_b) * dt;
+                kept = !(-expm1f(-tau) < A.tau_f);
+                if (!kept) tau = 0.0f;
+                A.samp[rr.off + k] = make_float4(tau, 0.0f, 0.0f, 0.0f);
+            }
+            unsigned m = __ballot_sync(FULL, kept);
+            int cnt = __popc(m);
+            int base_slot = 0;
+            if (lane == 0 && cnt) base_slot = atomicAdd(&A.hdr->n_kept, cnt);
+            base_slot = __shfl_sync(FULL, base_slot, 0);
+            if (kept) {
+                int rank = __popc(m & ((1u << lane) - 1u));
+                A.kept[base_slot + rank] = make_int2(rr.off + k, r);
+            }
+        }
+    }
+}
+
+__device__ void finish_loss_fine(const RenderArgs &A, float part) {
+    __shared__ float red[32];
+    __shared__ bool last;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    part = warp_sum(part);
+    if (lane == 0) red[wid] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        atomicAdd(&A.hdr->loss_acc, s);
+        __threadfence();
+        unsigned prev = atomicAdd(&A.hdr->done, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0 && A.loss_out) {
+        __threadfence();
+        float tot = atomicAdd(&A.hdr->loss_acc, 0.0f);
+        A.loss_out[0] = A.R > 0 ? tot / (float)A.R : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    float loss_part = 0.0f;
+    for (int r = warp; r < A.R; r += nwarps) {
+        const int n = A.rays[r].n, off = A.rays[r].off;
+        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int base = 0; base < n; base += 32) {
+            int k = base + lane;
+            float4 sv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (k < n) sv = A.samp[off + k];
+            float incl = warp_incl_scan(sv.x, lane);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0.0f;
+            float w = expf(-(carry + excl)) * -expm1f(-sv.x);
+            acc[0] = fmaf(w, sv.y, acc[0]);
+            acc[1] = fmaf(w, sv.z, acc[1]);
+            acc[2] = fmaf(w, sv.w, acc[2]);
+            carry += __shfl_sync(FULL, incl, 31);
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) acc[ch] = warp_sum(acc[ch]);
+        if (lane == 0) {
+            float TK = expf(-carry);
+            float rgb[3];
+            for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(TK, A.bg[ch], acc[ch]);
+            for (int ch = 0; ch < 3; ++ch) A.rgb_out[3 * r + ch] = rgb[ch];
+            if (A.tfinal_out) A.tfinal_out[r] = TK;
+            A.rayout[r] = make_float4(rgb[0], rgb[1], rgb[2], TK);
+            if (A.target) {
+                for (int ch = 0; ch < 3; ++ch) {
+                    float e = rgb[ch] - A.target[3 * r + ch];
+                    loss_part = fmaf(e, e, loss_part);
+                    if (A.dloss_out) A.dloss_out[3 * r + ch] = 2.0f * e / (float)A.R;
+                }
+            }
+        }
+    }
+    if (A.target) finish_loss_fine(A, loss_part);
+}
+
+__global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
+    int lane = threadIdx.x & 31;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < A.R; r += nwarps) {
+        const RayRec rr = A.rays[r];
+        if (rr.n == 0) continue;
+        const float4 ro = A.rayout[r];
+        const float Chat[3] = {ro.x, ro.y, ro.z};
+        const float TK = ro.w;
+        const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
+        const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
+        float carry = 0.0f, Acarry[3] = {0.0f, 0.0f, 0.0f};
+        for (int base = 0; base < rr.n; base += 32) {
+            int k = base + lane;
+            bool valid = k < rr.n;
+            float4 sv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (valid) sv = A.samp[rr.off + k];
+            const float cc[3] = {sv.y, sv.z, sv.w};
+            float incl = warp_incl_scan(sv.x, lane);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0.0f;
+            float T = expf(-(carry + excl));
+            float T1 = expf(-(carry + incl));
+            float w = T * -expm1f(-sv.x);
+            float Ain[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) Ain[ch] = Acarry[ch] + warp_incl_scan(w * cc[ch], lane);
+            float dtau = -gT * TK;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], T1 * cc[ch] - (Chat[ch] - Ain[ch]), dtau);
+            // kept samples have tau > 0 or an exactly-zero sigmoid factor; removed ones have tau = 0
+            bool act = valid && sv.x > 0.0f;
+            Cell c;
+            c.i0 = c.j0 = c.k0 = 0;
+            c.fx = c.fy = c.fz = 0.0f;
+            float dz = 0.0f;
+            if (valid) {
+                double t;
+                float dt;
+                sample_t(A, rr, r, k, t, dt);
+                double u[3];
+                lattice_coord(rr, t, u);
+                c = make_cell(u, A.nx, A.ny, A.nz);
+                dz = act ? dtau * dt * -expm1f(-sv.x / dt) : 0.0f;
+                // dL/dc_k for the colour backward (only kept samples are read back)
+                A.sgrad[rr.off + k] = make_float4(0.0f, g[0] * w, g[1] * w, g[2] * w);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int idx = (int)corner_index(c, q, A.ny, A.nz);
+                Seg sg = make_seg(act ? idx : -1 - lane, lane);
+                float v = seg_sum(dz * corner_weight(c, q), sg, lane);
+                if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
+            }
+            carry += __shfl_sync(FULL, incl, 31);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) Acarry[ch] = __shfl_sync(FULL, Ain[ch], 31);
+        }
+    }
+}
+
+int warp_grid(int R, int warps_per_block) {
+    int want = (R + warps_per_block - 1) / warps_per_block;
+    int cap = num_sms() * 16;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : want;
+}
+
+}  // namespace
+
+void launch_fine_density(const RenderArgs &A, cudaStream_t s) {
+    {
+        ProfScope ps_(DVGO_K_FINE_DENSITY, s);
+        fine_density_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+    }
+}
+void launch_fine_composite_fwd(const RenderArgs &A, cudaStream_t s) {
+    {
+        ProfScope ps_(DVGO_K_FINE_COMPOSITE, s);
+        fine_composite_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+    }
+}
+void launch_fine_composite_bwd(const RenderArgs &A, cudaStream_t s) {
+    {
+        ProfScope ps_(DVGO_K_FINE_COMP_BWD, s);
+        fine_comp_bwd_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+    }
+}
+
+}  // namespace dvgo

@@ -1,0 +1,178 @@
+// ray_setup.cu -- per-ray clipping and sample counting, and the exclusive scan of the counts.
+//
+// Sec. 4.2 (fine-stage points sampling): the near and far bounds of every ray become the two
+// ends of its intersection with the grid's bounding box (the near bound stays put when the
+// origin is inside).  Eq. coarse_sample / Supp. A: samples are equally spaced by the step and
+// shifted by the per-ray jitter p.  With a normalised direction the count is the number of k >= 0
+// with t_enter + (k + p) * step < t_exit.
+//
+// The count is an integer decided by floating point, so it is computed in FP64 with every
+// operation a separately rounded IEEE operation (__dadd_rn & co. keep nvcc from contracting
+// them into FMAs):
+//   len   = sqrt((dx*dx + dy*dy) + dz*dz),   dn = d / len
+//   per axis with dn != 0: t1 = (min - o) / dn, t2 = (max - o) / dn, lo = max(lo, min(t1, t2)),
+//                          hi = min(hi, max(t1, t2));  starting from lo = t_near, hi = t_far
+//   per axis with dn == 0 and o outside the slab: empty
+//   n = ceil((hi - lo) / step - p) when hi > lo, capped at ceil(|max - min| / step) + 1.
+
+#include "dvgo_internal.cuh"
+
+namespace dvgo {
+
+namespace {
+
+__global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float *__restrict__ rays_o,
+                                                        const float *__restrict__ rays_d,
+                                                        const float *__restrict__ jitter, double3 bmin,
+                                                        double3 bmax, double3 scale, double t_near,
+                                                        double t_far, double step, double cap,
+                                                        int n_expl) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) {
+        A.hdr->total = 0;
+        A.hdr->n_kept = 0;
+        A.hdr->done = 0u;
+        A.hdr->loss_acc = 0.0f;
+    }
+    if (r >= A.R) return;
+    double o[3] = {(double)rays_o[3 * r], (double)rays_o[3 * r + 1], (double)rays_o[3 * r + 2]};
+    double d[3] = {(double)rays_d[3 * r], (double)rays_d[3 * r + 1], (double)rays_d[3 * r + 2]};
+    double mn[3] = {bmin.x, bmin.y, bmin.z}, mx[3] = {bmax.x, bmax.y, bmax.z};
+    double sc[3] = {scale.x, scale.y, scale.z};
+    double p = jitter ? (double)jitter[r] : 0.5;
+
+    double len2 = __dmul_rn(d[0], d[0]);
+    len2 = __dadd_rn(len2, __dmul_rn(d[1], d[1]));
+    len2 = __dadd_rn(len2, __dmul_rn(d[2], d[2]));
+    double len = __dsqrt_rn(len2);
+    RayRec rec;
+    bool ok = (len > 0.0) && isfinite(len) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]);
+    double dn[3] = {0.0, 0.0, 0.0};
+    double lo = t_near, hi = t_far;
+    if (ok) {
+        for (int a = 0; a < 3; ++a) {
+            dn[a] = __ddiv_rn(d[a], len);
+            if (dn[a] != 0.0) {
+                double t1 = __ddiv_rn(__dsub_rn(mn[a], o[a]), dn[a]);
+                double t2 = __ddiv_rn(__dsub_rn(mx[a], o[a]), dn[a]);
+                double tl = t1 < t2 ? t1 : t2;
+                double th = t1 < t2 ? t2 : t1;
+                if (tl > lo) lo = tl;
+                if (th < hi) hi = th;
+            } else if (o[a] < mn[a] || o[a] > mx[a]) {
+                lo = 1.0;
+                hi = 0.0;
+            }
+        }
+    } else {
+        lo = 1.0;
+        hi = 0.0;
+    }
+    int n = 0;
+    if (hi > lo) {
+        double q = __ddiv_rn(__dsub_rn(hi, lo), step);
+        q = __dsub_rn(q, p);
+        double c = ceil(q);
+        if (c > cap) c = cap;
+        n = c > 0.0 ? (int)c : 0;
+        if (n_expl >= 0) n = n_expl;   // explicit samples: all or nothing
+    }
+    for (int a = 0; a < 3; ++a) {
+        rec.uo[a] = __dmul_rn(__dsub_rn(o[a], mn[a]), sc[a]);
+        rec.e[a] = __dmul_rn(dn[a], sc[a]);
+        rec.dir[a] = (float)dn[a];
+    }
+    rec.t_enter = lo;
+    rec.p = (float)p;
+    rec.n = n;
+    rec.off = ok ? 0 : -1;   // -1 marks a ray with a zero / non-finite direction for the scan
+    A.rays[r] = rec;
+}
+
+// Exclusive scan of RayRec::n into RayRec::off by one CTA of 1024 threads; the total and the
+// flag word (a ray with a zero / non-finite direction) go to the header.  Each thread scans a contiguous chunk serially, then the chunk sums are scanned
+// across the block with warp shuffles.
+__global__ void __launch_bounds__(1024) scan_counts_kernel(RenderArgs A) {
+    __shared__ int warp_tot[32];
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int per = (A.R + 1023) / 1024;
+    int beg = tid * per, end = min(beg + per, A.R);
+    int local = 0, bad = 0;
+    for (int i = beg; i < end; ++i) {
+        local += A.rays[i].n;
+        bad |= (A.rays[i].off < 0);
+    }
+    bad = __syncthreads_or(bad);
+    // inclusive warp scan of the chunk sums
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int n = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += n;
+        }
+        warp_tot[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+    for (int i = beg; i < end; ++i) {
+        A.rays[i].off = run;
+        run += A.rays[i].n;
+    }
+    if (tid == 1023) {
+        A.hdr->total = warp_tot[31];
+        A.hdr->flags = bad ? 1 : 0;
+    }
+}
+
+}  // namespace
+
+void launch_ray_setup(const RenderArgs &A, const float *rays_o, const float *rays_d, const float *jitter,
+                      const dvgo_params &p, const dvgo_grid_desc &g, long long cap, cudaStream_t s) {
+    double3 bmin = make_double3(g.xyz_min[0], g.xyz_min[1], g.xyz_min[2]);
+    double3 bmax = make_double3(g.xyz_max[0], g.xyz_max[1], g.xyz_max[2]);
+    double3 sc = make_double3((double)(g.nx - 1) / (bmax.x - bmin.x), (double)(g.ny - 1) / (bmax.y - bmin.y),
+                              (double)(g.nz - 1) / (bmax.z - bmin.z));
+    int blocks = (A.R + 63) / 64;
+    if (blocks < 1) blocks = 1;
+    {
+        ProfScope ps_(DVGO_K_RAY_SETUP, s);
+        ray_setup_kernel<<<blocks, 64, 0, s>>>(A, rays_o, rays_d, jitter, bmin, bmax, sc, (double)p.t_near,
+                                           (double)p.t_far, (double)p.step, (double)cap,
+                                           A.ts ? A.n_expl : -1);
+    }
+    {
+        ProfScope ps_(DVGO_K_SCAN, s);
+        scan_counts_kernel<<<1, 1024, 0, s>>>(A);
+    }
+}
+
+WsLayout ws_layout(int R, long long max_samples, int mode) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    WsLayout L;
+    size_t o = 0;
+    L.header = o; o += up(sizeof(WsHeader));
+    L.rays = o; o += up(sizeof(RayRec) * (size_t)(R > 0 ? R : 1));
+    L.rayout = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));
+    size_t S = (size_t)(max_samples > 0 ? max_samples : 1);
+    if (mode == DVGO_MODE_FINE) {
+        L.samp = o; o += up(sizeof(float4) * S);
+        L.sgrad = o; o += up(sizeof(float4) * S);
+        L.kept = o; o += up(sizeof(int2) * S);
+    } else {
+        L.samp = L.sgrad = L.kept = 0;
+    }
+    L.total = o;
+    L.max_samples = max_samples;
+    return L;
+}
+
+}  // namespace dvgo

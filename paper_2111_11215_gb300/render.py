@@ -1,0 +1,164 @@
+"""Torch-facing helpers over the C ABI: a renderer that owns the workspace, an autograd
+Function, the fine-stage model container and its Adam state.  Every step runs in libdvgo."""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+MLP_KEYS = ("w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def mlp_shapes(in_dim: int, hidden: int):
+    return {"w1": (in_dim, hidden), "b1": (hidden,), "w2": (hidden, hidden), "b2": (hidden,),
+            "w3": (hidden, 3), "b3": (3,)}
+
+
+def mlp_flat_size(in_dim: int = 39, hidden: int = 128) -> int:
+    return sum(int(torch.tensor(s).prod()) for s in mlp_shapes(in_dim, hidden).values())
+
+
+def mlp_views(flat: torch.Tensor, in_dim: int = 39, hidden: int = 128) -> dict:
+    """Views w1..b3 into one flat buffer laid out w1 | b1 | w2 | b2 | w3 | b3 (the ABI's order)."""
+    out, off = {}, 0
+    for k, shp in mlp_shapes(in_dim, hidden).items():
+        n = int(torch.tensor(shp).prod())
+        out[k] = flat[off:off + n].view(shp)
+        off += n
+    return out
+
+
+class Renderer:
+    """Owns the descriptors and the workspace of one ray-batch size."""
+
+    def __init__(self, params: B.Params, density_desc: B.GridDesc, cgrid_desc: B.GridDesc, n_rays: int,
+                 samples_per_ray: int | None = None, device="cuda"):
+        self.params, self.dd, self.cd = params, density_desc, cgrid_desc
+        self.n_rays = n_rays
+        dummy = None
+        if samples_per_ray is not None:
+            z = torch.empty((max(n_rays, 1), samples_per_ray), device=device)
+            dummy = (z, z)
+        self.ws_bytes = B.dvgo_workspace_size(params, density_desc, n_rays, dummy)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+    def forward(self, density, cgrid, mlp, rays_o, rays_d, jitter=None, samples=None, target=None,
+                rgb=None, tfinal=None, loss=None, dloss=None, stream=None):
+        R = rays_o.shape[0]
+        dev = rays_o.device
+        rgb = torch.empty((R, 3), device=dev) if rgb is None else rgb
+        tfinal = torch.empty(R, device=dev) if tfinal is None else tfinal
+        if target is not None:
+            loss = torch.empty(1, device=dev) if loss is None else loss
+        B.dvgo_render_fwd(self.params, self.dd, density, self.cd, cgrid, mlp, rays_o, rays_d, jitter, samples,
+                          target, rgb, tfinal, loss, dloss, self.workspace, stream)
+        return rgb, tfinal, loss
+
+    def backward(self, density, cgrid, mlp, rays_o, rays_d, jitter, samples, grad_rgb, grad_tfinal,
+                 grad_density, grad_cgrid, grad_mlp, stream=None):
+        B.dvgo_render_bwd(self.params, self.dd, density, self.cd, cgrid, mlp, rays_o, rays_d, jitter, samples,
+                          grad_rgb, grad_tfinal, grad_density, grad_cgrid, grad_mlp, self.workspace, stream)
+
+
+class RenderFunction(torch.autograd.Function):
+    """(density, cgrid, mlp_flat) -> (rgb, T_final) with the library's backward.
+
+    The forward leaves per-sample state in the renderer's workspace; the backward of a call
+    must run before the next forward on the same renderer (checked by a generation count)."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, density, cgrid, mlp_flat, rays_o, rays_d, jitter, samples_t, samples_dt):
+        samples = None if samples_t is None else (samples_t, samples_dt)
+        mlp = None
+        if renderer.params.mode == B.DVGO_MODE_FINE:
+            mlp = mlp_views(mlp_flat, renderer.cd.channels + 3 + 6 * renderer.params.n_freq_dir, renderer.params.hidden)
+        rgb, tfinal, _ = renderer.forward(density, cgrid, mlp, rays_o, rays_d, jitter, samples)
+        renderer._gen = getattr(renderer, "_gen", 0) + 1
+        ctx.gen = renderer._gen
+        ctx.renderer = renderer
+        ctx.mlp = mlp
+        ctx.samples = samples
+        ctx.cgrid_dtype = cgrid.dtype
+        ctx.save_for_backward(density, cgrid, mlp_flat, rays_o, rays_d, jitter)
+        return rgb, tfinal
+
+    @staticmethod
+    def backward(ctx, grad_rgb, grad_tfinal):
+        density, cgrid, mlp_flat, rays_o, rays_d, jitter = ctx.saved_tensors
+        r = ctx.renderer
+        if r._gen != ctx.gen:
+            raise RuntimeError("the renderer's workspace was reused by another forward before this backward")
+        g_d = torch.zeros_like(density)
+        g_c = torch.zeros(cgrid.shape, dtype=torch.float32, device=cgrid.device)
+        g_m = torch.zeros_like(mlp_flat) if mlp_flat is not None else None
+        grad_rgb = torch.zeros((rays_o.shape[0], 3), device=rays_o.device) if grad_rgb is None else grad_rgb.contiguous()
+        gT = None if grad_tfinal is None else grad_tfinal.contiguous()
+        r.backward(density, cgrid, ctx.mlp, rays_o, rays_d, jitter, ctx.samples, grad_rgb, gT, g_d, g_c, g_m)
+        return None, g_d, g_c, g_m, None, None, None, None, None
+
+
+class AdamState:
+    """First and second moments of one FP32 parameter tensor."""
+
+    def __init__(self, param: torch.Tensor):
+        self.m = torch.zeros_like(param)
+        self.v = torch.zeros_like(param)
+
+
+class FineModel:
+    """Fine-stage parameters (Sec. 4.2): density grid, feature grid (FP32 master, optional BF16
+    storage copy written by the Adam step), colour MLP in one flat buffer; their gradients and
+    Adam state; and one training step (forward, backward, Adam) on a ray batch."""
+
+    def __init__(self, density: torch.Tensor, feat: torch.Tensor, mlp_flat: torch.Tensor, params: B.Params,
+                 n_rays: int, bf16_feat: bool = False, box=((-1.0,) * 3, (1.0,) * 3),
+                 lr_grid: float = 0.1, lr_mlp: float = 1e-3, decay_steps: float = 20000.0):
+        self.params = params
+        res = tuple(density.shape)
+        C = feat.shape[-1]
+        self.density = density.contiguous()
+        self.feat = feat.contiguous()
+        self.mlp_flat = mlp_flat.contiguous()
+        self.mlp = mlp_views(self.mlp_flat, C + 3 + 6 * params.n_freq_dir, params.hidden)
+        self.bf16_feat = bf16_feat
+        self.feat_bf16 = self.feat.to(torch.bfloat16) if bf16_feat else None
+        self.dd = B.GridDesc(res, 1, box[0], box[1])
+        self.cd = B.GridDesc(res, C, box[0], box[1], B.DVGO_DTYPE_BF16 if bf16_feat else B.DVGO_DTYPE_F32)
+        self.renderer = Renderer(params, self.dd, self.cd, n_rays, device=density.device)
+        self.g_density = torch.zeros_like(self.density)
+        self.g_feat = torch.zeros_like(self.feat)
+        self.g_mlp = torch.zeros_like(self.mlp_flat)
+        self.adam = {k: AdamState(t) for k, t in (("density", self.density), ("feat", self.feat), ("mlp", self.mlp_flat))}
+        self.lr_grid, self.lr_mlp, self.decay_steps = lr_grid, lr_mlp, decay_steps
+        dev = density.device
+        self.rgb = torch.empty((n_rays, 3), device=dev)
+        self.tfinal = torch.empty(n_rays, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.dloss = torch.empty((n_rays, 3), device=dev)
+        self.step_count = 0
+
+    @property
+    def cgrid(self):
+        return self.feat_bf16 if self.bf16_feat else self.feat
+
+    def forward(self, rays_o, rays_d, jitter=None, target=None, stream=None):
+        return self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
+                                     self.rgb, self.tfinal, self.loss if target is not None else None,
+                                     self.dloss if target is not None else None, stream)
+
+    def train_step(self, rays_o, rays_d, jitter, target, stream=None):
+        """One optimisation step: render + MSE (Eq. photo_loss), backward, Adam on every parameter."""
+        self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
+                              self.rgb, self.tfinal, self.loss, self.dloss, stream)
+        self.renderer.backward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, self.dloss, None,
+                               self.g_density, self.g_feat, self.g_mlp, stream)
+        self.step_count += 1
+        t = self.step_count
+        lr_g = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
+        lr_m = B.dvgo_lr_at(self.lr_mlp, t - 1, self.decay_steps)
+        B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, t,
+                         stream=stream)
+        B.dvgo_adam_step(self.feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
+                         param_bf16_out=self.feat_bf16, stream=stream)
+        B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
+        return self.loss

@@ -1,0 +1,45 @@
+"""Shared test helpers: parameter conversion between the ABI and the oracle, tolerance checks."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+# Tolerances of the plain FP32 path against the FP64 oracle (per element, with a floor at 1% of
+# the largest magnitude because atomically accumulated FP32 sums lose relative accuracy on
+# near-zero elements).
+RTOL_COLOUR = 1e-5
+RTOL_GRAD = 1e-4
+FLOOR = 1e-2
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def oracle_params(p, grid_shape, feat_dim, box=((-1.0,) * 3, (1.0,) * 3)):
+    """The oracle's parameters for an ABI Params, every value rounded through FP32 exactly as the
+    library receives it."""
+    return oracle.Params(
+        grid_shape=tuple(grid_shape), xyz_min=tuple(f32(v) for v in box[0]), xyz_max=tuple(f32(v) for v in box[1]),
+        shift_b=f32(p.shift_b), delta=f32(p.step), tau_f=f32(p.tau_f), t_near=f32(p.t_near), t_far=f32(p.t_far),
+        bg=tuple(f32(v) for v in p.bg), mode=p.mode, rgb_act=p.rgb_act, feat_dim=feat_dim, n_freq=p.n_freq_dir,
+        hidden=p.hidden)
+
+
+def floor_err(got, ref, rtol, floor=FLOOR):
+    """max over elements of |got - ref| / (rtol * max(|ref|, floor * max|ref|)); <= 1 passes."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(np.abs(ref).max(initial=0.0), 1e-30)
+    den = rtol * np.maximum(np.abs(ref), floor * scale)
+    return float(np.max(np.abs(got - ref) / den, initial=0.0))
+
+
+def assert_close(got, ref, rtol, name, floor=FLOOR):
+    e = floor_err(got, ref, rtol, floor)
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    rel2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert e <= 1.0, f"{name}: normalised error {e:.3g} (> 1), relative L2 {rel2:.3g}"
+    return e, rel2

@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI: the library loads and exports every declared entry point, and the
+host-side helpers that need no GPU agree with the oracle."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(dvgo_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2111_11215_gb300 as dvgo
+    from paper_2111_11215_gb300 import build_lib
+    build_lib.build()
+    return dvgo.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), f"libdvgo.so does not export {n}"
+    import paper_2111_11215_gb300 as dvgo
+    assert set(names) == set(dvgo.EXPORTED_SYMBOLS)
+
+
+def test_abi_version_and_strings(lib):
+    import paper_2111_11215_gb300 as dvgo
+    assert dvgo.dvgo_abi_version() == 1
+    assert dvgo.dvgo_status_string(0) == "ok"
+    assert "workspace" in dvgo.dvgo_status_string(-2)
+
+
+def test_host_helpers_match_oracle(lib):
+    import oracle
+    import paper_2111_11215_gb300 as dvgo
+    for a, s in [(1e-6, 0.0625), (1e-2, 2 / 160), (1e-6, 2 / 160)]:
+        assert dvgo.dvgo_shift_from_alpha_init(a, s) == pytest.approx(oracle.shift_from_alpha_init(a, s), rel=1e-6)
+    for step in (0, 1, 777, 20000):
+        assert dvgo.dvgo_lr_at(0.1, step) == pytest.approx(oracle.lr_decay(0.1, step), rel=1e-6)
+
+
+def test_workspace_size_bounds_longest_ray(lib):
+    import paper_2111_11215_gb300 as dvgo
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=2 / 160 * 0.5)
+    g = dvgo.GridDesc((160, 160, 160), 1)
+    n1 = dvgo.dvgo_workspace_size(p, g, 1)
+    n2 = dvgo.dvgo_workspace_size(p, g, 8192)
+    # ~555 samples of 40 bytes per ray in the fine mode
+    assert n2 > 8192 * 555 * 40 and n2 < 8192 * 600 * 48
+    assert n1 > 0
+    assert dvgo.dvgo_workspace_size(dvgo.Params(step=0.0), g, 10) == 0

@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (plain FP32 path): colours 1e-5 and gradients 1e-4 relative per element, floored at
+1% of the largest magnitude; integer work (per-ray sample counts) bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+dvgo = pytest.importorskip("paper_2111_11215_gb300")
+
+
+def cuda(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _counts(renderer, R):
+    c = torch.empty(R, dtype=torch.int32, device="cuda")
+    tot = torch.empty(1, dtype=torch.int32, device="cuda")
+    dvgo.dvgo_sample_counts(renderer.workspace, R, c, tot)
+    return c.cpu().numpy(), int(tot.item())
+
+
+# ------------------------------------------------------------------------------------------
+# Coarse stage (config: 32^3 density + RGB, N(0, 0.1^2), 4096 rays)
+# ------------------------------------------------------------------------------------------
+
+def _run_coarse(case, p, jitter=None):
+    res = case["density"].shape[0]
+    dd = dvgo.GridDesc((res,) * 3, 1)
+    cd = dvgo.GridDesc((res,) * 3, 3)
+    R = case["rays_o"].shape[0]
+    r = dvgo.Renderer(p, dd, cd, R)
+    dens, rgbg = cuda(case["density"]), cuda(case["rgb"])
+    ro, rd, tgt = cuda(case["rays_o"]), cuda(case["rays_d"]), cuda(case["target"])
+    jit = None if jitter is None else cuda(jitter)
+    dloss = torch.empty((R, 3), device="cuda")
+    rgb, tf, loss = r.forward(dens, rgbg, None, ro, rd, jit, None, tgt, dloss=dloss)
+    counts, total = _counts(r, R)
+    P = oracle_params(p, (res,) * 3, 3)
+    ref = oracle.render(P, case["density"], case["rgb"], case["rays_o"], case["rays_d"], jitter=jitter,
+                        target=case["target"])
+    gC = 2.0 * (ref.rgb - case["target"]) / R
+    gT = np.random.default_rng(99).normal(scale=1e-3, size=R)
+    refb = oracle.render(P, case["density"], case["rgb"], case["rays_o"], case["rays_d"], jitter=jitter,
+                         grad_rgb=gC, grad_tfinal=gT)
+    g_d = torch.zeros_like(dens)
+    g_c = torch.zeros_like(rgbg)
+    r.backward(dens, rgbg, None, ro, rd, jit, None, cuda(gC), cuda(gT), g_d, g_c, None)
+    torch.cuda.synchronize()
+    return dict(rgb=rgb.cpu().numpy(), tfinal=tf.cpu().numpy(), loss=float(loss.item()),
+                dloss=dloss.cpu().numpy(), counts=counts, total=total, g_d=g_d.cpu().numpy(),
+                g_c=g_c.cpu().numpy()), ref, refb
+
+
+@pytest.mark.parametrize("b_kind,rgb_act", [("alpha_init", 0), ("zero", 0), ("zero", 1)])
+def test_coarse_parity_config1(b_kind, rgb_act):
+    case = synth.coarse_case(seed=0)
+    b = dvgo.dvgo_shift_from_alpha_init(1e-6, 0.0625) if b_kind == "alpha_init" else 0.0
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.03125, shift_b=b, bg=(1.0, 1.0, 1.0), rgb_act=rgb_act)
+    got, ref, refb = _run_coarse(case, p)
+    np.testing.assert_array_equal(got["counts"], ref.n_samples)
+    assert got["total"] == int(ref.n_samples.sum())
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
+    assert got["loss"] == pytest.approx(ref.loss, rel=1e-5)
+    assert_close(got["dloss"], 2.0 * (ref.rgb - case["target"]) / 4096, 1e-4, "dloss")
+    assert_close(got["g_d"], refb.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(got["g_c"], refb.grads["cgrid"], RTOL_GRAD, "grad_rgb")
+
+
+def test_coarse_parity_jittered_and_ragged():
+    case = synth.coarse_case(seed=3, n_rays=1000)
+    jit = synth.jitter(1000, 5)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.047, shift_b=0.3, bg=(0.2, 0.5, 0.9))
+    got, ref, refb = _run_coarse(case, p, jitter=jit)
+    np.testing.assert_array_equal(got["counts"], ref.n_samples)
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(got["g_d"], refb.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(got["g_c"], refb.grads["cgrid"], RTOL_GRAD, "grad_rgb")
+
+
+def test_coarse_edge_cases_zero_rays_misses_and_bad_direction():
+    res = 8
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 3)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.1, bg=(0.1, 0.2, 0.3))
+    dens = torch.randn(res, res, res, device="cuda")
+    rgbg = torch.rand(res, res, res, 3, device="cuda")
+    # zero rays: no launch, loss written as 0
+    r0 = dvgo.Renderer(p, dd, cd, 0)
+    e = torch.empty((0, 3), device="cuda")
+    loss = torch.full((1,), 5.0, device="cuda")
+    dvgo.dvgo_render_fwd(p, dd, dens, cd, rgbg, None, e, e, None, None, e, e, None, loss, None, r0.workspace)
+    assert loss.item() == 0.0
+    # rays that miss, a zero direction, a ray grazing one corner
+    o = np.array([[0, 3, 0], [0, 0, 0], [-3, 0.2, 0.1], [0, 5, 5]], np.float32)
+    d = np.array([[1, 0, 0], [0, 0, 0], [1, 0, 0], [0, -1, -1]], np.float32)
+    r = dvgo.Renderer(p, dd, cd, 4)
+    rgb, tf, _ = r.forward(dens, rgbg, None, cuda(o), cuda(d))
+    torch.cuda.synchronize()
+    assert dvgo.dvgo_workspace_status(r.workspace) == -5     # the zero direction is flagged
+    out = rgb.cpu().numpy()
+    np.testing.assert_allclose(out[0], [0.1, 0.2, 0.3], rtol=0, atol=0)
+    np.testing.assert_allclose(out[1], [0.1, 0.2, 0.3], rtol=0, atol=0)
+    counts, _ = _counts(r, 4)
+    assert counts[0] == 0 and counts[1] == 0 and counts[2] > 0
+    # a clean batch clears the flag
+    r.forward(dens, rgbg, None, cuda(o[2:3]), cuda(d[2:3]))
+    assert dvgo.dvgo_workspace_status(r.workspace) == 0
+
+
+def test_argument_errors_are_reported():
+    res = 8
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 3)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.1)
+    dens = torch.zeros(res ** 3, device="cuda")
+    rgbg = torch.zeros(res ** 3 * 3, device="cuda")
+    ro = torch.zeros((4, 3), device="cuda")
+    out = torch.empty((4, 3), device="cuda")
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dvgo.DVGOError) as ei:
+        dvgo.dvgo_render_fwd(p, dd, dens, cd, rgbg, None, ro, ro, None, None, None, out, None, None, None, small)
+    assert ei.value.status == -2
+    ws = torch.empty(dvgo.dvgo_workspace_size(p, dd, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(dvgo.DVGOError) as ei:
+        dvgo.dvgo_render_fwd(p, dd, dens, dvgo.GridDesc((res,) * 3, 4), rgbg, None, ro, ro, None, None, None, out,
+                             None, None, None, ws)
+    assert ei.value.status == -1
+    bad = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=-1.0)
+    with pytest.raises(dvgo.DVGOError):
+        dvgo.dvgo_render_fwd(bad, dd, dens, cd, rgbg, None, ro, ro, None, None, None, out, None, None, None, ws)
+
+
+# ------------------------------------------------------------------------------------------
+# Fine stage
+# ------------------------------------------------------------------------------------------
+
+def _fine_inputs(res, n_rays, seed, value=20.0, n_spheres=5):
+    c, rad = synth.random_spheres(n_spheres, seed, rmin=0.2, rmax=0.45)
+    dens = synth.sphere_density(res, c, rad, value) + synth.normal_grid((res,) * 3, 1, 0.5, seed + 1)
+    feat = synth.smooth_features(res, 12, seed + 2)
+    mlp = synth.mlp_weights(39, 128, 3, seed + 3)
+    mlp["b3"] = np.random.default_rng(seed + 4).normal(scale=0.3, size=3).astype(np.float32)
+    o, d, jit, tgt = synth.fine_batch(n_rays, seed + 5)
+    return dens.astype(np.float32), feat, mlp, o, d, jit, tgt
+
+
+def _mlp_flat(mlp):
+    return np.concatenate([mlp[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+def _run_fine(p, res, dens, feat, mlp, o, d, jit, gC, gT, feat_dtype=torch.float32, bwd=True):
+    R = o.shape[0]
+    fdt = dvgo.DVGO_DTYPE_BF16 if feat_dtype == torch.bfloat16 else dvgo.DVGO_DTYPE_F32
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12, dtype=fdt)
+    r = dvgo.Renderer(p, dd, cd, R)
+    flat = cuda(_mlp_flat(mlp))
+    views = dvgo.render.mlp_views(flat)
+    D, F = cuda(dens), cuda(feat, feat_dtype)
+    ro, rd, jt = cuda(o), cuda(d), (None if jit is None else cuda(jit))
+    rgb, tf, _ = r.forward(D, F, views, ro, rd, jt)
+    counts, total = _counts(r, R)
+    out = dict(rgb=rgb.cpu().numpy(), tfinal=tf.cpu().numpy(), counts=counts, total=total)
+    if bwd:
+        g_d = torch.zeros_like(D)
+        g_f = torch.zeros(F.shape, device="cuda")
+        g_m = torch.zeros_like(flat)
+        r.backward(D, F, views, ro, rd, jt, None, cuda(gC), cuda(gT), g_d, g_f, g_m)
+        torch.cuda.synchronize()
+        out.update(g_d=g_d.cpu().numpy(), g_f=g_f.cpu().numpy(), g_m=g_m.cpu().numpy())
+    return out
+
+
+@pytest.mark.parametrize("feat_dtype", [torch.float32, torch.bfloat16])
+def test_fine_fp32_mlp_parity_small(feat_dtype):
+    res, R = 24, 300
+    dens, feat, mlp, o, d, jit, _ = _fine_inputs(res, R, seed=10)
+    if feat_dtype == torch.bfloat16:
+        # the oracle sees the BF16-rounded feature values the kernel reads
+        feat = torch.as_tensor(feat).to(torch.bfloat16).float().numpy()
+    step = 2.0 / res * 0.5
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, shift_b=dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / res),
+                    bg=(1.0, 1.0, 1.0), mlp_prec=dvgo.DVGO_MLP_FP32)
+    g = np.random.default_rng(11)
+    gC = g.normal(scale=1e-2, size=(R, 3))
+    gT = g.normal(scale=1e-2, size=R)
+    got = _run_fine(p, res, dens, feat, mlp, o, d, jit, gC, gT, feat_dtype)
+    P = oracle_params(p, (res,) * 3, 12)
+    ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, grad_tfinal=gT)
+    np.testing.assert_array_equal(got["counts"], ref.n_samples)
+    assert got["total"] % 64 != 0 and got["total"] > 64 * 10     # several tiles and a ragged tail
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
+    assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat")
+    ref_m = np.concatenate([ref.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    off = 0
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        n = mlp[k].size
+        assert_close(got["g_m"][off:off + n], ref_m[off:off + n], RTOL_GRAD, f"grad_{k}")
+        off += n
+
+
+def test_fine_explicit_samples_parity():
+    res, R, K = 20, 96, 48
+    dens, feat, mlp, o, d, _, _ = _fine_inputs(res, R, seed=20)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.05, shift_b=-1.0, bg=(0.3, 0.3, 0.3))
+    P = oracle_params(p, (res,) * 3, 12)
+    base = oracle.render(P, dens, feat, o, d, mlp=mlp)
+    g = np.random.default_rng(21)
+    # sorted random samples inside each ray's clip interval, with deltas to the next sample
+    u = np.sort(g.uniform(size=(R, K)), axis=1)
+    t0, t1 = base.t_enter[:, None], base.t_exit[:, None]
+    ts = np.where(t1 > t0, t0 + u * (t1 - t0), 0.0).astype(np.float32)
+    dts = np.diff(np.concatenate([ts, ts[:, -1:] + 0.01], axis=1), axis=1).astype(np.float32)
+    gC = g.normal(scale=1e-2, size=(R, 3))
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12)
+    r = dvgo.Renderer(p, dd, cd, R, samples_per_ray=K)
+    flat = cuda(_mlp_flat(mlp))
+    views = dvgo.render.mlp_views(flat)
+    D, F = cuda(dens), cuda(feat)
+    samples = (cuda(ts), cuda(dts))
+    rgb, tf, _ = r.forward(D, F, views, cuda(o), cuda(d), None, samples)
+    g_d, g_f, g_m = torch.zeros_like(D), torch.zeros_like(F), torch.zeros_like(flat)
+    r.backward(D, F, views, cuda(o), cuda(d), None, samples, cuda(gC), None, g_d, g_f, g_m)
+    ref = oracle.render(P, dens, feat, o, d, mlp=mlp, explicit_t=ts, explicit_dt=dts, grad_rgb=gC)
+    assert_close(rgb.cpu().numpy(), ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(g_d.cpu().numpy(), ref.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(g_f.cpu().numpy(), ref.grads["cgrid"], RTOL_GRAD, "grad_feat")
+
+
+def test_fine_config2_full_size_sampled_rays():
+    """160^3 density (8 spheres of 50) + 12-channel smooth features, 8192 camera rays, the launch
+    the benchmark times; colours checked on a seeded sample of rays, gradients on a 192-ray batch
+    over the full-size grids."""
+    res, R = 160, 8192
+    dens, feat = synth.fine_scene(seed=0, res=res)
+    mlp = synth.mlp_weights(39, 128, 3, seed=3)
+    o, d, jit, tgt = synth.fine_batch(R, seed=1)
+    step = 2.0 / res * 0.5
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / res),
+                    bg=(1.0, 1.0, 1.0))
+    got = _run_fine(p, res, dens, feat, mlp, o, d, jit, None, None, bwd=False)
+    P = oracle_params(p, (res,) * 3, 12)
+    idx = np.random.default_rng(7).choice(R, 96, replace=False)
+    ref = oracle.render(P, dens, feat, o[idx], d[idx], jitter=jit[idx], mlp=mlp)
+    np.testing.assert_array_equal(got["counts"][idx], ref.n_samples)
+    assert_close(got["rgb"][idx], ref.rgb, RTOL_COLOUR, "rgb")
+    # gradients over the full-size grids on a 192-ray batch
+    sub = idx[:48]
+    o2, d2, j2 = o[:192].copy(), d[:192].copy(), jit[:192].copy()
+    gC = np.random.default_rng(8).normal(scale=1e-2, size=(192, 3))
+    g2 = _run_fine(p, res, dens, feat, mlp, o2, d2, j2, gC, np.zeros(192))
+    ref2 = oracle.render(P, dens, feat, o2, d2, jitter=j2, mlp=mlp, grad_rgb=gC)
+    assert_close(g2["rgb"], ref2.rgb, RTOL_COLOUR, "rgb_sub")
+    assert_close(g2["g_d"], ref2.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(g2["g_f"], ref2.grads["cgrid"], RTOL_GRAD, "grad_feat")
+    ref_m = np.concatenate([ref2.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    assert_close(g2["g_m"], ref_m, RTOL_GRAD, "grad_mlp")
+    assert len(sub) == 48
+
+
+# ------------------------------------------------------------------------------------------
+# Adam
+# ------------------------------------------------------------------------------------------
+
+def test_adam_parity_and_bf16_copy():
+    n = 100003      # ragged tail after the 4-wide vector part
+    g = np.random.default_rng(30)
+    p0 = g.normal(size=n)
+    scale = g.uniform(size=n)
+    P, Gd, M, V = cuda(p0), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    pb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    po = p0.astype(np.float32).astype(np.float64)
+    mo, vo = np.zeros(n), np.zeros(n)
+    for t in range(1, 4):
+        grad = g.normal(size=n).astype(np.float32)
+        Gd.copy_(cuda(grad))
+        lr = dvgo.dvgo_lr_at(0.1, t - 1)
+        dvgo.dvgo_adam_step(P, Gd, M, V, lr, t, lr_scale=cuda(scale), param_bf16_out=pb)
+        oracle.adam(po, grad.astype(np.float64), mo, vo, float(np.float32(lr)), t,
+                    lr_scale=scale.astype(np.float32).astype(np.float64))
+        assert torch.count_nonzero(Gd).item() == 0
+    torch.cuda.synchronize()
+    assert_close(P.cpu().numpy(), po, 1e-5, "param")
+    assert_close(M.cpu().numpy(), mo, 1e-5, "m")
+    assert_close(V.cpu().numpy(), vo, 1e-5, "v")
+    assert torch.equal(pb, P.to(torch.bfloat16))
