@@ -10,7 +10,7 @@
 // running carry, which keeps T exact to FP32 rounding of the sum even over hundreds of samples.
 //
 // Backward (recomputes the forward chunk by chunk, stores nothing per sample):
-//   dC/dc_k = w_k,  dC/dtau_k = T_{k+1} c_k - S_k,  S_k = C_hat - sum_{j<=k} w_j c_j,
+//   dC/dc_k = w_k,  dC/dtau_k = T_{k+1} c_k - S_k,  S_k = sum_{j>k} w_j c_j + T_K bg,
 //   dT_K/dtau_k = -T_K,  dtau_k/dsigma_ddot = dt * sigmoid(sigma_ddot + b);
 // gradients are scattered to the 8 lattice corners with weights equal to the trilinear weights,
 // summed first over runs of lanes that hit the same corner.
@@ -130,21 +130,50 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
     if (A.target) finish_loss(A, loss_part);
 }
 
+// Optical depth of one sample (density gather only), with the removal rule.
+__device__ __forceinline__ float coarse_tau(const RenderArgs &A, const RayRec &rr, int ray, int k) {
+    double t;
+    float dt;
+    sample_t(A, rr, ray, k, t, dt);
+    double u[3];
+    lattice_coord(rr, t, u);
+    Cell c = make_cell(u, A.nx, A.ny, A.nz);
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
+    float tau = softplusf(s + A.shift_b) * dt;
+    return (-expm1f(-tau) < A.tau_f) ? 0.0f : tau;
+}
+
+// Backward: pass 1 (front to back) recomputes the optical depth at the start of every chunk;
+// pass 2 (back to front) recomputes the samples and evaluates dC/dtau_k as the suffix sum
+// D_k = sum_{j>=k} T_{j+1} (c_j - c_{j+1}) with c_K = bg (from D_k - D_{k+1} = T_{k+1}(c_k - c_{k+1})
+// and D_{K-1} = T_K (c_{K-1} - bg)), which avoids the cancellation of T_{k+1} c_k - S_k.
 __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
-    int lane = threadIdx.x & 31;
+    __shared__ float s_pre[8][kMaxChunks];
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
         if (rr.n == 0) continue;
-        const float4 ro = A.rayout[r];
-        const float Chat[3] = {ro.x, ro.y, ro.z};
-        const float TK = ro.w;
+        const int nch = (rr.n + 31) >> 5;
+        const float TK = A.rayout[r].w;
         const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
         const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
-        float carry = 0.0f, Acarry[3] = {0.0f, 0.0f, 0.0f};
-        for (int base = 0; base < rr.n; base += 32) {
-            int k = base + lane;
+        float carry = 0.0f;
+        for (int ci = 0; ci < nch; ++ci) {
+            int k = ci * 32 + lane;
+            float tau = k < rr.n ? coarse_tau(A, rr, r, k) : 0.0f;
+            float incl = warp_incl_scan(tau, lane);
+            if (lane == 0) s_pre[wib][ci] = carry;
+            carry += __shfl_sync(FULL, incl, 31);
+        }
+        __syncwarp();
+        float Dc[3] = {0.0f, 0.0f, 0.0f};
+        float cnext[3] = {A.bg[0], A.bg[1], A.bg[2]};
+        for (int ci = nch - 1; ci >= 0; --ci) {
+            int k = ci * 32 + lane;
             bool valid = k < rr.n;
             CoarseSample S;
             S.tau = 0.0f;
@@ -155,18 +184,27 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
             S.cell.i0 = S.cell.j0 = S.cell.k0 = 0;
             S.cell.fx = S.cell.fy = S.cell.fz = 0.0f;
             if (valid) S = coarse_sample(A, rr, r, k);
+            float pre = s_pre[wib][ci];
             float incl = warp_incl_scan(S.tau, lane);
             float excl = __shfl_up_sync(FULL, incl, 1);
             if (lane == 0) excl = 0.0f;
-            float T = expf(-(carry + excl));
-            float T1 = expf(-(carry + incl));
+            float T = expf(-(pre + excl));
+            float T1 = expf(-(pre + incl));
             float w = T * -expm1f(-S.tau);
-            float Ain[3];
+            float D[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) Ain[ch] = Acarry[ch] + warp_incl_scan(w * S.c[ch], lane);
+            for (int ch = 0; ch < 3; ++ch) {
+                float cn = __shfl_down_sync(FULL, S.c[ch], 1);
+                if (lane == 31 || k + 1 >= rr.n) cn = (k + 1 >= rr.n) ? A.bg[ch] : cnext[ch];
+                float X = valid ? T1 * (S.c[ch] - cn) : 0.0f;
+                float sx = warp_suffix_scan(X, lane);
+                D[ch] = Dc[ch] + sx;
+                Dc[ch] += __shfl_sync(FULL, sx, 0);
+                cnext[ch] = __shfl_sync(FULL, S.c[ch], 0);
+            }
             float dtau = -gT * TK;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], T1 * S.c[ch] - (Chat[ch] - Ain[ch]), dtau);
+            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], D[ch], dtau);
             bool act = valid && S.kept;
             float dz = act ? dtau * S.dt * sigmoidf_(S.z) : 0.0f;
             float dc[3];
@@ -189,10 +227,8 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
                     if (act && sg.tail) atomicAdd(A.grad_cgrid + (long long)idx * 3 + ch, vc);
                 }
             }
-            carry += __shfl_sync(FULL, incl, 31);
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) Acarry[ch] = __shfl_sync(FULL, Ain[ch], 31);
         }
+        __syncwarp();
     }
 }
 

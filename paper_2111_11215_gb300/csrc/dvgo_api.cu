@@ -100,6 +100,8 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
         if (!ex->t || !ex->dt || ex->n_per_ray < 1) return DVGO_ERR_INVALID_ARG;
     }
     if (max_samples(p, dd, R, ex) >= (1LL << 31) - 1) return DVGO_ERR_UNSUPPORTED;
+    // the backward keeps one optical-depth value per 32-sample chunk of a ray in shared memory
+    if ((ex ? (long long)ex->n_per_ray : sample_cap(p, dd)) > kMaxSamplesPerRay) return DVGO_ERR_UNSUPPORTED;
     return DVGO_OK;
 }
 
@@ -216,7 +218,7 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode);
     if ((st = check_ws(L, ws, ws_bytes))) return st;
     if (R == 0) {
-        if (loss_out && target) cudaMemsetAsync(loss_out, 0, sizeof(float), s);
+        if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(float), s);
         return launch_status();
     }
     RenderArgs A = make_args(p, dd, density, cd, cgrid, mlp, R, ex, ws, L);

@@ -23,6 +23,8 @@ namespace dvgo {
 
 constexpr int kWarp = 32;
 constexpr int kMaxFeat = 16;
+constexpr int kMaxChunks = 64;                    // backward kernels: rays of <= 64 x 32 samples
+constexpr int kMaxSamplesPerRay = 32 * kMaxChunks;
 
 // Per-ray record written by ray_setup (80 bytes).
 struct RayRec {
@@ -151,6 +153,16 @@ __device__ __forceinline__ float warp_incl_scan(float v, int lane) {
     for (int o = 1; o < 32; o <<= 1) {
         float n = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Inclusive suffix sum over the lanes of a warp: lane i gets sum_{j >= i} v_j.
+__device__ __forceinline__ float warp_suffix_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float n = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < 32) v += n;
     }
     return v;
 }

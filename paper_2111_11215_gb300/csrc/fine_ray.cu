@@ -9,7 +9,11 @@
 // fine_composite: warp per ray.  T_k = exp(-sum_{j<k} tau_j), w_k = T_k alpha_k,
 //                 C_hat = sum w_k c_k + T_K bg (Eq. volume_rendering), loss (Eq. photo_loss).
 // fine_comp_bwd:  warp per ray.  dC/dc_k = w_k -> stored for the colour backward;
-//                 dC/dtau_k = T_{k+1} c_k - (C_hat - sum_{j<=k} w_j c_j), dT_K/dtau_k = -T_K;
+//                 dC/dtau_k = T_{k+1} c_k - S_k with S_k = sum_{j>k} w_j c_j + T_K bg, evaluated as
+//                 D_k = sum_{j>=k} T_{j+1} (c_j - c_{j+1}) (c_K = bg), which follows from
+//                 D_k - D_{k+1} = T_{k+1} (c_k - c_{k+1}) and D_{K-1} = T_K (c_{K-1} - bg); the sum
+//                 is taken from the back of the ray, so no large terms cancel when the colour in
+//                 front of a surface matches the colour behind it.  dT_K/dtau_k = -T_K;
 //                 dtau/dsigma_ddot = dt sigmoid(sigma_ddot + b) = dt (1 - exp(-tau/dt));
 //                 the density gradient is scattered to the 8 corners (runs of lanes that share a
 //                 corner are summed before one atomic).
@@ -128,36 +132,57 @@ __global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
 }
 
 __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
-    int lane = threadIdx.x & 31;
+    __shared__ float s_pre[8][kMaxChunks];   // optical depth before each chunk, per warp
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
         if (rr.n == 0) continue;
-        const float4 ro = A.rayout[r];
-        const float Chat[3] = {ro.x, ro.y, ro.z};
-        const float TK = ro.w;
+        const int nch = (rr.n + 31) >> 5;
+        const float TK = A.rayout[r].w;
         const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
         const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
-        float carry = 0.0f, Acarry[3] = {0.0f, 0.0f, 0.0f};
-        for (int base = 0; base < rr.n; base += 32) {
-            int k = base + lane;
+        // pass 1 (front to back): optical depth at the start of every chunk, as in the forward
+        float carry = 0.0f;
+        for (int ci = 0; ci < nch; ++ci) {
+            int k = ci * 32 + lane;
+            float tau = k < rr.n ? A.samp[rr.off + k].x : 0.0f;
+            float incl = warp_incl_scan(tau, lane);
+            if (lane == 0) s_pre[wib][ci] = carry;
+            carry += __shfl_sync(FULL, incl, 31);
+        }
+        __syncwarp();
+        // pass 2 (back to front): D_k = dC/dtau_k as a suffix sum of T_{j+1} (c_j - c_{j+1})
+        float Dc[3] = {0.0f, 0.0f, 0.0f};
+        float cnext[3] = {A.bg[0], A.bg[1], A.bg[2]};   // colour after the chunk's last sample
+        for (int ci = nch - 1; ci >= 0; --ci) {
+            int k = ci * 32 + lane;
             bool valid = k < rr.n;
             float4 sv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (valid) sv = A.samp[rr.off + k];
             const float cc[3] = {sv.y, sv.z, sv.w};
+            float pre = s_pre[wib][ci];
             float incl = warp_incl_scan(sv.x, lane);
             float excl = __shfl_up_sync(FULL, incl, 1);
             if (lane == 0) excl = 0.0f;
-            float T = expf(-(carry + excl));
-            float T1 = expf(-(carry + incl));
+            float T = expf(-(pre + excl));
+            float T1 = expf(-(pre + incl));
             float w = T * -expm1f(-sv.x);
-            float Ain[3];
+            float D[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) Ain[ch] = Acarry[ch] + warp_incl_scan(w * cc[ch], lane);
+            for (int ch = 0; ch < 3; ++ch) {
+                float cn = __shfl_down_sync(FULL, cc[ch], 1);
+                if (lane == 31 || k + 1 >= rr.n) cn = (k + 1 >= rr.n) ? A.bg[ch] : cnext[ch];
+                float X = valid ? T1 * (cc[ch] - cn) : 0.0f;
+                float sx = warp_suffix_scan(X, lane);
+                D[ch] = Dc[ch] + sx;
+                Dc[ch] += __shfl_sync(FULL, sx, 0);
+                cnext[ch] = __shfl_sync(FULL, cc[ch], 0);
+            }
             float dtau = -gT * TK;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], T1 * cc[ch] - (Chat[ch] - Ain[ch]), dtau);
+            for (int ch = 0; ch < 3; ++ch) dtau = fmaf(g[ch], D[ch], dtau);
             // kept samples have tau > 0 or an exactly-zero sigmoid factor; removed ones have tau = 0
             bool act = valid && sv.x > 0.0f;
             Cell c;
@@ -182,10 +207,8 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
                 float v = seg_sum(dz * corner_weight(c, q), sg, lane);
                 if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
             }
-            carry += __shfl_sync(FULL, incl, 31);
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) Acarry[ch] = __shfl_sync(FULL, Ain[ch], 31);
         }
+        __syncwarp();
     }
 }
 

@@ -41,5 +41,12 @@ def assert_close(got, ref, rtol, name, floor=FLOOR):
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     rel2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
-    assert e <= 1.0, f"{name}: normalised error {e:.3g} (> 1), relative L2 {rel2:.3g}"
+    if e > 1.0:
+        g, r = got.reshape(-1), ref.reshape(-1)
+        scale = np.abs(r).max()
+        den = rtol * np.maximum(np.abs(r), floor * scale)
+        i = int(np.argmax(np.abs(g - r) / den))
+        raise AssertionError(f"{name}: normalised error {e:.3g} (> 1), relative L2 {rel2:.3g}; worst element "
+                             f"{np.unravel_index(i, ref.shape)}: got {g[i]:.9g} ref {r[i]:.9g} "
+                             f"(|ref| / max|ref| = {abs(r[i]) / scale:.3g})")
     return e, rel2
