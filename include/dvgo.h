@@ -44,7 +44,8 @@ typedef enum {
     DVGO_ERR_WORKSPACE = -2,     /* workspace NULL, misaligned or smaller than required       */
     DVGO_ERR_UNSUPPORTED = -3,   /* a combination this build does not implement               */
     DVGO_ERR_CUDA = -4,          /* a kernel launch failed (cudaGetLastError)                 */
-    DVGO_ERR_DEVICE = -5         /* device-side flag: a ray had a zero / non-finite direction */
+    DVGO_ERR_DEVICE = -5,        /* device-side flag: a ray had a zero / non-finite direction */
+    DVGO_ERR_CAPACITY = -6       /* batch larger than the static scratch of dvgo_render_fwd_noalloc */
 } dvgo_status;
 
 enum { DVGO_DTYPE_F32 = 0, DVGO_DTYPE_BF16 = 1 };
@@ -174,6 +175,35 @@ int dvgo_workspace_status(void *workspace, void *stream);
  * from a workspace into counts_out [n_rays] (device int32), and the batch total into
  * total_out[0] (device, nullable).  n_rays must be the forward's ray count. */
 int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *total_out, void *stream);
+
+/*
+ * Allocation-free variant of the coarse-stage forward (dvgo_render_fwd with mode
+ * DVGO_MODE_COARSE and no MLP or explicit samples), for callers that cannot allocate device
+ * memory at all and so cannot provide a workspace: for example a plugin inside a host
+ * application whose memory manager owns the whole device, a real-time loop that forbids
+ * allocation after start-up, or a language binding with no device allocator.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Scratch memory: instead of a caller workspace it uses one static device array of
+ * DVGO_NOALLOC_SCRATCH_BYTES (about 1.5 MB) inside the library, which every GPU that loads the
+ * library holds until the process exits.  The caller still passes all inputs and outputs, with the
+ * meaning, layout and nullability of dvgo_render_fwd.  The call itself allocates nothing (no
+ * cudaMalloc / cudaFree or allocating library routine).
+ *   - n_rays may be at most DVGO_NOALLOC_MAX_RAYS; a larger batch returns DVGO_ERR_CAPACITY and
+ *     enqueues nothing.  Any mode other than DVGO_MODE_COARSE returns DVGO_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call, on every stream, shares the one array and overwrites what the previous call left
+ *     there.  Calls whose execution overlaps on the GPU (different streams without ordering between
+ *     them) race and give undefined results: order them on one stream or with events.
+ */
+#define DVGO_NOALLOC_MAX_RAYS 16384
+#define DVGO_NOALLOC_SCRATCH_BYTES 1573120
+int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_desc *density_desc, const float *density,
+                            const dvgo_grid_desc *cgrid_desc, const void *cgrid, int n_rays,
+                            const float *rays_o, const float *rays_d, const float *jitter,
+                            const float *target, float *rgb_out, float *tfinal_out, float *loss_out,
+                            float *dloss_drgb_out, void *stream);
 
 /* Kernel kinds for the optional per-kernel timing below. */
 enum {

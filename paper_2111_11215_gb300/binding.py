@@ -20,7 +20,9 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_lr_at",
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
+    "dvgo_render_fwd_noalloc",
 )
+DVGO_NOALLOC_MAX_RAYS = 16384
 
 KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
                 "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux")
@@ -87,6 +89,8 @@ def lib():
         L.dvgo_workspace_status.argtypes = [vp, vp]
         L.dvgo_sample_counts.restype = i
         L.dvgo_sample_counts.argtypes = [vp, i, vp, vp, vp]
+        L.dvgo_render_fwd_noalloc.restype = i
+        L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
         L.dvgo_profile_enable.argtypes = [i]
         L.dvgo_profile_read.restype = i
@@ -294,3 +298,18 @@ def dvgo_profile_read(kind) -> tuple:
 
 def dvgo_launch_counter() -> int:
     return int(lib().dvgo_launch_counter())
+
+
+def dvgo_render_fwd_noalloc(params: Params, density_desc: GridDesc, density, cgrid_desc: GridDesc, cgrid, rays_o,
+                            rays_d, jitter, target, rgb_out, tfinal_out, loss_out, dloss_drgb_out, stream=None):
+    """Coarse forward with the library's static scratch instead of a workspace (for callers that
+    cannot allocate device memory); at most DVGO_NOALLOC_MAX_RAYS rays per call."""
+    p, dd, cd = params.c(), density_desc.c(), cgrid_desc.c()
+    st = lib().dvgo_render_fwd_noalloc(
+        C.byref(p), C.byref(dd), _dev(density, "density", torch.float32), C.byref(cd),
+        _dev(cgrid, "cgrid", torch.float32), int(rays_o.shape[0]), _dev(rays_o, "rays_o", torch.float32),
+        _dev(rays_d, "rays_d", torch.float32), _dev(jitter, "jitter", torch.float32, True),
+        _dev(target, "target", torch.float32, True), _dev(rgb_out, "rgb_out", torch.float32),
+        _dev(tfinal_out, "tfinal_out", torch.float32, True), _dev(loss_out, "loss_out", torch.float32, True),
+        _dev(dloss_drgb_out, "dloss_drgb_out", torch.float32, True), _stream(stream))
+    _check(st, "dvgo_render_fwd_noalloc")

@@ -187,6 +187,7 @@ const char *dvgo_status_string(int s) {
         case DVGO_ERR_UNSUPPORTED: return "unsupported configuration";
         case DVGO_ERR_CUDA: return "CUDA launch error";
         case DVGO_ERR_DEVICE: return "a ray had a zero or non-finite direction";
+        case DVGO_ERR_CAPACITY: return "batch exceeds the static scratch capacity of dvgo_render_fwd_noalloc";
         default: return "unknown status";
     }
 }
