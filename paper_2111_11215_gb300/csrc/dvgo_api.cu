@@ -137,6 +137,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.rays = reinterpret_cast<RayRec *>(b + L.rays);
     A.rayout = reinterpret_cast<float4 *>(b + L.rayout);
     if (p->mode == DVGO_MODE_FINE) {
+        A.pe = reinterpret_cast<float *>(b + L.pe);
         A.samp = reinterpret_cast<float4 *>(b + L.samp);
         A.sgrad = reinterpret_cast<float4 *>(b + L.sgrad);
         A.kept = reinterpret_cast<int2 *>(b + L.kept);

@@ -23,6 +23,7 @@ namespace dvgo {
 
 constexpr int kWarp = 32;
 constexpr int kMaxFeat = 16;
+constexpr int kPeStride = 32;                      // floats per ray of the direction encoding
 constexpr int kMaxChunks = 64;                    // backward kernels: rays of <= 64 x 32 samples
 constexpr int kMaxSamplesPerRay = 32 * kMaxChunks;
 
@@ -51,7 +52,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader size");
 
 // Workspace layout; every block 256-byte aligned.
 struct WsLayout {
-    size_t header, rays, rayout, samp, sgrad, kept, total;
+    size_t header, rays, rayout, pe, samp, sgrad, kept, total;
     long long max_samples;
 };
 
@@ -73,6 +74,7 @@ struct RenderArgs {
     WsHeader *hdr;
     RayRec *rays;
     float4 *rayout;             // per ray: C_hat (xyz), T_K (w)
+    float *pe;                  // fine: per ray [d (3), sin (12), cos (12), 0 x 5] (kPeStride floats)
     float4 *samp;               // per sample slot: (tau, r, g, b)
     float4 *sgrad;              // per sample slot: (unused, dL/dc)
     int2 *kept;                 // compact list of kept samples: (slot, ray)

@@ -4,23 +4,29 @@
 // = 39 inputs, two hidden layers of 128 with ReLU, sigmoid output) with the two 128-wide layers
 // and all weight-gradient contractions on the 5th-generation tensor cores: BF16 operands in
 // shared memory (128-byte swizzled panels, see tc_helpers.cuh), FP32 accumulators in TMEM, MMAs
-// issued by one thread, completion signalled through an mbarrier.  The 128 -> 3 output layer,
-// the sigmoid and the element-wise steps run on the CUDA cores in the epilogues.
+// issued by one thread, completion signalled through mbarriers.  The 128 -> 3 output layer, the
+// sigmoid and the element-wise steps run on the CUDA cores in the epilogues.
 //
-// Persistent CTAs of 128 threads walk tiles of M = 128 kept samples; thread r owns sample row r
-// of the tile (and TMEM lane r) for the gather, the epilogues and the feature scatter.
+// Persistent CTAs of 384 threads walk tiles of M = 128 kept samples.  Warps 8-11 (producers)
+// gather the next tile -- features at the 8 lattice corners, the ray's direction encoding, the
+// bias column and, in the backward, dL/dc -- into one of two X panels, and in the backward also
+// scatter the feature gradients of the tile that last used that panel.  Warps 0-7 (consumers)
+// issue the MMAs (thread 0) and run the epilogues: warp w reads TMEM lanes 32 (w % 4)..+31 and
+// handles columns 64 (w / 4)..+63 of those rows, so two warps share each row.  full[b] / empty[b]
+// mbarriers hand the X panels over; every wait is bounded.
 //
-// Forward per tile:  X[128x64] (features, PE(d), 1) -> Z1 = X W1|b1 (TMEM) -> H1 = relu (BF16, smem)
-//                    -> Z2 = H1 W2 (TMEM) -> h2 = relu(Z2 + b2), c = sigmoid(h2 W3 + b3).
+// Forward per tile:  X[128x64] (features, PE(d), 1) -> Z1 = X W1|b1 -> H1 = relu(Z1) -> Z2 = H1 W2
+//                    -> H2 = relu(Z2 + b2) -> O = H2 W3 (N = 16, 3 used) -> c = sigmoid(O + b3).
 // Backward per tile (recomputes the forward), with dL/dc from the compositing backward:
-//   dout = dL/dc c (1 - c); dZ2 = (dout W3^T) [Z2 + b2 > 0]                         (epilogue)
-//   dH1 = dZ2 W2^T;  dW2 += H1^T dZ2;  dW3 += H2^T dout;  db2 += dZ2^T 1            (MMAs)
-//   dZ1 = dH1 [Z1 > 0]                                                              (epilogue)
-//   de = dZ1 W1[0:16]^T;  [dW1 | db1]^T += dZ1^T X                                  (MMAs)
-//   de[0:12] scattered to the feature grid with the trilinear weights              (epilogue)
-// TMEM columns: Z1 [0,128), Z2 / dH1 [128,256), dW2 [256,384), dW1^T [384,448), dW3 [448,464),
-// db2 [464,480), de [480,496).  The weight-gradient accumulators live in TMEM for the whole
-// launch and are added to global memory once per CTA.
+//   dout = dL/dc c (1 - c)                                        (epilogue, BF16 panel)
+//   dH2 = dout W3^T;  dZ2 = dH2 [Z2 + b2 > 0]                      (MMA, epilogue)
+//   dH1 = dZ2 W2^T;  dW2 += H1^T dZ2;  dW3 += H2^T dout;  db2 += dZ2^T 1     (MMAs)
+//   dZ1 = dH1 [Z1 > 0]                                             (epilogue)
+//   de = dZ1 W1[0:16]^T;  [dW1 | db1]^T += dZ1^T X                 (MMAs)
+//   de[0:12] -> shared memory -> scattered to the feature grid by the producers
+// TMEM columns: Z1 / O / dH2 [0,128), Z2 / dH1 [128,256), dW2 [256,384), dW1^T [384,448),
+// dW3 [448,464), db2 [464,480), de [480,496).  The weight-gradient accumulators live in TMEM for
+// the whole launch and are added to global memory once per CTA.
 
 #include <stddef.h>
 
@@ -34,96 +40,143 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;
-constexpr int NT = 128;
+constexpr int NT = 384;        // 8 consumer + 4 producer warps
+constexpr int NC = 256;        // consumer threads: warp w owns TMEM lanes 32 (w % 4).., columns 64 (w / 4)..
+constexpr int NP = 128;        // producer threads (one sample row each)
 constexpr int HID = 128;
 constexpr int FEAT = 12;
 constexpr int NF = 4;
 constexpr int IN = FEAT + 3 + 6 * NF;   // 39; column 39 of X carries the first-layer bias
 
-constexpr uint32_t COL_Z1 = 0, COL_Z2 = 128, COL_DW2 = 256, COL_DW1 = 384, COL_DW3 = 448, COL_DB2 = 464,
-                   COL_DE = 480;
+constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_DH2 = 0, COL_Z2 = 128, COL_DW2 = 256, COL_DW1 = 384, COL_DW3 = 448,
+                   COL_DB2 = 464, COL_DE = 480;
 
 // Small per-CTA state, padded to a multiple of 1024 bytes so that the panels after it stay
 // aligned to the 128-byte-swizzle atom.
 struct alignas(1024) SmallTC {
-    float w3[HID * 3];
     float b2[HID];
     float b3[4];
     float db3[4];
-    uint64_t mbar;
+    int slot[2][TM];          // sample slot per row, -1 for padding rows
+    int cbase[2][TM];         // flat index of the base lattice corner
+    float frac[2][TM][3];     // fractional offsets
+    float dc[2][TM][3];       // dL/dc (backward)
+    uint64_t full[2], empty[2], mma;
     uint32_t tmem_base;
+    int abort;
 };
 
 struct SmemTC {
     unsigned char w1t[kPanelBytes];       // W1|b1 transposed: row = hidden unit, 64 input columns
     unsigned char w2t[2 * kPanelBytes];   // W2 transposed: row = output unit, 128 input columns
-    unsigned char x[kPanelBytes];         // X: row = sample
+    unsigned char w3p[kPanelBytes];       // W3: row = hidden unit, columns 0-2 (3-63 zero)
+    unsigned char x[2][kPanelBytes];      // X (double-buffered): row = sample
     unsigned char h1[2 * kPanelBytes];    // H1, later dZ1
+    unsigned char h2[2 * kPanelBytes];    // H2
     SmallTC sm;
     // backward only (the forward allocates the struct up to here)
-    unsigned char h2[2 * kPanelBytes];    // H2
     unsigned char dz2[2 * kPanelBytes];   // dZ2
-    unsigned char dout[kPanelBytes];      // [dout_r, dout_g, dout_b, 1, 0, ...]
+    // columns 0-15: [dout_r, dout_g, dout_b, 1, 0, ...] (MMA operand); bytes 32-79 and 80-127 of
+    // every row (16-byte chunks 2-4 and 5-7): de[0:12] in FP32 for X buffer 0 and 1
+    unsigned char dout[kPanelBytes];
 };
 
-constexpr size_t smem_bytes(bool bwd) { return (bwd ? sizeof(SmemTC) : offsetof(SmemTC, h2)) + 1024; }
+constexpr size_t smem_bytes(bool bwd) { return (bwd ? sizeof(SmemTC) : offsetof(SmemTC, dz2)) + 1024; }
 
-struct RowInfo {
-    int slot;           // sample slot, -1 for padding rows
-    int cbase;          // flat index of the base corner
-    float fx, fy, fz;   // fractional offsets
-};
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
 
-// Gather one sample row into X (features, direction encoding, bias column) and remember where it
-// sits in the grid.
-template <typename FeatT>
-__device__ __forceinline__ RowInfo gather_row(const RenderArgs &A, unsigned char *xp, int e, int n_kept, int row) {
-    RowInfo ri;
-    ri.slot = -1;
-    ri.cbase = 0;
-    ri.fx = ri.fy = ri.fz = 0.0f;
+// Barrier among the 256 consumer threads only (the producers run on their own schedule).
+__device__ __forceinline__ void consumer_sync() {
+    fence_before();
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    fence_after();
+}
+
+// Operands written by the consumers become visible to the tensor core, then the consumers sync.
+__device__ __forceinline__ void consumer_publish() {
+    fence_async_smem();
+    consumer_sync();
+}
+
+// 16-byte chunk k (0-2) of the de[0:12] slot of X buffer b in row r of the dout panel.
+__device__ __forceinline__ float4 *de_slot(unsigned char *dout, int b, int r, int k) {
+    return reinterpret_cast<float4 *>(dout + panel_offset(r, 8 * (2 + 3 * b + k)));
+}
+
+// Producer: add a tile's feature gradients (de rows staged in the dout panel) to the grid.
+__device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int b, int row) {
+    const int slot = S.sm.slot[b][row];
+    if (slot < 0) return;
+    const float4 e0 = *de_slot(S.dout, b, row, 0), e1 = *de_slot(S.dout, b, row, 1), e2 = *de_slot(S.dout, b, row, 2);
+    const float fx = S.sm.frac[b][row][0], fy = S.sm.frac[b][row][1], fz = S.sm.frac[b][row][2];
+    const long long cb = S.sm.cbase[b][row];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
+        const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz);
+        const long long idx = cb + (long long)bx * A.ny * A.nz + (long long)by * A.nz + bz;
+        float4 *g = reinterpret_cast<float4 *>(A.grad_cgrid + idx * FEAT);
+        atomicAdd(g + 0, make_float4(w * e0.x, w * e0.y, w * e0.z, w * e0.w));
+        atomicAdd(g + 1, make_float4(w * e1.x, w * e1.y, w * e1.z, w * e1.w));
+        atomicAdd(g + 2, make_float4(w * e2.x, w * e2.y, w * e2.z, w * e2.w));
+    }
+}
+
+// Producer: gather sample row `row` of a tile into X panel b and the per-row tables.
+template <typename FeatT, bool BWD>
+__device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int e, int n_kept, int row) {
     float v[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+    int slot = -1, cbase = 0;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
     if (e < n_kept) {
-        int2 kv = A.kept[e];
+        const int2 kv = A.kept[e];
         const RayRec &rr = A.rays[kv.y];
         double t;
         float dt;
         sample_t(A, rr, kv.y, kv.x - rr.off, t, dt);
         double u[3];
         lattice_coord(rr, t, u);
-        Cell c = make_cell(u, A.nx, A.ny, A.nz);
-        ri.slot = kv.x;
-        ri.cbase = (int)corner_index(c, 0, A.ny, A.nz);
-        ri.fx = c.fx;
-        ri.fy = c.fy;
-        ri.fz = c.fz;
+        const Cell c = make_cell(u, A.nx, A.ny, A.nz);
+        slot = kv.x;
+        cbase = (int)corner_index(c, 0, A.ny, A.nz);
+        fx = c.fx;
+        fy = c.fy;
+        fz = c.fz;
+        if (BWD) {
+            const float4 gc = A.sgrad[slot];
+            d0 = gc.y;
+            d1 = gc.z;
+            d2 = gc.w;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
-            int qa = q << 1;
-            long long idx0 = corner_index(c, qa, A.ny, A.nz);
-            float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
+            const int qa = q << 1;
+            const long long idx0 = corner_index(c, qa, A.ny, A.nz);
+            const float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
             const FeatT *g = static_cast<const FeatT *>(A.cgrid) + idx0 * FEAT;
             if constexpr (sizeof(FeatT) == 4) {
                 const float4 *g4 = reinterpret_cast<const float4 *>(g);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    float4 a = __ldg(g4 + k), b = __ldg(g4 + 3 + k);
-                    v[4 * k + 0] += w0 * a.x + w1 * b.x;
-                    v[4 * k + 1] += w0 * a.y + w1 * b.y;
-                    v[4 * k + 2] += w0 * a.z + w1 * b.z;
-                    v[4 * k + 3] += w0 * a.w + w1 * b.w;
+                    const float4 a = __ldg(g4 + k), bb = __ldg(g4 + 3 + k);
+                    v[4 * k + 0] += w0 * a.x + w1 * bb.x;
+                    v[4 * k + 1] += w0 * a.y + w1 * bb.y;
+                    v[4 * k + 2] += w0 * a.z + w1 * bb.z;
+                    v[4 * k + 3] += w0 * a.w + w1 * bb.w;
                 }
             } else {
                 const uint2 *g2 = reinterpret_cast<const uint2 *>(g);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    uint2 a = __ldg(g2 + k), b = __ldg(g2 + 3 + k);
-                    float2 a0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.x));
-                    float2 a1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.y));
-                    float2 b0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&b.x));
-                    float2 b1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&b.y));
+                    uint2 a = __ldg(g2 + k), bb = __ldg(g2 + 3 + k);
+                    const float2 a0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.x));
+                    const float2 a1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.y));
+                    const float2 b0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&bb.x));
+                    const float2 b1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&bb.y));
                     v[4 * k + 0] += w0 * a0.x + w1 * b0.x;
                     v[4 * k + 1] += w0 * a0.y + w1 * b0.y;
                     v[4 * k + 2] += w0 * a1.x + w1 * b1.x;
@@ -131,312 +184,367 @@ __device__ __forceinline__ RowInfo gather_row(const RenderArgs &A, unsigned char
                 }
             }
         }
+        const float4 *pe = reinterpret_cast<const float4 *>(A.pe + (size_t)kv.y * kPeStride);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float d = rr.dir[a];
-            v[FEAT + a] = d;
-#pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                float s, cs;
-                sincosf(ldexpf(d, k), &s, &cs);
-                v[FEAT + 3 + a * NF + k] = s;
-                v[FEAT + 3 + 3 * NF + a * NF + k] = cs;
-            }
+        for (int k = 0; k < 7; ++k) {
+            const float4 q4 = __ldg(pe + k);
+            if (4 * k + 0 < 27) v[FEAT + 4 * k + 0] = q4.x;
+            if (4 * k + 1 < 27) v[FEAT + 4 * k + 1] = q4.y;
+            if (4 * k + 2 < 27) v[FEAT + 4 * k + 2] = q4.z;
+            if (4 * k + 3 < 27) v[FEAT + 4 * k + 3] = q4.w;
         }
         v[IN] = 1.0f;
     }
 #pragma unroll
-    for (int c = 0; c < 64; c += 8) panel_store8(xp, row, c, v + c);
-    return ri;
-}
-
-__device__ __forceinline__ void sync_all() {
-    fence_before();
-    __syncthreads();
-    fence_after();
-}
-
-// Operands written by the CUDA cores become visible to the tensor core, then the block syncs.
-__device__ __forceinline__ void publish_smem() {
-    fence_async_smem();
-    sync_all();
+    for (int c = 0; c < 64; c += 8) panel_store8(S.x[b], row, c, v + c);
+    S.sm.slot[b][row] = slot;
+    S.sm.cbase[b][row] = cbase;
+    S.sm.frac[b][row][0] = fx;
+    S.sm.frac[b][row][1] = fy;
+    S.sm.frac[b][row][2] = fz;
+    if (BWD) {
+        S.sm.dc[b][row][0] = d0;
+        S.sm.dc[b][row][1] = d1;
+        S.sm.dc[b][row][2] = d2;
+    }
 }
 
 template <typename FeatT, bool BWD>
-__global__ void __launch_bounds__(NT, BWD ? 1 : 2) fine_colour_tc_kernel(RenderArgs A) {
+__global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     extern __shared__ unsigned char smem_raw[];
     SmemTC &S = *reinterpret_cast<SmemTC *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
     constexpr uint32_t NCOLS = BWD ? 512 : 256;
 
-    if (tid == 0) mbar_init(&S.sm.mbar, 1);
+    if (tid == 0) {
+        mbar_init(&S.sm.full[0], NP);
+        mbar_init(&S.sm.full[1], NP);
+        mbar_init(&S.sm.empty[0], 1);
+        mbar_init(&S.sm.empty[1], 1);
+        mbar_init(&S.sm.mma, 1);
+        S.sm.abort = 0;
+    }
     if (warp == 0) tmem_alloc(&S.sm.tmem_base, NCOLS);
-    // weights: row n = tid of W1^T (64 input columns, bias in column 39) and of W2^T
-    {
+    if (tid < TM) {
+        // weights: row n = tid of W1^T (64 input columns, bias in column 39), of W2^T and of W3
         float v[64];
 #pragma unroll
         for (int k = 0; k < 64; ++k) v[k] = k < IN ? A.w1[k * HID + tid] : (k == IN ? A.b1[tid] : 0.0f);
 #pragma unroll
         for (int c = 0; c < 64; c += 8) panel_store8(S.w1t, tid, c, v + c);
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
+        for (int pnl = 0; pnl < 2; ++pnl) {
 #pragma unroll
-            for (int k = 0; k < 64; ++k) v[k] = A.w2[(p * 64 + k) * HID + tid];
+            for (int k = 0; k < 64; ++k) v[k] = A.w2[(pnl * 64 + k) * HID + tid];
 #pragma unroll
-            for (int c = 0; c < 64; c += 8) panel_store8(S.w2t + p * kPanelBytes, tid, c, v + c);
+            for (int c = 0; c < 64; c += 8) panel_store8(S.w2t + pnl * kPanelBytes, tid, c, v + c);
         }
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = k < 3 ? A.w3[3 * tid + k] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) panel_store8(S.w3p, tid, c, v + c);
         if (BWD) {
 #pragma unroll
             for (int k = 0; k < 64; ++k) v[k] = 0.0f;
 #pragma unroll
             for (int c = 0; c < 64; c += 8) panel_store8(S.dout, tid, c, v + c);
         }
-        for (int i = tid; i < HID * 3; i += NT) S.sm.w3[i] = A.w3[i];
         S.sm.b2[tid] = A.b2[tid];
         if (tid < 3) S.sm.b3[tid] = A.b3[tid];
         if (tid < 4) S.sm.db3[tid] = 0.0f;
     }
-    publish_smem();
-    const uint32_t tb = S.sm.tmem_base;
-    const uint32_t a_w1t = smem_u32(S.w1t), a_w2t = smem_u32(S.w2t), a_x = smem_u32(S.x), a_h1 = smem_u32(S.h1);
-    const uint32_t a_h2 = smem_u32(S.h2), a_dz2 = smem_u32(S.dz2), a_dout = smem_u32(S.dout);
-    const uint32_t id_128 = idesc_bf16(128, 128, 0, 0);
-    uint32_t phase = 0;
-    bool ok = true;
-    float db3_part[3] = {0.0f, 0.0f, 0.0f};
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
 
     const int n_kept = A.hdr->n_kept;
     const int ntiles = (n_kept + TM - 1) / TM;
-    bool any = false;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const uint32_t acc_w = any ? 1u : 0u;   // first tile of this CTA initialises the accumulators
-        any = true;
-        // ---- gather X ----
-        RowInfo ri = gather_row<FeatT>(A, S.x, tile * TM + tid, n_kept, tid);
-        publish_smem();
-        // ---- layer 1: Z1 = X W1 ----
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z1, desc_kmajor(a_x, kk), desc_kmajor(a_w1t, kk), id_128, kk > 0);
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-        // ---- epilogue 1: H1 = relu(Z1) ----
-        uint32_t m1[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z1 + 32 * c), z);
-            uint32_t bits = 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                bits |= (z[i] > 0.0f ? 1u : 0u) << i;
-                z[i] = fmaxf(z[i], 0.0f);
+    bool ok = true;
+    int ntile_mine = 0;
+
+    if (tid >= NC) {
+        // ------------------------------- producers -------------------------------
+        const int row = tid - NC;   // 0 .. NP-1
+        int i = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            if (i >= 2) {
+                if (!mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (BWD) scatter_row(A, S, b, row);   // feature gradients of tile i - 2
             }
-            m1[c] = bits;
-#pragma unroll
-            for (int i = 0; i < 32; i += 8) panel_store8(S.h1 + (c >> 1) * kPanelBytes, tid, (32 * c + i) & 63, z + i);
+            if (*(volatile int *)&S.sm.abort) break;
+            produce_row<FeatT, BWD>(A, S, b, tile * TM + row, n_kept, row);
+            fence_async_smem();
+            mbar_arrive(&S.sm.full[b]);
         }
-        publish_smem();
-        // ---- layer 2: Z2 = H1 W2 ----
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) mma(tb + COL_Z2, desc_kmajor(a_h1, kk), desc_kmajor(a_w2t, kk), id_128, kk > 0);
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-        // ---- epilogue 2: h2 = relu(Z2 + b2), c = sigmoid(h2 W3 + b3) ----
-        float o0 = S.sm.b3[0], o1 = S.sm.b3[1], o2 = S.sm.b3[2];
-        uint32_t m2[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * c), z);
-            uint32_t bits = 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                int j = 32 * c + i;
-                float h = z[i] + S.sm.b2[j];
-                bits |= (h > 0.0f ? 1u : 0u) << i;
-                h = fmaxf(h, 0.0f);
-                z[i] = h;
-                o0 = fmaf(h, S.sm.w3[3 * j + 0], o0);
-                o1 = fmaf(h, S.sm.w3[3 * j + 1], o1);
-                o2 = fmaf(h, S.sm.w3[3 * j + 2], o2);
-            }
-            m2[c] = bits;
-            if (BWD) {
-#pragma unroll
-                for (int i = 0; i < 32; i += 8) panel_store8(S.h2 + (c >> 1) * kPanelBytes, tid, (32 * c + i) & 63, z + i);
+        if (BWD && ok) {
+            // the last (up to) two tiles: wait until the consumers are done with them, then scatter
+            for (int j = (i >= 2 ? i - 2 : 0); j < i && ok; ++j) {
+                if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1)) ok = false;
+                else if (!*(volatile int *)&S.sm.abort) scatter_row(A, S, j & 1, row);
             }
         }
-        const float c0 = sigmoidf_(o0), c1 = sigmoidf_(o1), c2 = sigmoidf_(o2);
-        if (!BWD) {
-            if (ri.slot >= 0) {
-                float *sp = reinterpret_cast<float *>(A.samp + ri.slot);
-                sp[1] = c0;
-                sp[2] = c1;
-                sp[3] = c2;
+        if (!ok) atomicExch(&S.sm.abort, 1);
+    } else {
+        // ------------------------------- consumers -------------------------------
+        // thread: row r = 32 (warp % 4) + lane (its TMEM lane), column half hc = warp / 4
+        const int r = tid & (TM - 1), hc = tid >> 7;
+        const uint32_t tb = S.sm.tmem_base;
+        uint32_t mphase = 0;
+        float db3_part[3] = {0.0f, 0.0f, 0.0f};
+        int i = 0;
+        // waits for the current MMA batch; on a timeout every consumer leaves the loop
+        auto wait_mma = [&]() -> bool {
+            bool w = mbar_wait(&S.sm.mma, mphase);
+            mphase ^= 1;
+            fence_after();
+            return w;
+        };
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            const uint32_t acc_w = i > 0 ? 1u : 0u;   // first tile of this CTA initialises the accumulators
+            // opaque copies: keeps the compiler from hoisting every MMA descriptor out of the loop
+            uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.w3p);
+            uint32_t h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), dz2_ = smem_u32(S.dz2), dout_ = smem_u32(S.dout);
+            asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(h1_), "+r"(h2_), "+r"(dz2_), "+r"(dout_));
+            if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1)) ok = false;
+            fence_after();
+            if (!ok || *(volatile int *)&S.sm.abort) break;
+            // per-row tables of buffer b, read before the buffer is handed back to the producers
+            const int slot = S.sm.slot[b][r];
+            const float dc0 = BWD ? S.sm.dc[b][r][0] : 0.0f, dc1 = BWD ? S.sm.dc[b][r][1] : 0.0f,
+                        dc2 = BWD ? S.sm.dc[b][r][2] : 0.0f;
+            // ---- layer 1: Z1 = X W1 ----
+            if (tid == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tb + COL_Z1, desc_kmajor(x_, kk), desc_kmajor(w1t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                commit(&S.sm.mma);
             }
-            continue;
-        }
-        // ---- backward epilogue 2: dout, dZ2 ----
-        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
-        if (ri.slot >= 0) {
-            const float4 gc = A.sgrad[ri.slot];
-            d0 = gc.y * c0 * (1.0f - c0);
-            d1 = gc.z * c1 * (1.0f - c1);
-            d2 = gc.w * c2 * (1.0f - c2);
-        }
-        db3_part[0] += d0;
-        db3_part[1] += d1;
-        db3_part[2] += d2;
-        {
-            uint2 q;
-            q.x = pack_bf16(d0, d1);
-            q.y = pack_bf16(d2, 1.0f);
-            *reinterpret_cast<uint2 *>(S.dout + panel_offset(tid, 0)) = q;
-        }
+            if (!wait_mma()) { ok = false; break; }
+            if (!BWD && tid == 0) mbar_arrive(&S.sm.empty[b]);   // X[b] is free once layer 1 is done
+            // ---- epilogue 1: H1 = relu(Z1), my 64 columns ----
+            uint32_t m1lo = 0u, m1hi = 0u;   // ReLU masks of my 64 columns
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_Z1 + 64 * hc + 32 * g), z);
+                uint32_t bits = 0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float z[32];
+                for (int k = 0; k < 32; ++k) {
+                    bits |= (z[k] > 0.0f ? 1u : 0u) << k;
+                    z[k] = fmaxf(z[k], 0.0f);
+                }
+                if (g == 0) m1lo = bits;
+                else m1hi = bits;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                int j = 32 * c + i;
-                float dh = d0 * S.sm.w3[3 * j] + d1 * S.sm.w3[3 * j + 1] + d2 * S.sm.w3[3 * j + 2];
-                z[i] = ((m2[c] >> i) & 1u) ? dh : 0.0f;
+                for (int k = 0; k < 32; k += 8) panel_store8(S.h1 + hc * kPanelBytes, r, 32 * g + k, z + k);
             }
-#pragma unroll
-            for (int i = 0; i < 32; i += 8) panel_store8(S.dz2 + (c >> 1) * kPanelBytes, tid, (32 * c + i) & 63, z + i);
-        }
-        publish_smem();
-        if (tid == 0) {
-            const uint32_t id_mk = idesc_bf16(128, 128, 0, 1);   // K-major A, MN-major B
-            const uint32_t id_mm = idesc_bf16(128, 128, 1, 1);
-            const uint32_t id_n16 = idesc_bf16(128, 16, 1, 1);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                mma(tb + COL_Z2, desc_kmajor(a_dz2, kk), desc_mnmajor(a_w2t, kk), id_mk, kk > 0);      // dH1
-                mma(tb + COL_DW2, desc_mnmajor(a_h1, kk), desc_mnmajor(a_dz2, kk), id_mm, acc_w | (kk > 0));
-                mma(tb + COL_DW3, desc_mnmajor(a_h2, kk), desc_mnmajor(a_dout, kk), id_n16, acc_w | (kk > 0));
-                mma(tb + COL_DB2, desc_mnmajor(a_dz2, kk), desc_mnmajor(a_dout, kk), id_n16, acc_w | (kk > 0));
+            consumer_publish();
+            // ---- layer 2: Z2 = H1 W2 ----
+            if (tid == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tb + COL_Z2, desc_kmajor(h1_, kk), desc_kmajor(w2t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                commit(&S.sm.mma);
             }
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-        // ---- backward epilogue 3: dZ1 = dH1 [Z1 > 0], over H1 ----
+            if (!wait_mma()) { ok = false; break; }
+            // ---- epilogue 2: H2 = relu(Z2 + b2), my 64 columns ----
+            uint32_t m2lo = 0u, m2hi = 0u;
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                const int col = 64 * hc + 32 * g;
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_Z2 + col), z);
+                uint32_t bits = 0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * c), z);
+                for (int k = 0; k < 32; ++k) {
+                    const float h = z[k] + S.sm.b2[col + k];
+                    bits |= (h > 0.0f ? 1u : 0u) << k;
+                    z[k] = fmaxf(h, 0.0f);
+                }
+                if (g == 0) m2lo = bits;
+                else m2hi = bits;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) z[i] = ((m1[c] >> i) & 1u) ? z[i] : 0.0f;
-#pragma unroll
-            for (int i = 0; i < 32; i += 8) panel_store8(S.h1 + (c >> 1) * kPanelBytes, tid, (32 * c + i) & 63, z + i);
-        }
-        publish_smem();
-        if (tid == 0) {
-            const uint32_t id_de = idesc_bf16(128, 16, 0, 1);
-            const uint32_t id_w1 = idesc_bf16(128, 64, 1, 1);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                mma(tb + COL_DE, desc_kmajor(a_h1, kk), desc_mnmajor(a_w1t, kk), id_de, kk > 0);
-                mma(tb + COL_DW1, desc_mnmajor(a_h1, kk), desc_mnmajor(a_x, kk), id_w1, acc_w | (kk > 0));
+                for (int k = 0; k < 32; k += 8) panel_store8(S.h2 + hc * kPanelBytes, r, 32 * g + k, z + k);
             }
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-        // ---- backward epilogue 4: scatter de[0:12] to the feature grid ----
-        {
-            float de[16];
-            tmem_ld16(taddr(tb, warp, COL_DE), de);
-            if (ri.slot >= 0) {
+            consumer_publish();
+            // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used) ----
+            if (tid == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tb + COL_O, desc_kmajor(h2_, kk), desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
+                commit(&S.sm.mma);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            float o[16];
+            tmem_ld16(taddr(tb, warp, COL_O), o);
+            const float c0 = sigmoidf_(o[0] + S.sm.b3[0]), c1 = sigmoidf_(o[1] + S.sm.b3[1]),
+                        c2 = sigmoidf_(o[2] + S.sm.b3[2]);
+            if (!BWD) {
+                if (slot >= 0 && hc == 0) {
+                    float *sp = reinterpret_cast<float *>(A.samp + slot);
+                    sp[1] = c0;
+                    sp[2] = c1;
+                    sp[3] = c2;
+                }
+                consumer_sync();   // TMEM reads done before the next tile's MMAs
+                continue;
+            }
+            // ---- backward: dout = dL/dc c (1 - c) ----
+            const float d0 = dc0 * c0 * (1.0f - c0);
+            const float d1 = dc1 * c1 * (1.0f - c1);
+            const float d2 = dc2 * c2 * (1.0f - c2);
+            if (hc == 0) {
+                db3_part[0] += d0;
+                db3_part[1] += d1;
+                db3_part[2] += d2;
+                uint2 q;
+                q.x = pack_bf16(d0, d1);
+                q.y = pack_bf16(d2, 1.0f);
+                *reinterpret_cast<uint2 *>(S.dout + panel_offset(r, 0)) = q;
+            }
+            consumer_publish();
+            // ---- dH2 = dout W3^T (K = 16) ----
+            if (tid == 0) {
+                mma(tb + COL_DH2, desc_kmajor(dout_, 0), desc_kmajor(w3p_, 0), idesc_bf16(128, 128, 0, 0), 0u);
+                commit(&S.sm.mma);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            // ---- dZ2 = dH2 [Z2 + b2 > 0] ----
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                const uint32_t bits = g == 0 ? m2lo : m2hi;
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_DH2 + 64 * hc + 32 * g), z);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
-                    float w = (bx ? ri.fx : 1.0f - ri.fx) * (by ? ri.fy : 1.0f - ri.fy) * (bz ? ri.fz : 1.0f - ri.fz);
-                    long long idx = (long long)ri.cbase + (long long)bx * A.ny * A.nz + (long long)by * A.nz + bz;
-                    float4 *g = reinterpret_cast<float4 *>(A.grad_cgrid + idx * FEAT);
-                    atomicAdd(g + 0, make_float4(w * de[0], w * de[1], w * de[2], w * de[3]));
-                    atomicAdd(g + 1, make_float4(w * de[4], w * de[5], w * de[6], w * de[7]));
-                    atomicAdd(g + 2, make_float4(w * de[8], w * de[9], w * de[10], w * de[11]));
+                for (int k = 0; k < 32; ++k) z[k] = ((bits >> k) & 1u) ? z[k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) panel_store8(S.dz2 + hc * kPanelBytes, r, 32 * g + k, z + k);
+            }
+            consumer_publish();
+            if (tid == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk) {
+                    mma(tb + COL_Z2, desc_kmajor(dz2_, kk), desc_mnmajor(w2t_, kk), idesc_bf16(128, 128, 0, 1), kk > 0);  // dH1
+                    mma(tb + COL_DW2, desc_mnmajor(h1_, kk), desc_mnmajor(dz2_, kk), idesc_bf16(128, 128, 1, 1),
+                        acc_w | (kk > 0));
+                    mma(tb + COL_DW3, desc_mnmajor(h2_, kk), desc_mnmajor(dout_, kk), idesc_bf16(128, 16, 1, 1),
+                        acc_w | (kk > 0));
+                    mma(tb + COL_DB2, desc_mnmajor(dz2_, kk), desc_mnmajor(dout_, kk), idesc_bf16(128, 16, 1, 1),
+                        acc_w | (kk > 0));
+                }
+                commit(&S.sm.mma);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            // ---- dZ1 = dH1 [Z1 > 0], over H1 ----
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                const uint32_t bits = g == 0 ? m1lo : m1hi;
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_Z2 + 64 * hc + 32 * g), z);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) z[k] = ((bits >> k) & 1u) ? z[k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) panel_store8(S.h1 + hc * kPanelBytes, r, 32 * g + k, z + k);
+            }
+            consumer_publish();
+            if (tid == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk) {
+                    mma(tb + COL_DE, desc_kmajor(h1_, kk), desc_mnmajor(w1t_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
+                    mma(tb + COL_DW1, desc_mnmajor(h1_, kk), desc_mnmajor(x_, kk), idesc_bf16(128, 64, 1, 1),
+                        acc_w | (kk > 0));
+                }
+                commit(&S.sm.mma);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            // ---- stage de[0:12] for the producers' scatter, then release X[b] ----
+            {
+                float de[16];
+                tmem_ld16(taddr(tb, warp, COL_DE), de);
+                if (hc == 0) {
+                    *de_slot(S.dout, b, r, 0) = make_float4(de[0], de[1], de[2], de[3]);
+                    *de_slot(S.dout, b, r, 1) = make_float4(de[4], de[5], de[6], de[7]);
+                    *de_slot(S.dout, b, r, 2) = make_float4(de[8], de[9], de[10], de[11]);
                 }
             }
+            consumer_sync();
+            if (tid == 0) mbar_arrive(&S.sm.empty[b]);   // X[b] consumed, de staged
         }
-        sync_all();
-    }
-
-    ok = !__syncthreads_or(!ok);   // block-uniform from here on
-    if (!ok) {
-        if (tid == 0) atomicOr(&A.hdr->flags, 2);
-        mbar_wait(&S.sm.mbar, phase ^ 1);   // let the MMA that timed out finish (bounded)
-    }
-    sync_all();
-    if (BWD && ok && any) {
-        float *gW1 = A.grad_mlp, *gB1 = gW1 + IN * HID, *gW2 = gB1 + HID, *gB2 = gW2 + HID * HID;
-        float *gW3 = gB2 + HID, *gB3 = gW3 + HID * 3;
-        // dW2: lane = input unit (tid), columns = output units
+        ntile_mine = i;
+        if (!ok) atomicExch(&S.sm.abort, 1);
+        if (BWD) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v[32];
-            tmem_ld32(taddr(tb, warp, COL_DW2 + 32 * c), v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) atomicAdd(gW2 + tid * HID + 32 * c + i, v[i]);
-        }
-        // [dW1 | db1]^T: lane = hidden unit, columns = inputs (39 = bias)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float v[32];
-            tmem_ld32(taddr(tb, warp, COL_DW1 + 32 * c), v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                int k = 32 * c + i;
-                if (k < IN) atomicAdd(gW1 + k * HID + tid, v[i]);
-                else if (k == IN) atomicAdd(gB1 + tid, v[i]);
+            for (int ch = 0; ch < 3; ++ch) {
+                const float sum = warp_sum(db3_part[ch]);
+                if ((tid & 31) == 0) atomicAdd(&S.sm.db3[ch], sum);
             }
         }
-        {
-            float v[16];
-            tmem_ld16(taddr(tb, warp, COL_DW3), v);
-            atomicAdd(gW3 + tid * 3 + 0, v[0]);
-            atomicAdd(gW3 + tid * 3 + 1, v[1]);
-            atomicAdd(gW3 + tid * 3 + 2, v[2]);
-            tmem_ld16(taddr(tb, warp, COL_DB2), v);
-            atomicAdd(gB2 + tid, v[3]);
-        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const bool failed = S.sm.abort != 0;
+    if (failed) {
+        if (tid == 0) atomicOr(&A.hdr->flags, 2);
+        // an MMA batch whose completion timed out may still be running: wait (bounded) once more
+        if (tid < NC) mbar_wait(&S.sm.mma, 0);
+    }
+    if (BWD && !failed && tid < NC && ntile_mine > 0) {
+        const uint32_t tb = S.sm.tmem_base;
+        const int r = tid & (TM - 1), hc = tid >> 7;
+        float *gW1 = A.grad_mlp, *gB1 = gW1 + IN * HID, *gW2 = gB1 + HID, *gB2 = gW2 + HID * HID;
+        float *gW3 = gB2 + HID, *gB3 = gW3 + HID * 3;
+        // dW2: lane = input unit r, columns = output units (64 per half)
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            const int col = 64 * hc + 32 * c;
+            float v[32];
+            tmem_ld32(taddr(tb, warp, COL_DW2 + col), v);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float s = warp_sum(db3_part[ch]);
-            if ((tid & 31) == 0) atomicAdd(&S.sm.db3[ch], s);
+            for (int k = 0; k < 32; ++k) atomicAdd(gW2 + r * HID + col + k, v[k]);
         }
-        __syncthreads();
+        // [dW1 | db1]^T: lane = hidden unit r, columns = inputs (39 = bias), 32 per half
+        {
+            float v[32];
+            tmem_ld32(taddr(tb, warp, COL_DW1 + 32 * hc), v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int kin = 32 * hc + k;
+                if (kin < IN) atomicAdd(gW1 + kin * HID + r, v[k]);
+                else if (kin == IN) atomicAdd(gB1 + r, v[k]);
+            }
+        }
+        float v[16];
+        tmem_ld16(taddr(tb, warp, COL_DW3), v);
+        if (hc == 0) {
+            atomicAdd(gW3 + r * 3 + 0, v[0]);
+            atomicAdd(gW3 + r * 3 + 1, v[1]);
+            atomicAdd(gW3 + r * 3 + 2, v[2]);
+        }
+        tmem_ld16(taddr(tb, warp, COL_DB2), v);
+        if (hc == 0) atomicAdd(gB2 + r, v[3]);
         if (tid < 3) atomicAdd(gB3 + tid, S.sm.db3[tid]);
     }
-    sync_all();
-    if (warp == 0) tmem_dealloc(tb, NCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(S.sm.tmem_base, NCOLS);
 }
 
-// The forward holds 256 TMEM columns and ~100 KB of shared memory, so two CTAs share an SM; the
-// backward holds all 512 columns, one CTA per SM.
 template <typename FeatT, bool BWD>
 void launch_tc(const RenderArgs &A, int kind, cudaStream_t s) {
     auto kern = fine_colour_tc_kernel<FeatT, BWD>;
     const int bytes = (int)smem_bytes(BWD);
     ensure_smem(reinterpret_cast<const void *>(kern), bytes);
     ProfScope ps_(kind, s);
-    kern<<<num_sms() * (BWD ? 1 : 2), NT, bytes, s>>>(A);
+    kern<<<num_sms(), NT, bytes, s>>>(A);
 }
 
 }  // namespace

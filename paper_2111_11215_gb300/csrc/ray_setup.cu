@@ -84,6 +84,22 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
     }
     rec.t_enter = lo;
     rec.p = (float)p;
+    if (A.pe) {
+        // positional encoding of the normalised direction (fine-stage MLP input, Supp. A, k_d = 4):
+        // [d, sin(2^k d_c) (c-major), cos(2^k d_c) (c-major)]
+        float *pe = A.pe + (size_t)r * kPeStride;
+        for (int a = 0; a < 3; ++a) {
+            float dv = rec.dir[a];
+            pe[a] = dv;
+            for (int k = 0; k < 4; ++k) {
+                float sv, cv;
+                sincosf(ldexpf(dv, k), &sv, &cv);
+                pe[3 + a * 4 + k] = sv;
+                pe[15 + a * 4 + k] = cv;
+            }
+        }
+        for (int k = 27; k < kPeStride; ++k) pe[k] = 0.0f;
+    }
     rec.n = n;
     rec.off = ok ? 0 : -1;   // -1 marks a ray with a zero / non-finite direction for the scan
     A.rays[r] = rec;
@@ -163,7 +179,9 @@ WsLayout ws_layout(int R, long long max_samples, int mode) {
     L.rays = o; o += up(sizeof(RayRec) * (size_t)(R > 0 ? R : 1));
     L.rayout = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));
     size_t S = (size_t)(max_samples > 0 ? max_samples : 1);
+    L.pe = 0;
     if (mode == DVGO_MODE_FINE) {
+        L.pe = o; o += up(sizeof(float) * kPeStride * (size_t)(R > 0 ? R : 1));
         L.samp = o; o += up(sizeof(float4) * S);
         L.sgrad = o; o += up(sizeof(float4) * S);
         L.kept = o; o += up(sizeof(int2) * S);
