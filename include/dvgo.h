@@ -205,6 +205,59 @@ int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_desc *density_
                             const float *target, float *rgb_out, float *tfinal_out, float *loss_out,
                             float *dloss_drgb_out, void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned sample proposal.  The paper samples every ray uniformly and leaves hierarchical
+ * sampling to future work (Supp. B, step-size ablation); this proposal is the library's
+ * addition.  A small MLP predicts, for each ray, a piecewise-constant PDF over n_bins equal bins
+ * of the clipped interval [t_enter, t_exit]; it is trained with a softmax cross-entropy on the
+ * per-bin compositing weights of a uniform render, and its PDF is sampled by inverse CDF to give
+ * the explicit samples (dvgo_samples) of a cheaper render.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int n_bins;          /* bins per ray; this build supports 64                                 */
+    int n_freq;          /* PE frequencies on the bin centre x_b; this build supports 6            */
+    int width;           /* MLP width; this build supports 64                                     */
+} dvgo_proposal_desc;
+
+/* Proposal MLP, FP32 row-major [in][out]: in = 3 + 6 n_freq (= 39) -> width -> width -> width -> 1,
+ * ReLU after the hidden layers; input row [x, sin(2^k x_c) (c-major), cos(2^k x_c) (c-major)] of the
+ * bin centre x_b = o + t_b d, t_b = t_enter + (b + 0.5)(t_exit - t_enter) / n_bins. */
+typedef struct {
+    const float *w0, *b0, *w1, *b1, *w2, *b2, *w3, *b3;
+} dvgo_proposal_mlp;
+
+/* Labels for the proposal: per ray, the compositing weights w_k = T_k alpha_k of a uniform-step
+ * fine forward (Eq. volume_rendering) summed into n_bins equal bins of [t_enter, t_exit] and
+ * normalised to sum 1 (uniform when their sum is below 1e-4).  `workspace` must hold the state of
+ * a dvgo_render_fwd in DVGO_MODE_FINE without explicit samples on the same p, density_desc and
+ * n_rays.  labels_out [n_rays * n_bins]; n_bins <= 128. */
+int dvgo_weight_bins(const dvgo_params *p, const dvgo_grid_desc *density_desc, int n_rays, int n_bins,
+                     const void *workspace, size_t workspace_bytes, float *labels_out, void *stream);
+
+/* Proposal forward: probs_out [n_rays * n_bins] = softmax over the bins of the MLP logits (a ray
+ * that misses the box gets the uniform PDF).  With labels [n_rays * n_bins] (nullable),
+ * loss_out[0] = -(1/R) sum_r sum_b h_rb log p_rb.  Needs no workspace. */
+int dvgo_proposal_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, const dvgo_proposal_desc *pd,
+                      const dvgo_proposal_mlp *mlp, int n_rays, const float *rays_o, const float *rays_d,
+                      const float *labels, float *probs_out, float *loss_out, void *stream);
+
+/* Proposal backward: ACCUMULATES the gradient of the cross-entropy loss above into grad_mlp,
+ * packed w0 | b0 | w1 | b1 | w2 | b2 | w3 | b3 (recomputes the forward). */
+int dvgo_proposal_bwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, const dvgo_proposal_desc *pd,
+                      const dvgo_proposal_mlp *mlp, int n_rays, const float *rays_o, const float *rays_d,
+                      const float *labels, float *grad_mlp, void *stream);
+
+/* Inverse-CDF sampling of n_samples sorted samples per ray from probs [n_rays * n_bins]: the PDF
+ * is mixed with the uniform one, q_b = (1 - eta) p_b + eta / n_bins; sample j sits at quantile
+ * u_j = (j + jit) / n_samples (jit = jitter[r], or 0.5 when jitter is NULL) with linear
+ * interpolation inside its bin.  t_out, dt_out [n_rays * n_samples]: distances along the
+ * normalised direction and step lengths (t_{j+1} - t_j; for the last sample the bin width over
+ * n_samples times the bin's normalised probability), ready for dvgo_samples.  Rays that miss the
+ * box get zeros.  Bin decisions are taken in FP64. */
+int dvgo_sample_pdf(const dvgo_params *p, const dvgo_grid_desc *density_desc, int n_rays, const float *rays_o,
+                    const float *rays_d, const float *probs, int n_bins, int n_samples, const float *jitter,
+                    float eta, float *t_out, float *dt_out, void *stream);
+
 /* Kernel kinds for the optional per-kernel timing below. */
 enum {
     DVGO_K_RAY_SETUP = 0, DVGO_K_SCAN = 1, DVGO_K_COARSE_FWD = 2, DVGO_K_COARSE_BWD = 3,

@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_lr_at",
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
-    "dvgo_render_fwd_noalloc",
+    "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 
@@ -89,6 +89,14 @@ def lib():
         L.dvgo_workspace_status.argtypes = [vp, vp]
         L.dvgo_sample_counts.restype = i
         L.dvgo_sample_counts.argtypes = [vp, i, vp, vp, vp]
+        L.dvgo_weight_bins.restype = i
+        L.dvgo_weight_bins.argtypes = [vp, vp, i, i, vp, sz, vp, vp]
+        L.dvgo_proposal_fwd.restype = i
+        L.dvgo_proposal_fwd.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp]
+        L.dvgo_proposal_bwd.restype = i
+        L.dvgo_proposal_bwd.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp, vp]
+        L.dvgo_sample_pdf.restype = i
+        L.dvgo_sample_pdf.argtypes = [vp, vp, i, vp, vp, vp, i, i, vp, f, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -313,3 +321,69 @@ def dvgo_render_fwd_noalloc(params: Params, density_desc: GridDesc, density, cgr
         _dev(tfinal_out, "tfinal_out", torch.float32, True), _dev(loss_out, "loss_out", torch.float32, True),
         _dev(dloss_drgb_out, "dloss_drgb_out", torch.float32, True), _stream(stream))
     _check(st, "dvgo_render_fwd_noalloc")
+
+
+# ----------------------------------------------------------------------------------------------
+# Learned sample proposal
+# ----------------------------------------------------------------------------------------------
+
+PROP_KEYS = ("w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+class _PropDesc(C.Structure):
+    _fields_ = [("n_bins", C.c_int), ("n_freq", C.c_int), ("width", C.c_int)]
+
+
+class _PropMlp(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in PROP_KEYS]
+
+
+def _prop(n_bins, n_freq, width, mlp):
+    d = _PropDesc()
+    d.n_bins, d.n_freq, d.width = int(n_bins), int(n_freq), int(width)
+    m = _PropMlp()
+    for k in PROP_KEYS:
+        setattr(m, k, _dev(mlp[k], f"proposal.{k}", torch.float32))
+    return d, m
+
+
+def dvgo_weight_bins(params: Params, density_desc: GridDesc, n_rays: int, n_bins: int, workspace, labels_out,
+                     stream=None):
+    p, g = params.c(), density_desc.c()
+    st = lib().dvgo_weight_bins(C.byref(p), C.byref(g), int(n_rays), int(n_bins),
+                                _dev(workspace, "workspace", torch.uint8), workspace.numel(),
+                                _dev(labels_out, "labels_out", torch.float32), _stream(stream))
+    _check(st, "dvgo_weight_bins")
+
+
+def dvgo_proposal_fwd(params: Params, density_desc: GridDesc, n_bins: int, n_freq: int, width: int, mlp, rays_o,
+                      rays_d, labels, probs_out, loss_out, stream=None):
+    p, g = params.c(), density_desc.c()
+    d, m = _prop(n_bins, n_freq, width, mlp)
+    st = lib().dvgo_proposal_fwd(C.byref(p), C.byref(g), C.byref(d), C.byref(m), int(rays_o.shape[0]),
+                                 _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
+                                 _dev(labels, "labels", torch.float32, True), _dev(probs_out, "probs_out", torch.float32),
+                                 _dev(loss_out, "loss_out", torch.float32, True), _stream(stream))
+    _check(st, "dvgo_proposal_fwd")
+
+
+def dvgo_proposal_bwd(params: Params, density_desc: GridDesc, n_bins: int, n_freq: int, width: int, mlp, rays_o,
+                      rays_d, labels, grad_mlp, stream=None):
+    p, g = params.c(), density_desc.c()
+    d, m = _prop(n_bins, n_freq, width, mlp)
+    st = lib().dvgo_proposal_bwd(C.byref(p), C.byref(g), C.byref(d), C.byref(m), int(rays_o.shape[0]),
+                                 _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
+                                 _dev(labels, "labels", torch.float32), _dev(grad_mlp, "grad_mlp", torch.float32),
+                                 _stream(stream))
+    _check(st, "dvgo_proposal_bwd")
+
+
+def dvgo_sample_pdf(params: Params, density_desc: GridDesc, rays_o, rays_d, probs, n_samples: int, jitter, eta,
+                    t_out, dt_out, stream=None):
+    p, g = params.c(), density_desc.c()
+    st = lib().dvgo_sample_pdf(C.byref(p), C.byref(g), int(rays_o.shape[0]), _dev(rays_o, "rays_o", torch.float32),
+                               _dev(rays_d, "rays_d", torch.float32), _dev(probs, "probs", torch.float32),
+                               int(probs.shape[-1]), int(n_samples), _dev(jitter, "jitter", torch.float32, True),
+                               float(eta), _dev(t_out, "t_out", torch.float32), _dev(dt_out, "dt_out", torch.float32),
+                               _stream(stream))
+    _check(st, "dvgo_sample_pdf")

@@ -138,6 +138,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.rayout = reinterpret_cast<float4 *>(b + L.rayout);
     if (p->mode == DVGO_MODE_FINE) {
         A.pe = reinterpret_cast<float *>(b + L.pe);
+        A.texit = reinterpret_cast<double *>(b + L.texit);
         A.samp = reinterpret_cast<float4 *>(b + L.samp);
         A.sgrad = reinterpret_cast<float4 *>(b + L.sgrad);
         A.kept = reinterpret_cast<int2 *>(b + L.kept);

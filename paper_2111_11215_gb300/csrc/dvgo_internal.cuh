@@ -52,7 +52,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader size");
 
 // Workspace layout; every block 256-byte aligned.
 struct WsLayout {
-    size_t header, rays, rayout, pe, samp, sgrad, kept, total;
+    size_t header, rays, rayout, pe, texit, samp, sgrad, kept, total;
     long long max_samples;
 };
 
@@ -75,6 +75,7 @@ struct RenderArgs {
     RayRec *rays;
     float4 *rayout;             // per ray: C_hat (xyz), T_K (w)
     float *pe;                  // fine: per ray [d (3), sin (12), cos (12), 0 x 5] (kPeStride floats)
+    double *texit;              // fine: per ray clipped exit distance
     float4 *samp;               // per sample slot: (tau, r, g, b)
     float4 *sgrad;              // per sample slot: (unused, dL/dc)
     int2 *kept;                 // compact list of kept samples: (slot, ray)
@@ -104,6 +105,51 @@ __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf
 __device__ __forceinline__ void lattice_coord(const RayRec &r, double t, double u[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = fma(t, r.e[a], r.uo[a]);
+}
+
+// Ray / box clip in FP64 with every operation separately rounded (no FMA contraction), in the
+// order the sample count depends on (Sec. 4.2 fine-stage points sampling):
+//   len = sqrt((dx*dx + dy*dy) + dz*dz), dn = d / len;
+//   per axis with dn != 0: t1 = (min - o) / dn, t2 = (max - o) / dn, lo = max(lo, min(t1, t2)),
+//   hi = min(hi, max(t1, t2)), starting from lo = t_near, hi = t_far; an axis with dn == 0 and o
+//   outside the slab empties the interval.  ok is false for a zero or non-finite direction.
+struct Clip {
+    double dn[3];
+    double lo, hi;
+    bool ok;
+};
+
+__device__ __forceinline__ Clip slab_clip(const double o[3], const double d[3], const double mn[3], const double mx[3],
+                                          double t_near, double t_far) {
+    Clip c;
+    double len2 = __dmul_rn(d[0], d[0]);
+    len2 = __dadd_rn(len2, __dmul_rn(d[1], d[1]));
+    len2 = __dadd_rn(len2, __dmul_rn(d[2], d[2]));
+    const double len = __dsqrt_rn(len2);
+    c.ok = (len > 0.0) && isfinite(len) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]);
+    c.dn[0] = c.dn[1] = c.dn[2] = 0.0;
+    c.lo = t_near;
+    c.hi = t_far;
+    if (c.ok) {
+        for (int a = 0; a < 3; ++a) {
+            c.dn[a] = __ddiv_rn(d[a], len);
+            if (c.dn[a] != 0.0) {
+                const double t1 = __ddiv_rn(__dsub_rn(mn[a], o[a]), c.dn[a]);
+                const double t2 = __ddiv_rn(__dsub_rn(mx[a], o[a]), c.dn[a]);
+                const double tl = t1 < t2 ? t1 : t2;
+                const double th = t1 < t2 ? t2 : t1;
+                if (tl > c.lo) c.lo = tl;
+                if (th < c.hi) c.hi = th;
+            } else if (o[a] < mn[a] || o[a] > mx[a]) {
+                c.lo = 1.0;
+                c.hi = 0.0;
+            }
+        }
+    } else {
+        c.lo = 1.0;
+        c.hi = 0.0;
+    }
+    return c;
 }
 
 // Base corner (clamped to [0, n-2]) and FP32 fractional offsets of a lattice coordinate.

@@ -41,33 +41,11 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
     double sc[3] = {scale.x, scale.y, scale.z};
     double p = jitter ? (double)jitter[r] : 0.5;
 
-    double len2 = __dmul_rn(d[0], d[0]);
-    len2 = __dadd_rn(len2, __dmul_rn(d[1], d[1]));
-    len2 = __dadd_rn(len2, __dmul_rn(d[2], d[2]));
-    double len = __dsqrt_rn(len2);
+    const Clip cl = slab_clip(o, d, mn, mx, t_near, t_far);
+    const bool ok = cl.ok;
+    const double lo = cl.lo, hi = cl.hi;
+    const double *dn = cl.dn;
     RayRec rec;
-    bool ok = (len > 0.0) && isfinite(len) && isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]);
-    double dn[3] = {0.0, 0.0, 0.0};
-    double lo = t_near, hi = t_far;
-    if (ok) {
-        for (int a = 0; a < 3; ++a) {
-            dn[a] = __ddiv_rn(d[a], len);
-            if (dn[a] != 0.0) {
-                double t1 = __ddiv_rn(__dsub_rn(mn[a], o[a]), dn[a]);
-                double t2 = __ddiv_rn(__dsub_rn(mx[a], o[a]), dn[a]);
-                double tl = t1 < t2 ? t1 : t2;
-                double th = t1 < t2 ? t2 : t1;
-                if (tl > lo) lo = tl;
-                if (th < hi) hi = th;
-            } else if (o[a] < mn[a] || o[a] > mx[a]) {
-                lo = 1.0;
-                hi = 0.0;
-            }
-        }
-    } else {
-        lo = 1.0;
-        hi = 0.0;
-    }
     int n = 0;
     if (hi > lo) {
         double q = __ddiv_rn(__dsub_rn(hi, lo), step);
@@ -84,6 +62,7 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
     }
     rec.t_enter = lo;
     rec.p = (float)p;
+    if (A.texit) A.texit[r] = hi;
     if (A.pe) {
         // positional encoding of the normalised direction (fine-stage MLP input, Supp. A, k_d = 4):
         // [d, sin(2^k d_c) (c-major), cos(2^k d_c) (c-major)]
@@ -179,9 +158,10 @@ WsLayout ws_layout(int R, long long max_samples, int mode) {
     L.rays = o; o += up(sizeof(RayRec) * (size_t)(R > 0 ? R : 1));
     L.rayout = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));
     size_t S = (size_t)(max_samples > 0 ? max_samples : 1);
-    L.pe = 0;
+    L.pe = L.texit = 0;
     if (mode == DVGO_MODE_FINE) {
         L.pe = o; o += up(sizeof(float) * kPeStride * (size_t)(R > 0 ? R : 1));
+        L.texit = o; o += up(sizeof(double) * (size_t)(R > 0 ? R : 1));
         L.samp = o; o += up(sizeof(float4) * S);
         L.sgrad = o; o += up(sizeof(float4) * S);
         L.kept = o; o += up(sizeof(int2) * S);

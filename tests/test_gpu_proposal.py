@@ -1,0 +1,116 @@
+"""GPU parity of the learned sample proposal against the FP64 oracle: weight-histogram labels,
+proposal MLP forward (softmax, cross-entropy) and backward, inverse-CDF sampling, and a render
+with the sampled explicit samples."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from test_gpu_parity import _fine_inputs, _mlp_flat, cuda
+
+pytestmark = pytest.mark.gpu
+
+dvgo = pytest.importorskip("paper_2111_11215_gb300")
+
+NB, NFQ, PW = 64, 6, 64
+
+
+def _proposal_weights(seed):
+    w = synth.proposal_weights(3 + 6 * NFQ, PW, seed)
+    w["b3"] = np.array([0.1], np.float32)
+    return w
+
+
+def _setup(res=24, R=160, seed=70):
+    dens, feat, mlp, o, d, jit, _ = _fine_inputs(res, R, seed=seed)
+    # a few rays that miss the box
+    o[:3] = np.array([[0.0, 3.0, 0.0], [3.0, 3.0, 0.0], [0.0, 0.0, 5.0]], np.float32)
+    d[:3] = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]], np.float32)
+    step = 2.0 / res * 0.5
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, shift_b=dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / res),
+                    bg=(1.0, 1.0, 1.0))
+    return dens, feat, mlp, o, d, jit, p
+
+
+def test_weight_bins_labels_match_oracle():
+    res = 24
+    dens, feat, mlp, o, d, jit, p = _setup(res)
+    R = o.shape[0]
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12)
+    r = dvgo.Renderer(p, dd, cd, R)
+    views = dvgo.render.mlp_views(cuda(_mlp_flat(mlp)))
+    r.forward(cuda(dens), cuda(feat), views, cuda(o), cuda(d), cuda(jit))
+    labels = torch.empty((R, NB), device="cuda")
+    dvgo.dvgo_weight_bins(p, dd, R, NB, r.workspace, labels)
+    torch.cuda.synchronize()
+    ref = oracle.render(oracle_params(p, (res,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, n_bins=NB)
+    got = labels.cpu().numpy()
+    np.testing.assert_allclose(got.sum(axis=1), 1.0, rtol=1e-5)
+    np.testing.assert_allclose(got[:3], 1.0 / NB)              # misses: uniform
+    assert_close(got, ref.wbins, RTOL_COLOUR, "labels")
+
+
+def test_proposal_forward_backward_match_oracle():
+    res = 24
+    dens, feat, mlp, o, d, jit, p = _setup(res, R=157)        # odd: a half tile
+    R = o.shape[0]
+    dd = dvgo.GridDesc((res,) * 3, 1)
+    w = _proposal_weights(71)
+    labels = np.random.default_rng(72).dirichlet(np.full(NB, 0.3), size=R).astype(np.float32)
+    wd = {k: cuda(v) for k, v in w.items()}
+    probs = torch.empty((R, NB), device="cuda")
+    loss = torch.empty(1, device="cuda")
+    dvgo.dvgo_proposal_fwd(p, dd, NB, NFQ, PW, wd, cuda(o), cuda(d), cuda(labels), probs, loss)
+    flat = torch.zeros(sum(v.size for v in w.values()), device="cuda")
+    dvgo.dvgo_proposal_bwd(p, dd, NB, NFQ, PW, wd, cuda(o), cuda(d), cuda(labels), flat)
+    torch.cuda.synchronize()
+    P = oracle_params(p, (res,) * 3, 12)
+    ref_p, ref_loss, ref_g = oracle.proposal(P, w, NB, NFQ, o, d, labels=labels, want_grads=True)
+    assert_close(probs.cpu().numpy(), ref_p, RTOL_COLOUR, "probs")
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
+    g = flat.cpu().numpy()
+    off = 0
+    for k in oracle.PROP_KEYS:
+        n = w[k].size
+        if k == "b3":
+            # d loss / d b3 = (1/R) sum_r sum_b (p_rb - h_rb) = 0 exactly: both sum to 1 per ray, so
+            # only rounding noise (terms of order 1/R) remains on either side
+            assert abs(g[off]) < 1e-6 and abs(ref_g[k][0]) < 1e-9
+        else:
+            assert_close(g[off:off + n], ref_g[k].reshape(-1), RTOL_GRAD, f"grad_{k}")
+        off += n
+
+
+def test_sample_pdf_matches_oracle_and_renders():
+    res = 24
+    dens, feat, mlp, o, d, jit, p = _setup(res, R=96)
+    R = o.shape[0]
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12)
+    g = np.random.default_rng(80)
+    probs = g.dirichlet(np.full(NB, 0.2), size=R).astype(np.float32)
+    probs[5] = 0.0
+    probs[5, 17] = 1.0                                         # one-hot PDF
+    ts, dts = torch.empty((R, 48), device="cuda"), torch.empty((R, 48), device="cuda")
+    pj = synth.jitter(R, 81)
+    dvgo.dvgo_sample_pdf(p, dd, cuda(o), cuda(d), cuda(probs), 48, cuda(pj), 1e-3, ts, dts)
+    torch.cuda.synchronize()
+    t_gpu, dt_gpu = ts.cpu().numpy(), dts.cpu().numpy()
+    P = oracle_params(p, (res,) * 3, 12)
+    for r in range(R):
+        rc, t0, t1, dn, n = oracle.ray_bounds(P, o[r], d[r])
+        if not t1 > t0:
+            assert np.all(t_gpu[r] == 0)
+            continue
+        t, dt = oracle.sample_pdf(probs[r].astype(np.float64), t0, t1, 48, jit=float(pj[r]),
+                                  eta=float(np.float32(1e-3)))
+        np.testing.assert_allclose(t_gpu[r], t, rtol=2e-7, atol=1e-7)
+        np.testing.assert_allclose(dt_gpu[r], dt, rtol=2e-6, atol=1e-7)
+        assert np.all(np.diff(t_gpu[r]) >= 0)
+    # the explicit samples drive a render that matches the oracle on the same samples
+    rend = dvgo.Renderer(p, dd, cd, R, samples_per_ray=48)
+    views = dvgo.render.mlp_views(cuda(_mlp_flat(mlp)))
+    rgb, _, _ = rend.forward(cuda(dens), cuda(feat), views, cuda(o), cuda(d), None, (ts, dts))
+    ref = oracle.render(P, dens, feat, o, d, mlp=mlp, explicit_t=t_gpu, explicit_dt=dt_gpu)
+    assert_close(rgb.cpu().numpy(), ref.rgb, RTOL_COLOUR, "rgb_explicit")
