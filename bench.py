@@ -7,8 +7,13 @@ colour MLP 39 -> 128 -> 128 -> 3, step 0.5 voxel, shift b for alpha_init = 1e-6,
 rays drawn from 100 inward-facing 800x800 views (radius 4, focal 1111).  One step = forward render
 + MSE + backward + Adam on every parameter (density, features, MLP).
 
-Forms: --form plain  = FP32 feature grid, FP32 SIMT MLP;
-       --form chosen = BF16 feature storage (FP32 master updated by Adam), BF16 tensor-core MLP.
+Forms (both are timed by default; `value` is the chosen form):
+  plain  = uniform 0.5-voxel steps, FP32 feature grid, FP32 SIMT MLP;
+  chosen = learned proposal (64-bin PDF from a BF16 tensor-core proposal MLP, 48 inverse-CDF
+           samples per ray; one proposal Adam step every 8 steps on 2048 rays with labels from a
+           uniform forward), BF16 feature storage with an FP32 master copy, BF16 tensor-core MLP.
+The line also carries the sample-proposal evaluation on this scene (`proposal_eval`) and, at one
+GPU, the FP64 CPU oracle's rate on a bounded sample (`cpu_baseline`).
 
 --impl reference times the FP64 CPU oracle on the same workload (bounded ray sample per step).
 """
@@ -31,8 +36,12 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-stage train rays/s (fwd+bwd) and secs to PSNR target, plain vs chosen"
 RES, FEAT, HID, NRAYS = 160, 12, 128, 8192
 N_BATCHES = 8
-MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                              # 43,520
+N_PROP_SAMPLES = 48
+PROPOSAL_EVERY = 8
+PROPOSAL_TRAIN_RAYS = 2048
+MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                                    # 43,520
 MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 128)   # 80,128
+N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
 
 
 def workload(seed=0):
@@ -101,33 +110,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(dens, feat, mlp, batch, n_rays_sample, with_adam=True):
-    """The FP64 oracle on n rays of one batch (fwd + bwd), plus one oracle Adam sweep over all
-    parameters; projected to a full 8192-ray step."""
-    import oracle
-    o, d, jit, tgt = batch
-    step = 2.0 / RES * 0.5
-    P = oracle.Params(grid_shape=(RES,) * 3, shift_b=float(np.float32(oracle.shift_from_alpha_init(1e-6, 2.0 / RES))),
-                      delta=float(np.float32(step)), bg=(1.0, 1.0, 1.0), mode=1, feat_dim=FEAT, n_freq=4, hidden=HID)
-    n = n_rays_sample
-    dens64, feat64 = dens.astype(np.float64), feat.astype(np.float64)
-    mlp64 = {k: v.astype(np.float64) for k, v in mlp.items()}
-    t0 = time.perf_counter()
-    fwd = oracle.render(P, dens64, feat64, o[:n], d[:n], jitter=jit[:n], mlp=mlp64, target=tgt[:n])
-    gC = 2.0 * (fwd.rgb - tgt[:n]) / n
-    oracle.render(P, dens64, feat64, o[:n], d[:n], jitter=jit[:n], mlp=mlp64, grad_rgb=gC)
-    t_render = time.perf_counter() - t0
-    t_adam = 0.0
-    if with_adam:
-        nparam = dens.size + feat.size + sum(v.size for v in mlp.values())
-        p = np.zeros(nparam); g = np.ones(nparam); m = np.zeros(nparam); v = np.zeros(nparam)
+# ------------------------------------------------------------------------------------------------
+# CPU legs (the FP64 oracle)
+# ------------------------------------------------------------------------------------------------
+
+class OracleStep:
+    """The FP64 oracle on n rays of a batch (fwd + bwd) plus one oracle Adam sweep over all
+    parameters, projected to a full 8192-ray step."""
+
+    def __init__(self, dens, feat, mlp):
+        import oracle
+        self.oracle = oracle
+        step = 2.0 / RES * 0.5
+        self.P = oracle.Params(grid_shape=(RES,) * 3,
+                               shift_b=float(np.float32(oracle.shift_from_alpha_init(1e-6, 2.0 / RES))),
+                               delta=float(np.float32(step)), bg=(1.0, 1.0, 1.0), mode=1, feat_dim=FEAT, n_freq=4,
+                               hidden=HID)
+        self.dens64, self.feat64 = dens.astype(np.float64), feat.astype(np.float64)
+        self.mlp64 = {k: v.astype(np.float64) for k, v in mlp.items()}
+        self.adam_arrays = [np.zeros(N_PARAMS), np.ones(N_PARAMS), np.zeros(N_PARAMS), np.zeros(N_PARAMS)]
+        self.t = 0
+
+    def run(self, batch, n):
+        o, d, jit, tgt = batch
+        t0 = time.perf_counter()
+        fwd = self.oracle.render(self.P, self.dens64, self.feat64, o[:n], d[:n], jitter=jit[:n], mlp=self.mlp64,
+                                 target=tgt[:n])
+        gC = 2.0 * (fwd.rgb - tgt[:n]) / n
+        self.oracle.render(self.P, self.dens64, self.feat64, o[:n], d[:n], jitter=jit[:n], mlp=self.mlp64,
+                           grad_rgb=gC)
+        t_render = time.perf_counter() - t0
+        self.t += 1
+        p, g, m, v = self.adam_arrays
         t1 = time.perf_counter()
-        oracle.adam(p, g, m, v, 0.1, 1)
+        self.oracle.adam(p, g, m, v, 0.1, self.t, zero_grad=False)
         t_adam = time.perf_counter() - t1
-    step_s = t_render * NRAYS / n + t_adam
-    return {"value": NRAYS / step_s, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} of 8192 rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam sweep over "
-                      f"all {dens.size + feat.size + 22019} parameters ({t_adam:.2f} s), projected to a full step"}
+        step_s = t_render * NRAYS / n + t_adam
+        return {"value": NRAYS / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(), "kind": "oracle",
+                "sample": f"{n} of 8192 rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam sweep over "
+                          f"all {N_PARAMS} parameters ({t_adam:.2f} s), projected to a full step"}
 
 
 def run_reference(args, rank, world):
@@ -135,60 +156,90 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     dens, feat, mlp, batches = workload()
-    n = args.ref_rays
+    ostep = OracleStep(dens, feat, mlp)
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(dens, feat, mlp, batches[i % N_BATCHES], n, with_adam=True)
+        r = ostep.run(batches[i % N_BATCHES], args.ref_rays)
         if i >= args.warmup:
             vals.append(r)
     value = statistics.median(v["value"] for v in vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": NRAYS / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args),
+            "config": workload_config(args, "plain"),
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args):
+def workload_config(args, form):
     return {"workload": "DVGO fine stage, 160^3 density + 12-ch feature grid, MLP 39-128-128-3, 8192 rays/batch, "
                         "step 0.5 voxel, 8 balls (raw density 50) + smooth albedo, 100 views 800x800",
-            "form": args.form, "global_batch": NRAYS * args.gpus, "grid": RES, "feat_dim": FEAT, "hidden": HID,
+            "form": form, "global_batch": NRAYS * args.gpus, "grid": RES, "feat_dim": FEAT, "hidden": HID,
             "parallelism": f"replicas x{args.gpus} (independent problems)",
             "l2": "inputs larger than L2: Adam sweeps ~1.7 GB of parameters and moments every step"}
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    import paper_2111_11215_gb300 as dvgo
-    from paper_2111_11215_gb300 import build_lib
+# ------------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------------
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dens, feat, mlp, batches = workload(seed=0)
-    chosen = args.form == "chosen"
-    step = 2.0 / RES * 0.5
-    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES),
-                    bg=(1.0, 1.0, 1.0), mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
+class Form:
+    """One training form on the benchmark scene: its model, its step, and what it processes."""
+
+    def __init__(self, name, dev, dens, feat, mlp, dvgo, torch):
+        import synth
+        self.name, self.dvgo, self.torch = name, dvgo, torch
+        chosen = name == "chosen"
+        step = 2.0 / RES * 0.5
+        self.p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step,
+                             shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES), bg=(1.0, 1.0, 1.0),
+                             mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
+        self.model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), self.p, NRAYS, bf16_feat=chosen)
+        self.proposal = None
+        if chosen:
+            self.proposal = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
+                                          sample_precision=dvgo.DVGO_MLP_BF16)
+            self.t_buf = torch.empty((NRAYS, N_PROP_SAMPLES), device=dev)
+            self.dt_buf = torch.empty((NRAYS, N_PROP_SAMPLES), device=dev)
+        self.i = 0
+
+    def step(self, batch):
+        o, d, jit, tgt = batch
+        if self.proposal is None:
+            loss = self.model.train_step(o, d, jit, tgt)
+        else:
+            if self.i % PROPOSAL_EVERY == 0:
+                self.model.forward(o, d, jit)                                   # uniform forward -> labels
+                self.proposal.train_step(self.model.renderer.workspace, o, d, n_train=PROPOSAL_TRAIN_RAYS,
+                                         with_loss=False)
+            ts, dts = self.proposal.sample(o, d, jit, N_PROP_SAMPLES, t_out=self.t_buf, dt_out=self.dt_buf)
+            loss = self.model.train_step(o, d, jit, tgt, samples=(ts, dts))
+        self.i += 1
+        return loss
+
+
+def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, local_rank, peaks):
+    form = Form(name, dev, dens, feat, mlp, dvgo, torch)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
-    model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p, NRAYS, bf16_feat=chosen)
     dbatches = [tuple(t(x) for x in b) for b in batches]
-    # per-batch sample totals (units of the colour kernels)
-    totals = []
+    # samples per batch of the uniform forward (units of the colour kernels)
     cnt = torch.empty(NRAYS, dtype=torch.int32, device=dev)
     tot = torch.empty(1, dtype=torch.int32, device=dev)
+    totals, hits = [], []
     for b in dbatches:
-        model.forward(b[0], b[1], b[2])
-        dvgo.dvgo_sample_counts(model.renderer.workspace, NRAYS, cnt, tot)
+        form.model.forward(b[0], b[1], b[2])
+        dvgo.dvgo_sample_counts(form.model.renderer.workspace, NRAYS, cnt, tot)
         totals.append(int(tot.item()))
-    mean_samples = float(np.mean(totals))
-    # training-quality sanity: loss is finite
+        hits.append(int((cnt > 0).sum().item()))
+    dense_samples = float(np.mean(totals))
+    hit_rays = float(np.mean(hits))
     for i in range(args.warmup):
-        model.train_step(*dbatches[i % N_BATCHES])
+        form.step(dbatches[i % N_BATCHES])
     torch.cuda.synchronize()
-    assert np.isfinite(model.loss.item())
+    assert np.isfinite(form.model.loss.item())
 
     if world > 1:
         torch.distributed.barrier()
@@ -203,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     for i in range(args.steps):
-        model.train_step(*dbatches[i % N_BATCHES])
+        form.step(dbatches[i % N_BATCHES])
     e1.record(s)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -233,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
         hb = host[i % N_BATCHES]
         for dst, src in zip(bufs, hb):
             dst.copy_(src, non_blocking=True)
-        loss = model.train_step(*bufs)
+        loss = form.step(bufs)
         loss_host[i:i + 1].copy_(loss, non_blocking=True)
     e3.record(s)
     torch.cuda.synchronize()
@@ -242,59 +293,147 @@ def run_ours(args, rank, world, local_rank):
         tt = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-    e2e_value = NRAYS * world * args.steps / (e2e_ms / 1e3)
     assert np.all(np.isfinite(loss_host.numpy()))
 
-    if rank != 0:
-        return
-    import json as _json
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = _json.load(open(pk_path))
-    # dominant kernel and its roofline
-    dom = max(per_kind.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    avg_ms = dom_ms / max(dom_n, 1)
-    roof = roofline(dom_name, avg_ms, mean_samples, chosen, peaks)
-    line = {
-        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if chosen else "f32", "data": "synthetic",
-        "config": workload_config(args) | {"mean_samples_per_batch": mean_samples},
-        "roofline": roof,
-        "kernels_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in per_kind.items() if v[1]},
-        "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
-        "gpu_launches": launches,
-        "clocks": clk,
-    }
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(dens, feat, mlp, batches[0], args.cpu_rays)
-    print(json.dumps(line), flush=True)
+    # units processed per launch of the colour kernels
+    if name == "plain":
+        fwd_units = bwd_units = dense_samples
+    else:
+        expl = hit_rays * N_PROP_SAMPLES
+        n_dense = len(range(0, args.steps, PROPOSAL_EVERY))
+        fwd_units = (args.steps * expl + n_dense * dense_samples) / (args.steps + n_dense)
+        bwd_units = expl
+    dom_name, (dom_ms, dom_n) = max(per_kind.items(), key=lambda kv: kv[1][0])
+    roof = roofline(dom_name, dom_ms / max(dom_n, 1), fwd_units, bwd_units, name == "chosen", peaks)
+    return {"value": value, "ms_per_step": ms / args.steps, "dtype": "bf16" if name == "chosen" else "f32",
+            "config": workload_config(args, name) | {"dense_samples_per_batch": dense_samples,
+                                                     "hit_rays_per_batch": hit_rays,
+                                                     "samples_per_hit_ray": N_PROP_SAMPLES if name == "chosen" else None},
+            "roofline": roof,
+            "kernels_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in per_kind.items() if v[1]},
+            "e2e": {"value": NRAYS * world * args.steps / (e2e_ms / 1e3), "unit": "rays/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+            "gpu_launches": launches, "clocks": clk}
 
 
-def roofline(kind, avg_ms, samples, chosen, peaks):
+def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
     hbm = peaks.get("hbm_gbs")
     if kind in ("fine_colour_bwd", "fine_colour_fwd"):
-        flop = samples * (MLP_FWD_FLOP + (MLP_BWD_FLOP if kind == "fine_colour_bwd" else 0))
+        units = bwd_units if kind == "fine_colour_bwd" else fwd_units
+        flop = units * (MLP_FWD_FLOP + (MLP_BWD_FLOP if kind == "fine_colour_bwd" else 0))
         achieved = flop / (avg_ms * 1e-3) / 1e12
         if chosen:
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
             return {"bound": "tensor", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": "measured bf16 sustained"}
-        # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2.07 GHz
+                    "frac": achieved / peak, "traffic": None, "units_per_launch": units,
+                    "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         return {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2.07 GHz"}
+                "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen), "units_per_launch": units,
+                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz"}
     if kind == "adam":
-        nparam = RES ** 3 * (1 + FEAT) + 22019
-        byts = nparam * (32 + (2 if chosen else 0)) / 3.0   # average over the three launches per step
-        achieved = byts / (avg_ms * 1e-3) / 1e9
+        # three launches per step (density, features, MLP); per-launch average of the step's bytes
+        byts = N_PARAMS * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
+        achieved = byts / 3.0 / (avg_ms * 1e-3) / 1e9
         peak = hbm or 6800.0
         return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": "measured" if hbm else "fallback"}
     return {"bound": "hbm", "kernel": kind, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
             "traffic": None}
+
+
+def traffic_from_profiles(kind, chosen):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if it was taken on the
+    current source (the summary records the source file's hash)."""
+    import hashlib
+    import re
+    src = "fine_tc.cu" if chosen else "fine_simt.cu"
+    prof = {("fine_colour_bwd", False): "fine_colour_bwd_fp32_160cube_8192rays.md",
+            ("fine_colour_bwd", True): "fine_colour_bwd_bf16tc_160cube_8192rays.md"}.get((kind, chosen))
+    if prof is None or not os.path.exists(os.path.join(ROOT, "profiles", prof)):
+        return None
+    text = open(os.path.join(ROOT, "profiles", prof)).read()
+    m = re.search(r"traffic_bytes_per_launch: (\d+) \(\S+ sha256 prefix: (\w+)\)", text)
+    if not m:
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2111_11215_gb300", "csrc", src), "rb").read()).hexdigest()
+    return int(m.group(1)) if sha.startswith(m.group(2)) else None
+
+
+def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
+    """Sample proposal on the benchmark scene (fixed grids and MLP): train the proposal on labels
+    from uniform FP32 renders, then compare 48 proposal samples and 48 uniform samples per ray
+    against the uniform 0.5-voxel FP32 render (which matches the FP64 oracle to 1e-5)."""
+    import synth
+    step = 2.0 / RES * 0.5
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
+    mk = lambda prec: dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, bg=(1.0, 1.0, 1.0), mlp_prec=prec,
+                                  shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES))
+    p32 = mk(dvgo.DVGO_MLP_FP32)
+    m32 = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p32, NRAYS)
+    prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p32, m32.dd, NRAYS,
+                         sample_precision=dvgo.DVGO_MLP_BF16)
+    losses = []
+    for i in range(n_train):
+        o, d, _, _ = (t(x) for x in synth.fine_batch(NRAYS, seed=5000 + i))
+        m32.forward(o, d, None)
+        losses.append(prop.train_step(m32.renderer.workspace, o, d).clone())
+    losses = [float(x.item()) for x in losses[::50]] + [float(losses[-1].item())]
+    o, d, _, _ = (t(x) for x in synth.fine_batch(NRAYS, seed=9999))
+    ref = m32.forward(o, d, None)[0].clone()
+    ts, dts = prop.sample(o, d, None, N_PROP_SAMPLES)
+    rend = m32.explicit_renderer(N_PROP_SAMPLES)
+    c_prop = rend.forward(m32.density, m32.cgrid, m32.mlp, o, d, None, (ts, dts))[0].clone()
+    uni = torch.full((NRAYS, 64), 1.0 / 64, device=dev)
+    tu, dtu = torch.empty_like(ts), torch.empty_like(dts)
+    dvgo.dvgo_sample_pdf(p32, m32.dd, o, d, uni, N_PROP_SAMPLES, None, 1e-3, tu, dtu)
+    c_uni = rend.forward(m32.density, m32.cgrid, m32.mlp, o, d, None, (tu, dtu))[0].clone()
+    # the chosen form's arithmetic: BF16 feature storage and BF16 tensor-core MLP on the proposal samples
+    pbf = mk(dvgo.DVGO_MLP_BF16)
+    mbf = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), pbf, NRAYS, bf16_feat=True)
+    c_chosen = mbf.explicit_renderer(N_PROP_SAMPLES).forward(mbf.density, mbf.cgrid, mbf.mlp, o, d, None,
+                                                             (ts, dts))[0].clone()
+    torch.cuda.synchronize()
+
+    def stats(c):
+        err = (c - ref).abs()
+        mse = float(((c - ref) ** 2).mean().item())
+        return {"psnr_vs_uniform_dense": -10 * np.log10(max(mse, 1e-20)), "max_abs": float(err.max().item()),
+                "mean_abs": float(err.mean().item())}
+    return {"train_steps": n_train, "loss_every_50": losses, "samples_per_ray": N_PROP_SAMPLES,
+            "reference": "uniform 0.5-voxel FP32 render (matches the FP64 oracle to 1e-5, tests/test_gpu_parity.py)",
+            "proposal_fp32_mlp": stats(c_prop), "uniform48_fp32_mlp": stats(c_uni),
+            "proposal_chosen_bf16": stats(c_chosen)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2111_11215_gb300 as dvgo
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dens, feat, mlp, batches = workload(seed=0)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    forms = ["plain", "chosen"] if args.form == "both" else [args.form]
+    res = {name: measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, local_rank, peaks)
+           for name in forms}
+    if rank != 0:
+        return
+    head = res["chosen" if "chosen" in res else forms[0]]
+    line = {"metric": METRIC, "value": head["value"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic", "config": head["config"],
+            "roofline": head["roofline"], "kernels_ms_per_step": head["kernels_ms_per_step"], "e2e": head["e2e"],
+            "gpu_launches": sum(r["gpu_launches"] for r in res.values()), "clocks": head["clocks"],
+            "forms": res}
+    if not args.no_proposal_eval and world == 1:
+        line["proposal_eval"] = proposal_eval(dev, dens, feat, mlp, dvgo, torch)
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = OracleStep(dens, feat, mlp).run(batches[0], args.cpu_rays)
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -303,10 +442,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["plain", "chosen"], default="plain")
-    ap.add_argument("--cpu-rays", type=int, default=512)
+    ap.add_argument("--form", choices=["both", "plain", "chosen"], default="both")
+    ap.add_argument("--cpu-rays", type=int, default=2048)
     ap.add_argument("--ref-rays", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposal-eval", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

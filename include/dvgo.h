@@ -217,6 +217,9 @@ typedef struct {
     int n_bins;          /* bins per ray; this build supports 64                                 */
     int n_freq;          /* PE frequencies on the bin centre x_b; this build supports 6            */
     int width;           /* MLP width; this build supports 64                                     */
+    int precision;       /* forward arithmetic: DVGO_MLP_FP32 (SIMT) or DVGO_MLP_BF16 (tensor cores,
+                            BF16 operands, FP32 accumulation; the encoding is evaluated in FP32);
+                            the backward is always FP32                                           */
 } dvgo_proposal_desc;
 
 /* Proposal MLP, FP32 row-major [in][out]: in = 3 + 6 n_freq (= 39) -> width -> width -> width -> 1,
@@ -263,7 +266,8 @@ enum {
     DVGO_K_RAY_SETUP = 0, DVGO_K_SCAN = 1, DVGO_K_COARSE_FWD = 2, DVGO_K_COARSE_BWD = 3,
     DVGO_K_FINE_DENSITY = 4, DVGO_K_FINE_COLOUR_FWD = 5, DVGO_K_FINE_COMPOSITE = 6,
     DVGO_K_FINE_COMP_BWD = 7, DVGO_K_FINE_COLOUR_BWD = 8, DVGO_K_ADAM = 9, DVGO_K_AUX = 10,
-    DVGO_K_COUNT = 11
+    DVGO_K_WEIGHT_BINS = 11, DVGO_K_PROPOSAL_FWD = 12, DVGO_K_PROPOSAL_BWD = 13, DVGO_K_SAMPLE_PDF = 14,
+    DVGO_K_COUNT = 15
 };
 
 /* Benchmarking aid.  While enabled (on != 0), every kernel launch of this library is bracketed

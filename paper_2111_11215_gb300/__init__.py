@@ -14,4 +14,4 @@ from .binding import (  # noqa: F401
     dvgo_profile_read, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
     dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS,
 )
-from .render import Renderer, RenderFunction, FineModel, AdamState, mlp_flat_size  # noqa: F401
+from .render import Renderer, RenderFunction, FineModel, AdamState, Proposal, mlp_flat_size  # noqa: F401

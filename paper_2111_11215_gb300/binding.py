@@ -25,7 +25,8 @@ EXPORTED_SYMBOLS = (
 DVGO_NOALLOC_MAX_RAYS = 16384
 
 KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
-                "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux")
+                "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux", "weight_bins", "proposal_fwd",
+                "proposal_bwd", "sample_pdf")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -331,16 +332,16 @@ PROP_KEYS = ("w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3")
 
 
 class _PropDesc(C.Structure):
-    _fields_ = [("n_bins", C.c_int), ("n_freq", C.c_int), ("width", C.c_int)]
+    _fields_ = [("n_bins", C.c_int), ("n_freq", C.c_int), ("width", C.c_int), ("precision", C.c_int)]
 
 
 class _PropMlp(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in PROP_KEYS]
 
 
-def _prop(n_bins, n_freq, width, mlp):
+def _prop(n_bins, n_freq, width, mlp, precision=DVGO_MLP_FP32):
     d = _PropDesc()
-    d.n_bins, d.n_freq, d.width = int(n_bins), int(n_freq), int(width)
+    d.n_bins, d.n_freq, d.width, d.precision = int(n_bins), int(n_freq), int(width), int(precision)
     m = _PropMlp()
     for k in PROP_KEYS:
         setattr(m, k, _dev(mlp[k], f"proposal.{k}", torch.float32))
@@ -357,9 +358,9 @@ def dvgo_weight_bins(params: Params, density_desc: GridDesc, n_rays: int, n_bins
 
 
 def dvgo_proposal_fwd(params: Params, density_desc: GridDesc, n_bins: int, n_freq: int, width: int, mlp, rays_o,
-                      rays_d, labels, probs_out, loss_out, stream=None):
+                      rays_d, labels, probs_out, loss_out, stream=None, precision=DVGO_MLP_FP32):
     p, g = params.c(), density_desc.c()
-    d, m = _prop(n_bins, n_freq, width, mlp)
+    d, m = _prop(n_bins, n_freq, width, mlp, precision)
     st = lib().dvgo_proposal_fwd(C.byref(p), C.byref(g), C.byref(d), C.byref(m), int(rays_o.shape[0]),
                                  _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
                                  _dev(labels, "labels", torch.float32, True), _dev(probs_out, "probs_out", torch.float32),

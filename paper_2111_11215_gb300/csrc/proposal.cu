@@ -504,6 +504,10 @@ __global__ void sample_pdf_kernel(int R, BoxD B, const float *ro, const float *r
 
 }  // namespace
 
+int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const dvgo_proposal_mlp &m, int R,
+                           const float *ro, const float *rd, const float *labels, float *probs, float *loss,
+                           cudaStream_t s);
+
 }  // namespace dvgo
 
 using namespace dvgo;
@@ -539,7 +543,7 @@ int dvgo_weight_bins(const dvgo_params *p, const dvgo_grid_desc *dd, int n_rays,
     int blocks = (n_rays + 7) / 8;
     if (blocks > num_sms() * 16) blocks = num_sms() * 16;
     {
-        ProfScope ps_(DVGO_K_AUX, s);
+        ProfScope ps_(DVGO_K_WEIGHT_BINS, s);
         weight_bins_kernel<<<blocks, 256, 0, s>>>(A, n_bins, labels_out);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
@@ -551,12 +555,16 @@ static int proposal_launch(bool bwd, const dvgo_params *p, const dvgo_grid_desc 
     if (!p || !dd || !pd || !m || n_rays < 0) return DVGO_ERR_INVALID_ARG;
     if (!m->w0 || !m->b0 || !m->w1 || !m->b1 || !m->w2 || !m->b2 || !m->w3 || !m->b3) return DVGO_ERR_INVALID_ARG;
     if (pd->n_bins != NB || pd->n_freq != NFQ || pd->width != PW) return DVGO_ERR_UNSUPPORTED;
+    if (pd->precision != DVGO_MLP_FP32 && pd->precision != DVGO_MLP_BF16) return DVGO_ERR_INVALID_ARG;
     if (n_rays > 0 && (!rays_o || !rays_d)) return DVGO_ERR_INVALID_ARG;
     if (bwd && (!labels || !grad)) return DVGO_ERR_INVALID_ARG;
     if (!bwd && n_rays > 0 && !probs_out) return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (loss_out && !bwd) cudaMemsetAsync(loss_out, 0, sizeof(float), s);
     if (n_rays == 0) return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
+    if (!bwd && pd->precision == DVGO_MLP_BF16)
+        return launch_proposal_fwd_tc(*p, *dd, *m, n_rays, rays_o, rays_d, labels, probs_out,
+                                      labels ? loss_out : nullptr, s);
     PropArgs P;
     P.R = n_rays;
     P.box = make_box(*p, *dd);
@@ -572,7 +580,7 @@ static int proposal_launch(bool bwd, const dvgo_params *p, const dvgo_grid_desc 
     int ntiles = (n_rays + 1) / 2;
     int blocks = ntiles < num_sms() ? ntiles : num_sms();
     {
-        ProfScope ps_(DVGO_K_AUX, s);
+        ProfScope ps_(bwd ? DVGO_K_PROPOSAL_BWD : DVGO_K_PROPOSAL_FWD, s);
         kern<<<blocks, PNT, sizeof(PropSmem), s>>>(P);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
@@ -599,7 +607,7 @@ int dvgo_sample_pdf(const dvgo_params *p, const dvgo_grid_desc *dd, int n_rays, 
     if (n_rays == 0) return DVGO_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
-        ProfScope ps_(DVGO_K_AUX, s);
+        ProfScope ps_(DVGO_K_SAMPLE_PDF, s);
         sample_pdf_kernel<<<(n_rays + 127) / 128, 128, 0, s>>>(n_rays, make_box(*p, *dd), rays_o, rays_d, probs, n_bins,
                                                                n_samples, jitter, (double)eta, t_out, dt_out);
     }

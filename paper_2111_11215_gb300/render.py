@@ -146,12 +146,24 @@ class FineModel:
                                      self.rgb, self.tfinal, self.loss if target is not None else None,
                                      self.dloss if target is not None else None, stream)
 
-    def train_step(self, rays_o, rays_d, jitter, target, stream=None):
-        """One optimisation step: render + MSE (Eq. photo_loss), backward, Adam on every parameter."""
-        self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
-                              self.rgb, self.tfinal, self.loss, self.dloss, stream)
-        self.renderer.backward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, self.dloss, None,
-                               self.g_density, self.g_feat, self.g_mlp, stream)
+    def explicit_renderer(self, n_per_ray: int) -> Renderer:
+        """Renderer (and workspace) for explicit samples of n_per_ray per ray."""
+        r = getattr(self, "_expl", None)
+        if r is None or r[0] != n_per_ray:
+            rend = Renderer(self.params, self.dd, self.cd, self.renderer.n_rays, samples_per_ray=n_per_ray,
+                            device=self.density.device)
+            self._expl = (n_per_ray, rend)
+        return self._expl[1]
+
+    def train_step(self, rays_o, rays_d, jitter, target, stream=None, samples=None):
+        """One optimisation step: render + MSE (Eq. photo_loss), backward, Adam on every parameter.
+        `samples` = (t, dt) [R, n] renders with explicit samples (e.g. from a Proposal) instead of
+        uniform steps."""
+        rend = self.renderer if samples is None else self.explicit_renderer(samples[0].shape[1])
+        rend.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, target,
+                     self.rgb, self.tfinal, self.loss, self.dloss, stream)
+        rend.backward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, self.dloss, None,
+                      self.g_density, self.g_feat, self.g_mlp, stream)
         self.step_count += 1
         t = self.step_count
         lr_g = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
@@ -162,3 +174,61 @@ class FineModel:
                          param_bf16_out=self.feat_bf16, stream=stream)
         B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
         return self.loss
+
+
+class Proposal:
+    """Learned sample proposal (the library's addition; the paper samples uniformly): an MLP on
+    the encoded bin centres gives a 64-bin PDF per ray, trained with cross-entropy against the
+    binned compositing weights of a uniform render and sampled by inverse CDF."""
+
+    N_BINS, N_FREQ, WIDTH = 64, 6, 64
+
+    def __init__(self, weights: dict, params: B.Params, density_desc: B.GridDesc, n_rays: int, lr: float = 5e-3,
+                 device="cuda", sample_precision: int = B.DVGO_MLP_FP32):
+        self.params, self.dd = params, density_desc
+        self.sample_precision = sample_precision
+        shapes = {"w0": (3 + 6 * self.N_FREQ, self.WIDTH), "b0": (self.WIDTH,), "w1": (self.WIDTH, self.WIDTH),
+                  "b1": (self.WIDTH,), "w2": (self.WIDTH, self.WIDTH), "b2": (self.WIDTH,), "w3": (self.WIDTH, 1),
+                  "b3": (1,)}
+        n = sum(int(torch.tensor(v).prod()) for v in shapes.values())
+        self.flat = torch.empty(n, dtype=torch.float32, device=device)
+        self.w, off = {}, 0
+        for k, shp in shapes.items():
+            m = int(torch.tensor(shp).prod())
+            self.w[k] = self.flat[off:off + m].view(shp)
+            self.w[k].copy_(torch.as_tensor(weights[k]).reshape(shp))
+            off += m
+        self.grad = torch.zeros_like(self.flat)
+        self.adam = AdamState(self.flat)
+        self.lr, self.step_count = lr, 0
+        self.labels = torch.empty((n_rays, self.N_BINS), device=device)
+        self.probs = torch.empty((n_rays, self.N_BINS), device=device)
+        self.loss = torch.zeros(1, device=device)
+
+    def train_step(self, uniform_workspace, rays_o, rays_d, stream=None, n_train=None, with_loss=True):
+        """Labels from the workspace of a uniform fine forward on these rays, then one Adam step
+        on the cross-entropy loss of the first n_train rays (all by default); returns the loss
+        (device tensor, before the step) when with_loss."""
+        R = rays_o.shape[0]
+        n = R if n_train is None else min(int(n_train), R)
+        B.dvgo_weight_bins(self.params, self.dd, R, self.N_BINS, uniform_workspace, self.labels[:R], stream)
+        if with_loss:
+            B.dvgo_proposal_fwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o[:n],
+                                rays_d[:n], self.labels[:n], self.probs[:n], self.loss, stream)
+        B.dvgo_proposal_bwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o[:n],
+                            rays_d[:n], self.labels[:n], self.grad, stream)
+        self.step_count += 1
+        B.dvgo_adam_step(self.flat, self.grad, self.adam.m, self.adam.v, self.lr, self.step_count, stream=stream)
+        return self.loss
+
+    def sample(self, rays_o, rays_d, jitter=None, n_samples: int = 48, eta: float = 1e-3, t_out=None, dt_out=None,
+               stream=None):
+        """Explicit samples (t, dt) [R, n_samples] drawn from the predicted PDFs."""
+        R = rays_o.shape[0]
+        t_out = torch.empty((R, n_samples), device=rays_o.device) if t_out is None else t_out
+        dt_out = torch.empty((R, n_samples), device=rays_o.device) if dt_out is None else dt_out
+        B.dvgo_proposal_fwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o, rays_d,
+                            None, self.probs[:R], None, stream, precision=self.sample_precision)
+        B.dvgo_sample_pdf(self.params, self.dd, rays_o, rays_d, self.probs[:R], n_samples, jitter, eta, t_out, dt_out,
+                          stream)
+        return t_out, dt_out
