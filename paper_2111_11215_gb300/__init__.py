@@ -14,4 +14,6 @@ from .binding import (  # noqa: F401
     dvgo_profile_read, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
     dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS,
 )
-from .render import Renderer, RenderFunction, FineModel, AdamState, Proposal, mlp_flat_size  # noqa: F401
+from .render import (  # noqa: F401
+    AdamState, CoarseModel, FineModel, Proposal, Renderer, RenderFunction, mlp_flat_size, mlp_views,
+)

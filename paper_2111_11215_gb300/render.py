@@ -176,6 +176,47 @@ class FineModel:
         return self.loss
 
 
+class CoarseModel:
+    """Coarse-stage parameters (Sec. 4.1): density grid and view-invariant colour grid, their
+    gradients and Adam state, and one training step (forward, backward, Adam) on a ray batch."""
+
+    def __init__(self, density: torch.Tensor, rgb: torch.Tensor, params: B.Params, n_rays: int,
+                 box=((-1.0,) * 3, (1.0,) * 3), lr_grid: float = 0.1, decay_steps: float = 20000.0):
+        self.params = params
+        res = tuple(density.shape)
+        self.density, self.rgb_grid = density.contiguous(), rgb.contiguous()
+        self.dd = B.GridDesc(res, 1, box[0], box[1])
+        self.cd = B.GridDesc(res, 3, box[0], box[1])
+        self.renderer = Renderer(params, self.dd, self.cd, n_rays, device=density.device)
+        self.g_density = torch.zeros_like(self.density)
+        self.g_rgb = torch.zeros_like(self.rgb_grid)
+        self.adam = {"density": AdamState(self.density), "rgb": AdamState(self.rgb_grid)}
+        self.lr_grid, self.decay_steps = lr_grid, decay_steps
+        dev = density.device
+        self.rgb = torch.empty((n_rays, 3), device=dev)
+        self.tfinal = torch.empty(n_rays, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.dloss = torch.empty((n_rays, 3), device=dev)
+        self.step_count = 0
+
+    def forward(self, rays_o, rays_d, jitter=None, stream=None):
+        return self.renderer.forward(self.density, self.rgb_grid, None, rays_o, rays_d, jitter, None, None,
+                                     self.rgb, self.tfinal, None, None, stream)
+
+    def train_step(self, rays_o, rays_d, jitter, target, stream=None):
+        self.renderer.forward(self.density, self.rgb_grid, None, rays_o, rays_d, jitter, None, target, self.rgb,
+                              self.tfinal, self.loss, self.dloss, stream)
+        self.renderer.backward(self.density, self.rgb_grid, None, rays_o, rays_d, jitter, None, self.dloss, None,
+                               self.g_density, self.g_rgb, None, stream)
+        self.step_count += 1
+        t = self.step_count
+        lr = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
+        B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr, t,
+                         stream=stream)
+        B.dvgo_adam_step(self.rgb_grid, self.g_rgb, self.adam["rgb"].m, self.adam["rgb"].v, lr, t, stream=stream)
+        return self.loss
+
+
 class Proposal:
     """Learned sample proposal (the library's addition; the paper samples uniformly): an MLP on
     the encoded bin centres gives a 64-bin PDF per ray, trained with cross-entropy against the

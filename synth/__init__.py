@@ -207,3 +207,113 @@ def fine_batch(n_rays: int, seed: int, rig_seed: int = 1234, n_views: int = 100)
     rig = hemisphere_rig(n_views, rig_seed)
     o, d, _ = random_pixel_rays(rig, n_rays, seed)
     return o, d, jitter(n_rays, seed + 7), targets(n_rays, seed + 11)
+
+
+# ----------------------------------------------------------------------------------------------
+# Analytic ground-truth scene (stand-in for a Synthetic-NeRF object): ray-cast primitives
+# ----------------------------------------------------------------------------------------------
+
+@dataclass
+class AnalyticScene:
+    kind: np.ndarray       # [P] 0 = sphere, 1 = axis-aligned box
+    centre: np.ndarray     # [P, 3]
+    size: np.ndarray       # [P, 3] sphere: radius in [0]; box: half extents
+    albedo: np.ndarray     # [P, 3]
+    spec: np.ndarray       # [P] specular weight
+    shininess: np.ndarray  # [P]
+    light: np.ndarray      # [3] unit direction towards the light
+
+
+def analytic_scene(seed: int = 0, n_prims: int = 20) -> AnalyticScene:
+    """n_prims seeded spheres / boxes of size 0.1-0.4 inside [-0.8, 0.8]^3 with Lambert albedo and a
+    Blinn-Phong specular lobe."""
+    g = rng(seed)
+    kind = g.integers(0, 2, size=n_prims)
+    size = np.zeros((n_prims, 3))
+    size[:, 0] = g.uniform(0.1, 0.4, size=n_prims)
+    box = kind == 1
+    size[box] = g.uniform(0.08, 0.3, size=(int(box.sum()), 3))
+    ext = np.where(kind == 0, size[:, 0], size.max(axis=1))
+    centre = g.uniform(-0.8 + ext[:, None] * 0.5, 0.8 - ext[:, None] * 0.5, size=(n_prims, 3))
+    light = np.array([0.4, 0.3, 0.87])
+    return AnalyticScene(kind=kind, centre=centre, size=size, albedo=g.uniform(0.1, 0.95, size=(n_prims, 3)),
+                         spec=g.uniform(0.0, 0.6, size=n_prims), shininess=g.uniform(8.0, 64.0, size=n_prims),
+                         light=light / np.linalg.norm(light))
+
+
+def render_analytic(scene: AnalyticScene, rays_o, rays_d, bg=(1.0, 1.0, 1.0)):
+    """Ray-cast the primitives (torch, on the tensors' device): nearest hit, Lambert + ambient
+    + Blinn-Phong highlight, background colour where nothing is hit.  Returns [N, 3] in [0, 1]."""
+    import torch
+    dev = rays_o.device
+    o = rays_o.to(torch.float32)
+    d = rays_d.to(torch.float32)
+    d = d / d.norm(dim=-1, keepdim=True)
+    N = o.shape[0]
+    t_best = torch.full((N,), float("inf"), device=dev)
+    nrm = torch.zeros((N, 3), device=dev)
+    pid = torch.full((N,), -1, dtype=torch.long, device=dev)
+    for i in range(len(scene.kind)):
+        c = torch.tensor(scene.centre[i], dtype=torch.float32, device=dev)
+        if scene.kind[i] == 0:
+            r = float(scene.size[i, 0])
+            oc = o - c
+            b = (oc * d).sum(-1)
+            disc = b * b - ((oc * oc).sum(-1) - r * r)
+            hit = disc > 0
+            sq = torch.sqrt(torch.clamp(disc, min=0.0))
+            t = -b - sq
+            t = torch.where(t > 1e-4, t, -b + sq)
+            hit &= t > 1e-4
+            n = (o + t[:, None] * d - c) / r
+        else:
+            h = torch.tensor(scene.size[i], dtype=torch.float32, device=dev)
+            inv = 1.0 / torch.where(d.abs() < 1e-12, torch.full_like(d, 1e-12), d)
+            t1 = (c - h - o) * inv
+            t2 = (c + h - o) * inv
+            tmin = torch.minimum(t1, t2).amax(-1)
+            tmax = torch.maximum(t1, t2).amin(-1)
+            hit = (tmax > torch.clamp(tmin, min=1e-4))
+            t = torch.where(tmin > 1e-4, tmin, tmax)
+            p = o + t[:, None] * d - c
+            q = (p / h).abs()
+            ax = q.argmax(-1)
+            n = torch.zeros_like(p)
+            n.scatter_(1, ax[:, None], torch.sign(p.gather(1, ax[:, None])))
+        better = hit & (t < t_best)
+        t_best = torch.where(better, t, t_best)
+        nrm = torch.where(better[:, None], n, nrm)
+        pid = torch.where(better, torch.full_like(pid, i), pid)
+    out = torch.tensor(bg, dtype=torch.float32, device=dev).expand(N, 3).clone()
+    hitm = pid >= 0
+    if bool(hitm.any()):
+        idx = pid[hitm]
+        alb = torch.tensor(scene.albedo, dtype=torch.float32, device=dev)[idx]
+        spw = torch.tensor(scene.spec, dtype=torch.float32, device=dev)[idx]
+        shn = torch.tensor(scene.shininess, dtype=torch.float32, device=dev)[idx]
+        L = torch.tensor(scene.light, dtype=torch.float32, device=dev)
+        n = nrm[hitm]
+        n = n / n.norm(dim=-1, keepdim=True).clamp(min=1e-12)
+        v = -d[hitm]
+        hv = L + v
+        hv = hv / hv.norm(dim=-1, keepdim=True).clamp(min=1e-12)
+        diff = torch.clamp((n * L).sum(-1), min=0.0)
+        spec = torch.clamp((n * hv).sum(-1), min=0.0) ** shn
+        col = alb * (0.25 + 0.75 * diff[:, None]) + (spw * spec)[:, None]
+        out[hitm] = torch.clamp(col, 0.0, 1.0)
+    return out
+
+
+def rig_rays_torch(rig: CameraRig, device):
+    """All pixel rays of every view of a rig as flat [V*H*W, 3] tensors (origins, directions)."""
+    import torch
+    H, W = rig.height, rig.width
+    cols = torch.arange(W, device=device, dtype=torch.float32)
+    rows = torch.arange(H, device=device, dtype=torch.float32)
+    yy, xx = torch.meshgrid(rows, cols, indexing="ij")
+    dc = torch.stack([(xx + 0.5 - W * 0.5) / rig.focal, -(yy + 0.5 - H * 0.5) / rig.focal,
+                      -torch.ones_like(xx)], dim=-1).reshape(-1, 3)
+    c2w = torch.tensor(rig.c2w, dtype=torch.float32, device=device)
+    d = torch.einsum("vij,nj->vni", c2w[:, :, :3], dc).reshape(-1, 3)
+    o = c2w[:, :, 3][:, None, :].expand(-1, H * W, 3).reshape(-1, 3)
+    return o.contiguous(), d.contiguous()

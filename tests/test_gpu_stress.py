@@ -1,0 +1,69 @@
+"""Parity at the large-grid stress size: 256^3 density with one dense ball (raw density 200,
+radius 0.3), 12-channel features, rays from the radius-4 sphere aimed into the ball (~500 samples
+per ray, the longest rays of any workload).  Colours on sampled rays and gradients on a small batch
+against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import FLOOR_FINE_GRAD, NORM_RTOL_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from test_gpu_parity import _mlp_flat, _run_fine
+
+pytestmark = pytest.mark.gpu
+
+dvgo = pytest.importorskip("paper_2111_11215_gb300")
+
+RES = 256
+
+
+@pytest.fixture(scope="module")
+def scene():
+    dens = synth.sphere_density(RES, [(0.0, 0.0, 0.0)], [0.3], 200.0)
+    feat = synth.smooth_features(RES, 12, seed=21)
+    mlp = synth.mlp_weights(39, 128, 3, seed=22)
+    mlp["b3"] = np.array([0.2, -0.1, 0.05], np.float32)
+    return dens, feat, mlp
+
+
+def _params(prec):
+    return dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / RES, bg=(1.0, 1.0, 1.0), mlp_prec=prec,
+                       shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES))
+
+
+def test_stress_colours_fp32_and_bf16(scene):
+    dens, feat, mlp = scene
+    R = 4096
+    o, d = synth.blob_rays(R, seed=300)
+    jit = synth.jitter(R, 400)
+    p = _params(dvgo.DVGO_MLP_FP32)
+    got = _run_fine(p, RES, dens, feat, mlp, o, d, jit, None, None, bwd=False)
+    assert got["counts"].max() >= 480 and got["total"] > 4096 * 400
+    idx = np.random.default_rng(5).choice(R, 24, replace=False)
+    ref = oracle.render(oracle_params(p, (RES,) * 3, 12), dens, feat, o[idx], d[idx], jitter=jit[idx], mlp=mlp)
+    np.testing.assert_array_equal(got["counts"][idx], ref.n_samples)
+    assert_close(got["rgb"][idx], ref.rgb, RTOL_COLOUR, "rgb_fp32")
+    featb = torch.as_tensor(feat).to(torch.bfloat16)
+    pb = _params(dvgo.DVGO_MLP_BF16)
+    gotb = _run_fine(pb, RES, dens, featb.float().numpy(), mlp, o, d, jit, None, None, torch.bfloat16, bwd=False)
+    refb = oracle.render(oracle_params(pb, (RES,) * 3, 12), dens, featb.float().numpy(), o[idx], d[idx],
+                         jitter=jit[idx], mlp=mlp)
+    assert np.abs(gotb["rgb"][idx] - refb.rgb).max() < 1e-2
+
+
+def test_stress_gradients_fp32(scene):
+    dens, feat, mlp = scene
+    R = 48
+    o, d = synth.blob_rays(R, seed=301)
+    jit = synth.jitter(R, 401)
+    p = _params(dvgo.DVGO_MLP_FP32)
+    gC = np.random.default_rng(6).normal(scale=1e-2, size=(R, 3))
+    got = _run_fine(p, RES, dens, feat, mlp, o, d, jit, gC, np.zeros(R))
+    ref = oracle.render(oracle_params(p, (RES,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC)
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    ref_m = np.concatenate([ref.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    for name, g, r in (("grad_density", got["g_d"], ref.grads["density"]), ("grad_feat", got["g_f"], ref.grads["cgrid"]),
+                       ("grad_mlp", got["g_m"], ref_m)):
+        _, rel2 = assert_close(g, r, RTOL_GRAD, name, floor=FLOOR_FINE_GRAD)
+        assert rel2 <= NORM_RTOL_GRAD, (name, rel2)
