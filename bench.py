@@ -10,8 +10,9 @@ rays drawn from 100 inward-facing 800x800 views (radius 4, focal 1111).  One ste
 Forms (both are timed by default; `value` is the chosen form):
   plain  = uniform 0.5-voxel steps, FP32 feature grid, FP32 SIMT MLP;
   chosen = learned proposal (64-bin PDF from a BF16 tensor-core proposal MLP, 48 inverse-CDF
-           samples per ray; one proposal Adam step every 8 steps on 2048 rays with labels from a
-           uniform forward), BF16 feature storage with an FP32 master copy, BF16 tensor-core MLP.
+           samples per ray from the PDF mixed 0.05 with the uniform one; every 4th step is a full
+           uniform step whose forward also labels 2048 rays for one proposal Adam step), BF16
+           feature storage with an FP32 master copy, BF16 tensor-core MLP.
 The line also carries the sample-proposal evaluation on this scene (`proposal_eval`) and, at one
 GPU, the FP64 CPU oracle's rate on a bounded sample (`cpu_baseline`).
 
@@ -37,8 +38,9 @@ METRIC = "fine-stage train rays/s (fwd+bwd) and secs to PSNR target, plain vs ch
 RES, FEAT, HID, NRAYS = 160, 12, 128, 8192
 N_BATCHES = 8
 N_PROP_SAMPLES = 48
-PROPOSAL_EVERY = 8
+PROPOSAL_EVERY = 4
 PROPOSAL_TRAIN_RAYS = 2048
+PROPOSAL_ETA = 0.05
 MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                                    # 43,520
 MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 128)   # 80,128
 N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
@@ -198,27 +200,18 @@ class Form:
                              mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
         self.model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), self.p, NRAYS, bf16_feat=chosen)
-        self.proposal = None
+        self.trainer = None
         if chosen:
-            self.proposal = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
-                                          sample_precision=dvgo.DVGO_MLP_BF16)
-            self.t_buf = torch.empty((NRAYS, N_PROP_SAMPLES), device=dev)
-            self.dt_buf = torch.empty((NRAYS, N_PROP_SAMPLES), device=dev)
-        self.i = 0
+            prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
+                                 sample_precision=dvgo.DVGO_MLP_BF16)
+            self.trainer = dvgo.ProposalTrainer(self.model, prop, N_PROP_SAMPLES, PROPOSAL_EVERY, 0,
+                                                PROPOSAL_TRAIN_RAYS, PROPOSAL_ETA)
 
     def step(self, batch):
         o, d, jit, tgt = batch
-        if self.proposal is None:
-            loss = self.model.train_step(o, d, jit, tgt)
-        else:
-            if self.i % PROPOSAL_EVERY == 0:
-                self.model.forward(o, d, jit)                                   # uniform forward -> labels
-                self.proposal.train_step(self.model.renderer.workspace, o, d, n_train=PROPOSAL_TRAIN_RAYS,
-                                         with_loss=False)
-            ts, dts = self.proposal.sample(o, d, jit, N_PROP_SAMPLES, t_out=self.t_buf, dt_out=self.dt_buf)
-            loss = self.model.train_step(o, d, jit, tgt, samples=(ts, dts))
-        self.i += 1
-        return loss
+        if self.trainer is None:
+            return self.model.train_step(o, d, jit, tgt)
+        return self.trainer.step(o, d, jit, tgt)
 
 
 def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, local_rank, peaks):
@@ -252,6 +245,7 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     clocks.start()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_first = form.trainer.i if form.trainer is not None else 0
     e0.record(s)
     for i in range(args.steps):
         form.step(dbatches[i % N_BATCHES])
@@ -295,14 +289,13 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
         e2e_ms = float(tt.item())
     assert np.all(np.isfinite(loss_host.numpy()))
 
-    # units processed per launch of the colour kernels
+    # units processed per launch of the colour kernels (uniform and proposal steps of the timed region)
     if name == "plain":
         fwd_units = bwd_units = dense_samples
     else:
         expl = hit_rays * N_PROP_SAMPLES
-        n_dense = len(range(0, args.steps, PROPOSAL_EVERY))
-        fwd_units = (args.steps * expl + n_dense * dense_samples) / (args.steps + n_dense)
-        bwd_units = expl
+        n_dense = sum(form.trainer.is_uniform(i) for i in range(t_first, t_first + args.steps))
+        fwd_units = bwd_units = ((args.steps - n_dense) * expl + n_dense * dense_samples) / args.steps
     dom_name, (dom_ms, dom_n) = max(per_kind.items(), key=lambda kv: kv[1][0])
     roof = roofline(dom_name, dom_ms / max(dom_n, 1), fwd_units, bwd_units, name == "chosen", peaks)
     return {"value": value, "ms_per_step": ms / args.steps, "dtype": "bf16" if name == "chosen" else "f32",
@@ -488,29 +481,31 @@ def run_time_to_psnr(args):
         mse = float(se.item()) / (3 * (n_rays // NRAYS) * NRAYS)
         return -10 * np.log10(max(mse, 1e-20))
 
+    # form name -> (BF16 MLP + BF16 feature storage, learned proposal)
+    form_defs = {"plain": (False, False), "chosen": (True, True), "bf16-uniform": (True, False),
+                 "fp32-proposal": (False, True)}
+    forms = [f for f in args.ttp_forms.split(",") if f]
+    n_ps, every, eta = args.prop_samples, args.prop_every, args.prop_eta
     results = {}
-    for form in ("plain", "chosen"):
-        chosen = form == "chosen"
+    for form in forms:
+        bf16, use_prop = form_defs[form]
         p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / rf, shift_b=b_f, bg=(1.0, 1.0, 1.0),
-                        mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
-        model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=chosen)
-        prop = None
-        if chosen:
+                        mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32)
+        model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16)
+        prop = trainer = None
+        if use_prop:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p, model.dd, NRAYS,
                                  sample_precision=dvgo.DVGO_MLP_BF16)
-            tb, dtb = torch.empty((NRAYS, N_PROP_SAMPLES), device=dev), torch.empty((NRAYS, N_PROP_SAMPLES), device=dev)
+            trainer = dvgo.ProposalTrainer(model, prop, n_ps, every, args.prop_warmup, PROPOSAL_TRAIN_RAYS, eta)
+            tb, dtb = torch.empty((NRAYS, n_ps), device=dev), torch.empty((NRAYS, n_ps), device=dev)
         st = [0]
 
         def fine_step():
             o, d, jit, tgt = batch(st[0], 2)
-            if prop is None:
+            if trainer is None:
                 model.train_step(o, d, jit, tgt)
             else:
-                if st[0] % PROPOSAL_EVERY == 0:
-                    model.forward(o, d, jit)
-                    prop.train_step(model.renderer.workspace, o, d, n_train=PROPOSAL_TRAIN_RAYS, with_loss=False)
-                ts, dts = prop.sample(o, d, jit, N_PROP_SAMPLES, t_out=tb, dt_out=dtb)
-                model.train_step(o, d, jit, tgt, samples=(ts, dts))
+                trainer.step(o, d, jit, tgt)
             st[0] += 1
         curve, t_train = [], 0.0
         while st[0] < args.fine_steps:
@@ -520,29 +515,36 @@ def run_time_to_psnr(args):
         results[form] = {"curve": curve, "fine_train_s": t_train, "final_psnr_2views": curve[-1]["psnr"],
                          "final_psnr_20views": psnr(model, o_te.shape[0]),
                          "ms_per_step": 1e3 * t_train / args.fine_steps}
-        if chosen:
-            # the chosen form's own inference: proposal samples + BF16 MLP
+        if prop is not None:
+            # the form's own inference: proposal samples + its MLP precision
             se, nb = 0.0, 0
             for s in range(0, n_eval, NRAYS):
                 o, d, c = o_te[s:s + NRAYS].contiguous(), d_te[s:s + NRAYS].contiguous(), c_te[s:s + NRAYS]
-                ts, dts = prop.sample(o, d, None, N_PROP_SAMPLES, t_out=tb, dt_out=dtb)
-                rgb = model.explicit_renderer(N_PROP_SAMPLES).forward(model.density, model.cgrid, model.mlp, o, d,
-                                                                       None, (ts, dts))[0]
+                ts, dts = prop.sample(o, d, None, n_ps, eta=eta, t_out=tb, dt_out=dtb)
+                rgb = model.explicit_renderer(n_ps).forward(model.density, model.cgrid, model.mlp, o, d,
+                                                            None, (ts, dts))[0]
                 se += float(((rgb - c) ** 2).sum().item())
                 nb += 1
             results[form]["own_inference_psnr_2views"] = -10 * np.log10(se / (3 * nb * NRAYS))
+    if args.psnr_target is None and "plain" not in results:
+        raise SystemExit("time-to-psnr: give --psnr-target when the plain form is not run")
     target = args.psnr_target if args.psnr_target is not None else results["plain"]["final_psnr_2views"] - 0.5
     for form, r in results.items():
         hit = [c for c in r["curve"] if c["psnr"] >= target]
         r["secs_to_target"] = hit[0]["train_s"] if hit else None
         r["steps_to_target"] = hit[0]["step"] if hit else None
     line = {"metric": METRIC, "workload": "time-to-psnr", "unit": "s", "higher_is_better": False,
-            "value": results["chosen"]["secs_to_target"], "psnr_target": target,
+            "value": results["chosen"]["secs_to_target"] if "chosen" in results else None, "psnr_target": target,
             "psnr_target_rule": "given" if args.psnr_target is not None else "plain final PSNR (2 held-out views) - 0.5 dB",
             "coarse_steps": args.coarse_steps, "coarse_s": t_coarse, "fine_steps": args.fine_steps,
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
-            "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)", "forms": results,
-            "chosen_minus_plain_final_psnr_db": results["chosen"]["final_psnr_20views"] - results["plain"]["final_psnr_20views"]}
+            "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
+            "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
+                         "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
+            "forms": results}
+    if "chosen" in results and "plain" in results:
+        line["chosen_minus_plain_final_psnr_db"] = (results["chosen"]["final_psnr_20views"]
+                                                    - results["plain"]["final_psnr_20views"])
     print(json.dumps(line), flush=True)
 
 
@@ -651,6 +653,12 @@ def main():
     ap.add_argument("--coarse-steps", type=int, default=5000)
     ap.add_argument("--fine-steps", type=int, default=20000)
     ap.add_argument("--eval-every", type=int, default=1000)
+    ap.add_argument("--ttp-forms", default="plain,chosen",
+                    help="time-to-psnr forms, comma separated: plain, chosen, bf16-uniform, fp32-proposal")
+    ap.add_argument("--prop-samples", type=int, default=N_PROP_SAMPLES)
+    ap.add_argument("--prop-every", type=int, default=PROPOSAL_EVERY)
+    ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
+    ap.add_argument("--prop-warmup", type=int, default=0)
     # frozen from the first full plain run: its final held-out PSNR (2 views) 29.391 dB - 0.5 dB
     ap.add_argument("--psnr-target", type=float, default=28.891)
     args = ap.parse_args()

@@ -155,13 +155,16 @@ class FineModel:
             self._expl = (n_per_ray, rend)
         return self._expl[1]
 
-    def train_step(self, rays_o, rays_d, jitter, target, stream=None, samples=None):
+    def train_step(self, rays_o, rays_d, jitter, target, stream=None, samples=None, after_forward=None):
         """One optimisation step: render + MSE (Eq. photo_loss), backward, Adam on every parameter.
         `samples` = (t, dt) [R, n] renders with explicit samples (e.g. from a Proposal) instead of
-        uniform steps."""
+        uniform steps.  `after_forward(renderer)` (optional) is called between the forward and the
+        backward, while the renderer's workspace holds this batch's forward samples."""
         rend = self.renderer if samples is None else self.explicit_renderer(samples[0].shape[1])
         rend.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, target,
                      self.rgb, self.tfinal, self.loss, self.dloss, stream)
+        if after_forward is not None:
+            after_forward(rend)
         rend.backward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, self.dloss, None,
                       self.g_density, self.g_feat, self.g_mlp, stream)
         self.step_count += 1
@@ -225,7 +228,7 @@ class Proposal:
     N_BINS, N_FREQ, WIDTH = 64, 6, 64
 
     def __init__(self, weights: dict, params: B.Params, density_desc: B.GridDesc, n_rays: int, lr: float = 5e-3,
-                 device="cuda", sample_precision: int = B.DVGO_MLP_FP32):
+                 device="cuda", sample_precision: int = B.DVGO_MLP_FP32, decay_steps: float = 5000.0):
         self.params, self.dd = params, density_desc
         self.sample_precision = sample_precision
         shapes = {"w0": (3 + 6 * self.N_FREQ, self.WIDTH), "b0": (self.WIDTH,), "w1": (self.WIDTH, self.WIDTH),
@@ -241,15 +244,16 @@ class Proposal:
             off += m
         self.grad = torch.zeros_like(self.flat)
         self.adam = AdamState(self.flat)
-        self.lr, self.step_count = lr, 0
+        self.lr, self.decay_steps, self.step_count = lr, decay_steps, 0
         self.labels = torch.empty((n_rays, self.N_BINS), device=device)
         self.probs = torch.empty((n_rays, self.N_BINS), device=device)
         self.loss = torch.zeros(1, device=device)
 
     def train_step(self, uniform_workspace, rays_o, rays_d, stream=None, n_train=None, with_loss=True):
         """Labels from the workspace of a uniform fine forward on these rays, then one Adam step
-        on the cross-entropy loss of the first n_train rays (all by default); returns the loss
-        (device tensor, before the step) when with_loss."""
+        on the cross-entropy loss of the first n_train rays (all by default), at the rate lr decayed
+        by 0.1 over decay_steps proposal steps; returns the loss (device tensor, before the step)
+        when with_loss."""
         R = rays_o.shape[0]
         n = R if n_train is None else min(int(n_train), R)
         B.dvgo_weight_bins(self.params, self.dd, R, self.N_BINS, uniform_workspace, self.labels[:R], stream)
@@ -259,12 +263,14 @@ class Proposal:
         B.dvgo_proposal_bwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o[:n],
                             rays_d[:n], self.labels[:n], self.grad, stream)
         self.step_count += 1
-        B.dvgo_adam_step(self.flat, self.grad, self.adam.m, self.adam.v, self.lr, self.step_count, stream=stream)
+        lr = B.dvgo_lr_at(self.lr, self.step_count - 1, self.decay_steps)
+        B.dvgo_adam_step(self.flat, self.grad, self.adam.m, self.adam.v, lr, self.step_count, stream=stream)
         return self.loss
 
-    def sample(self, rays_o, rays_d, jitter=None, n_samples: int = 48, eta: float = 1e-3, t_out=None, dt_out=None,
+    def sample(self, rays_o, rays_d, jitter=None, n_samples: int = 48, eta: float = 0.05, t_out=None, dt_out=None,
                stream=None):
-        """Explicit samples (t, dt) [R, n_samples] drawn from the predicted PDFs."""
+        """Explicit samples (t, dt) [R, n_samples] drawn from the predicted PDFs mixed with the
+        uniform PDF at weight eta (0.05 keeps ~2 of 48 samples spread along the whole ray)."""
         R = rays_o.shape[0]
         t_out = torch.empty((R, n_samples), device=rays_o.device) if t_out is None else t_out
         dt_out = torch.empty((R, n_samples), device=rays_o.device) if dt_out is None else dt_out
@@ -273,3 +279,45 @@ class Proposal:
         B.dvgo_sample_pdf(self.params, self.dd, rays_o, rays_d, self.probs[:R], n_samples, jitter, eta, t_out, dt_out,
                           stream)
         return t_out, dt_out
+
+
+class ProposalTrainer:
+    """Fine-stage training with the learned proposal (the library's chosen form).  Most steps
+    render and back-propagate only the proposal's n_samples importance samples per ray.  The
+    first `warmup` steps and then every `uniform_every`-th step are full uniform steps (Sec. 4.2
+    sampling): their forward also labels the proposal's training rays, and their backward gives
+    every voxel along the batch's rays a gradient, including small structures the proposal's
+    smooth field cannot resolve, so they are not left untouched."""
+
+    def __init__(self, model: FineModel, proposal: "Proposal", n_samples: int = 48, uniform_every: int = 4,
+                 warmup: int = 0, train_rays: int = 2048, eta: float = 0.05):
+        if uniform_every < 1 or n_samples < 1:
+            raise ValueError("uniform_every and n_samples must be >= 1")
+        self.model, self.proposal = model, proposal
+        self.n_samples, self.uniform_every, self.warmup = int(n_samples), int(uniform_every), int(warmup)
+        self.train_rays, self.eta = int(train_rays), float(eta)
+        R, dev = model.renderer.n_rays, model.density.device
+        self.t_buf = torch.empty((R, self.n_samples), device=dev)
+        self.dt_buf = torch.empty((R, self.n_samples), device=dev)
+        self.i = 0
+        self.n_uniform = self.n_proposal = 0
+
+    def is_uniform(self, i: int) -> bool:
+        return i < self.warmup or i % self.uniform_every == 0
+
+    def step(self, rays_o, rays_d, jitter, target, stream=None):
+        """One step; returns the model's loss (device tensor)."""
+        if self.is_uniform(self.i):
+            def label(rend):
+                self.proposal.train_step(rend.workspace, rays_o, rays_d, stream=stream, n_train=self.train_rays,
+                                         with_loss=False)
+            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, after_forward=label)
+            self.n_uniform += 1
+        else:
+            R = rays_o.shape[0]
+            ts, dts = self.proposal.sample(rays_o, rays_d, jitter, self.n_samples, eta=self.eta,
+                                           t_out=self.t_buf[:R], dt_out=self.dt_buf[:R], stream=stream)
+            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, samples=(ts, dts))
+            self.n_proposal += 1
+        self.i += 1
+        return loss

@@ -118,7 +118,9 @@ def test_sample_pdf_matches_oracle_and_renders():
 
 def test_trained_proposal_beats_uniform_48_samples():
     """Gain test: after training on labels from uniform renders, 48 proposal samples per ray give a
-    smaller colour error against the oracle's uniform 0.5-voxel render than 48 uniform samples."""
+    clearly smaller colour error against the oracle's uniform 0.5-voxel render than 48 uniform
+    samples.  The proposal backward accumulates its weight gradients with atomics, so the trained
+    weights (and the error ratio) vary a little from run to run; the bound leaves room for that."""
     res, R = 128, 2048
     c, rad = synth.random_spheres(6, 90, rmin=0.15, rmax=0.35)
     dens = synth.sphere_density(res, c, rad, 50.0)
@@ -130,7 +132,7 @@ def test_trained_proposal_beats_uniform_48_samples():
     model = dvgo.FineModel(cuda(dens), cuda(feat), cuda(_mlp_flat(mlp)), p, R)
     prop = dvgo.Proposal(_proposal_weights(93), p, model.dd, R)
     losses = []
-    for i in range(200):
+    for i in range(300):
         o, d, _, _ = (cuda(x) for x in synth.fine_batch(R, seed=400 + i))
         model.forward(o, d, None)
         losses.append(prop.train_step(model.renderer.workspace, o, d).clone())

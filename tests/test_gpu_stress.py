@@ -53,7 +53,13 @@ def test_stress_colours_fp32_and_bf16(scene):
 
 
 def test_stress_gradients_fp32(scene):
-    dens, feat, mlp = scene
+    """Gradients at 256^3 with per-voxel random features.  (With the smooth albedo field the colour
+    barely changes along a ray through the blob, dC/dtau_k = sum_{j>=k} T_{j+1}(c_j - c_{j+1}) is of
+    order 1e-2, and the ~1e-6 FP32 colour error of the MLP bounds the density-gradient accuracy at
+    ~1e-4 relative; random features keep the problem well conditioned so the FP32 backward itself
+    is checked at the usual tolerances.)"""
+    dens, _, mlp = scene
+    feat = synth.normal_grid((RES,) * 3, 12, 0.5, seed=23)
     R = 48
     o, d = synth.blob_rays(R, seed=301)
     jit = synth.jitter(R, 401)
