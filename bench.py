@@ -9,10 +9,11 @@ rays drawn from 100 inward-facing 800x800 views (radius 4, focal 1111).  One ste
 
 Forms (both are timed by default; `value` is the chosen form):
   plain  = uniform 0.5-voxel steps, FP32 feature grid, FP32 SIMT MLP;
-  chosen = learned proposal (64-bin PDF from a BF16 tensor-core proposal MLP, 48 inverse-CDF
-           samples per ray from the PDF mixed 0.05 with the uniform one; every 4th step is a full
-           uniform step whose forward also labels 2048 rays for one proposal Adam step), BF16
-           feature storage with an FP32 master copy, BF16 tensor-core MLP.
+  chosen = learned proposal (64-bin PDF from a BF16 tensor-core proposal MLP trained by its BF16
+           tensor-core backward; 48 inverse-CDF samples per ray from the PDF mixed 0.05 with the
+           uniform one; every 4th step is a full uniform step whose forward also labels 2048 rays
+           for one proposal Adam step), BF16 feature storage with an FP32 master copy, BF16
+           tensor-core MLP.
 The line also carries the sample-proposal evaluation on this scene (`proposal_eval`) and, at one
 GPU, the FP64 CPU oracle's rate on a bounded sample (`cpu_baseline`).
 
@@ -203,7 +204,7 @@ class Form:
         self.trainer = None
         if chosen:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
-                                 sample_precision=dvgo.DVGO_MLP_BF16)
+                                 sample_precision=dvgo.DVGO_MLP_BF16, train_precision=dvgo.DVGO_MLP_BF16)
             self.trainer = dvgo.ProposalTrainer(self.model, prop, N_PROP_SAMPLES, PROPOSAL_EVERY, 0,
                                                 PROPOSAL_TRAIN_RAYS, PROPOSAL_ETA)
 
@@ -354,8 +355,8 @@ def traffic_from_profiles(kind, chosen):
 
 
 def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
-    """Sample proposal on the benchmark scene (fixed grids and MLP): train the proposal on labels
-    from uniform FP32 renders, then compare 48 proposal samples and 48 uniform samples per ray
+    """Sample proposal on the benchmark scene (fixed grids and MLP): train the proposal (BF16
+    tensor-core forward and backward) on labels from uniform FP32 renders, then compare 48 proposal samples and 48 uniform samples per ray
     against the uniform 0.5-voxel FP32 render (which matches the FP64 oracle to 1e-5)."""
     import synth
     step = 2.0 / RES * 0.5
@@ -365,7 +366,7 @@ def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
     p32 = mk(dvgo.DVGO_MLP_FP32)
     m32 = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p32, NRAYS)
     prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p32, m32.dd, NRAYS,
-                         sample_precision=dvgo.DVGO_MLP_BF16)
+                         sample_precision=dvgo.DVGO_MLP_BF16, train_precision=dvgo.DVGO_MLP_BF16)
     losses = []
     for i in range(n_train):
         o, d, _, _ = (t(x) for x in synth.fine_batch(NRAYS, seed=5000 + i))
@@ -495,7 +496,7 @@ def run_time_to_psnr(args):
         prop = trainer = None
         if use_prop:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p, model.dd, NRAYS,
-                                 sample_precision=dvgo.DVGO_MLP_BF16)
+                                 sample_precision=dvgo.DVGO_MLP_BF16, train_precision=dvgo.DVGO_MLP_BF16)
             trainer = dvgo.ProposalTrainer(model, prop, n_ps, every, args.prop_warmup, PROPOSAL_TRAIN_RAYS, eta)
             tb, dtb = torch.empty((NRAYS, n_ps), device=dev), torch.empty((NRAYS, n_ps), device=dev)
         st = [0]
@@ -641,7 +642,9 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 1000 for the training step -- long enough for several clock "
+                         "samples -- 50 for the stress workload, 5 for the oracle reference arm)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["both", "plain", "chosen"], default="both")
@@ -663,6 +666,8 @@ def main():
     ap.add_argument("--psnr-target", type=float, default=28.891)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else (50 if args.workload == "stress" else 1000)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -217,9 +217,10 @@ typedef struct {
     int n_bins;          /* bins per ray; this build supports 64                                 */
     int n_freq;          /* PE frequencies on the bin centre x_b; this build supports 6            */
     int width;           /* MLP width; this build supports 64                                     */
-    int precision;       /* forward arithmetic: DVGO_MLP_FP32 (SIMT) or DVGO_MLP_BF16 (tensor cores,
-                            BF16 operands, FP32 accumulation; the encoding is evaluated in FP32);
-                            the backward is always FP32                                           */
+    int precision;       /* arithmetic of the forward and the backward: DVGO_MLP_FP32 (SIMT) or
+                            DVGO_MLP_BF16 (tcgen05 tensor cores: BF16 operands -- inputs,
+                            activations, weights, dlogit and the dZ of each layer -- with FP32
+                            accumulation; the encoding and the softmax in FP32)                   */
 } dvgo_proposal_desc;
 
 /* Proposal MLP, FP32 row-major [in][out]: in = 3 + 6 n_freq (= 39) -> width -> width -> width -> 1,
@@ -245,7 +246,8 @@ int dvgo_proposal_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, 
                       const float *labels, float *probs_out, float *loss_out, void *stream);
 
 /* Proposal backward: ACCUMULATES the gradient of the cross-entropy loss above into grad_mlp,
- * packed w0 | b0 | w1 | b1 | w2 | b2 | w3 | b3 (recomputes the forward). */
+ * packed w0 | b0 | w1 | b1 | w2 | b2 | w3 | b3 (recomputes the forward).  labels is required.
+ * With DVGO_MLP_BF16, a tensor-core wait that gives up (~2 s) adds NaN to grad_mlp[0]. */
 int dvgo_proposal_bwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, const dvgo_proposal_desc *pd,
                       const dvgo_proposal_mlp *mlp, int n_rays, const float *rays_o, const float *rays_d,
                       const float *labels, float *grad_mlp, void *stream);

@@ -369,9 +369,9 @@ def dvgo_proposal_fwd(params: Params, density_desc: GridDesc, n_bins: int, n_fre
 
 
 def dvgo_proposal_bwd(params: Params, density_desc: GridDesc, n_bins: int, n_freq: int, width: int, mlp, rays_o,
-                      rays_d, labels, grad_mlp, stream=None):
+                      rays_d, labels, grad_mlp, stream=None, precision=DVGO_MLP_FP32):
     p, g = params.c(), density_desc.c()
-    d, m = _prop(n_bins, n_freq, width, mlp)
+    d, m = _prop(n_bins, n_freq, width, mlp, precision)
     st = lib().dvgo_proposal_bwd(C.byref(p), C.byref(g), C.byref(d), C.byref(m), int(rays_o.shape[0]),
                                  _dev(rays_o, "rays_o", torch.float32), _dev(rays_d, "rays_d", torch.float32),
                                  _dev(labels, "labels", torch.float32), _dev(grad_mlp, "grad_mlp", torch.float32),

@@ -507,6 +507,8 @@ __global__ void sample_pdf_kernel(int R, BoxD B, const float *ro, const float *r
 int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const dvgo_proposal_mlp &m, int R,
                            const float *ro, const float *rd, const float *labels, float *probs, float *loss,
                            cudaStream_t s);
+int launch_proposal_bwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const dvgo_proposal_mlp &m, int R,
+                           const float *ro, const float *rd, const float *labels, float *grad, cudaStream_t s);
 
 }  // namespace dvgo
 
@@ -565,6 +567,8 @@ static int proposal_launch(bool bwd, const dvgo_params *p, const dvgo_grid_desc 
     if (!bwd && pd->precision == DVGO_MLP_BF16)
         return launch_proposal_fwd_tc(*p, *dd, *m, n_rays, rays_o, rays_d, labels, probs_out,
                                       labels ? loss_out : nullptr, s);
+    if (bwd && pd->precision == DVGO_MLP_BF16)
+        return launch_proposal_bwd_tc(*p, *dd, *m, n_rays, rays_o, rays_d, labels, grad, s);
     PropArgs P;
     P.R = n_rays;
     P.box = make_box(*p, *dd);

@@ -8,8 +8,17 @@
 // evaluates sin / cos of the FP32 bin centre once per axis and doubles the angle with the identities
 // sin 2a = 2 sin a cos a, cos 2a = 1 - 2 sin^2 a for the higher frequencies.
 //
-// CTA: 128 threads, thread r owns row r of the tile (TMEM lane r); 256 TMEM columns and ~100 KB
-// of shared memory, so two CTAs share an SM.
+// Forward CTA: 128 threads, thread r owns row r of the tile (TMEM lane r); 256 TMEM columns and
+// ~100 KB of shared memory, so two CTAs share an SM.
+//
+// The backward recomputes the forward the same way and then runs every contraction of the chain
+// rule on the tensor cores: dH1 = dZ2 W2^T and dH0 = dZ1 W1^T (the transposed weight panels of
+// the forward read MN-major), and the weight gradients dW_l = H_l^T dZ_{l+1}, reduced over the 128
+// rows of the tile, with the H and dZ panels read MN-major.  Those are M = 128 MMAs whose upper 64
+// rows of A are a constant panel E (column 0 = 1), so row 64 of each accumulator is the column sum
+// of dZ, i.e. the bias gradient.  The gradients accumulate in TMEM over all tiles of the CTA and
+// are added to global memory once.  dW3 / db3 come the same way from a panel holding dlogit in
+// column 0.  One CTA per SM (512 TMEM columns, ~180 KB of shared memory).
 
 #include <math.h>
 
@@ -51,6 +60,7 @@ struct PropTcArgs {
     const float *ro, *rd, *labels;
     const float *w0, *b0, *w1, *b1, *w2, *b2, *w3, *b3;
     float *probs, *loss;
+    float *grad;    // backward: w0 | b0 | w1 | b1 | w2 | b2 | w3 | b3
 };
 
 __device__ __forceinline__ void sync_fenced() {
@@ -59,31 +69,89 @@ __device__ __forceinline__ void sync_fenced() {
     fence_after();
 }
 
+// W0^T | b0 (bias in input column 39), W1^T, W2^T as K-major BF16 panels (rows = outputs) and the
+// FP32 vectors b1, b2, w3, b3.
+__device__ __forceinline__ void load_weights(const PropTcArgs &P, unsigned char *w0t, unsigned char *w1t,
+                                             unsigned char *w2t, float *b1, float *b2, float *w3, float *b3) {
+    const int tid = threadIdx.x;
+    if (tid < PW) {
+        float v[64];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = k < PIN ? P.w0[k * PW + tid] : (k == PIN ? P.b0[tid] : 0.0f);
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) panel_store8(w0t, tid, c, v + c);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = P.w1[k * PW + tid];
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) panel_store8(w1t, tid, c, v + c);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = P.w2[k * PW + tid];
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) panel_store8(w2t, tid, c, v + c);
+        b1[tid] = P.b1[tid];
+        b2[tid] = P.b2[tid];
+        w3[tid] = P.w3[tid];
+    }
+    if (tid == 0) b3[0] = P.b3[0];
+}
+
+// Clip of the tile's two rays (threads 0 and 64).
+__device__ __forceinline__ void clip_tile_rays(const PropTcArgs &P, int tile, double *t0, double *t1, double (*dn)[3],
+                                               int *hit_out) {
+    const int tid = threadIdx.x, rl = tid >> 6, r = 2 * tile + rl;
+    if ((tid & 63) == 0) {
+        int hit = 0;
+        if (r < P.R) {
+            const double o[3] = {(double)P.ro[3 * r], (double)P.ro[3 * r + 1], (double)P.ro[3 * r + 2]};
+            const double d[3] = {(double)P.rd[3 * r], (double)P.rd[3 * r + 1], (double)P.rd[3 * r + 2]};
+            const Clip c = slab_clip(o, d, P.mn, P.mx, P.t_near, P.t_far);
+            hit = c.hi > c.lo;
+            t0[rl] = c.lo;
+            t1[rl] = c.hi;
+            for (int a = 0; a < 3; ++a) dn[rl][a] = c.dn[a];
+        }
+        hit_out[rl] = hit;
+    }
+}
+
+// Input row of this thread's bin centre into the X panel (zeros for a ray that misses or does
+// not exist).
+__device__ __forceinline__ void encode_row(const PropTcArgs &P, int tile, bool hit, double t0, double t1,
+                                           const double *dn, unsigned char *x) {
+    const int tid = threadIdx.x, rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
+    float v[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = 0.0f;
+    if (hit) {
+        const double tb_ = t0 + ((double)bin + 0.5) * (t1 - t0) / (double)NB;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float xa = (float)((double)P.ro[3 * r + a] + tb_ * dn[a]);
+            v[a] = xa;
+            float sn, cs;
+            sincosf(xa, &sn, &cs);
+#pragma unroll
+            for (int k = 0; k < NFQ; ++k) {
+                v[3 + a * NFQ + k] = sn;
+                v[3 + 3 * NFQ + a * NFQ + k] = cs;
+                const float s2 = 2.0f * sn * cs, c2 = 1.0f - 2.0f * sn * sn;
+                sn = s2;
+                cs = c2;
+            }
+        }
+        v[PIN] = 1.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < 64; c += 8) panel_store8(x, tid, c, v + c);
+}
+
 __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
     extern __shared__ unsigned char smem_raw[];
     SmemP &S = *reinterpret_cast<SmemP *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) mbar_init(&S.sm.mbar, 1);
     if (warp == 0) tmem_alloc(&S.sm.tmem_base, 256);
-    if (tid < PW) {
-        float v[64];
-#pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = k < PIN ? P.w0[k * PW + tid] : (k == PIN ? P.b0[tid] : 0.0f);
-#pragma unroll
-        for (int c = 0; c < 64; c += 8) panel_store8(S.w0t, tid, c, v + c);
-#pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = P.w1[k * PW + tid];
-#pragma unroll
-        for (int c = 0; c < 64; c += 8) panel_store8(S.w1t, tid, c, v + c);
-#pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = P.w2[k * PW + tid];
-#pragma unroll
-        for (int c = 0; c < 64; c += 8) panel_store8(S.w2t, tid, c, v + c);
-        S.sm.b1[tid] = P.b1[tid];
-        S.sm.b2[tid] = P.b2[tid];
-        S.sm.w3[tid] = P.w3[tid];
-    }
-    if (tid == 0) S.sm.b3[0] = P.b3[0];
+    load_weights(P, S.w0t, S.w1t, S.w2t, S.sm.b1, S.sm.b2, S.sm.w3, S.sm.b3);
     fence_async_smem();
     sync_fenced();
     const uint32_t tb = S.sm.tmem_base;
@@ -97,48 +165,9 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
         uint32_t h0_ = smem_u32(S.h0), h1_ = smem_u32(S.h1);
         asm volatile("" : "+r"(x_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_), "+r"(h1_));
         const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
-        if ((tid & 63) == 0) {
-            int hit = 0;
-            if (r < P.R) {
-                const double o[3] = {(double)P.ro[3 * r], (double)P.ro[3 * r + 1], (double)P.ro[3 * r + 2]};
-                const double d[3] = {(double)P.rd[3 * r], (double)P.rd[3 * r + 1], (double)P.rd[3 * r + 2]};
-                const Clip c = slab_clip(o, d, P.mn, P.mx, P.t_near, P.t_far);
-                hit = c.hi > c.lo;
-                S.sm.t0[rl] = c.lo;
-                S.sm.t1[rl] = c.hi;
-                for (int a = 0; a < 3; ++a) S.sm.dn[rl][a] = c.dn[a];
-            }
-            S.sm.hit[rl] = hit;
-        }
+        clip_tile_rays(P, tile, S.sm.t0, S.sm.t1, S.sm.dn, S.sm.hit);
         __syncthreads();
-        // ---- encode the bin centre of row tid ----
-        {
-            float v[64];
-#pragma unroll
-            for (int k = 0; k < 64; ++k) v[k] = 0.0f;
-            if (S.sm.hit[rl]) {
-                const double t0 = S.sm.t0[rl], t1 = S.sm.t1[rl];
-                const double tb_ = t0 + ((double)bin + 0.5) * (t1 - t0) / (double)NB;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float x = (float)((double)P.ro[3 * r + a] + tb_ * S.sm.dn[rl][a]);
-                    v[a] = x;
-                    float s, c;
-                    sincosf(x, &s, &c);
-#pragma unroll
-                    for (int k = 0; k < NFQ; ++k) {
-                        v[3 + a * NFQ + k] = s;
-                        v[3 + 3 * NFQ + a * NFQ + k] = c;
-                        const float s2 = 2.0f * s * c, c2 = 1.0f - 2.0f * s * s;
-                        s = s2;
-                        c = c2;
-                    }
-                }
-                v[PIN] = 1.0f;
-            }
-#pragma unroll
-            for (int c = 0; c < 64; c += 8) panel_store8(S.x, tid, c, v + c);
-        }
+        encode_row(P, tile, S.sm.hit[rl] != 0, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.x);
         fence_async_smem();
         sync_fenced();
         // ---- layer 0 ----
@@ -236,12 +265,293 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
     if (warp == 0) tmem_dealloc(S.sm.tmem_base, 256);
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------------------------
+
+// TMEM columns: the layer accumulator (Z, then dH) and the weight-gradient accumulators.
+constexpr uint32_t BCOL_Z = 0, BCOL_DW2 = 64, BCOL_DW1 = 128, BCOL_DW0 = 192, BCOL_DW3 = 256, BCOLS = 512;
+
+struct alignas(1024) SmallB {
+    float b1[PW], b2[PW], w3[PW];
+    float b3[4];
+    float red[2][2][2];
+    double t0[2], t1[2], dn[2][3];
+    int hit[2];
+    uint64_t mbar;
+    uint32_t tmem_base;
+};
+
+struct SmemB {
+    unsigned char w0t[kPanelBytes];
+    unsigned char w1t[kPanelBytes];
+    unsigned char w2t[kPanelBytes];
+    unsigned char x[kPanelBytes];
+    unsigned char h0[kPanelBytes];
+    unsigned char h1[kPanelBytes];
+    unsigned char h2[kPanelBytes];
+    unsigned char dza[kPanelBytes];   // dZ2, then dZ0
+    unsigned char dzb[kPanelBytes];   // dZ1
+    unsigned char dl[kPanelBytes];    // column 0 = dlogit, columns 1..15 = 0
+    unsigned char e[kPanelBytes];     // column 0 = 1 (must follow x, h0, h1, h2: it is their second M half)
+    SmallB sm;
+};
+
+// MN-major A operand of M = 128 whose first 64 rows are panel `base` and last 64 rows the panel
+// `lbo` bytes after it; k-step kk = 16 tile rows.
+__device__ __forceinline__ uint64_t desc_mn_pair(uint32_t base, int kk, uint32_t lbo) {
+    return sdesc(base + (uint32_t)kk * 2u * kGroupBytes, lbo, kGroupBytes);
+}
+
+// ReLU epilogue of one 64-column layer accumulator: h = max(z + b, 0) into the panel, the ReLU mask
+// into two 32-bit words; with w_out, also returns the output-layer dot product h . w_out.
+__device__ __forceinline__ float relu_epilogue(uint32_t tb, int warp, const float *bias, unsigned char *panel,
+                                               uint32_t (&mask)[2], const float *w_out) {
+    const int tid = threadIdx.x;
+    float da = 0.0f, db = 0.0f;
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        float z[32];
+        tmem_ld32(taddr(tb, warp, BCOL_Z + 32 * g), z);
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            z[k] = fmaxf(z[k] + (bias ? bias[32 * g + k] : 0.0f), 0.0f);
+            m |= (z[k] > 0.0f ? 1u : 0u) << k;
+        }
+        if (w_out) {
+#pragma unroll
+            for (int k = 0; k < 32; k += 2) {
+                da = fmaf(z[k], w_out[32 * g + k], da);
+                db = fmaf(z[k + 1], w_out[32 * g + k + 1], db);
+            }
+        }
+        mask[g] = m;
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) panel_store8(panel, tid, 32 * g + k, z + k);
+    }
+    return da + db;
+}
+
+// dZ = dH * mask from the layer accumulator into the panel.
+__device__ __forceinline__ void mask_epilogue(uint32_t tb, int warp, const uint32_t (&mask)[2], unsigned char *panel) {
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        float z[32];
+        tmem_ld32(taddr(tb, warp, BCOL_Z + 32 * g), z);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z[k] = (mask[g] >> k) & 1u ? z[k] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) panel_store8(panel, tid, 32 * g + k, z + k);
+    }
+}
+
+// Adds rows [0, nrows) of a 64-column gradient accumulator (lane = row) to dst[row * 64 + n] and
+// row `bias_row` to bias[n], scaled by s.  Every thread of the CTA calls it (TMEM loads are
+// warp-collective).
+__device__ __forceinline__ void flush_acc(uint32_t tb, int warp, uint32_t col, int nrows, int bias_row, float *dst,
+                                          float *bias, float s) {
+    const int row = threadIdx.x;
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        float v[32];
+        tmem_ld32(taddr(tb, warp, col + 32 * g), v);
+        if (row < nrows) {
+            for (int k = 0; k < 32; ++k) atomicAdd(dst + row * PW + 32 * g + k, v[k] * s);
+        } else if (row == bias_row) {
+            for (int k = 0; k < 32; ++k) atomicAdd(bias + 32 * g + k, v[k] * s);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TT, 1) proposal_bwd_tc_kernel(PropTcArgs P) {
+    extern __shared__ unsigned char smem_raw[];
+    SmemB &S = *reinterpret_cast<SmemB *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) mbar_init(&S.sm.mbar, 1);
+    if (warp == 0) tmem_alloc(&S.sm.tmem_base, BCOLS);
+    load_weights(P, S.w0t, S.w1t, S.w2t, S.sm.b1, S.sm.b2, S.sm.w3, S.sm.b3);
+    {
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = (c == 0 && k == 0) ? 1.0f : 0.0f;
+            panel_store8(S.e, tid, c, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+            panel_store8(S.dl, tid, c, v);
+        }
+    }
+    fence_async_smem();
+    sync_fenced();
+    const uint32_t tb = S.sm.tmem_base;
+    const uint32_t id_fwd = idesc_bf16(128, 64, 0, 0);   // Z = A W: A K-major, W^T panel K-major
+    const uint32_t id_dh = idesc_bf16(128, 64, 0, 1);    // dH = dZ W^T: dZ K-major, W^T panel MN-major
+    const uint32_t id_dw = idesc_bf16(128, 64, 1, 1);    // [H | E]^T dZ: both MN-major
+    const uint32_t id_dw3 = idesc_bf16(128, 16, 1, 1);
+    uint32_t phase = 0;
+    bool ok = true;
+    uint32_t acc = 0;   // 0 until the first tile's weight-gradient MMAs have initialised TMEM
+    const int ntiles = (P.R + 1) / 2;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        uint32_t x_ = smem_u32(S.x), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
+        uint32_t h0_ = smem_u32(S.h0), h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), e_ = smem_u32(S.e);
+        uint32_t dza_ = smem_u32(S.dza), dzb_ = smem_u32(S.dzb), dl_ = smem_u32(S.dl);
+        asm volatile("" : "+r"(x_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_), "+r"(h1_), "+r"(h2_), "+r"(e_));
+        asm volatile("" : "+r"(dza_), "+r"(dzb_), "+r"(dl_));
+        const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
+        clip_tile_rays(P, tile, S.sm.t0, S.sm.t1, S.sm.dn, S.sm.hit);
+        __syncthreads();
+        const bool hit = S.sm.hit[rl] != 0;
+        encode_row(P, tile, hit, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.x);
+        fence_async_smem();
+        sync_fenced();
+        uint32_t m0[2], m1[2], m2[2];
+        // ---- forward: three layers ----
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk) mma(tb + BCOL_Z, desc_kmajor(x_, kk), desc_kmajor(w0_, kk), id_fwd, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        relu_epilogue(tb, warp, nullptr, S.h0, m0, nullptr);
+        fence_async_smem();
+        sync_fenced();
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk) mma(tb + BCOL_Z, desc_kmajor(h0_, kk), desc_kmajor(w1_, kk), id_fwd, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        relu_epilogue(tb, warp, S.sm.b1, S.h1, m1, nullptr);
+        fence_async_smem();
+        sync_fenced();
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk) mma(tb + BCOL_Z, desc_kmajor(h1_, kk), desc_kmajor(w2_, kk), id_fwd, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        const float logit = S.sm.b3[0] + relu_epilogue(tb, warp, S.sm.b2, S.h2, m2, S.sm.w3);
+        // ---- softmax over the 64 rows of a ray; dlogit = p - h (the 1/R is applied at the flush) ----
+        float m = logit;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) S.sm.red[rl][warp & 1][0] = m;
+        __syncthreads();
+        m = fmaxf(S.sm.red[rl][0][0], S.sm.red[rl][1][0]);
+        const float ex = expf(logit - m);
+        const float es = warp_sum(ex);
+        if (lane == 0) S.sm.red[rl][warp & 1][1] = es;
+        __syncthreads();
+        const float zs = S.sm.red[rl][0][1] + S.sm.red[rl][1][1];
+        float dlog = 0.0f;
+        if (r < P.R && hit) dlog = ex / zs - P.labels[(size_t)r * NB + bin];
+        {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = k == 0 ? dlog : 0.0f;
+            panel_store8(S.dl, tid, 0, v);
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                float z[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) z[k] = (m2[g] >> k) & 1u ? dlog * S.sm.w3[32 * g + k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) panel_store8(S.dza, tid, 32 * g + k, z + k);
+            }
+        }
+        fence_async_smem();
+        sync_fenced();
+        // ---- dW2 | db2, dW3 | db3, dH1 ----
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tb + BCOL_DW2, desc_mn_pair(h1_, kk, e_ - h1_), desc_mnmajor(dza_, kk), id_dw, acc | (kk > 0));
+#pragma unroll 1
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tb + BCOL_DW3, desc_mn_pair(h2_, kk, e_ - h2_), desc_mnmajor(dl_, kk), id_dw3, acc | (kk > 0));
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk) mma(tb + BCOL_Z, desc_kmajor(dza_, kk), desc_mnmajor(w2_, kk), id_dh, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        mask_epilogue(tb, warp, m1, S.dzb);
+        fence_async_smem();
+        sync_fenced();
+        // ---- dW1 | db1, dH0 ----
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tb + BCOL_DW1, desc_mn_pair(h0_, kk, e_ - h0_), desc_mnmajor(dzb_, kk), id_dw, acc | (kk > 0));
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk) mma(tb + BCOL_Z, desc_kmajor(dzb_, kk), desc_mnmajor(w1_, kk), id_dh, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        mask_epilogue(tb, warp, m0, S.dza);
+        fence_async_smem();
+        sync_fenced();
+        // ---- [dW0 | db0] (input column 39 is the constant 1) ----
+        if (tid == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tb + BCOL_DW0, desc_mn_pair(x_, kk, e_ - x_), desc_mnmajor(dza_, kk), id_dw, acc | (kk > 0));
+            commit(&S.sm.mbar);
+        }
+        ok = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) break;
+        fence_after();
+        acc = 1;
+        __syncthreads();
+    }
+    ok = !__syncthreads_or(!ok);
+    if (!ok) {
+        mbar_wait(&S.sm.mbar, phase ^ 1);
+        if (tid == 0) atomicAdd(P.grad, __int_as_float(0x7fc00000));   // NaN marks the failed launch
+    }
+    sync_fenced();
+    if (ok && acc) {
+        const float s = 1.0f / (float)P.R;
+        float *G0 = P.grad, *GB0 = G0 + PIN * PW, *G1 = GB0 + PW, *GB1 = G1 + PW * PW, *G2 = GB1 + PW;
+        float *GB2 = G2 + PW * PW, *G3 = GB2 + PW, *GB3 = G3 + PW;
+        flush_acc(tb, warp, BCOL_DW0, PIN, PIN, G0, GB0, s);
+        flush_acc(tb, warp, BCOL_DW1, PW, PW, G1, GB1, s);
+        flush_acc(tb, warp, BCOL_DW2, PW, PW, G2, GB2, s);
+        float v[16];
+        tmem_ld16(taddr(tb, warp, BCOL_DW3), v);
+        if (tid < PW) atomicAdd(G3 + tid, v[0] * s);
+        else if (tid == PW) atomicAdd(GB3, v[0] * s);
+    }
+    sync_fenced();
+    if (warp == 0) tmem_dealloc(S.sm.tmem_base, BCOLS);
+}
+
 }  // namespace
 
 int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const dvgo_proposal_mlp &m, int R,
                            const float *ro, const float *rd, const float *labels, float *probs, float *loss,
                            cudaStream_t s) {
-    PropTcArgs P;
+    PropTcArgs P{};
     P.R = R;
     for (int a = 0; a < 3; ++a) {
         P.mn[a] = g.xyz_min[a];
@@ -263,6 +573,33 @@ int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const 
     {
         ProfScope ps_(DVGO_K_PROPOSAL_FWD, s);
         proposal_fwd_tc_kernel<<<blocks, TT, bytes, s>>>(P);
+    }
+    return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
+}
+
+int launch_proposal_bwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const dvgo_proposal_mlp &m, int R,
+                           const float *ro, const float *rd, const float *labels, float *grad, cudaStream_t s) {
+    PropTcArgs P{};
+    P.R = R;
+    for (int a = 0; a < 3; ++a) {
+        P.mn[a] = g.xyz_min[a];
+        P.mx[a] = g.xyz_max[a];
+    }
+    P.t_near = p.t_near;
+    P.t_far = p.t_far;
+    P.ro = ro;
+    P.rd = rd;
+    P.labels = labels;
+    P.w0 = m.w0; P.b0 = m.b0; P.w1 = m.w1; P.b1 = m.b1; P.w2 = m.w2; P.b2 = m.b2; P.w3 = m.w3; P.b3 = m.b3;
+    P.grad = grad;
+    const int bytes = (int)sizeof(SmemB) + 1024;
+    ensure_smem(reinterpret_cast<const void *>(proposal_bwd_tc_kernel), bytes);
+    const int ntiles = (R + 1) / 2;
+    int blocks = num_sms();
+    if (blocks > ntiles) blocks = ntiles;
+    {
+        ProfScope ps_(DVGO_K_PROPOSAL_BWD, s);
+        proposal_bwd_tc_kernel<<<blocks, TT, bytes, s>>>(P);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
 }

@@ -228,9 +228,10 @@ class Proposal:
     N_BINS, N_FREQ, WIDTH = 64, 6, 64
 
     def __init__(self, weights: dict, params: B.Params, density_desc: B.GridDesc, n_rays: int, lr: float = 5e-3,
-                 device="cuda", sample_precision: int = B.DVGO_MLP_FP32, decay_steps: float = 5000.0):
+                 device="cuda", sample_precision: int = B.DVGO_MLP_FP32, decay_steps: float = 5000.0,
+                 train_precision: int = B.DVGO_MLP_FP32):
         self.params, self.dd = params, density_desc
-        self.sample_precision = sample_precision
+        self.sample_precision, self.train_precision = sample_precision, train_precision
         shapes = {"w0": (3 + 6 * self.N_FREQ, self.WIDTH), "b0": (self.WIDTH,), "w1": (self.WIDTH, self.WIDTH),
                   "b1": (self.WIDTH,), "w2": (self.WIDTH, self.WIDTH), "b2": (self.WIDTH,), "w3": (self.WIDTH, 1),
                   "b3": (1,)}
@@ -261,7 +262,7 @@ class Proposal:
             B.dvgo_proposal_fwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o[:n],
                                 rays_d[:n], self.labels[:n], self.probs[:n], self.loss, stream)
         B.dvgo_proposal_bwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o[:n],
-                            rays_d[:n], self.labels[:n], self.grad, stream)
+                            rays_d[:n], self.labels[:n], self.grad, stream, precision=self.train_precision)
         self.step_count += 1
         lr = B.dvgo_lr_at(self.lr, self.step_count - 1, self.decay_steps)
         B.dvgo_adam_step(self.flat, self.grad, self.adam.m, self.adam.v, lr, self.step_count, stream=stream)
