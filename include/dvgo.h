@@ -185,7 +185,7 @@ int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *
  * counterpart; this is a deployment convenience.
  *
  * Scratch memory: instead of a caller workspace it uses one static device array of
- * DVGO_NOALLOC_SCRATCH_BYTES (about 1.5 MB) inside the library, which every GPU that loads the
+ * DVGO_NOALLOC_SCRATCH_BYTES (about 2.4 MB) inside the library, which every GPU that loads the
  * library holds until the process exits.  The caller still passes all inputs and outputs, with the
  * meaning, layout and nullability of dvgo_render_fwd.  The call itself allocates nothing (no
  * cudaMalloc / cudaFree or allocating library routine).
@@ -198,7 +198,7 @@ int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *
  *     them) race and give undefined results: order them on one stream or with events.
  */
 #define DVGO_NOALLOC_MAX_RAYS 16384
-#define DVGO_NOALLOC_SCRATCH_BYTES 1573120
+#define DVGO_NOALLOC_SCRATCH_BYTES 2359552
 int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_desc *density_desc, const float *density,
                             const dvgo_grid_desc *cgrid_desc, const void *cgrid, int n_rays,
                             const float *rays_o, const float *rays_d, const float *jitter,
@@ -254,8 +254,9 @@ int dvgo_proposal_bwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, 
 
 /* Inverse-CDF sampling of n_samples sorted samples per ray from probs [n_rays * n_bins]: the PDF
  * is mixed with the uniform one, q_b = (1 - eta) p_b + eta / n_bins; sample j sits at quantile
- * u_j = (j + jit) / n_samples (jit = jitter[r], or 0.5 when jitter is NULL) with linear
- * interpolation inside its bin.  t_out, dt_out [n_rays * n_samples]: distances along the
+ * u_j = (j + jit) / n_samples of the CDF (jit = jitter[r], or 0.5 when jitter is NULL) with linear
+ * interpolation inside its bin (CDF, quantiles and bin choice in FP64, the fraction inside the bin
+ * in FP32).  t_out, dt_out [n_rays * n_samples]: distances along the
  * normalised direction and step lengths (t_{j+1} - t_j; for the last sample the bin width over
  * n_samples times the bin's normalised probability), ready for dvgo_samples.  Rays that miss the
  * box get zeros.  Bin decisions are taken in FP64. */

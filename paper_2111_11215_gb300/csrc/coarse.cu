@@ -34,11 +34,7 @@ struct CoarseSample {
 
 __device__ __forceinline__ CoarseSample coarse_sample(const RenderArgs &A, const RayRec &rr, int ray, int k) {
     CoarseSample S;
-    double t;
-    sample_t(A, rr, ray, k, t, S.dt);
-    double u[3];
-    lattice_coord(rr, t, u);
-    S.cell = make_cell(u, A.nx, A.ny, A.nz);
+    S.cell = sample_cell(A, rr, ray, k, S.dt);
     const float *rgb = static_cast<const float *>(A.cgrid);
     float s = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -132,12 +128,8 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
 
 // Optical depth of one sample (density gather only), with the removal rule.
 __device__ __forceinline__ float coarse_tau(const RenderArgs &A, const RayRec &rr, int ray, int k) {
-    double t;
     float dt;
-    sample_t(A, rr, ray, k, t, dt);
-    double u[3];
-    lattice_coord(rr, t, u);
-    Cell c = make_cell(u, A.nx, A.ny, A.nz);
+    Cell c = sample_cell(A, rr, ray, k, dt);
     float s = 0.0f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);

@@ -27,17 +27,25 @@ constexpr int kPeStride = 32;                      // floats per ray of the dire
 constexpr int kMaxChunks = 64;                    // backward kernels: rays of <= 64 x 32 samples
 constexpr int kMaxSamplesPerRay = 32 * kMaxChunks;
 
-// Per-ray record written by ray_setup (80 bytes).
+// Lattice coordinates of samples are carried in 64-bit fixed point with kFxBits fractional bits
+// (resolution 9e-13 lattice units, range +-8.4e6): the per-sample position then needs no FP64
+// arithmetic, which this GPU executes at a small fraction of its FP32 / integer rate.
+constexpr int kFxBits = 40;
+
+// Per-ray record written by ray_setup (128 bytes).  Lattice coordinate u = (x - xyz_min) (n - 1) /
+// (xyz_max - xyz_min) per axis; the FP64 values below are rounded once into fixed point.
 struct RayRec {
-    double uo[3];     // ray origin in lattice coordinates: (o - xyz_min) * (n - 1) / (xyz_max - xyz_min)
-    double e[3];      // normalised direction in lattice coordinates per unit of t
-    double t_enter;   // clipped entry distance
-    float dir[3];     // normalised direction (FP32, positional encoding input)
-    float p;          // jitter in [0, 1)
-    int n;            // number of samples
-    int off;          // first sample slot (exclusive scan of n)
+    long long uefx[3];   // entry point (t = t_enter), fixed point
+    double e[3];         // normalised direction in lattice units per unit of t
+    long long u0fx[3];   // uniform stepping: sample 0 at t_enter + p * step, fixed point
+    long long dfx[3];    // uniform stepping: step * e, fixed point
+    double t_enter;      // clipped entry distance
+    float dir[3];        // normalised direction (FP32, positional encoding input)
+    float p;             // jitter in [0, 1)
+    int n;               // number of samples
+    int off;             // first sample slot (exclusive scan of n)
 };
-static_assert(sizeof(RayRec) == 80, "RayRec layout");
+static_assert(sizeof(RayRec) == 128, "RayRec layout");
 
 // Workspace header (first 256 bytes of the workspace).
 struct WsHeader {
@@ -101,11 +109,8 @@ __device__ __forceinline__ float softplusf(float z) {
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 
-// Lattice coordinate of sample (ray, t) along one axis, in FP64 (see RayRec).
-__device__ __forceinline__ void lattice_coord(const RayRec &r, double t, double u[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = fma(t, r.e[a], r.uo[a]);
-}
+// FP64 value -> fixed point (round to nearest).
+__device__ __forceinline__ long long to_fx(double v) { return __double2ll_rn(v * 0x1p40); }
 
 // Ray / box clip in FP64 with every operation separately rounded (no FMA contraction), in the
 // order the sample count depends on (Sec. 4.2 fine-stage points sampling):
@@ -158,13 +163,19 @@ struct Cell {
     float fx, fy, fz;
 };
 
-__device__ __forceinline__ Cell make_cell(const double u[3], int nx, int ny, int nz) {
-    Cell c;
-    double fl;
-    fl = floor(u[0]); fl = fmin(fmax(fl, 0.0), (double)(nx - 2)); c.i0 = (int)fl; c.fx = (float)(u[0] - fl);
-    fl = floor(u[1]); fl = fmin(fmax(fl, 0.0), (double)(ny - 2)); c.j0 = (int)fl; c.fy = (float)(u[1] - fl);
-    fl = floor(u[2]); fl = fmin(fmax(fl, 0.0), (double)(nz - 2)); c.k0 = (int)fl; c.fz = (float)(u[2] - fl);
-    return c;
+// One axis of a fixed-point lattice coordinate: i0 = clamp(floor(u), 0, n - 2), f = u - i0.  Inside
+// the lattice the 40 fractional bits are converted as two 20-bit halves (each exact in FP32) with
+// one final rounding; at the clamped edges f = u - i0 is formed in FP64.
+__device__ __forceinline__ void fx_axis(long long ufx, int n, int &i0, float &f) {
+    const long long ip = ufx >> kFxBits;
+    const long long ic = ip < 0 ? 0LL : (ip > (long long)(n - 2) ? (long long)(n - 2) : ip);
+    i0 = (int)ic;
+    if (ip == ic) {
+        const unsigned long long fr = (unsigned long long)ufx & ((1ULL << kFxBits) - 1ULL);
+        f = fmaf(__uint2float_rn((unsigned)(fr >> 20)), 0x1p-20f, __uint2float_rn((unsigned)(fr & 0xFFFFFULL)) * 0x1p-40f);
+    } else {
+        f = (float)((double)(ufx - (ic << kFxBits)) * 0x1p-40);
+    }
 }
 
 // Corner q (bits x = q>>2, y = (q>>1)&1, z = q&1): flat lattice index and trilinear weight.
@@ -178,16 +189,26 @@ __device__ __forceinline__ float corner_weight(const Cell &c, int q) {
     return wx * wy * wz;
 }
 
-// Sample position along a ray: uniform stepping or explicit list.
-__device__ __forceinline__ void sample_t(const RenderArgs &A, const RayRec &r, int ray, int k,
-                                         double &t, float &dt) {
+// Cell and step length of sample k of a ray: uniform stepping (t_k = t_enter + (k + p) step, so
+// u_k = u_0 + k (step e) in integer arithmetic) or the explicit list (u = u_entry + (t - t_enter) e,
+// the offset in FP64).
+__device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r, int ray, int k, float &dt) {
+    Cell c;
+    long long u[3];
     if (A.ts) {
-        t = (double)A.ts[(long long)ray * A.n_expl + k];
+        const double t = (double)A.ts[(long long)ray * A.n_expl + k];
         dt = A.dts[(long long)ray * A.n_expl + k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = r.uefx[a] + to_fx((t - r.t_enter) * r.e[a]);
     } else {
-        t = fma((double)k + (double)r.p, (double)A.step, r.t_enter);
         dt = A.step;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = r.u0fx[a] + (long long)k * r.dfx[a];
     }
+    fx_axis(u[0], A.nx, c.i0, c.fx);
+    fx_axis(u[1], A.ny, c.j0, c.fy);
+    fx_axis(u[2], A.nz, c.k0, c.fz);
+    return c;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

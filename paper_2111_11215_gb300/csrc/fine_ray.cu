@@ -38,12 +38,8 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
             float tau = 0.0f;
             bool kept = false;
             if (valid) {
-                double t;
                 float dt;
-                sample_t(A, rr, r, k, t, dt);
-                double u[3];
-                lattice_coord(rr, t, u);
-                Cell c = make_cell(u, A.nx, A.ny, A.nz);
+                Cell c = sample_cell(A, rr, r, k, dt);
                 float s = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
@@ -190,12 +186,8 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
             c.fx = c.fy = c.fz = 0.0f;
             float dz = 0.0f;
             if (valid) {
-                double t;
                 float dt;
-                sample_t(A, rr, r, k, t, dt);
-                double u[3];
-                lattice_coord(rr, t, u);
-                c = make_cell(u, A.nx, A.ny, A.nz);
+                c = sample_cell(A, rr, r, k, dt);
                 dz = act ? dtau * dt * -expm1f(-sv.x / dt) : 0.0f;
                 // dL/dc_k for the colour backward (only kept samples are read back)
                 A.sgrad[rr.off + k] = make_float4(0.0f, g[0] * w, g[1] * w, g[2] * w);

@@ -87,12 +87,8 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
         rp = A.rays + ray;
         const RayRec &rr = *rp;
         int k = slot - rr.off;
-        double t;
         float dt;
-        sample_t(A, rr, ray, k, t, dt);
-        double u[3];
-        lattice_coord(rr, t, u);
-        Cell c = make_cell(u, A.nx, A.ny, A.nz);
+        Cell c = sample_cell(A, rr, ray, k, dt);
         if (q == 0) {
             S.cbase[i] = (int)corner_index(c, 0, A.ny, A.nz);
             S.frac[3 * i] = c.fx;

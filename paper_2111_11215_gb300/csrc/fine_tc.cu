@@ -135,12 +135,8 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
     if (e < n_kept) {
         const int2 kv = A.kept[e];
         const RayRec &rr = A.rays[kv.y];
-        double t;
         float dt;
-        sample_t(A, rr, kv.y, kv.x - rr.off, t, dt);
-        double u[3];
-        lattice_coord(rr, t, u);
-        const Cell c = make_cell(u, A.nx, A.ny, A.nz);
+        const Cell c = sample_cell(A, rr, kv.y, kv.x - rr.off, dt);
         slot = kv.x;
         cbase = (int)corner_index(c, 0, A.ny, A.nz);
         fx = c.fx;

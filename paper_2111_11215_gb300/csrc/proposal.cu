@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(256) weight_bins_kernel(RenderArgs A, int nbin
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
         const double t0 = rr.t_enter, t1 = A.texit[r];
+        // bin of sample k: floor((t_k - t_enter) / (t_exit - t_enter) nbins), t_k - t_enter = (k + p) step
+        const double bin_scale = __ddiv_rn(__dmul_rn((double)A.step, (double)nbins), __dsub_rn(t1, t0));
         for (int b = lane; b < nbins; b += 32) bins[wib][b] = 0.0f;
         __syncwarp();
         float carry = 0.0f, wsum = 0.0f;
@@ -79,8 +81,7 @@ __global__ void __launch_bounds__(256) weight_bins_kernel(RenderArgs A, int nbin
             if (lane == 0) excl = 0.0f;
             const float w = expf(-(carry + excl)) * -expm1f(-tau);
             if (k < rr.n) {
-                const double tk = __dadd_rn(t0, __dmul_rn((double)k + (double)rr.p, (double)A.step));
-                int b = (int)floor(__dmul_rn(__ddiv_rn(__dsub_rn(tk, t0), __dsub_rn(t1, t0)), (double)nbins));
+                int b = (int)floor(__dmul_rn(__dadd_rn((double)k, (double)rr.p), bin_scale));
                 b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
                 atomicAdd(&bins[wib][b], w);
             }
@@ -463,11 +464,15 @@ __global__ void __launch_bounds__(PNT, 1) proposal_kernel(PropArgs P) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Inverse-CDF sampling, thread per ray, FP64 with separately rounded operations
+// Inverse-CDF sampling, thread per ray.  The CDF, the quantiles and every bin decision are FP64;
+// the position inside the chosen bin, (u - Q_b) / q_b in [0, 1], is divided in FP32 and the sample
+// assembled in FP64 (FP64 arithmetic is scarce on this GPU: the quantile uses one reciprocal per
+// ray instead of a division per sample).
 // ---------------------------------------------------------------------------------------------
 
-__global__ void sample_pdf_kernel(int R, BoxD B, const float *ro, const float *rd, const float *probs, int nb, int ns,
-                                  const float *jitter, double eta, float *t_out, float *dt_out) {
+__global__ void __launch_bounds__(32) sample_pdf_kernel(int R, BoxD B, const float *ro, const float *rd,
+                                                        const float *probs, int nb, int ns, const float *jitter,
+                                                        double eta, float *t_out, float *dt_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const Clip c = clip_ray(B, ro, rd, r);
@@ -483,18 +488,20 @@ __global__ void sample_pdf_kernel(int R, BoxD B, const float *ro, const float *r
     double Qtot = 0.0;
     for (int b = 0; b < nb; ++b) Qtot = __dadd_rn(Qtot, __dadd_rn(__dmul_rn(one_m_eta, (double)p[b]), eta_nb));
     const double jit = jitter ? (double)jitter[r] : 0.5;
+    const double du = __ddiv_rn(Qtot, (double)ns);
     int b = 0;
     double Qb = 0.0;                                                               // CDF at the left edge of bin b
     double qb = __dadd_rn(__dmul_rn(one_m_eta, (double)p[0]), eta_nb);
     double tprev = 0.0;
     for (int j = 0; j < ns; ++j) {
-        const double u = __dmul_rn(__ddiv_rn(__dadd_rn((double)j, jit), (double)ns), Qtot);
+        const double u = __dmul_rn(__dadd_rn((double)j, jit), du);
         while (b < nb - 1 && __dadd_rn(Qb, qb) <= u) {
             Qb = __dadd_rn(Qb, qb);
             ++b;
             qb = __dadd_rn(__dmul_rn(one_m_eta, (double)p[b]), eta_nb);
         }
-        const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)b, __ddiv_rn(__dsub_rn(u, Qb), qb)), w));
+        const float frac = __fdiv_rn((float)__dsub_rn(u, Qb), (float)qb);
+        const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)b, (double)frac), w));
         to[j] = (float)t;
         if (j > 0) dto[j - 1] = (float)__dsub_rn(t, tprev);
         tprev = t;
@@ -612,8 +619,8 @@ int dvgo_sample_pdf(const dvgo_params *p, const dvgo_grid_desc *dd, int n_rays, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         ProfScope ps_(DVGO_K_SAMPLE_PDF, s);
-        sample_pdf_kernel<<<(n_rays + 127) / 128, 128, 0, s>>>(n_rays, make_box(*p, *dd), rays_o, rays_d, probs, n_bins,
-                                                               n_samples, jitter, (double)eta, t_out, dt_out);
+        sample_pdf_kernel<<<(n_rays + 31) / 32, 32, 0, s>>>(n_rays, make_box(*p, *dd), rays_o, rays_d, probs, n_bins,
+                                                             n_samples, jitter, (double)eta, t_out, dt_out);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
 }

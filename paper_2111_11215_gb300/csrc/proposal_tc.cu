@@ -8,8 +8,9 @@
 // evaluates sin / cos of the FP32 bin centre once per axis and doubles the angle with the identities
 // sin 2a = 2 sin a cos a, cos 2a = 1 - 2 sin^2 a for the higher frequencies.
 //
-// Forward CTA: 128 threads, thread r owns row r of the tile (TMEM lane r); 256 TMEM columns and
-// ~100 KB of shared memory, so two CTAs share an SM.
+// Forward CTA: 128 threads, thread r owns row r of the tile (TMEM lane r); one 64-column TMEM
+// accumulator used by the three layers in turn and ~57 KB of shared memory (64-row weight panels,
+// H1 written over X), so three CTAs share an SM.
 //
 // The backward recomputes the forward the same way and then runs every contraction of the chain
 // rule on the tensor cores: dH1 = dZ2 W2^T and dH0 = dZ1 W1^T (the transposed weight panels of
@@ -32,7 +33,7 @@ namespace {
 using namespace tc;
 
 constexpr int NB = 64, NFQ = 6, PIN = 3 + 6 * NFQ, PW = 64, TT = 128;
-constexpr uint32_t COL_Z0 = 0, COL_Z1 = 64, COL_Z2 = 128;
+constexpr uint32_t COL_Z = 0, FWD_COLS = 64;   // the three layers use one accumulator in turn
 
 struct alignas(1024) SmallP {
     float b1[PW], b2[PW], w3[PW];
@@ -44,13 +45,14 @@ struct alignas(1024) SmallP {
     uint32_t tmem_base;
 };
 
+constexpr uint32_t kHalfPanelBytes = kPanelBytes / 2;   // 64 rows: a K-major operand of N = 64
+
 struct SmemP {
-    unsigned char w0t[kPanelBytes];   // rows = 64 outputs, 64 input columns (bias in column 39)
-    unsigned char w1t[kPanelBytes];
-    unsigned char w2t[kPanelBytes];
-    unsigned char x[kPanelBytes];
+    unsigned char w0t[kHalfPanelBytes];   // rows = 64 outputs, 64 input columns (bias in column 39)
+    unsigned char w1t[kHalfPanelBytes];
+    unsigned char w2t[kHalfPanelBytes];
+    unsigned char xh1[kPanelBytes];       // X, then H1 (X is dead once layer 0's MMAs complete)
     unsigned char h0[kPanelBytes];
-    unsigned char h1[kPanelBytes];
     SmallP sm;
 };
 
@@ -145,12 +147,12 @@ __device__ __forceinline__ void encode_row(const PropTcArgs &P, int tile, bool h
     for (int c = 0; c < 64; c += 8) panel_store8(x, tid, c, v + c);
 }
 
-__global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
+__global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
     extern __shared__ unsigned char smem_raw[];
     SmemP &S = *reinterpret_cast<SmemP *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) mbar_init(&S.sm.mbar, 1);
-    if (warp == 0) tmem_alloc(&S.sm.tmem_base, 256);
+    if (warp == 0) tmem_alloc(&S.sm.tmem_base, FWD_COLS);
     load_weights(P, S.w0t, S.w1t, S.w2t, S.sm.b1, S.sm.b2, S.sm.w3, S.sm.b3);
     fence_async_smem();
     sync_fenced();
@@ -161,19 +163,19 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
     const float invR = 1.0f / (float)P.R;
     const int ntiles = (P.R + 1) / 2;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        uint32_t x_ = smem_u32(S.x), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
-        uint32_t h0_ = smem_u32(S.h0), h1_ = smem_u32(S.h1);
-        asm volatile("" : "+r"(x_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_), "+r"(h1_));
+        uint32_t xh1_ = smem_u32(S.xh1), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
+        uint32_t h0_ = smem_u32(S.h0);
+        asm volatile("" : "+r"(xh1_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_));
         const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
         clip_tile_rays(P, tile, S.sm.t0, S.sm.t1, S.sm.dn, S.sm.hit);
         __syncthreads();
-        encode_row(P, tile, S.sm.hit[rl] != 0, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.x);
+        encode_row(P, tile, S.sm.hit[rl] != 0, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.xh1);
         fence_async_smem();
         sync_fenced();
         // ---- layer 0 ----
         if (tid == 0) {
 #pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z0, desc_kmajor(x_, kk), desc_kmajor(w0_, kk), id64, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(xh1_, kk), desc_kmajor(w0_, kk), id64, kk > 0);
             commit(&S.sm.mbar);
         }
         ok = mbar_wait(&S.sm.mbar, phase);
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
             float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z0 + 32 * g), z);
+            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
 #pragma unroll
             for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k], 0.0f);
 #pragma unroll
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
         // ---- layer 1 ----
         if (tid == 0) {
 #pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z1, desc_kmajor(h0_, kk), desc_kmajor(w1_, kk), id64, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(h0_, kk), desc_kmajor(w1_, kk), id64, kk > 0);
             commit(&S.sm.mbar);
         }
         ok = mbar_wait(&S.sm.mbar, phase);
@@ -204,18 +206,18 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
             float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z1 + 32 * g), z);
+            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
 #pragma unroll
             for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k] + S.sm.b1[32 * g + k], 0.0f);
 #pragma unroll
-            for (int k = 0; k < 32; k += 8) panel_store8(S.h1, tid, 32 * g + k, z + k);
+            for (int k = 0; k < 32; k += 8) panel_store8(S.xh1, tid, 32 * g + k, z + k);
         }
         fence_async_smem();
         sync_fenced();
         // ---- layer 2 and the output logit ----
         if (tid == 0) {
 #pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z2, desc_kmajor(h1_, kk), desc_kmajor(w2_, kk), id64, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(xh1_, kk), desc_kmajor(w2_, kk), id64, kk > 0);
             commit(&S.sm.mbar);
         }
         ok = mbar_wait(&S.sm.mbar, phase);
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
             float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * g), z);
+            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const float h = fmaxf(z[k] + S.sm.b2[32 * g + k], 0.0f);
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(TT, 2) proposal_fwd_tc_kernel(PropTcArgs P) {
     ok = !__syncthreads_or(!ok);
     if (!ok) mbar_wait(&S.sm.mbar, phase ^ 1);
     sync_fenced();
-    if (warp == 0) tmem_dealloc(S.sm.tmem_base, 256);
+    if (warp == 0) tmem_dealloc(S.sm.tmem_base, FWD_COLS);
 }
 
 
@@ -568,7 +570,7 @@ int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const 
     const int bytes = (int)sizeof(SmemP) + 1024;
     ensure_smem(reinterpret_cast<const void *>(proposal_fwd_tc_kernel), bytes);
     const int ntiles = (R + 1) / 2;
-    int blocks = 2 * num_sms();
+    int blocks = 3 * num_sms();
     if (blocks > ntiles) blocks = ntiles;
     {
         ProfScope ps_(DVGO_K_PROPOSAL_FWD, s);

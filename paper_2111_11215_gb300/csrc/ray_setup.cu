@@ -55,10 +55,16 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
         n = c > 0.0 ? (int)c : 0;
         if (n_expl >= 0) n = n_expl;   // explicit samples: all or nothing
     }
+    const bool uniform = n > 0 && n_expl < 0;
+    const double t_first = uniform ? fma(p, step, lo) : 0.0;   // t of sample 0 of the uniform stepping
     for (int a = 0; a < 3; ++a) {
-        rec.uo[a] = __dmul_rn(__dsub_rn(o[a], mn[a]), sc[a]);
+        const double uo = __dmul_rn(__dsub_rn(o[a], mn[a]), sc[a]);
         rec.e[a] = __dmul_rn(dn[a], sc[a]);
         rec.dir[a] = (float)dn[a];
+        // fixed-point values only where they are used: in range for any sample inside the box
+        rec.uefx[a] = n > 0 ? to_fx(fma(lo, rec.e[a], uo)) : 0;
+        rec.u0fx[a] = uniform ? to_fx(fma(t_first, rec.e[a], uo)) : 0;
+        rec.dfx[a] = uniform ? to_fx(step * rec.e[a]) : 0;
     }
     rec.t_enter = lo;
     rec.p = (float)p;

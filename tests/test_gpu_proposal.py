@@ -212,6 +212,39 @@ def test_sample_pdf_matches_oracle_and_renders():
     assert_close(rgb.cpu().numpy(), ref.rgb, RTOL_COLOUR, "rgb_explicit")
 
 
+@pytest.mark.parametrize("nb,ns,eta", [(50, 100, 0.0), (64, 48, 0.05), (7, 3, 0.3)])
+def test_sample_pdf_shapes_and_zero_bins(nb, ns, eta):
+    """Inverse-CDF sampling against the oracle for bin counts that are not a multiple of the warp
+    width, more samples than bins, eta = 0 with zero-mass bins, and a one-hot PDF."""
+    res, R = 24, 96
+    _, _, _, o, d, _, p = _setup(res, R=R, seed=76)
+    dd = dvgo.GridDesc((res,) * 3, 1)
+    rng = np.random.default_rng(77)
+    probs = rng.dirichlet(np.full(nb, 0.5), size=R)
+    probs[rng.random((R, nb)) < 0.3] = 0.0                    # zero-mass bins
+    probs[5] = 0.0
+    probs[5, nb // 2] = 1.0                                   # one-hot
+    probs = (probs / probs.sum(axis=1, keepdims=True)).astype(np.float32)
+    jit = synth.jitter(R, 78)
+    ts, dts = torch.empty((R, ns), device="cuda"), torch.empty((R, ns), device="cuda")
+    dvgo.dvgo_sample_pdf(p, dd, cuda(o), cuda(d), cuda(probs), ns, cuda(jit), eta, ts, dts)
+    torch.cuda.synchronize()
+    t_gpu, dt_gpu = ts.cpu().numpy(), dts.cpu().numpy()
+    P = oracle_params(p, (res,) * 3, 12)
+    for r in range(R):
+        _, t0, t1, _, _ = oracle.ray_bounds(P, o[r], d[r])
+        if not t1 > t0:
+            assert np.all(t_gpu[r] == 0) and np.all(dt_gpu[r] == 0)
+            continue
+        t, dt = oracle.sample_pdf(probs[r].astype(np.float64), t0, t1, ns, jit=float(jit[r]),
+                                  eta=float(np.float32(eta)))
+        np.testing.assert_allclose(t_gpu[r], t, rtol=2e-7, atol=1e-7)
+        np.testing.assert_allclose(dt_gpu[r], dt, rtol=2e-6, atol=1e-7)
+        if r == 5 and eta == 0.0:
+            w = (t1 - t0) / nb
+            assert np.all((t_gpu[r] >= t0 + (nb // 2) * w - 1e-6) & (t_gpu[r] <= t0 + (nb // 2 + 1) * w + 1e-6))
+
+
 def test_trained_proposal_beats_uniform_48_samples():
     """Gain test: after training on labels from uniform renders, 48 proposal samples per ray give a
     clearly smaller colour error against the oracle's uniform 0.5-voxel render than 48 uniform
