@@ -108,27 +108,34 @@ class AdamState:
 class FineModel:
     """Fine-stage parameters (Sec. 4.2): density grid, feature grid (FP32 master, optional BF16
     storage copy written by the Adam step), colour MLP in one flat buffer; their gradients and
-    Adam state; and one training step (forward, backward, Adam) on a ray batch."""
+    Adam state; and one training step (forward, backward, Adam) on a ray batch.
+
+    overlap_adam: the feature-grid Adam step (HBM-bound, the largest of the three) is deferred to a
+    side stream: it is launched by launch_feat_adam (after the backward and after whatever the
+    caller queued meanwhile, e.g. the next step's proposal forward, so that it overlaps the work
+    queued next that does not read the features), or at the latest by the next read of the
+    features through this object (wait_params)."""
 
     def __init__(self, density: torch.Tensor, feat: torch.Tensor, mlp_flat: torch.Tensor, params: B.Params,
                  n_rays: int, bf16_feat: bool = False, box=((-1.0,) * 3, (1.0,) * 3),
-                 lr_grid: float = 0.1, lr_mlp: float = 1e-3, decay_steps: float = 20000.0):
+                 lr_grid: float = 0.1, lr_mlp: float = 1e-3, decay_steps: float = 20000.0,
+                 overlap_adam: bool = False):
         self.params = params
         res = tuple(density.shape)
         C = feat.shape[-1]
         self.density = density.contiguous()
-        self.feat = feat.contiguous()
+        self._feat = feat.contiguous()
         self.mlp_flat = mlp_flat.contiguous()
         self.mlp = mlp_views(self.mlp_flat, C + 3 + 6 * params.n_freq_dir, params.hidden)
         self.bf16_feat = bf16_feat
-        self.feat_bf16 = self.feat.to(torch.bfloat16) if bf16_feat else None
+        self._feat_bf16 = self._feat.to(torch.bfloat16) if bf16_feat else None
         self.dd = B.GridDesc(res, 1, box[0], box[1])
         self.cd = B.GridDesc(res, C, box[0], box[1], B.DVGO_DTYPE_BF16 if bf16_feat else B.DVGO_DTYPE_F32)
         self.renderer = Renderer(params, self.dd, self.cd, n_rays, device=density.device)
         self.g_density = torch.zeros_like(self.density)
-        self.g_feat = torch.zeros_like(self.feat)
+        self.g_feat = torch.zeros_like(self._feat)
         self.g_mlp = torch.zeros_like(self.mlp_flat)
-        self.adam = {k: AdamState(t) for k, t in (("density", self.density), ("feat", self.feat), ("mlp", self.mlp_flat))}
+        self.adam = {k: AdamState(t) for k, t in (("density", self.density), ("feat", self._feat), ("mlp", self.mlp_flat))}
         self.lr_grid, self.lr_mlp, self.decay_steps = lr_grid, lr_mlp, decay_steps
         dev = density.device
         self.rgb = torch.empty((n_rays, 3), device=dev)
@@ -136,12 +143,58 @@ class FineModel:
         self.loss = torch.zeros(1, device=dev)
         self.dloss = torch.empty((n_rays, 3), device=dev)
         self.step_count = 0
+        self._side = torch.cuda.Stream(device=dev) if overlap_adam else None
+        self._ev_bwd = torch.cuda.Event() if overlap_adam else None
+        self._ev_after = torch.cuda.Event() if overlap_adam else None
+        self._ev_feat = torch.cuda.Event() if overlap_adam else None
+        self._feat_pending = False     # an Adam step was launched on the side stream
+        self._feat_deferred = None     # (lr, t) of an Adam step not launched yet
+
+    @property
+    def feat(self):
+        """FP32 feature grid (master copy), ordered after any pending Adam step on the current stream."""
+        self.wait_params()
+        return self._feat
+
+    @property
+    def feat_bf16(self):
+        """BF16 storage copy of the feature grid (None without bf16_feat), ordered like feat."""
+        self.wait_params()
+        return self._feat_bf16
 
     @property
     def cgrid(self):
-        return self.feat_bf16 if self.bf16_feat else self.feat
+        """The feature grid the renderer reads (BF16 copy or FP32), ordered like feat."""
+        self.wait_params()
+        return self._feat_bf16 if self.bf16_feat else self._feat
+
+    def _cur(self, stream):
+        return stream if stream is not None else torch.cuda.current_stream(self.density.device)
+
+    def launch_feat_adam(self, stream=None):
+        """Launch a deferred feature-grid Adam step on the side stream, ordered after the backward
+        and after everything queued on `stream` so far."""
+        if self._feat_deferred is None:
+            return
+        lr_g, t = self._feat_deferred
+        self._feat_deferred = None
+        self._ev_after.record(self._cur(stream))
+        self._side.wait_event(self._ev_bwd)
+        self._side.wait_event(self._ev_after)
+        B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
+                         param_bf16_out=self._feat_bf16, stream=self._side)
+        self._ev_feat.record(self._side)
+        self._feat_pending = True
+
+    def wait_params(self, stream=None):
+        """Order `stream` (default: the current stream) after the feature-grid Adam step (launching
+        it first if it is still deferred)."""
+        self.launch_feat_adam(stream)
+        if self._feat_pending:
+            self._cur(stream).wait_event(self._ev_feat)
 
     def forward(self, rays_o, rays_d, jitter=None, target=None, stream=None):
+        self.wait_params(stream)
         return self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
                                      self.rgb, self.tfinal, self.loss if target is not None else None,
                                      self.dloss if target is not None else None, stream)
@@ -161,6 +214,7 @@ class FineModel:
         uniform steps.  `after_forward(renderer)` (optional) is called between the forward and the
         backward, while the renderer's workspace holds this batch's forward samples."""
         rend = self.renderer if samples is None else self.explicit_renderer(samples[0].shape[1])
+        self.wait_params(stream)
         rend.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, target,
                      self.rgb, self.tfinal, self.loss, self.dloss, stream)
         if after_forward is not None:
@@ -171,10 +225,14 @@ class FineModel:
         t = self.step_count
         lr_g = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
         lr_m = B.dvgo_lr_at(self.lr_mlp, t - 1, self.decay_steps)
+        if self._side is not None:
+            self._ev_bwd.record(self._cur(stream))
+            self._feat_deferred = (lr_g, t)
+        else:
+            B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
+                             param_bf16_out=self._feat_bf16, stream=stream)
         B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, t,
                          stream=stream)
-        B.dvgo_adam_step(self.feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
-                         param_bf16_out=self.feat_bf16, stream=stream)
         B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
         return self.loss
 
@@ -269,14 +327,17 @@ class Proposal:
         return self.loss
 
     def sample(self, rays_o, rays_d, jitter=None, n_samples: int = 48, eta: float = 0.05, t_out=None, dt_out=None,
-               stream=None):
+               stream=None, after_forward=None):
         """Explicit samples (t, dt) [R, n_samples] drawn from the predicted PDFs mixed with the
-        uniform PDF at weight eta (0.05 keeps ~2 of 48 samples spread along the whole ray)."""
+        uniform PDF at weight eta (0.05 keeps ~2 of 48 samples spread along the whole ray).
+        after_forward() (optional) is called between the proposal forward and the sampling."""
         R = rays_o.shape[0]
         t_out = torch.empty((R, n_samples), device=rays_o.device) if t_out is None else t_out
         dt_out = torch.empty((R, n_samples), device=rays_o.device) if dt_out is None else dt_out
         B.dvgo_proposal_fwd(self.params, self.dd, self.N_BINS, self.N_FREQ, self.WIDTH, self.w, rays_o, rays_d,
                             None, self.probs[:R], None, stream, precision=self.sample_precision)
+        if after_forward is not None:
+            after_forward()
         B.dvgo_sample_pdf(self.params, self.dd, rays_o, rays_d, self.probs[:R], n_samples, jitter, eta, t_out, dt_out,
                           stream)
         return t_out, dt_out
@@ -316,8 +377,10 @@ class ProposalTrainer:
             self.n_uniform += 1
         else:
             R = rays_o.shape[0]
+            # the previous step's feature-grid Adam (when deferred) overlaps the sampling
             ts, dts = self.proposal.sample(rays_o, rays_d, jitter, self.n_samples, eta=self.eta,
-                                           t_out=self.t_buf[:R], dt_out=self.dt_buf[:R], stream=stream)
+                                           t_out=self.t_buf[:R], dt_out=self.dt_buf[:R], stream=stream,
+                                           after_forward=lambda: self.model.launch_feat_adam(stream))
             loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, samples=(ts, dts))
             self.n_proposal += 1
         self.i += 1
