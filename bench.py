@@ -327,7 +327,7 @@ def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
         if chosen:
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
             return {"bound": "tensor", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "units_per_launch": units,
+                    "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen), "units_per_launch": units,
                     "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         return {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -339,7 +339,8 @@ def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
         achieved = byts / 3.0 / (avg_ms * 1e-3) / 1e9
         peak = hbm or 6800.0
         return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "measured" if hbm else "fallback"}
+                "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen),
+                "algorithmic_bytes_per_launch": byts / 3.0, "peak_source": "measured" if hbm else "fallback"}
     return {"bound": "hbm", "kernel": kind, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
             "traffic": None}
 
@@ -349,9 +350,10 @@ def traffic_from_profiles(kind, chosen):
     current source (the summary records the source file's hash)."""
     import hashlib
     import re
-    src = "fine_tc.cu" if chosen else "fine_simt.cu"
-    prof = {("fine_colour_bwd", False): "fine_colour_bwd_fp32_160cube_8192rays.md",
-            ("fine_colour_bwd", True): "fine_colour_bwd_bf16tc_160cube_8192rays.md"}.get((kind, chosen))
+    prof, src = {("fine_colour_bwd", False): ("fine_colour_bwd_fp32_160cube_8192rays.md", "fine_simt.cu"),
+                 ("fine_colour_bwd", True): ("fine_kernels_bf16_chosen_160cube_8192rays.md", "fine_tc.cu"),
+                 ("adam", False): ("adam_fine_step_160cube.md", "adam.cu"),
+                 ("adam", True): ("adam_fine_step_160cube.md", "adam.cu")}.get((kind, chosen), (None, None))
     if prof is None or not os.path.exists(os.path.join(ROOT, "profiles", prof)):
         return None
     text = open(os.path.join(ROOT, "profiles", prof)).read()
@@ -571,7 +573,7 @@ def run_stress(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    rs, nr = 256, 65536
+    rs, nr = 256, args.stress_rays
     dens = synth.sphere_density(rs, [(0.0, 0.0, 0.0)], [0.3], 200.0)
     feat = synth.smooth_features(rs, FEAT, seed=21)
     mlp = synth.mlp_weights(39, HID, 3, seed=22)
@@ -673,6 +675,7 @@ def main():
     ap.add_argument("--prop-every", type=int, default=PROPOSAL_EVERY)
     ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
     ap.add_argument("--prop-warmup", type=int, default=0)
+    ap.add_argument("--stress-rays", type=int, default=65536, help="rays per batch of the 256^3 stress workload")
     # frozen from the first full plain run: its final held-out PSNR (2 views) 29.391 dB - 0.5 dB
     ap.add_argument("--psnr-target", type=float, default=28.891)
     args = ap.parse_args()
