@@ -47,6 +47,23 @@ MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 
 N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The maximum of x over all ranks (identity on one rank); device is where the process group's
+    backend keeps its tensors (CUDA for NCCL, CPU for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks processed divided by the
+    slowest rank's time (weak scaling: every rank processes the same units)."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def workload(seed=0):
     import synth
     dens, feat = synth.fine_scene(seed=seed, res=RES, feat_dim=FEAT)
@@ -263,12 +280,8 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     launches = dvgo.dvgo_launch_counter() - launches0
     dvgo.dvgo_profile_enable(False)
     per_kind = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = NRAYS * world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = whole_job_rate(NRAYS * args.steps, world, ms)
 
     # end to end through the public API with host buffers: H2D of each step's rays / jitter /
     # targets from pinned memory, the step, and a D2H read of its loss
@@ -291,11 +304,7 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     form.finish()
     e3.record(s)
     torch.cuda.synchronize()
-    e2e_ms = max(e2.elapsed_time(e3), (time.perf_counter() - t_host0) * 1e3)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(max(e2.elapsed_time(e3), (time.perf_counter() - t_host0) * 1e3), world, dev)
     assert np.all(np.isfinite(loss_host.numpy()))
 
     # units processed per launch of the colour kernels (uniform and proposal steps of the timed region)
@@ -313,7 +322,7 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
                                                      "samples_per_hit_ray": N_PROP_SAMPLES if name == "chosen" else None},
             "roofline": roof,
             "kernels_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in per_kind.items() if v[1]},
-            "e2e": {"value": NRAYS * world * args.steps / (e2e_ms / 1e3), "unit": "rays/s",
+            "e2e": {"value": whole_job_rate(NRAYS * args.steps, world, e2e_ms), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": clk}
 
