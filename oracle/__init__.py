@@ -70,8 +70,15 @@ class _Params(C.Structure):
                 ("t_far", C.c_double), ("bg", C.c_double * 3)]
 
 
+class _FreeSpace(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("xyz_min", C.c_double * 3),
+                ("xyz_max", C.c_double * 3), ("shift_b", C.c_double), ("delta", C.c_double), ("tau", C.c_double),
+                ("density", _dp)]
+
+
 class _Model(C.Structure):
-    _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")]
+    _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")] + \
+        [("fs", C.POINTER(_FreeSpace))]
 
 
 class _Grads(C.Structure):
@@ -150,14 +157,58 @@ def lr_decay(lr0: float, step: int, decay_steps: float = 20000.0) -> float:
     return float(lib().oracle_lr_decay(lr0, step, decay_steps))
 
 
+@dataclass
+class FreeSpace:
+    """Known free space of Sec. 4.2: the optimised coarse density grid with its lattice, shift b_c,
+    step delta_c and threshold tau_c."""
+    density: np.ndarray
+    xyz_min: tuple = (-1.0, -1.0, -1.0)
+    xyz_max: tuple = (1.0, 1.0, 1.0)
+    shift_b: float = 0.0
+    delta: float = 0.03125
+    tau: float = 1e-3
+
+    def _c(self):
+        F = _FreeSpace()
+        d = _f64(self.density)
+        F.nx, F.ny, F.nz = (int(v) for v in d.shape[:3])
+        F.xyz_min[:] = [float(v) for v in self.xyz_min]
+        F.xyz_max[:] = [float(v) for v in self.xyz_max]
+        F.shift_b, F.delta, F.tau = float(self.shift_b), float(self.delta), float(self.tau)
+        F.density = _ptr(d)
+        return F, d
+
+
+def coarse_alpha(fs: FreeSpace, x) -> float:
+    """Post-activated alpha of the coarse grid at one point (the known-free-space test)."""
+    F, keep = fs._c()
+    lib().oracle_coarse_alpha.restype = C.c_double
+    lib().oracle_coarse_alpha.argtypes = [C.POINTER(_FreeSpace), _dp]
+    return float(lib().oracle_coarse_alpha(C.byref(F), _ptr(_f64(x))))
+
+
+def unknown_bbox(fs: FreeSpace):
+    """Sec. 4.2 fine voxels allocation: (count, lo, hi) lattice-index box of the cells that can hold
+    unknown space (alpha_c >= tau_c); lo = hi = None when everything is known free."""
+    F, keep = fs._c()
+    lo = (C.c_int * 3)()
+    hi = (C.c_int * 3)()
+    lib().oracle_unknown_bbox.restype = C.c_long
+    n = int(lib().oracle_unknown_bbox(C.byref(F), lo, hi))
+    if n == 0:
+        return 0, None, None
+    return n, tuple(lo), tuple(hi)
+
+
 def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dict | None = None,
            target=None, grad_rgb=None, grad_tfinal=None, explicit_t=None, explicit_dt=None,
-           n_bins: int = 0) -> RenderResult:
+           n_bins: int = 0, freespace: FreeSpace | None = None) -> RenderResult:
     """Render a ray batch forward and, if ``grad_rgb`` is given, backward (Sec. 2-4).
 
     density: [nx, ny, nz]; cgrid: [nx, ny, nz, C] (coarse colour or fine features);
     rays_o, rays_d: [R, 3]; jitter: [R] in [0, 1) or None (0.5); mlp: dict of w1..b3 (fine);
-    grad_rgb: [R, 3] upstream dL/dC_hat; grad_tfinal: [R] or None.
+    grad_rgb: [R, 3] upstream dL/dC_hat; grad_tfinal: [R] or None; freespace: the known-free-space
+    test of Sec. 4.2 (skips points where the coarse grid's alpha is below tau_c).
     Returns colours, final transmittances, sample counts, clip bounds, loss and gradients.
     """
     P = params._c()
@@ -169,6 +220,9 @@ def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dic
     jit = None if jitter is None else _f64(jitter).reshape(R)
     M = _Model()
     M.density, M.cgrid = _ptr(density), _ptr(cgrid)
+    if freespace is not None:
+        fs_c, fs_keep = freespace._c()
+        M.fs = C.pointer(fs_c)
     mlp_arrs = {}
     if params.mode == 1:
         for k in MLP_KEYS:

@@ -64,11 +64,25 @@ typedef struct {
     double bg[3];      /* background colour c_bg of Eq. volume_rendering                         */
 } og_params;
 
+/* Known free space (Sec. 4.2): the optimised coarse-stage density grid with its own lattice,
+ * shift b_c and step delta_c.  A fine-stage query point x lies in the known free space when
+ *     alpha_c(x) = 1 - exp(-softplus(interp(x, V_c) + b_c) delta_c) < tau_c,
+ * and is then skipped like a point below tau_f (alpha := 0, no colour, no gradient). */
+typedef struct {
+    int nx, ny, nz;
+    double xyz_min[3], xyz_max[3];
+    double shift_b;    /* b_c of the coarse stage                                                */
+    double delta;      /* delta_c, the coarse stage's step                                       */
+    double tau;        /* tau_c                                                                  */
+    const double *density;   /* [nx][ny][nz]                                                    */
+} og_freespace;
+
 typedef struct {
     const double *density;      /* [nx][ny][nz]                                               */
     const double *cgrid;        /* [nx][ny][nz][C]                                             */
     /* fine MLP, row-major [in][out]: in_dim = C + 3 + 6*n_freq -> hidden -> hidden -> 3       */
     const double *w1, *b1, *w2, *b2, *w3, *b3;
+    const og_freespace *fs;     /* nullable: no known-free-space test                           */
 } og_model;
 
 typedef struct {
@@ -193,6 +207,56 @@ double oracle_alpha_at(const og_params *P, const double *density, const double x
     return -expm1(-sigma * delta);
 }
 
+/* Post-activated alpha of the coarse grid at x (the known-free-space test of Sec. 4.2). */
+double oracle_coarse_alpha(const og_freespace *F, const double x[3]) {
+    og_params Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.nx = F->nx;
+    Q.ny = F->ny;
+    Q.nz = F->nz;
+    for (int a = 0; a < 3; ++a) {
+        Q.xyz_min[a] = F->xyz_min[a];
+        Q.xyz_max[a] = F->xyz_max[a];
+    }
+    Q.shift_b = F->shift_b;
+    return oracle_alpha_at(&Q, F->density, x, F->delta);
+}
+
+/*
+ * Fine voxels allocation (Sec. 4.2): a box enclosing the unknown space of the coarse grid.
+ * Lattice point v is "unknown" when alpha(softplus(V_c[v] + b_c), delta_c) >= tau_c.  Inside a cell
+ * the interpolated raw density is a convex combination of the 8 corner values and alpha is
+ * increasing in it, so a cell whose corners are all known free is known free everywhere; the
+ * unknown space therefore lies in the cells touching an unknown lattice point, i.e. in the
+ * lattice-index box [min - 1, max + 1] of the unknown points, clamped to [0, N - 1] per axis.
+ * Writes lo[3], hi[3] (lattice indices) and returns the number of unknown lattice points (0: the
+ * whole grid is known free and lo / hi are left unchanged).
+ */
+long oracle_unknown_bbox(const og_freespace *F, int lo[3], int hi[3]) {
+    int N[3] = {F->nx, F->ny, F->nz};
+    int mn[3] = {N[0], N[1], N[2]}, mx[3] = {-1, -1, -1};
+    long count = 0;
+    for (int i = 0; i < N[0]; ++i)
+        for (int j = 0; j < N[1]; ++j)
+            for (int k = 0; k < N[2]; ++k) {
+                double v = F->density[((long)i * N[1] + j) * N[2] + k];
+                double alpha = -expm1(-og_softplus(v + F->shift_b) * F->delta);
+                if (alpha < F->tau) continue;
+                ++count;
+                int ijk[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a) {
+                    if (ijk[a] < mn[a]) mn[a] = ijk[a];
+                    if (ijk[a] > mx[a]) mx[a] = ijk[a];
+                }
+            }
+    if (count == 0) return 0;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = mn[a] - 1 < 0 ? 0 : mn[a] - 1;
+        hi[a] = mx[a] + 1 > N[a] - 1 ? N[a] - 1 : mx[a] + 1;
+    }
+    return count;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Colour model                                                                                 */
 /* ------------------------------------------------------------------------------------------ */
@@ -301,6 +365,11 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             s->dt = P->delta;
         }
         for (int a = 0; a < 3; ++a) s->x[a] = o[a] + s->t * dn[a];
+        if (M->fs && M->fs->density && oracle_coarse_alpha(M->fs, s->x) < M->fs->tau) {
+            s->kept = 0;      /* known free space: no fine query, alpha 0, no gradient */
+            s->alpha = 0.0;
+            continue;
+        }
         og_corners(P, s->x, s->idx, s->cw);
         double raw = 0.0;
         for (int c = 0; c < 8; ++c) raw += s->cw[c] * M->density[s->idx[c]];
