@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 1
+#define DVGO_ABI_VERSION 2
 
 typedef enum {
     DVGO_OK = 0,
@@ -61,6 +61,23 @@ typedef struct {
     int dtype;           /* DVGO_DTYPE_F32, or DVGO_DTYPE_BF16 for the fine feature grid only   */
 } dvgo_grid_desc;
 
+/*
+ * Known free space of the fine stage (Sec. 4.2, "Known free space and unknown space" and "Free
+ * space skipping"): the optimised coarse-stage density grid with its own lattice and box
+ * (desc.channels = 1, FP32), the coarse stage's shift b_c and step delta_c.  A fine-stage query
+ * point x is skipped -- alpha := 0, no fine density or colour query, no gradient -- when
+ *     alpha_c(x) = 1 - exp(-softplus(interp(x, V_c) + b_c) delta_c) < tau,
+ * evaluated in FP32 (trilinear interpolation with the same edge clamping as the fine grid).
+ * The struct is read on the host during the call; density is a device pointer.
+ */
+typedef struct {
+    dvgo_grid_desc desc;
+    const float *density;    /* [nx*ny*nz] FP32; NULL disables the test                          */
+    float shift_b;           /* b_c                                                              */
+    float step;              /* delta_c, world units                                             */
+    float tau;               /* tau_c (Supp. A: 1e-3)                                            */
+} dvgo_freespace;
+
 /* Render parameters. */
 typedef struct {
     int mode;            /* DVGO_MODE_COARSE: colour = interp(x, V_rgb) (Sec. 4.1 Eq. coarse_queries)
@@ -76,6 +93,7 @@ typedef struct {
     float tau_f;         /* samples with alpha < tau_f are removed (Sec. 4.2 free space skipping) */
     float t_near, t_far; /* ray clip range before the box intersection                           */
     float bg[3];         /* c_bg of Eq. volume_rendering                                          */
+    const dvgo_freespace *freespace;   /* fine stage only, nullable: skip the known free space   */
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
@@ -204,6 +222,17 @@ int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_desc *density_
                             const float *rays_o, const float *rays_d, const float *jitter,
                             const float *target, float *rgb_out, float *tfinal_out, float *loss_out,
                             float *dloss_drgb_out, void *stream);
+
+/*
+ * Fine voxels allocation (Sec. 4.2): the lattice-index box of the coarse grid's cells that can
+ * hold unknown space.  A lattice point v is unknown when 1 - exp(-softplus(V_c[v] + b_c) delta_c)
+ * >= tau (FP32); interpolation inside a cell is a convex combination of its corners and alpha
+ * increases with the raw density, so a cell whose 8 corners are known free is known free
+ * everywhere, and the unknown space lies in [min - 1, max + 1] of the unknown lattice points,
+ * clamped to [0, n - 1] per axis.  out (device, 7 ints): count of unknown lattice points, then
+ * lo[3], hi[3] (undefined when the count is 0).  Three small kernels on `stream`.
+ */
+int dvgo_unknown_bbox(const dvgo_freespace *fs, int *out, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Learned sample proposal.  The paper samples every ray uniformly and leaves hierarchical

@@ -21,6 +21,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
+    "dvgo_unknown_bbox",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 
@@ -47,10 +48,16 @@ class _GridDesc(C.Structure):
                 ("xyz_min", C.c_float * 3), ("xyz_max", C.c_float * 3), ("dtype", C.c_int)]
 
 
+class _FreeSpace(C.Structure):
+    _fields_ = [("desc", _GridDesc), ("density", C.c_void_p), ("shift_b", C.c_float), ("step", C.c_float),
+                ("tau", C.c_float)]
+
+
 class _Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("rgb_act", C.c_int), ("mlp_prec", C.c_int), ("n_freq_dir", C.c_int),
                 ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
-                ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3)]
+                ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
+                ("freespace", C.POINTER(_FreeSpace))]
 
 
 class _Mlp(C.Structure):
@@ -98,6 +105,8 @@ def lib():
         L.dvgo_proposal_bwd.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, vp, vp]
         L.dvgo_sample_pdf.restype = i
         L.dvgo_sample_pdf.argtypes = [vp, vp, i, vp, vp, vp, i, i, vp, f, vp, vp, vp]
+        L.dvgo_unknown_bbox.restype = i
+        L.dvgo_unknown_bbox.argtypes = [vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -138,6 +147,25 @@ class GridDesc:
 
 
 @dataclass
+class FreeSpace:
+    """Known free space of the fine stage (Sec. 4.2): the optimised coarse density grid (CUDA
+    FP32 tensor [nx, ny, nz]) on its lattice `desc`, with the coarse stage's shift and step, and
+    the threshold tau_c."""
+    density: torch.Tensor
+    desc: "GridDesc"
+    shift_b: float
+    step: float
+    tau: float = 1e-3
+
+    def c(self) -> _FreeSpace:
+        f = _FreeSpace()
+        f.desc = self.desc.c()
+        f.density = _dev(self.density, "freespace.density", torch.float32)
+        f.shift_b, f.step, f.tau = float(self.shift_b), float(self.step), float(self.tau)
+        return f
+
+
+@dataclass
 class Params:
     mode: int = DVGO_MODE_COARSE
     step: float = 0.03125
@@ -150,6 +178,7 @@ class Params:
     mlp_prec: int = DVGO_MLP_FP32
     n_freq_dir: int = 4
     hidden: int = 128
+    freespace: FreeSpace | None = None
 
     def c(self) -> _Params:
         p = _Params()
@@ -158,6 +187,9 @@ class Params:
         p.step, p.shift_b, p.tau_f = float(self.step), float(self.shift_b), float(self.tau_f)
         p.t_near, p.t_far = float(self.t_near), float(self.t_far)
         p.bg[:] = [float(v) for v in self.bg]
+        if self.freespace is not None:
+            p._fs = self.freespace.c()          # kept alive with the struct that points to it
+            p.freespace = C.pointer(p._fs)
         return p
 
 
@@ -388,3 +420,11 @@ def dvgo_sample_pdf(params: Params, density_desc: GridDesc, rays_o, rays_d, prob
                                float(eta), _dev(t_out, "t_out", torch.float32), _dev(dt_out, "dt_out", torch.float32),
                                _stream(stream))
     _check(st, "dvgo_sample_pdf")
+
+
+def dvgo_unknown_bbox(fs: FreeSpace, out=None, stream=None):
+    """Sec. 4.2 fine voxels allocation on the coarse grid: int32 device tensor [count, lo(3), hi(3)]."""
+    out = torch.empty(7, dtype=torch.int32, device=fs.density.device) if out is None else out
+    f = fs.c()
+    _check(lib().dvgo_unknown_bbox(C.byref(f), _dev(out, "out", torch.int32), _stream(stream)), "dvgo_unknown_bbox")
+    return out

@@ -99,6 +99,19 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
     if (ex) {
         if (!ex->t || !ex->dt || ex->n_per_ray < 1) return DVGO_ERR_INVALID_ARG;
     }
+    if (p->freespace && p->freespace->density) {
+        const dvgo_freespace &f = *p->freespace;
+        if (p->mode != DVGO_MODE_FINE) return DVGO_ERR_INVALID_ARG;
+        if (!grid_ok(&f.desc) || f.desc.channels != 1 || f.desc.dtype != DVGO_DTYPE_F32) return DVGO_ERR_INVALID_ARG;
+        if (!finite_pos(f.step) || !isfinite(f.shift_b) || !isfinite(f.tau)) return DVGO_ERR_INVALID_ARG;
+        // the fixed-point map onto the coarse lattice: its scale must fit kFsScaleBits fractional bits
+        for (int a = 0; a < 3; ++a) {
+            const int nf[3] = {dd->nx, dd->ny, dd->nz}, nc[3] = {f.desc.nx, f.desc.ny, f.desc.nz};
+            const double sf = (nf[a] - 1) / ((double)dd->xyz_max[a] - dd->xyz_min[a]);
+            const double sc = (nc[a] - 1) / ((double)f.desc.xyz_max[a] - f.desc.xyz_min[a]);
+            if (!(sc / sf < 32768.0)) return DVGO_ERR_UNSUPPORTED;
+        }
+    }
     if (max_samples(p, dd, R, ex) >= (1LL << 31) - 1) return DVGO_ERR_UNSUPPORTED;
     // the backward keeps one optical-depth value per 32-sample chunk of a ray in shared memory
     if ((ex ? (long long)ex->n_per_ray : sample_cap(p, dd)) > kMaxSamplesPerRay) return DVGO_ERR_UNSUPPORTED;
@@ -144,6 +157,24 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
         A.kept = reinterpret_cast<int2 *>(b + L.kept);
     }
     A.max_samples = L.max_samples;
+    if (p->mode == DVGO_MODE_FINE && p->freespace && p->freespace->density) {
+        const dvgo_freespace &f = *p->freespace;
+        A.fs_density = f.density;
+        A.fs_nx = f.desc.nx;
+        A.fs_ny = f.desc.ny;
+        A.fs_nz = f.desc.nz;
+        A.fs_shift_b = f.shift_b;
+        A.fs_step = f.step;
+        A.fs_tau = f.tau;
+        const int nf[3] = {dd->nx, dd->ny, dd->nz}, nc[3] = {f.desc.nx, f.desc.ny, f.desc.nz};
+        for (int a = 0; a < 3; ++a) {
+            // u_c = (x - min_c) sc_c with x = min_f + u_f / sf:  u_c = (min_f - min_c) sc_c + u_f sc_c / sf
+            const double sf = (nf[a] - 1) / ((double)dd->xyz_max[a] - dd->xyz_min[a]);
+            const double sc = (nc[a] - 1) / ((double)f.desc.xyz_max[a] - f.desc.xyz_min[a]);
+            A.fs_scale[a] = llrint(sc / sf * 0x1p48);
+            A.fs_off[a] = llrint(((double)dd->xyz_min[a] - f.desc.xyz_min[a]) * sc * 0x1p40);
+        }
+    }
     if (mlp) {
         A.w1 = mlp->w1;
         A.b1 = mlp->b1;

@@ -96,7 +96,16 @@ struct RenderArgs {
     // MLP
     const float *w1, *b1, *w2, *b2, *w3, *b3;
     int in_dim;
+    // known free space (fine stage, nullable fs_density): the coarse grid and the affine map of
+    // fine lattice coordinates onto its lattice, u_c = fs_off + u_f * fs_scale / 2^kFsScaleBits
+    // (both fixed point; fs_off with kFxBits fractional bits)
+    const float *fs_density;
+    int fs_nx, fs_ny, fs_nz;
+    float fs_shift_b, fs_step, fs_tau;
+    long long fs_scale[3], fs_off[3];
 };
+
+constexpr int kFsScaleBits = 48;
 
 // ---------------------------------------------------------------------------------------------
 // Device helpers
@@ -189,12 +198,11 @@ __device__ __forceinline__ float corner_weight(const Cell &c, int q) {
     return wx * wy * wz;
 }
 
-// Cell and step length of sample k of a ray: uniform stepping (t_k = t_enter + (k + p) step, so
-// u_k = u_0 + k (step e) in integer arithmetic) or the explicit list (u = u_entry + (t - t_enter) e,
-// the offset in FP64).
-__device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r, int ray, int k, float &dt) {
-    Cell c;
-    long long u[3];
+// Fixed-point lattice coordinate and step length of sample k of a ray: uniform stepping
+// (t_k = t_enter + (k + p) step, so u_k = u_0 + k (step e) in integer arithmetic) or the explicit
+// list (u = u_entry + (t - t_enter) e, the offset in FP64).
+__device__ __forceinline__ void sample_fx(const RenderArgs &A, const RayRec &r, int ray, int k, float &dt,
+                                          long long u[3]) {
     if (A.ts) {
         const double t = (double)A.ts[(long long)ray * A.n_expl + k];
         dt = A.dts[(long long)ray * A.n_expl + k];
@@ -205,10 +213,35 @@ __device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = r.u0fx[a] + (long long)k * r.dfx[a];
     }
-    fx_axis(u[0], A.nx, c.i0, c.fx);
-    fx_axis(u[1], A.ny, c.j0, c.fy);
-    fx_axis(u[2], A.nz, c.k0, c.fz);
+}
+
+__device__ __forceinline__ Cell cell_from_fx(const long long u[3], int nx, int ny, int nz) {
+    Cell c;
+    fx_axis(u[0], nx, c.i0, c.fx);
+    fx_axis(u[1], ny, c.j0, c.fy);
+    fx_axis(u[2], nz, c.k0, c.fz);
     return c;
+}
+
+// Cell and step length of sample k of a ray.
+__device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r, int ray, int k, float &dt) {
+    long long u[3];
+    sample_fx(A, r, ray, k, dt, u);
+    return cell_from_fx(u, A.nx, A.ny, A.nz);
+}
+
+// Known-free-space test of Sec. 4.2 at a sample with fine lattice coordinate u: the coarse grid's
+// post-activated alpha, 1 - exp(-softplus(interp(x, V_c) + b_c) delta_c), below tau_c.
+__device__ __forceinline__ bool known_free(const RenderArgs &A, const long long u[3]) {
+    long long uc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        uc[a] = A.fs_off[a] + (long long)(((__int128)u[a] * (__int128)A.fs_scale[a]) >> kFsScaleBits);
+    const Cell c = cell_from_fx(uc, A.fs_nx, A.fs_ny, A.fs_nz);
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), __ldg(A.fs_density + corner_index(c, q, A.fs_ny, A.fs_nz)), s);
+    return -expm1f(-softplusf(s + A.fs_shift_b) * A.fs_step) < A.fs_tau;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -1,9 +1,11 @@
 // fine_ray.cu -- the per-ray kernels of the fine-stage render (Sec. 4.2).
 //
-// fine_density:   warp per ray.  For each sample k of the ray: position, density gather,
-//                 sigma_ddot = interp(x, V_density) (Eq. fine_queries_densities),
-//                 tau_k = softplus(sigma_ddot + b) * dt_k (Eq. density_activation, post-activation),
-//                 removed when alpha_k = 1 - exp(-tau_k) < tau_f (Sec. 4.2 free space skipping).
+// fine_density:   warp per ray.  For each sample k of the ray: position; optionally the
+//                 known-free-space test on the coarse grid (Sec. 4.2), which removes the sample
+//                 before any fine query; density gather, sigma_ddot = interp(x, V_density)
+//                 (Eq. fine_queries_densities), tau_k = softplus(sigma_ddot + b) * dt_k
+//                 (Eq. density_activation, post-activation), removed when
+//                 alpha_k = 1 - exp(-tau_k) < tau_f (Sec. 4.2 free space skipping).
 //                 Writes tau_k to the sample slot and appends kept samples to a compact list
 //                 (one atomic per warp chunk, lane order kept) for the colour kernel.
 // fine_composite: warp per ray.  T_k = exp(-sum_{j<k} tau_j), w_k = T_k alpha_k,
@@ -39,14 +41,18 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
             bool kept = false;
             if (valid) {
                 float dt;
-                Cell c = sample_cell(A, rr, r, k, dt);
-                float s = 0.0f;
+                long long u[3];
+                sample_fx(A, rr, r, k, dt, u);
+                if (!(A.fs_density && known_free(A, u))) {   // known free space: no fine query
+                    const Cell c = cell_from_fx(u, A.nx, A.ny, A.nz);
+                    float s = 0.0f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
-                tau = softplusf(s + A.shift_b) * dt;
-                kept = !(-expm1f(-tau) < A.tau_f);
-                if (!kept) tau = 0.0f;
+                    for (int q = 0; q < 8; ++q)
+                        s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
+                    tau = softplusf(s + A.shift_b) * dt;
+                    kept = !(-expm1f(-tau) < A.tau_f);
+                    if (!kept) tau = 0.0f;
+                }
                 A.samp[rr.off + k] = make_float4(tau, 0.0f, 0.0f, 0.0f);
             }
             unsigned m = __ballot_sync(FULL, kept);

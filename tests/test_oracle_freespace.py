@@ -7,14 +7,14 @@ import oracle
 import synth
 
 
-def _coarse(res=12, seed=70):
+def _coarse(res=12, seed=70, r_in=0.35, r_out=0.6, v_in=8.0):
     """Coarse raw density: known free (-20) except a ball of high density and a shell of values
     that straddle the threshold."""
     g = np.linspace(-1.0, 1.0, res)
     X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
     r = np.sqrt((X - 0.2) ** 2 + (Y + 0.1) ** 2 + (Z - 0.05) ** 2)
-    v = np.where(r < 0.35, 8.0, -20.0)
-    shell = (r >= 0.35) & (r < 0.6)
+    v = np.where(r < r_in, v_in, -20.0)
+    shell = (r >= r_in) & (r < r_out)
     v[shell] = synth.normal_grid((res,) * 3, 1, 3.0, seed)[shell] - 6.0
     return v
 
