@@ -480,15 +480,37 @@ def run_time_to_psnr(args):
     t_coarse = timed_loop(coarse_step, args.coarse_steps)
 
     # ---------------- fine-stage initial state (shared by both forms) ----------------
-    rf = RES
-    b_f = dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / rf)
-    # same activated density on the finer lattice: raw_f = resize(raw_c) + b_c - b_f (trilinear, Sec. 4.2)
-    dens0 = F.interpolate(coarse.density[None, None], size=(rf,) * 3, mode="trilinear", align_corners=True)[0, 0]
+    box = ((-1.0,) * 3, (1.0,) * 3)
+    fshape, s_f = (RES,) * 3, 2.0 / RES
+    freespace, tau_f, recipe = None, 0.0, {"name": "full-box", "grid": list(fshape), "box": box}
+    if args.fine_recipe == "paper":
+        # Sec. 4.2: known free space of the coarse grid (tau_c = 1e-3), the fine grid allocated on the
+        # box of the unknown space with M_f = 160^3 voxels, and tau_f = 1e-4 (Supp. A)
+        freespace = dvgo.FreeSpace(density=coarse.density, desc=dvgo.GridDesc((rc,) * 3, 1), shift_b=pc.shift_b,
+                                   step=pc.step, tau=1e-3)
+        bb = dvgo.dvgo_unknown_bbox(freespace).cpu().numpy()
+        h = 2.0 / (rc - 1)
+        bmin, bmax = -1.0 + bb[1:4] * h, -1.0 + bb[4:7] * h
+        ext = bmax - bmin
+        s_f = float(np.prod(ext) / RES ** 3) ** (1.0 / 3.0)
+        fshape = tuple(int(v) for v in np.floor(ext / s_f))
+        box = (tuple(float(v) for v in bmin), tuple(float(v) for v in bmax))
+        tau_f = 1e-4
+        recipe = {"name": "paper (coarse known free space tau_c=1e-3, fine box from the coarse grid, tau_f=1e-4)",
+                  "grid": list(fshape), "box": box, "unknown_coarse_points": int(bb[0])}
+    b_f = dvgo.dvgo_shift_from_alpha_init(1e-2, s_f)
+    # same activated density on the finer lattice: raw_f = resize(raw_c) + b_c - b_f (trilinear, Sec. 4.2);
+    # the fine lattice points are sampled from the coarse grid (whose box is [-1, 1]^3)
+    axes = [torch.linspace(box[0][a], box[1][a], fshape[a], device=dev) for a in range(3)]
+    X, Y, Z = torch.meshgrid(*axes, indexing="ij")
+    where = torch.stack([Z, Y, X], dim=-1)[None]          # grid_sample wants (x = last axis, y, z)
+    dens0 = F.grid_sample(coarse.density[None, None], where, mode="bilinear", align_corners=True)[0, 0]
     dens0 = (dens0 + (pc.shift_b - b_f)).contiguous()
-    feat0 = torch.as_tensor(synth.normal_grid((rf,) * 3, FEAT, 1e-2, seed=11), device=dev)
+    feat0 = torch.as_tensor(synth.normal_grid(fshape, FEAT, 1e-2, seed=11), device=dev)
     mlp0 = torch.as_tensor(mlp_flat(synth.mlp_weights(39, HID, 3, seed=12)), device=dev)
-    p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / rf, shift_b=b_f, bg=(1.0, 1.0, 1.0))
-    dd, cd32 = dvgo.GridDesc((rf,) * 3, 1), dvgo.GridDesc((rf,) * 3, FEAT)
+    p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
+                         freespace=freespace)
+    dd, cd32 = dvgo.GridDesc(fshape, 1, box[0], box[1]), dvgo.GridDesc(fshape, FEAT, box[0], box[1])
     eval_r = dvgo.Renderer(p_eval, dd, cd32, NRAYS)
 
     def psnr(model, n_rays):
@@ -511,10 +533,10 @@ def run_time_to_psnr(args):
     results = {}
     for form in forms:
         bf16, use_prop = form_defs[form]
-        p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / rf, shift_b=b_f, bg=(1.0, 1.0, 1.0),
-                        mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32)
+        p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0),
+                        mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace)
         model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16,
-                               overlap_adam=use_prop)
+                               overlap_adam=use_prop, box=box)
         prop = trainer = None
         if use_prop:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p, model.dd, NRAYS,
@@ -562,6 +584,7 @@ def run_time_to_psnr(args):
             "coarse_steps": args.coarse_steps, "coarse_s": t_coarse, "fine_steps": args.fine_steps,
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
+            "fine_recipe": recipe,
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
             "forms": results}
@@ -685,6 +708,9 @@ def main():
     ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
     ap.add_argument("--prop-warmup", type=int, default=0)
     ap.add_argument("--stress-rays", type=int, default=65536, help="rays per batch of the 256^3 stress workload")
+    ap.add_argument("--fine-recipe", choices=["full-box", "paper"], default="full-box",
+                    help="time-to-psnr fine stage: 160^3 on the full box, or the paper's Sec. 4.2 recipe "
+                         "(fine box from the coarse grid's unknown space, known-free-space and tau_f skipping)")
     # frozen from the first full plain run: its final held-out PSNR (2 views) 29.391 dB - 0.5 dB
     ap.add_argument("--psnr-target", type=float, default=28.891)
     args = ap.parse_args()
