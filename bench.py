@@ -654,6 +654,53 @@ def run_stress(args):
                       "clocks": clk}), flush=True)
 
 
+def run_render(args):
+    """Test-time rendering (forward only) of full 800x800 frames of the config-2 scene (160^3 density
+    of 8 balls, 12-channel features, MLP 39-128-128-3, 0.5-voxel steps) in 65,536-ray chunks, FP32 and
+    BF16 MLP, without skipping and with the paper's test-time skipping of samples below
+    tau_f = 1e-4 (Sec. 4.2).  The paper's figure for context: 0.64 s per 800x800 frame on an
+    RTX 2080 Ti (Sec. 5, trained Synthetic-NeRF scenes)."""
+    import torch
+    import synth
+    import paper_2111_11215_gb300 as dvgo
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    dens, feat, mlp, _ = workload()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
+    D, Fe, flat = t(dens), t(feat), t(mlp_flat(mlp))
+    Fb = Fe.to(torch.bfloat16)
+    views = dvgo.mlp_views(flat)
+    rig = synth.hemisphere_rig(args.frames, seed=4242)
+    o, d = synth.rig_rays_torch(rig, dev)
+    n_px = rig.height * rig.width
+    dd = dvgo.GridDesc((RES,) * 3, 1)
+    out = {}
+    for name, prec, tau_f in (("fp32", dvgo.DVGO_MLP_FP32, 0.0), ("fp32_skip", dvgo.DVGO_MLP_FP32, 1e-4),
+                              ("bf16", dvgo.DVGO_MLP_BF16, 0.0), ("bf16_skip", dvgo.DVGO_MLP_BF16, 1e-4)):
+        p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / RES, bg=(1.0, 1.0, 1.0), mlp_prec=prec, tau_f=tau_f,
+                        shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES))
+        bf = prec == dvgo.DVGO_MLP_BF16
+        cd = dvgo.GridDesc((RES,) * 3, FEAT, dtype=dvgo.DVGO_DTYPE_BF16 if bf else dvgo.DVGO_DTYPE_F32)
+        fr = dvgo.FrameRenderer(p, dd, cd, chunk=65536)
+        grid = Fb if bf else Fe
+        fr.render(D, grid, views, o[:n_px], d[:n_px])          # warm-up frame
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rgb, _ = fr.render(D, grid, views, o, d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"s_per_frame": ms / 1e3 / args.frames, "rays_per_s": o.shape[0] / (ms / 1e3),
+                     "mean_rgb": float(rgb.mean().item())}
+    print(json.dumps({"metric": "test-time render, 800x800 frames", "workload": "render", "unit": "s/frame",
+                      "higher_is_better": False, "value": out["bf16_skip"]["s_per_frame"], "frames": args.frames,
+                      "chunk_rays": 65536, "data": "synthetic (config-2 scene: 8 balls of raw density 50, smooth albedo)",
+                      "forms": out, "paper_context": "0.64 s/frame on an RTX 2080 Ti (trained Synthetic-NeRF scenes)"}),
+          flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2111_11215_gb300 as dvgo
@@ -697,7 +744,8 @@ def main():
     ap.add_argument("--ref-rays", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal-eval", action="store_true")
-    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress"], default="step")
+    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render"], default="step")
+    ap.add_argument("--frames", type=int, default=8, help="render workload: 800x800 frames timed")
     ap.add_argument("--coarse-steps", type=int, default=5000)
     ap.add_argument("--fine-steps", type=int, default=20000)
     ap.add_argument("--eval-every", type=int, default=1000)
@@ -737,6 +785,10 @@ def main():
     if args.workload == "stress":
         if rank == 0:
             run_stress(args)
+        return
+    if args.workload == "render":
+        if rank == 0:
+            run_render(args)
         return
     run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -15,5 +15,6 @@ from .binding import (  # noqa: F401
     dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS, FreeSpace, dvgo_unknown_bbox,
 )
 from .render import (  # noqa: F401
-    AdamState, CoarseModel, FineModel, Proposal, ProposalTrainer, Renderer, RenderFunction, mlp_flat_size, mlp_views,
+    AdamState, CoarseModel, FineModel, FrameRenderer, Proposal, ProposalTrainer, Renderer, RenderFunction,
+    mlp_flat_size, mlp_views,
 )

@@ -60,6 +60,27 @@ class Renderer:
                           grad_rgb, grad_tfinal, grad_density, grad_cgrid, grad_mlp, self.workspace, stream)
 
 
+class FrameRenderer:
+    """Forward-only rendering of any number of rays (e.g. full frames at test time) in fixed-size
+    chunks through one workspace; free-space skipping (tau_f, params.freespace) applies as in
+    training (Sec. 4.2: "in both training and testing")."""
+
+    def __init__(self, params: B.Params, density_desc: B.GridDesc, cgrid_desc: B.GridDesc, chunk: int = 65536,
+                 device="cuda"):
+        self.chunk = int(chunk)
+        self.renderer = Renderer(params, density_desc, cgrid_desc, self.chunk, device=device)
+
+    def render(self, density, cgrid, mlp, rays_o, rays_d, rgb=None, tfinal=None, stream=None):
+        R, dev = rays_o.shape[0], rays_o.device
+        rgb = torch.empty((R, 3), device=dev) if rgb is None else rgb
+        tfinal = torch.empty(R, device=dev) if tfinal is None else tfinal
+        for s in range(0, R, self.chunk):
+            e = min(R, s + self.chunk)
+            self.renderer.forward(density, cgrid, mlp, rays_o[s:e], rays_d[s:e], None, None, None, rgb[s:e],
+                                  tfinal[s:e], stream=stream)
+        return rgb, tfinal
+
+
 class RenderFunction(torch.autograd.Function):
     """(density, cgrid, mlp_flat) -> (rgb, T_final) with the library's backward.
 

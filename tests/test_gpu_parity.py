@@ -296,3 +296,19 @@ def test_adam_parity_and_bf16_copy():
     assert_close(M.cpu().numpy(), mo, 1e-5, "m")
     assert_close(V.cpu().numpy(), vo, 1e-5, "v")
     assert torch.equal(pb, P.to(torch.bfloat16))
+
+
+def test_frame_renderer_chunks_match_one_batch():
+    """Forward-only rendering in chunks through one workspace gives the same colours, bit for bit,
+    as one batch (every value of a ray depends only on that ray), including a ragged last chunk."""
+    res, R = 24, 1000
+    dens, feat, mlp, o, d, _, _ = _fine_inputs(res, R, seed=40)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=2.0 / res * 0.5, bg=(1.0, 1.0, 1.0), tau_f=1e-4,
+                    shift_b=dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / res))
+    dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12)
+    views = dvgo.render.mlp_views(cuda(_mlp_flat(mlp)))
+    D, F, ro, rd = cuda(dens), cuda(feat), cuda(o), cuda(d)
+    one, t_one, _ = dvgo.Renderer(p, dd, cd, R).forward(D, F, views, ro, rd)
+    rgb, tf = dvgo.FrameRenderer(p, dd, cd, chunk=384).render(D, F, views, ro, rd)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, one) and torch.equal(tf, t_one)
