@@ -62,6 +62,13 @@ typedef struct {
     double tau_f;      /* skip threshold on alpha (Sec. 4.2 free space skipping)                 */
     double t_near, t_far;
     double bg[3];      /* background colour c_bg of Eq. volume_rendering                         */
+    /* Auxiliary losses (Supp. A weights w_pt_rgb, w_bg; used when a target is given):
+     *   per-point rgb loss  L_pt = (1/R) sum_r sum_k w_k ||c_k - C_r||^2 with the compositing
+     *                       weights w_k = T_k alpha_k held constant (it supervises the emitted colour
+     *                       of every query point, Supp. "Effect of the auxiliary losses");
+     *   background entropy  L_bg = (1/R) sum_r H(A_r), H(a) = -a log a - (1 - a) log(1 - a) of the
+     *                       accumulated alpha A_r = 1 - T_K,r clamped to [1e-6, 1 - 1e-6]. */
+    double w_pt, w_bg;
 } og_params;
 
 /* Known free space (Sec. 4.2): the optimised coarse-stage density grid with its own lattice,
@@ -94,6 +101,21 @@ typedef struct {
 /* ------------------------------------------------------------------------------------------ */
 
 static double og_softplus(double z) { return (z > 0 ? z : 0.0) + log1p(exp(-fabs(z))); }
+
+#define OG_BG_EPS 1e-6
+/* Background entropy of the accumulated alpha a = 1 - T_K (clamped) and its derivative d/dT_K
+ * (zero where the clamp is active): dH/dT = -dH/da = log(a / (1 - a)). */
+static double og_bg_entropy(double TK) {
+    double a = 1.0 - TK;
+    if (a < OG_BG_EPS) a = OG_BG_EPS;
+    if (a > 1.0 - OG_BG_EPS) a = 1.0 - OG_BG_EPS;
+    return -a * log(a) - (1.0 - a) * log(1.0 - a);
+}
+static double og_bg_entropy_dT(double TK) {
+    double a = 1.0 - TK;
+    if (a < OG_BG_EPS || a > 1.0 - OG_BG_EPS) return 0.0;
+    return log(a) - log(1.0 - a);
+}
 static double og_sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
 
 int oracle_num_threads(void) {
@@ -337,7 +359,8 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                           const double d[3], double p, int n_expl, const double *ts,
                           const double *dts, double rgb[3], double *tfinal, int *nsamp,
                           double *tin, double *tout, const double *gC, double gT, og_grads *G,
-                          og_grads *L, double *wbins, int nbins) {
+                          og_grads *L, double *wbins, int nbins, const double *tgt, double aux_scale,
+                          double *aux_loss) {
     double dn[3], t_enter, t_exit;
     int n;
     oracle_ray_bounds(P, o, d, p, &t_enter, &t_exit, dn, &n);
@@ -354,7 +377,7 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
     double *feat = (double *)malloc(sizeof(double) * (C > 0 ? C : 1));
 
     /* Forward: sample, query, composite (Eq. volume_rendering). */
-    double T = 1.0, acc[3] = {0, 0, 0};
+    double T = 1.0, acc[3] = {0, 0, 0}, pt = 0.0;
     for (int k = 0; k < n; ++k) {
         og_sample *s = &S[k];
         if (ts) {
@@ -395,10 +418,13 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
         }
         double w = T * s->alpha;
         for (int ch = 0; ch < 3; ++ch) acc[ch] += w * s->c[ch];
+        if (tgt)
+            for (int ch = 0; ch < 3; ++ch) pt += w * (s->c[ch] - tgt[ch]) * (s->c[ch] - tgt[ch]);
         T = T * (1.0 - s->alpha);
     }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] = acc[ch] + T * P->bg[ch];
     *tfinal = T;
+    if (aux_loss) *aux_loss = tgt ? P->w_pt * pt + P->w_bg * og_bg_entropy(T) : 0.0;
 
     /* Optional: per-ray histogram of normalised compositing weights over nbins equal bins of
      * [t_enter, t_exit] (labels for the sample proposal). */
@@ -431,7 +457,9 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             og_sample *s = &S[k];
             double w = Tk[k] * s->alpha;
             if (s->kept) {
-                double dtau = -gT * Tk[n];
+                /* the background entropy enters through T_K like gT */
+                double gTe = gT + (tgt ? P->w_bg * aux_scale * og_bg_entropy_dT(Tk[n]) : 0.0);
+                double dtau = -gTe * Tk[n];
                 for (int ch = 0; ch < 3; ++ch) dtau += gC[ch] * (Tk[k + 1] * s->c[ch] - Ssuf[ch]);
                 double dz = dtau * s->dt * og_sigmoid(s->z);
                 for (int c = 0; c < 8; ++c) {
@@ -439,7 +467,11 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                     G->density[s->idx[c]] += dz * s->cw[c];
                 }
                 double dc[3];
-                for (int ch = 0; ch < 3; ++ch) dc[ch] = gC[ch] * w;
+                for (int ch = 0; ch < 3; ++ch) {
+                    dc[ch] = gC[ch] * w;
+                    /* per-point rgb loss: w_k held constant, d/dc_k = 2 w_k (c_k - C) */
+                    if (tgt) dc[ch] += P->w_pt * aux_scale * 2.0 * w * (s->c[ch] - tgt[ch]);
+                }
                 if (P->mode == 0) {
                     for (int ch = 0; ch < 3; ++ch) {
                         double g = dc[ch];
@@ -504,9 +536,11 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
  * Explicit-sample mode when ts != NULL: ray r uses n_expl samples ts[r*n_expl + j] with deltas
  * dts[...] (a ray that misses the box still gets none).
  * Outputs rgb [R][3], tfinal [R], nsamp [R], t_enter/t_exit [R] (each nullable except rgb).
- * If target != NULL, *loss = (1/R) sum (C_hat - C)^2 (Eq. photo_loss).
- * If gC != NULL (per-ray dL/dC_hat, [R][3]) the gradients of sum_r (gC_r . C_hat_r + gT_r T_r)
- * are ACCUMULATED into G (gT nullable = 0).  wbins (nullable): [R][nbins] weight histograms.
+ * If target != NULL, *loss = (1/R) sum (C_hat - C)^2 (Eq. photo_loss) + w_pt L_pt + w_bg L_bg
+ * (the auxiliary losses of og_params, zero with zero weights).
+ * If gC != NULL (per-ray dL/dC_hat, [R][3]) the gradients of sum_r (gC_r . C_hat_r + gT_r T_r),
+ * plus those of w_pt L_pt + w_bg L_bg when target != NULL, are ACCUMULATED into G (gT nullable
+ * = 0).  wbins (nullable): [R][nbins] weight histograms.
  */
 void oracle_render(const og_params *P, const og_model *M, int R, const double *rays_o,
                    const double *rays_d, const double *jitter, int n_expl, const double *ts,
@@ -517,6 +551,7 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
     /* Sizes of the MLP parameter blocks w1, b1, w2, b2, w3, b3. */
     long nw[6] = {(long)I * H, H, (long)H * H, H, (long)H * 3, 3};
     int want_mlp = (gC != NULL) && (P->mode == 1);
+    double *aux = target ? (double *)calloc(R > 0 ? R : 1, sizeof(double)) : NULL;
 #pragma omp parallel
     {
         /* Thread-local MLP gradient buffers (summed into G at the end); grid gradients are
@@ -545,7 +580,8 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
                           dts ? dts + (size_t)r * n_expl : NULL, rgb + 3 * r, &tf,
                           nsamp ? nsamp + r : NULL, t_enter ? t_enter + r : NULL,
                           t_exit ? t_exit + r : NULL, gC ? gC + 3 * r : NULL, gT ? gT[r] : 0.0,
-                          G, &L, wbins ? wbins + (size_t)r * nbins : NULL, nbins);
+                          G, &L, wbins ? wbins + (size_t)r * nbins : NULL, nbins,
+                          target ? target + 3 * r : NULL, R > 0 ? 1.0 / R : 0.0, aux ? aux + r : NULL);
             if (tfinal) tfinal[r] = tf;
         }
         if (want_mlp) {
@@ -563,8 +599,10 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
             double e = rgb[i] - target[i];
             Ls += e * e;
         }
+        for (long r = 0; r < R; ++r) Ls += aux[r];    /* auxiliary losses (zero weights: zero) */
         *loss = R > 0 ? Ls / R : 0.0;
     }
+    free(aux);
 }
 
 /* ------------------------------------------------------------------------------------------ */
