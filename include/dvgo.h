@@ -94,6 +94,13 @@ typedef struct {
     float t_near, t_far; /* ray clip range before the box intersection                           */
     float bg[3];         /* c_bg of Eq. volume_rendering                                          */
     const dvgo_freespace *freespace;   /* fine stage only, nullable: skip the known free space   */
+    /* Auxiliary losses of Supp. A, added when dvgo_render_fwd gets a target (0 disables):
+     *   w_pt_rgb: per-point rgb loss L_pt = (1/R) sum_r sum_k w_k ||c_k - C_r||^2 with the
+     *             compositing weights w_k held constant (the loss supervises each point's colour);
+     *   w_bg:     background entropy L_bg = (1/R) sum_r H(A_r), H the natural-log binary entropy of
+     *             the accumulated alpha A = 1 - T_K clamped to [1e-6, 1 - 1e-6].
+     * Supp. A: 1e-1 / 1e-2 in the coarse stage, 1e-2 / 1e-3 in the fine stage.                 */
+    float w_pt_rgb, w_bg;
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
@@ -133,8 +140,9 @@ size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, 
  *   rays_o, rays_d [n_rays*3] FP32; jitter [n_rays] in [0,1) or NULL (p = 0.5);
  *   target [n_rays*3] or NULL.
  * Outputs: rgb_out [n_rays*3]; tfinal_out [n_rays] (T_K) or NULL; if target is given,
- *   loss_out[0] = (1/R) sum_r ||C_hat_r - C_r||^2 (Eq. photo_loss) and dloss_drgb_out
- *   [n_rays*3] = 2 (C_hat - C) / R, each nullable.
+ *   loss_out[0] = (1/R) sum_r ||C_hat_r - C_r||^2 (Eq. photo_loss) + w_pt_rgb L_pt + w_bg L_bg and
+ *   dloss_drgb_out [n_rays*3] = 2 (C_hat - C) / R (the photometric part), each nullable; with
+ *   non-zero auxiliary weights the workspace keeps the targets for dvgo_render_bwd.
  * The workspace keeps the per-ray and per-sample state that dvgo_render_bwd consumes; it must
  * not be modified between the two calls, which must see the same inputs.
  */
@@ -147,7 +155,8 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, co
 
 /*
  * Backward of dvgo_render_fwd: accumulates into the gradients the derivative of
- *     sum_r ( grad_rgb_r . C_hat_r + grad_tfinal_r * T_K,r )
+ *     sum_r ( grad_rgb_r . C_hat_r + grad_tfinal_r * T_K,r ),
+ * plus that of w_pt_rgb L_pt + w_bg L_bg when the forward had a target and non-zero weights
  * with respect to the density grid, the colour / feature grid and the MLP parameters.
  * Compositing state (T_k, the weights and the suffix colour sums) is recomputed from the
  * per-sample values the forward left in the workspace; the MLP activations are recomputed.

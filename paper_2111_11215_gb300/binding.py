@@ -57,7 +57,7 @@ class _Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("rgb_act", C.c_int), ("mlp_prec", C.c_int), ("n_freq_dir", C.c_int),
                 ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
-                ("freespace", C.POINTER(_FreeSpace))]
+                ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float)]
 
 
 class _Mlp(C.Structure):
@@ -179,6 +179,8 @@ class Params:
     n_freq_dir: int = 4
     hidden: int = 128
     freespace: FreeSpace | None = None
+    w_pt_rgb: float = 0.0        # per-point rgb loss weight (Supp. A)
+    w_bg: float = 0.0            # background entropy loss weight (Supp. A)
 
     def c(self) -> _Params:
         p = _Params()
@@ -187,6 +189,7 @@ class Params:
         p.step, p.shift_b, p.tau_f = float(self.step), float(self.shift_b), float(self.tau_f)
         p.t_near, p.t_far = float(self.t_near), float(self.t_far)
         p.bg[:] = [float(v) for v in self.bg]
+        p.w_pt_rgb, p.w_bg = float(self.w_pt_rgb), float(self.w_bg)
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)

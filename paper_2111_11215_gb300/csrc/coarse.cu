@@ -87,9 +87,13 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     float loss_part = 0.0f;
+    const bool aux = A.target && (A.w_pt != 0.0f || A.w_bg != 0.0f);
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
-        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        float tg[3] = {0.0f, 0.0f, 0.0f};
+        if (aux)
+            for (int ch = 0; ch < 3; ++ch) tg[ch] = A.target[3 * r + ch];
+        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f}, pt = 0.0f;
         for (int base = 0; base < rr.n; base += 32) {
             int k = base + lane;
             CoarseSample S;
@@ -102,11 +106,16 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
             float T = expf(-(carry + excl));
             float w = T * -expm1f(-S.tau);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(w, S.c[ch], acc[ch]);
+            for (int ch = 0; ch < 3; ++ch) {
+                acc[ch] = fmaf(w, S.c[ch], acc[ch]);
+                const float e = S.c[ch] - tg[ch];
+                pt = fmaf(w * e, e, pt);          // per-point rgb loss
+            }
             carry += __shfl_sync(FULL, incl, 31);
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) acc[ch] = warp_sum(acc[ch]);
+        if (aux) pt = warp_sum(pt);
         if (lane == 0) {
             float TK = expf(-carry);
             float rgb[3];
@@ -120,6 +129,10 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
                     loss_part = fmaf(e, e, loss_part);
                     if (A.dloss_out) A.dloss_out[3 * r + ch] = 2.0f * e / (float)A.R;
                 }
+            }
+            if (aux) {
+                loss_part += A.w_pt * pt + A.w_bg * bg_entropy(TK);
+                A.rtarget[r] = make_float4(tg[0], tg[1], tg[2], 0.0f);
             }
         }
     }
@@ -152,7 +165,15 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
         const int nch = (rr.n + 31) >> 5;
         const float TK = A.rayout[r].w;
         const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
-        const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
+        // auxiliary losses of the forward: the background entropy enters through T_K, the
+        // per-point rgb loss adds 2 w_pt w_k (c_k - C) / R to dL/dc_k
+        const bool aux = A.hdr->aux != 0;
+        float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (aux) tg = A.rtarget[r];
+        const float tgc[3] = {tg.x, tg.y, tg.z};
+        const float gT = (A.grad_tfinal ? A.grad_tfinal[r] : 0.0f) +
+                         (aux ? A.w_bg * bg_entropy_dT(TK) / (float)A.R : 0.0f);
+        const float kpt = aux ? 2.0f * A.w_pt / (float)A.R : 0.0f;
         float carry = 0.0f;
         for (int ci = 0; ci < nch; ++ci) {
             int k = ci * 32 + lane;
@@ -202,7 +223,7 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
             float dc[3];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                float gc = g[ch] * w;
+                float gc = g[ch] * w + kpt * w * (S.c[ch] - tgc[ch]);
                 if (A.rgb_act) gc *= S.c[ch] * (1.0f - S.c[ch]);
                 dc[ch] = act ? gc : 0.0f;
             }

@@ -83,6 +83,7 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
     if (!same_lattice(dd, cd)) return DVGO_ERR_INVALID_ARG;
     if (!finite_pos(p->step) || !isfinite(p->shift_b) || !isfinite(p->tau_f) || isnan(p->t_near) || isnan(p->t_far))
         return DVGO_ERR_INVALID_ARG;
+    if (!isfinite(p->w_pt_rgb) || !isfinite(p->w_bg)) return DVGO_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
         if (!isfinite(p->bg[c])) return DVGO_ERR_INVALID_ARG;
     if (p->mode == DVGO_MODE_COARSE) {
@@ -149,6 +150,9 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.hdr = reinterpret_cast<WsHeader *>(b + L.header);
     A.rays = reinterpret_cast<RayRec *>(b + L.rays);
     A.rayout = reinterpret_cast<float4 *>(b + L.rayout);
+    A.rtarget = reinterpret_cast<float4 *>(b + L.rtarget);
+    A.w_pt = p->w_pt_rgb;
+    A.w_bg = p->w_bg;
     if (p->mode == DVGO_MODE_FINE) {
         A.pe = reinterpret_cast<float *>(b + L.pe);
         A.texit = reinterpret_cast<double *>(b + L.texit);

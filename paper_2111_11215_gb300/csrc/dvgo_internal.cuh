@@ -54,13 +54,14 @@ struct WsHeader {
     int n_kept;          // fine stage: samples kept after the tau_f test
     unsigned done;       // block-completion counter of the loss reduction
     float loss_acc;      // sum over rays of ||C_hat - C||^2
-    int pad[59];
+    int aux;             // 1: the last forward had a target and auxiliary loss weights (rtarget valid)
+    int pad[58];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader size");
 
 // Workspace layout; every block 256-byte aligned.
 struct WsLayout {
-    size_t header, rays, rayout, pe, texit, samp, sgrad, kept, total;
+    size_t header, rays, rayout, rtarget, pe, texit, samp, sgrad, kept, total;
     long long max_samples;
 };
 
@@ -82,6 +83,8 @@ struct RenderArgs {
     WsHeader *hdr;
     RayRec *rays;
     float4 *rayout;             // per ray: C_hat (xyz), T_K (w)
+    float4 *rtarget;            // per ray: the forward's target (auxiliary losses)
+    float w_pt, w_bg;           // auxiliary loss weights
     float *pe;                  // fine: per ray [d (3), sin (12), cos (12), 0 x 5] (kPeStride floats)
     double *texit;              // fine: per ray clipped exit distance
     float4 *samp;               // per sample slot: (tau, r, g, b)
@@ -117,6 +120,19 @@ __device__ __forceinline__ float softplusf(float z) {
 }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Background entropy loss term (Supp. A): natural-log binary entropy of the accumulated alpha
+// a = 1 - T_K clamped to [1e-6, 1 - 1e-6], and its derivative with respect to T_K,
+// log(a) - log(1 - a), which is 0 where the clamp is active.
+constexpr float kBgEps = 1e-6f;
+__device__ __forceinline__ float bg_entropy(float TK) {
+    const float a = fminf(fmaxf(1.0f - TK, kBgEps), 1.0f - kBgEps);
+    return -a * logf(a) - (1.0f - a) * log1pf(-a);
+}
+__device__ __forceinline__ float bg_entropy_dT(float TK) {
+    const float a = 1.0f - TK;
+    return (a < kBgEps || a > 1.0f - kBgEps) ? 0.0f : logf(a) - log1pf(-a);
+}
 
 // FP64 value -> fixed point (round to nearest).
 __device__ __forceinline__ long long to_fx(double v) { return __double2ll_rn(v * 0x1p40); }

@@ -96,9 +96,13 @@ __global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     float loss_part = 0.0f;
+    const bool aux = A.target && (A.w_pt != 0.0f || A.w_bg != 0.0f);
     for (int r = warp; r < A.R; r += nwarps) {
         const int n = A.rays[r].n, off = A.rays[r].off;
-        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
+        float tg[3] = {0.0f, 0.0f, 0.0f};
+        if (aux)
+            for (int ch = 0; ch < 3; ++ch) tg[ch] = A.target[3 * r + ch];
+        float carry = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f}, pt = 0.0f;
         for (int base = 0; base < n; base += 32) {
             int k = base + lane;
             float4 sv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -110,10 +114,13 @@ __global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
             acc[0] = fmaf(w, sv.y, acc[0]);
             acc[1] = fmaf(w, sv.z, acc[1]);
             acc[2] = fmaf(w, sv.w, acc[2]);
+            const float e0 = sv.y - tg[0], e1 = sv.z - tg[1], e2 = sv.w - tg[2];
+            pt = fmaf(w, fmaf(e0, e0, fmaf(e1, e1, e2 * e2)), pt);   // per-point rgb loss
             carry += __shfl_sync(FULL, incl, 31);
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) acc[ch] = warp_sum(acc[ch]);
+        if (aux) pt = warp_sum(pt);
         if (lane == 0) {
             float TK = expf(-carry);
             float rgb[3];
@@ -127,6 +134,10 @@ __global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
                     loss_part = fmaf(e, e, loss_part);
                     if (A.dloss_out) A.dloss_out[3 * r + ch] = 2.0f * e / (float)A.R;
                 }
+            }
+            if (aux) {
+                loss_part += A.w_pt * pt + A.w_bg * bg_entropy(TK);
+                A.rtarget[r] = make_float4(tg[0], tg[1], tg[2], 0.0f);
             }
         }
     }
@@ -144,7 +155,14 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
         const int nch = (rr.n + 31) >> 5;
         const float TK = A.rayout[r].w;
         const float g[3] = {A.grad_rgb[3 * r], A.grad_rgb[3 * r + 1], A.grad_rgb[3 * r + 2]};
-        const float gT = A.grad_tfinal ? A.grad_tfinal[r] : 0.0f;
+        // auxiliary losses of the forward: the background entropy enters through T_K, the
+        // per-point rgb loss adds 2 w_pt w_k (c_k - C) / R to dL/dc_k
+        const bool aux = A.hdr->aux != 0;
+        float4 tg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (aux) tg = A.rtarget[r];
+        const float gT = (A.grad_tfinal ? A.grad_tfinal[r] : 0.0f) +
+                         (aux ? A.w_bg * bg_entropy_dT(TK) / (float)A.R : 0.0f);
+        const float kpt = aux ? 2.0f * A.w_pt / (float)A.R : 0.0f;
         // pass 1 (front to back): optical depth at the start of every chunk, as in the forward
         float carry = 0.0f;
         for (int ci = 0; ci < nch; ++ci) {
@@ -196,7 +214,9 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
                 c = sample_cell(A, rr, r, k, dt);
                 dz = act ? dtau * dt * -expm1f(-sv.x / dt) : 0.0f;
                 // dL/dc_k for the colour backward (only kept samples are read back)
-                A.sgrad[rr.off + k] = make_float4(0.0f, g[0] * w, g[1] * w, g[2] * w);
+                A.sgrad[rr.off + k] = make_float4(0.0f, fmaf(kpt * w, cc[0] - tg.x, g[0] * w),
+                                                  fmaf(kpt * w, cc[1] - tg.y, g[1] * w),
+                                                  fmaf(kpt * w, cc[2] - tg.z, g[2] * w));
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {

@@ -57,6 +57,7 @@ extern "C" int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_des
                                        const float *target, float *rgb_out, float *tfinal_out, float *loss_out,
                                        float *dloss_drgb_out, void *stream) {
     if (!p || p->mode != DVGO_MODE_COARSE) return DVGO_ERR_UNSUPPORTED;
+    if (p->w_pt_rgb != 0.0f || p->w_bg != 0.0f) return DVGO_ERR_UNSUPPORTED;   // no room for the targets
     if (n_rays > DVGO_NOALLOC_MAX_RAYS) return DVGO_ERR_CAPACITY;
     void *scratch = nullptr;
     int st = dvgo::scratch_address(&scratch);

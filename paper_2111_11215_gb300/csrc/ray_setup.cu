@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
         A.hdr->n_kept = 0;
         A.hdr->done = 0u;
         A.hdr->loss_acc = 0.0f;
+        A.hdr->aux = (A.target && (A.w_pt != 0.0f || A.w_bg != 0.0f)) ? 1 : 0;
     }
     if (r >= A.R) return;
     double o[3] = {(double)rays_o[3 * r], (double)rays_o[3 * r + 1], (double)rays_o[3 * r + 2]};
@@ -174,7 +175,8 @@ WsLayout ws_layout(int R, long long max_samples, int mode) {
     } else {
         L.samp = L.sgrad = L.kept = 0;
     }
-    L.total = o;
+    L.rtarget = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));   // last: the allocation-free
+    L.total = o;                                                       // forward does not reach it
     L.max_samples = max_samples;
     return L;
 }
