@@ -469,8 +469,10 @@ def run_time_to_psnr(args):
 
     # ---------------- coarse stage ----------------
     rc = 100
+    # Supp. A auxiliary loss weights (per-point rgb, background entropy): 1e-1 / 1e-2 coarse, 1e-2 / 1e-3 fine
+    aux_c, aux_f = ((0.1, 0.01), (1e-2, 1e-3)) if args.aux_losses else ((0.0, 0.0), (0.0, 0.0))
     pc = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.5 * 2.0 / rc, bg=(1.0, 1.0, 1.0),
-                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rc))
+                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rc), w_pt_rgb=aux_c[0], w_bg=aux_c[1])
     coarse = dvgo.CoarseModel(torch.zeros((rc,) * 3, device=dev), torch.zeros((rc,) * 3 + (3,), device=dev), pc, NRAYS)
     it = [0]
 
@@ -534,7 +536,8 @@ def run_time_to_psnr(args):
     for form in forms:
         bf16, use_prop = form_defs[form]
         p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0),
-                        mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace)
+                        mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace,
+                        w_pt_rgb=aux_f[0], w_bg=aux_f[1])
         model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16,
                                overlap_adam=use_prop, box=box)
         prop = trainer = None
@@ -584,7 +587,7 @@ def run_time_to_psnr(args):
             "coarse_steps": args.coarse_steps, "coarse_s": t_coarse, "fine_steps": args.fine_steps,
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
-            "fine_recipe": recipe,
+            "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f},
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
             "forms": results}
@@ -756,6 +759,8 @@ def main():
     ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
     ap.add_argument("--prop-warmup", type=int, default=0)
     ap.add_argument("--stress-rays", type=int, default=65536, help="rays per batch of the 256^3 stress workload")
+    ap.add_argument("--aux-losses", action="store_true",
+                    help="time-to-psnr: add the per-point rgb and background entropy losses with the Supp. A weights")
     ap.add_argument("--fine-recipe", choices=["full-box", "paper"], default="full-box",
                     help="time-to-psnr fine stage: 160^3 on the full box, or the paper's Sec. 4.2 recipe "
                          "(fine box from the coarse grid's unknown space, known-free-space and tau_f skipping)")
