@@ -67,7 +67,8 @@ class _Params(C.Structure):
                 ("hidden", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("xyz_min", C.c_double * 3), ("xyz_max", C.c_double * 3), ("shift_b", C.c_double),
                 ("delta", C.c_double), ("tau_f", C.c_double), ("t_near", C.c_double),
-                ("t_far", C.c_double), ("bg", C.c_double * 3), ("w_pt", C.c_double), ("w_bg", C.c_double)]
+                ("t_far", C.c_double), ("bg", C.c_double * 3), ("w_pt", C.c_double), ("w_bg", C.c_double),
+                ("act_order", C.c_int)]
 
 
 class _FreeSpace(C.Structure):
@@ -121,6 +122,7 @@ class Params:
     hidden: int = 128
     w_pt: float = 0.0            # per-point rgb loss weight (Supp. A w_pt_rgb)
     w_bg: float = 0.0            # background entropy loss weight (Supp. A w_bg)
+    act_order: int = 0           # Sec. 3: 0 post- (the paper's), 1 pre-, 2 in-activation
 
     def _c(self) -> _Params:
         p = _Params()
@@ -132,6 +134,7 @@ class Params:
         p.t_near, p.t_far = float(self.t_near), float(self.t_far)
         p.bg[:] = [float(v) for v in self.bg]
         p.w_pt, p.w_bg = float(self.w_pt), float(self.w_bg)
+        p.act_order = int(self.act_order)
         return p
 
 

@@ -69,6 +69,11 @@ typedef struct {
      *   background entropy  L_bg = (1/R) sum_r H(A_r), H(a) = -a log a - (1 - a) log(1 - a) of the
      *                       accumulated alpha A_r = 1 - T_K,r clamped to [1e-6, 1 - 1e-6]. */
     double w_pt, w_bg;
+    /* Order of interpolation and activation (Sec. 3 Eq. pre_in_post):
+     *   0 post: alpha = alpha(softplus(interp(x, V) + b))        (the paper's choice)
+     *   1 pre:  alpha = interp(x, alpha(softplus(V + b)))
+     *   2 in:   alpha = alpha(interp(x, softplus(V + b)))                                    */
+    int act_order;
 } og_params;
 
 /* Known free space (Sec. 4.2): the optimised coarse-stage density grid with its own lattice,
@@ -394,11 +399,21 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             continue;
         }
         og_corners(P, s->x, s->idx, s->cw);
-        double raw = 0.0;
-        for (int c = 0; c < 8; ++c) raw += s->cw[c] * M->density[s->idx[c]];
-        s->z = raw + P->shift_b;
-        double sigma = og_softplus(s->z);
-        s->alpha = -expm1(-sigma * s->dt);
+        if (P->act_order == 1) {            /* pre: interpolate the corners' alphas */
+            s->alpha = 0.0;
+            for (int c = 0; c < 8; ++c)
+                s->alpha += s->cw[c] * -expm1(-og_softplus(M->density[s->idx[c]] + P->shift_b) * s->dt);
+        } else if (P->act_order == 2) {     /* in: interpolate the corners' densities */
+            double sigma = 0.0;
+            for (int c = 0; c < 8; ++c) sigma += s->cw[c] * og_softplus(M->density[s->idx[c]] + P->shift_b);
+            s->alpha = -expm1(-sigma * s->dt);
+        } else {                            /* post: activate the interpolated raw density */
+            double raw = 0.0;
+            for (int c = 0; c < 8; ++c) raw += s->cw[c] * M->density[s->idx[c]];
+            s->z = raw + P->shift_b;
+            double sigma = og_softplus(s->z);
+            s->alpha = -expm1(-sigma * s->dt);
+        }
         s->kept = !(s->alpha < P->tau_f);
         if (!s->kept) s->alpha = 0.0;
         if (s->kept) {
@@ -461,10 +476,20 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                 double gTe = gT + (tgt ? P->w_bg * aux_scale * og_bg_entropy_dT(Tk[n]) : 0.0);
                 double dtau = -gTe * Tk[n];
                 for (int ch = 0; ch < 3; ++ch) dtau += gC[ch] * (Tk[k + 1] * s->c[ch] - Ssuf[ch]);
-                double dz = dtau * s->dt * og_sigmoid(s->z);
+                /* dL/dV_q = dL/dtau dtau/dV_q, tau = -log(1 - alpha) */
                 for (int c = 0; c < 8; ++c) {
+                    double g;
+                    if (P->act_order == 1) {
+                        double sp = og_softplus(M->density[s->idx[c]] + P->shift_b);
+                        g = dtau / (1.0 - s->alpha) * s->cw[c] * exp(-sp * s->dt) * s->dt *
+                            og_sigmoid(M->density[s->idx[c]] + P->shift_b);
+                    } else if (P->act_order == 2) {
+                        g = dtau * s->dt * s->cw[c] * og_sigmoid(M->density[s->idx[c]] + P->shift_b);
+                    } else {
+                        g = dtau * s->dt * og_sigmoid(s->z) * s->cw[c];
+                    }
 #pragma omp atomic
-                    G->density[s->idx[c]] += dz * s->cw[c];
+                    G->density[s->idx[c]] += g;
                 }
                 double dc[3];
                 for (int ch = 0; ch < 3; ++ch) {
