@@ -38,6 +38,11 @@ extern "C" {
 
 #define DVGO_ABI_VERSION 2
 
+/* Interpolation / activation order of the density (dvgo_params.act_order). */
+#define DVGO_ACT_POST 0
+#define DVGO_ACT_PRE 1
+#define DVGO_ACT_IN 2
+
 typedef enum {
     DVGO_OK = 0,
     DVGO_ERR_INVALID_ARG = -1,   /* null pointer, bad size, inconsistent descriptors          */
@@ -101,6 +106,9 @@ typedef struct {
      *             the accumulated alpha A = 1 - T_K clamped to [1e-6, 1 - 1e-6].
      * Supp. A: 1e-1 / 1e-2 in the coarse stage, 1e-2 / 1e-3 in the fine stage.                 */
     float w_pt_rgb, w_bg;
+    int act_order;       /* Sec. 3 Eq. pre_in_post: DVGO_ACT_POST (the paper's choice),
+                            DVGO_ACT_PRE  alpha = interp(x, alpha(softplus(V + b))),
+                            DVGO_ACT_IN   alpha = alpha(interp(x, softplus(V + b)))              */
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:

@@ -12,7 +12,8 @@ from .binding import (  # noqa: F401
     dvgo_render_fwd, dvgo_sample_counts, dvgo_shift_from_alpha_init, dvgo_status_string, dvgo_workspace_size,
     dvgo_workspace_status, lib, library_path, EXPORTED_SYMBOLS, KERNEL_KINDS, dvgo_profile_enable,
     dvgo_profile_read, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
-    dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS, FreeSpace, dvgo_unknown_bbox,
+    dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS, FreeSpace, dvgo_unknown_bbox, DVGO_ACT_POST, DVGO_ACT_PRE,
+    DVGO_ACT_IN,
 )
 from .render import (  # noqa: F401
     AdamState, CoarseModel, FineModel, FrameRenderer, Proposal, ProposalTrainer, Renderer, RenderFunction,

@@ -24,6 +24,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_unknown_bbox",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
+DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
 
 KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
                 "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux", "weight_bins", "proposal_fwd",
@@ -57,7 +58,8 @@ class _Params(C.Structure):
     _fields_ = [("mode", C.c_int), ("rgb_act", C.c_int), ("mlp_prec", C.c_int), ("n_freq_dir", C.c_int),
                 ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
-                ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float)]
+                ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
+                ("act_order", C.c_int)]
 
 
 class _Mlp(C.Structure):
@@ -181,6 +183,7 @@ class Params:
     freespace: FreeSpace | None = None
     w_pt_rgb: float = 0.0        # per-point rgb loss weight (Supp. A)
     w_bg: float = 0.0            # background entropy loss weight (Supp. A)
+    act_order: int = 0           # Sec. 3 interpolation / activation order: 0 post, 1 pre, 2 in
 
     def c(self) -> _Params:
         p = _Params()
@@ -190,6 +193,7 @@ class Params:
         p.t_near, p.t_far = float(self.t_near), float(self.t_far)
         p.bg[:] = [float(v) for v in self.bg]
         p.w_pt_rgb, p.w_bg = float(self.w_pt_rgb), float(self.w_bg)
+        p.act_order = int(self.act_order)
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)

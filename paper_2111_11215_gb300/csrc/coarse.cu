@@ -36,19 +36,20 @@ __device__ __forceinline__ CoarseSample coarse_sample(const RenderArgs &A, const
     CoarseSample S;
     S.cell = sample_cell(A, rr, ray, k, S.dt);
     const float *rgb = static_cast<const float *>(A.cgrid);
-    float s = 0.0f, col[3] = {0.0f, 0.0f, 0.0f};
+    float s = 0.0f, col[3] = {0.0f, 0.0f, 0.0f}, v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         long long idx = corner_index(S.cell, q, A.ny, A.nz);
         float w = corner_weight(S.cell, q);
-        s = fmaf(w, __ldg(A.density + idx), s);
+        v[q] = __ldg(A.density + idx);
+        s = fmaf(w, v[q], s);
         const float *cp = rgb + idx * 3;
         col[0] = fmaf(w, __ldg(cp + 0), col[0]);
         col[1] = fmaf(w, __ldg(cp + 1), col[1]);
         col[2] = fmaf(w, __ldg(cp + 2), col[2]);
     }
     S.z = s + A.shift_b;
-    S.tau = softplusf(S.z) * S.dt;
+    S.tau = A.act_order == DVGO_ACT_POST ? softplusf(S.z) * S.dt : tau_pre_in(A.act_order, S.cell, v, A.shift_b, S.dt);
     float alpha = -expm1f(-S.tau);
     S.kept = !(alpha < A.tau_f);
     if (!S.kept) S.tau = 0.0f;
@@ -143,10 +144,13 @@ __global__ void __launch_bounds__(256) coarse_fwd_kernel(RenderArgs A) {
 __device__ __forceinline__ float coarse_tau(const RenderArgs &A, const RayRec &rr, int ray, int k) {
     float dt;
     Cell c = sample_cell(A, rr, ray, k, dt);
-    float s = 0.0f;
+    float s = 0.0f, v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
-    float tau = softplusf(s + A.shift_b) * dt;
+    for (int q = 0; q < 8; ++q) {
+        v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz));
+        s = fmaf(corner_weight(c, q), v[q], s);
+    }
+    float tau = A.act_order == DVGO_ACT_POST ? softplusf(s + A.shift_b) * dt : tau_pre_in(A.act_order, c, v, A.shift_b, dt);
     return (-expm1f(-tau) < A.tau_f) ? 0.0f : tau;
 }
 
@@ -232,7 +236,12 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
                 int idx = (int)corner_index(S.cell, q, A.ny, A.nz);
                 float cw = corner_weight(S.cell, q);
                 Seg sg = make_seg(act ? idx : -1 - lane, lane);
-                float v = seg_sum(dz * cw, sg, lane);
+                float gq = dz * cw;
+                if (A.act_order != DVGO_ACT_POST)
+                    gq = act ? dtau * dtau_dv_pre_in(A.act_order, S.cell, q, __ldg(A.density + idx), A.shift_b, S.dt,
+                                                     S.tau)
+                             : 0.0f;
+                float v = seg_sum(gq, sg, lane);
                 if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {

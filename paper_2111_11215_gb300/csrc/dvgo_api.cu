@@ -84,6 +84,8 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
     if (!finite_pos(p->step) || !isfinite(p->shift_b) || !isfinite(p->tau_f) || isnan(p->t_near) || isnan(p->t_far))
         return DVGO_ERR_INVALID_ARG;
     if (!isfinite(p->w_pt_rgb) || !isfinite(p->w_bg)) return DVGO_ERR_INVALID_ARG;
+    if (p->act_order != DVGO_ACT_POST && p->act_order != DVGO_ACT_PRE && p->act_order != DVGO_ACT_IN)
+        return DVGO_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
         if (!isfinite(p->bg[c])) return DVGO_ERR_INVALID_ARG;
     if (p->mode == DVGO_MODE_COARSE) {
@@ -153,6 +155,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.rtarget = reinterpret_cast<float4 *>(b + L.rtarget);
     A.w_pt = p->w_pt_rgb;
     A.w_bg = p->w_bg;
+    A.act_order = p->act_order;
     if (p->mode == DVGO_MODE_FINE) {
         A.pe = reinterpret_cast<float *>(b + L.pe);
         A.texit = reinterpret_cast<double *>(b + L.texit);

@@ -85,6 +85,7 @@ struct RenderArgs {
     float4 *rayout;             // per ray: C_hat (xyz), T_K (w)
     float4 *rtarget;            // per ray: the forward's target (auxiliary losses)
     float w_pt, w_bg;           // auxiliary loss weights
+    int act_order;              // DVGO_ACT_POST / PRE / IN
     float *pe;                  // fine: per ray [d (3), sin (12), cos (12), 0 x 5] (kPeStride floats)
     double *texit;              // fine: per ray clipped exit distance
     float4 *samp;               // per sample slot: (tau, r, g, b)
@@ -244,6 +245,31 @@ __device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r
     long long u[3];
     sample_fx(A, r, ray, k, dt, u);
     return cell_from_fx(u, A.nx, A.ny, A.nz);
+}
+
+// Optical depth of a sample under the pre- or in-activation order (Sec. 3 Eq. pre_in_post) from its
+// corner raw densities v[8]: in: tau = dt sum_q w_q softplus(v_q + b); pre: alpha = sum_q w_q
+// (1 - exp(-softplus(v_q + b) dt)), tau = -log(1 - alpha).  (The post order activates the
+// interpolated raw density and is computed inline by the kernels.)
+__device__ __forceinline__ float tau_pre_in(int order, const Cell &c, const float v[8], float b, float dt) {
+    float s = 0.0f;
+    if (order == DVGO_ACT_IN) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), softplusf(v[q] + b), s);
+        return s * dt;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), -expm1f(-softplusf(v[q] + b) * dt), s);
+    return -log1pf(-s);
+}
+
+// dtau / dv_q under the pre- or in-activation order (tau of the sample given; the exp(tau) factor of
+// the pre order, 1 / (1 - alpha), is capped so that a saturated sample gives a finite value).
+__device__ __forceinline__ float dtau_dv_pre_in(int order, const Cell &c, int q, float vq, float b, float dt,
+                                                float tau) {
+    const float w = corner_weight(c, q), sg = sigmoidf_(vq + b);
+    if (order == DVGO_ACT_IN) return w * dt * sg;
+    return w * expf(-softplusf(vq + b) * dt) * dt * sg * expf(fminf(tau, 80.0f));
 }
 
 // Known-free-space test of Sec. 4.2 at a sample with fine lattice coordinate u: the coarse grid's

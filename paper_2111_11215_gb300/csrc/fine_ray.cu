@@ -45,11 +45,18 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
                 sample_fx(A, rr, r, k, dt, u);
                 if (!(A.fs_density && known_free(A, u))) {   // known free space: no fine query
                     const Cell c = cell_from_fx(u, A.nx, A.ny, A.nz);
-                    float s = 0.0f;
+                    if (A.act_order == DVGO_ACT_POST) {
+                        float s = 0.0f;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
-                    tau = softplusf(s + A.shift_b) * dt;
+                        for (int q = 0; q < 8; ++q)
+                            s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
+                        tau = softplusf(s + A.shift_b) * dt;
+                    } else {
+                        float v[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz));
+                        tau = tau_pre_in(A.act_order, c, v, A.shift_b, dt);
+                    }
                     kept = !(-expm1f(-tau) < A.tau_f);
                     if (!kept) tau = 0.0f;
                 }
@@ -208,11 +215,10 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
             Cell c;
             c.i0 = c.j0 = c.k0 = 0;
             c.fx = c.fy = c.fz = 0.0f;
-            float dz = 0.0f;
+            float dz = 0.0f, dt = 0.0f;
             if (valid) {
-                float dt;
                 c = sample_cell(A, rr, r, k, dt);
-                dz = act ? dtau * dt * -expm1f(-sv.x / dt) : 0.0f;
+                dz = act ? dtau * dt * -expm1f(-sv.x / dt) : 0.0f;   // post: dt sigmoid(z) = dt (1 - e^{-tau/dt})
                 // dL/dc_k for the colour backward (only kept samples are read back)
                 A.sgrad[rr.off + k] = make_float4(0.0f, fmaf(kpt * w, cc[0] - tg.x, g[0] * w),
                                                   fmaf(kpt * w, cc[1] - tg.y, g[1] * w),
@@ -222,7 +228,14 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
             for (int q = 0; q < 8; ++q) {
                 int idx = (int)corner_index(c, q, A.ny, A.nz);
                 Seg sg = make_seg(act ? idx : -1 - lane, lane);
-                float v = seg_sum(dz * corner_weight(c, q), sg, lane);
+                float gq;
+                if (A.act_order == DVGO_ACT_POST) {
+                    gq = dz * corner_weight(c, q);
+                } else {
+                    gq = act ? dtau * dtau_dv_pre_in(A.act_order, c, q, __ldg(A.density + idx), A.shift_b, dt, sv.x)
+                             : 0.0f;
+                }
+                float v = seg_sum(gq, sg, lane);
                 if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
             }
         }

@@ -1,0 +1,48 @@
+"""GPU parity of the pre- and in-activation orders (Sec. 3 Eq. pre_in_post) against the FP64
+oracle, coarse and fine, forward and backward, at the FP32 tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import FLOOR_FINE_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from test_gpu_parity import _fine_inputs, _run_coarse, _run_fine
+
+pytestmark = pytest.mark.gpu
+
+dvgo = pytest.importorskip("paper_2111_11215_gb300")
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_coarse_orders(order):
+    case = synth.coarse_case(seed=1, n_rays=1500)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.03125, shift_b=0.5, bg=(0.3, 0.6, 0.9), act_order=order)
+    got, ref, refb = _run_coarse(case, p)
+    np.testing.assert_array_equal(got["counts"], ref.n_samples)
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
+    assert_close(got["g_d"], refb.grads["density"], RTOL_GRAD, "grad_density")
+    assert_close(got["g_c"], refb.grads["cgrid"], RTOL_GRAD, "grad_rgb")
+    # the order matters on this input
+    post = oracle.render(oracle_params(dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.03125, shift_b=0.5,
+                                                   bg=(0.3, 0.6, 0.9)), (32,) * 3, 3),
+                         case["density"], case["rgb"], case["rays_o"], case["rays_d"])
+    assert np.abs(post.tfinal - ref.tfinal).max() > 1e-4
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_fine_orders_fp32(order):
+    res, R = 24, 300
+    dens, feat, mlp, o, d, jit, _ = _fine_inputs(res, R, seed=60)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=2.0 / res * 0.5, bg=(1.0, 1.0, 1.0), act_order=order,
+                    shift_b=dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / res))
+    g = np.random.default_rng(61)
+    gC = g.normal(scale=1e-2, size=(R, 3))
+    gT = g.normal(scale=1e-2, size=R)
+    got = _run_fine(p, res, dens, feat, mlp, o, d, jit, gC, gT)
+    ref = oracle.render(oracle_params(p, (res,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC,
+                        grad_tfinal=gT)
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
+    assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
+    assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
