@@ -45,6 +45,7 @@ PROPOSAL_ETA = 0.05
 MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                                    # 43,520
 MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 128)   # 80,128
 N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
+ACT_ORDERS = {"post": 0, "pre": 1, "in": 2}   # Sec. 3 interpolation / activation orders
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -472,7 +473,8 @@ def run_time_to_psnr(args):
     # Supp. A auxiliary loss weights (per-point rgb, background entropy): 1e-1 / 1e-2 coarse, 1e-2 / 1e-3 fine
     aux_c, aux_f = ((0.1, 0.01), (1e-2, 1e-3)) if args.aux_losses else ((0.0, 0.0), (0.0, 0.0))
     pc = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.5 * 2.0 / rc, bg=(1.0, 1.0, 1.0),
-                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rc), w_pt_rgb=aux_c[0], w_bg=aux_c[1])
+                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rc), w_pt_rgb=aux_c[0], w_bg=aux_c[1],
+                     act_order=ACT_ORDERS[args.act_order])
     coarse = dvgo.CoarseModel(torch.zeros((rc,) * 3, device=dev), torch.zeros((rc,) * 3 + (3,), device=dev), pc, NRAYS)
     it = [0]
 
@@ -511,7 +513,7 @@ def run_time_to_psnr(args):
     feat0 = torch.as_tensor(synth.normal_grid(fshape, FEAT, 1e-2, seed=11), device=dev)
     mlp0 = torch.as_tensor(mlp_flat(synth.mlp_weights(39, HID, 3, seed=12)), device=dev)
     p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
-                         freespace=freespace)
+                         freespace=freespace, act_order=ACT_ORDERS[args.act_order])
     dd, cd32 = dvgo.GridDesc(fshape, 1, box[0], box[1]), dvgo.GridDesc(fshape, FEAT, box[0], box[1])
     eval_r = dvgo.Renderer(p_eval, dd, cd32, NRAYS)
 
@@ -537,7 +539,7 @@ def run_time_to_psnr(args):
         bf16, use_prop = form_defs[form]
         p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0),
                         mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace,
-                        w_pt_rgb=aux_f[0], w_bg=aux_f[1])
+                        w_pt_rgb=aux_f[0], w_bg=aux_f[1], act_order=ACT_ORDERS[args.act_order])
         model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16,
                                overlap_adam=use_prop, box=box)
         prop = trainer = None
@@ -587,7 +589,7 @@ def run_time_to_psnr(args):
             "coarse_steps": args.coarse_steps, "coarse_s": t_coarse, "fine_steps": args.fine_steps,
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
-            "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f},
+            "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
             "forms": results}
@@ -759,6 +761,8 @@ def main():
     ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
     ap.add_argument("--prop-warmup", type=int, default=0)
     ap.add_argument("--stress-rays", type=int, default=65536, help="rays per batch of the 256^3 stress workload")
+    ap.add_argument("--act-order", choices=list(ACT_ORDERS), default="post",
+                    help="time-to-psnr: interpolation / activation order of the density in both stages (Sec. 3)")
     ap.add_argument("--aux-losses", action="store_true",
                     help="time-to-psnr: add the per-point rgb and background entropy losses with the Supp. A weights")
     ap.add_argument("--fine-recipe", choices=["full-box", "paper"], default="full-box",

@@ -249,7 +249,9 @@ __device__ __forceinline__ Cell sample_cell(const RenderArgs &A, const RayRec &r
 
 // Optical depth of a sample under the pre- or in-activation order (Sec. 3 Eq. pre_in_post) from its
 // corner raw densities v[8]: in: tau = dt sum_q w_q softplus(v_q + b); pre: alpha = sum_q w_q
-// (1 - exp(-softplus(v_q + b) dt)), tau = -log(1 - alpha).  (The post order activates the
+// (1 - exp(-softplus(v_q + b) dt)), tau = -log(1 - alpha), formed as -log1p(-alpha) while alpha
+// is small and as -log(sum_q w_q exp(-softplus(v_q + b) dt)) otherwise (no cancellation, and no
+// alpha rounded above 1 when every corner saturates).  (The post order activates the
 // interpolated raw density and is computed inline by the kernels.)
 __device__ __forceinline__ float tau_pre_in(int order, const Cell &c, const float v[8], float b, float dt) {
     float s = 0.0f;
@@ -260,7 +262,11 @@ __device__ __forceinline__ float tau_pre_in(int order, const Cell &c, const floa
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), -expm1f(-softplusf(v[q] + b) * dt), s);
-    return -log1pf(-s);
+    if (s < 0.5f) return -log1pf(-s);
+    float t = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t = fmaf(corner_weight(c, q), expf(-softplusf(v[q] + b) * dt), t);
+    return -logf(t);
 }
 
 // dtau / dv_q under the pre- or in-activation order (tau of the sample given; the exp(tau) factor of

@@ -46,3 +46,16 @@ def test_fine_orders_fp32(order):
     assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
     assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
     assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
+
+
+def test_pre_order_saturated_corners_stay_finite():
+    """Corners dense enough that every alpha rounds to 1 in FP32: transmittance 0 behind them,
+    finite gradients, and agreement with the oracle."""
+    case = synth.coarse_case(seed=2, n_rays=512)
+    case["density"] = case["density"] * 0.0 + 400.0
+    case["density"][:, :, :16] = -5.0                      # an empty half in front of the wall
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.03125, shift_b=0.0, bg=(0.3, 0.6, 0.9), act_order=1)
+    got, ref, refb = _run_coarse(case, p)
+    assert np.all(np.isfinite(got["rgb"])) and np.all(np.isfinite(got["g_d"])) and np.all(np.isfinite(got["g_c"]))
+    assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
+    assert got["tfinal"].min() < 1e-6
