@@ -28,6 +28,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Specialised on the known-free-space test and the activation order (uniform per launch), so the
+// default configuration carries neither.
+template <bool kFreeSpace, int kOrder>
 __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -43,9 +46,9 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
                 float dt;
                 long long u[3];
                 sample_fx(A, rr, r, k, dt, u);
-                if (!(A.fs_density && known_free(A, u))) {   // known free space: no fine query
+                if (!(kFreeSpace && known_free(A, u))) {   // known free space: no fine query
                     const Cell c = cell_from_fx(u, A.nx, A.ny, A.nz);
-                    if (A.act_order == DVGO_ACT_POST) {
+                    if (kOrder == DVGO_ACT_POST) {
                         float s = 0.0f;
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
                         float v[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz));
-                        tau = tau_pre_in(A.act_order, c, v, A.shift_b, dt);
+                        tau = tau_pre_in(kOrder, c, v, A.shift_b, dt);
                     }
                     kept = !(-expm1f(-tau) < A.tau_f);
                     if (!kept) tau = 0.0f;
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(256) fine_composite_kernel(RenderArgs A) {
     if (A.target) finish_loss_fine(A, loss_part);
 }
 
+template <int kOrder>
 __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
     __shared__ float s_pre[8][kMaxChunks];   // optical depth before each chunk, per warp
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -229,11 +233,10 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
                 int idx = (int)corner_index(c, q, A.ny, A.nz);
                 Seg sg = make_seg(act ? idx : -1 - lane, lane);
                 float gq;
-                if (A.act_order == DVGO_ACT_POST) {
+                if (kOrder == DVGO_ACT_POST) {
                     gq = dz * corner_weight(c, q);
                 } else {
-                    gq = act ? dtau * dtau_dv_pre_in(A.act_order, c, q, __ldg(A.density + idx), A.shift_b, dt, sv.x)
-                             : 0.0f;
+                    gq = act ? dtau * dtau_dv_pre_in(kOrder, c, q, __ldg(A.density + idx), A.shift_b, dt, sv.x) : 0.0f;
                 }
                 float v = seg_sum(gq, sg, lane);
                 if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
@@ -255,7 +258,16 @@ int warp_grid(int R, int warps_per_block) {
 void launch_fine_density(const RenderArgs &A, cudaStream_t s) {
     {
         ProfScope ps_(DVGO_K_FINE_DENSITY, s);
-        fine_density_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+        const dim3 g(warp_grid(A.R, 8));
+        const bool fs = A.fs_density != nullptr;
+        switch (A.act_order * 2 + (fs ? 1 : 0)) {
+            case 0: fine_density_kernel<false, DVGO_ACT_POST><<<g, 256, 0, s>>>(A); break;
+            case 1: fine_density_kernel<true, DVGO_ACT_POST><<<g, 256, 0, s>>>(A); break;
+            case 2: fine_density_kernel<false, DVGO_ACT_PRE><<<g, 256, 0, s>>>(A); break;
+            case 3: fine_density_kernel<true, DVGO_ACT_PRE><<<g, 256, 0, s>>>(A); break;
+            case 4: fine_density_kernel<false, DVGO_ACT_IN><<<g, 256, 0, s>>>(A); break;
+            default: fine_density_kernel<true, DVGO_ACT_IN><<<g, 256, 0, s>>>(A); break;
+        }
     }
 }
 void launch_fine_composite_fwd(const RenderArgs &A, cudaStream_t s) {
@@ -267,7 +279,10 @@ void launch_fine_composite_fwd(const RenderArgs &A, cudaStream_t s) {
 void launch_fine_composite_bwd(const RenderArgs &A, cudaStream_t s) {
     {
         ProfScope ps_(DVGO_K_FINE_COMP_BWD, s);
-        fine_comp_bwd_kernel<<<warp_grid(A.R, 8), 256, 0, s>>>(A);
+        const dim3 g(warp_grid(A.R, 8));
+        if (A.act_order == DVGO_ACT_PRE) fine_comp_bwd_kernel<DVGO_ACT_PRE><<<g, 256, 0, s>>>(A);
+        else if (A.act_order == DVGO_ACT_IN) fine_comp_bwd_kernel<DVGO_ACT_IN><<<g, 256, 0, s>>>(A);
+        else fine_comp_bwd_kernel<DVGO_ACT_POST><<<g, 256, 0, s>>>(A);
     }
 }
 
