@@ -36,7 +36,18 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 2
+#define DVGO_ABI_VERSION 3
+
+/* Grid memory layouts (dvgo_grid_desc.layout).
+ *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
+ *   PACKED:    4x4x4-point bricks in row-major brick order (ceil(n/4) bricks per axis) with the
+ *              64 points of a brick in Morton order (bits i0 j0 k0 in the low three, i1 j1 k1
+ *              above), channel-last inside a point: ceil(nx/4)*ceil(ny/4)*ceil(nz/4)*64*C
+ *              elements, padding points included (they stay 0 under training: they get no
+ *              gradient).  The eight corners of a cell share a brick unless the cell straddles
+ *              one, and are eight consecutive points when the cell's base indices are even. */
+#define DVGO_LAYOUT_CANONICAL 0
+#define DVGO_LAYOUT_PACKED 1
 
 /* Interpolation / activation order of the density (dvgo_params.act_order). */
 #define DVGO_ACT_POST 0
@@ -64,7 +75,18 @@ typedef struct {
     float xyz_min[3];    /* box corners; the density and colour grids must share the box        */
     float xyz_max[3];
     int dtype;           /* DVGO_DTYPE_F32, or DVGO_DTYPE_BF16 for the fine feature grid only   */
+    int layout;          /* DVGO_LAYOUT_CANONICAL or DVGO_LAYOUT_PACKED; a render's density and
+                            colour / feature grids share one layout                            */
 } dvgo_grid_desc;
+
+/* Number of scalar elements of a grid's storage in its layout (padding points included). */
+size_t dvgo_grid_elements(const dvgo_grid_desc *g);
+
+/* Copies a grid into another layout and / or element type on the same lattice (nx, ny, nz,
+ * channels and box equal): FP32 <-> BF16 (round to nearest even), canonical <-> packed; padding
+ * points of a packed output are set to 0.  in / out are device buffers of dvgo_grid_elements()
+ * elements of their descriptors; they must not overlap. */
+int dvgo_pack_grid(const dvgo_grid_desc *src, const void *in, const dvgo_grid_desc *dst, void *out, void *stream);
 
 /*
  * Known free space of the fine stage (Sec. 4.2, "Known free space and unknown space" and "Free

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import dataclasses
 from dataclasses import dataclass
 
 import torch
@@ -21,10 +22,11 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
-    "dvgo_unknown_bbox",
+    "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
+DVGO_LAYOUT_CANONICAL, DVGO_LAYOUT_PACKED = 0, 1     # grid storage layouts
 
 KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
                 "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux", "weight_bins", "proposal_fwd",
@@ -46,7 +48,7 @@ class DVGOError(RuntimeError):
 
 class _GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("channels", C.c_int),
-                ("xyz_min", C.c_float * 3), ("xyz_max", C.c_float * 3), ("dtype", C.c_int)]
+                ("xyz_min", C.c_float * 3), ("xyz_max", C.c_float * 3), ("dtype", C.c_int), ("layout", C.c_int)]
 
 
 class _FreeSpace(C.Structure):
@@ -109,6 +111,10 @@ def lib():
         L.dvgo_sample_pdf.argtypes = [vp, vp, i, vp, vp, vp, i, i, vp, f, vp, vp, vp]
         L.dvgo_unknown_bbox.restype = i
         L.dvgo_unknown_bbox.argtypes = [vp, vp, vp]
+        L.dvgo_grid_elements.restype = sz
+        L.dvgo_grid_elements.argtypes = [vp]
+        L.dvgo_pack_grid.restype = i
+        L.dvgo_pack_grid.argtypes = [vp, vp, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -137,6 +143,7 @@ class GridDesc:
     xyz_min: tuple = (-1.0, -1.0, -1.0)
     xyz_max: tuple = (1.0, 1.0, 1.0)
     dtype: int = DVGO_DTYPE_F32
+    layout: int = DVGO_LAYOUT_CANONICAL
 
     def c(self) -> _GridDesc:
         g = _GridDesc()
@@ -145,7 +152,11 @@ class GridDesc:
         g.xyz_min[:] = [float(v) for v in self.xyz_min]
         g.xyz_max[:] = [float(v) for v in self.xyz_max]
         g.dtype = int(self.dtype)
+        g.layout = int(self.layout)
         return g
+
+    def with_(self, **kw) -> "GridDesc":
+        return dataclasses.replace(self, **kw)
 
 
 @dataclass
@@ -434,4 +445,26 @@ def dvgo_unknown_bbox(fs: FreeSpace, out=None, stream=None):
     out = torch.empty(7, dtype=torch.int32, device=fs.density.device) if out is None else out
     f = fs.c()
     _check(lib().dvgo_unknown_bbox(C.byref(f), _dev(out, "out", torch.int32), _stream(stream)), "dvgo_unknown_bbox")
+    return out
+
+
+def dvgo_grid_elements(desc: GridDesc) -> int:
+    """Scalar elements of a grid's storage in its layout (padding points of the packed layout
+    included)."""
+    g = desc.c()
+    return int(lib().dvgo_grid_elements(C.byref(g)))
+
+
+def dvgo_pack_grid(src_desc: GridDesc, src, dst_desc: GridDesc, out=None, stream=None):
+    """Copy a grid into another layout / element type on the same lattice; returns the (flat)
+    output tensor."""
+    dt = torch.bfloat16 if dst_desc.dtype == DVGO_DTYPE_BF16 else torch.float32
+    st = torch.bfloat16 if src_desc.dtype == DVGO_DTYPE_BF16 else torch.float32
+    if out is None:
+        out = torch.empty(dvgo_grid_elements(dst_desc), dtype=dt, device=src.device)
+    if out.numel() != dvgo_grid_elements(dst_desc) or src.numel() != dvgo_grid_elements(src_desc):
+        raise ValueError("dvgo_pack_grid: tensor sizes do not match the descriptors")
+    a, b = src_desc.c(), dst_desc.c()
+    _check(lib().dvgo_pack_grid(C.byref(a), _dev(src, "src", st), C.byref(b), _dev(out, "out", dt), _stream(stream)),
+           "dvgo_pack_grid")
     return out

@@ -39,7 +39,7 @@ __device__ __forceinline__ CoarseSample coarse_sample(const RenderArgs &A, const
     float s = 0.0f, col[3] = {0.0f, 0.0f, 0.0f}, v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        long long idx = corner_index(S.cell, q, A.ny, A.nz);
+        long long idx = corner_index(S.cell, q, A.ny, A.nz, A.packed);
         float w = corner_weight(S.cell, q);
         v[q] = __ldg(A.density + idx);
         s = fmaf(w, v[q], s);
@@ -147,7 +147,7 @@ __device__ __forceinline__ float coarse_tau(const RenderArgs &A, const RayRec &r
     float s = 0.0f, v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz));
+        v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed));
         s = fmaf(corner_weight(c, q), v[q], s);
     }
     float tau = A.act_order == DVGO_ACT_POST ? softplusf(s + A.shift_b) * dt : tau_pre_in(A.act_order, c, v, A.shift_b, dt);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) coarse_bwd_kernel(RenderArgs A) {
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                int idx = (int)corner_index(S.cell, q, A.ny, A.nz);
+                int idx = (int)corner_index(S.cell, q, A.ny, A.nz, A.packed);
                 float cw = corner_weight(S.cell, q);
                 Seg sg = make_seg(act ? idx : -1 - lane, lane);
                 float gq = dz * cw;

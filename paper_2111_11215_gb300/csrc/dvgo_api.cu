@@ -46,14 +46,15 @@ bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
 bool grid_ok(const dvgo_grid_desc *g) {
     if (!g) return false;
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->channels < 1) return false;
+    if (g->layout != DVGO_LAYOUT_CANONICAL && g->layout != DVGO_LAYOUT_PACKED) return false;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(g->xyz_min[a]) || !isfinite(g->xyz_max[a]) || !(g->xyz_max[a] > g->xyz_min[a])) return false;
-    long long n = (long long)g->nx * g->ny * g->nz * g->channels;
+    long long n = (long long)((g->nx + 3) / 4 * 4) * ((g->ny + 3) / 4 * 4) * ((g->nz + 3) / 4 * 4) * g->channels;
     return n < (1LL << 31);
 }
 
 bool same_lattice(const dvgo_grid_desc *a, const dvgo_grid_desc *b) {
-    if (a->nx != b->nx || a->ny != b->ny || a->nz != b->nz) return false;
+    if (a->nx != b->nx || a->ny != b->ny || a->nz != b->nz || a->layout != b->layout) return false;
     for (int i = 0; i < 3; ++i)
         if (a->xyz_min[i] != b->xyz_min[i] || a->xyz_max[i] != b->xyz_max[i]) return false;
     return true;
@@ -156,6 +157,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.w_pt = p->w_pt_rgb;
     A.w_bg = p->w_bg;
     A.act_order = p->act_order;
+    A.packed = dd->layout == DVGO_LAYOUT_PACKED;
     if (p->mode == DVGO_MODE_FINE) {
         A.pe = reinterpret_cast<float *>(b + L.pe);
         A.texit = reinterpret_cast<double *>(b + L.texit);
@@ -173,6 +175,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
         A.fs_shift_b = f.shift_b;
         A.fs_step = f.step;
         A.fs_tau = f.tau;
+        A.fs_packed = f.desc.layout == DVGO_LAYOUT_PACKED;
         const int nf[3] = {dd->nx, dd->ny, dd->nz}, nc[3] = {f.desc.nx, f.desc.ny, f.desc.nz};
         for (int a = 0; a < 3; ++a) {
             // u_c = (x - min_c) sc_c with x = min_f + u_f / sf:  u_c = (min_f - min_c) sc_c + u_f sc_c / sf

@@ -86,6 +86,8 @@ struct RenderArgs {
     float4 *rtarget;            // per ray: the forward's target (auxiliary losses)
     float w_pt, w_bg;           // auxiliary loss weights
     int act_order;              // DVGO_ACT_POST / PRE / IN
+    int packed;                 // density and colour / feature grids in DVGO_LAYOUT_PACKED
+    int fs_packed;              // the known-free-space grid in DVGO_LAYOUT_PACKED
     float *pe;                  // fine: per ray [d (3), sin (12), cos (12), 0 x 5] (kPeStride floats)
     double *texit;              // fine: per ray clipped exit distance
     float4 *samp;               // per sample slot: (tau, r, g, b)
@@ -204,9 +206,33 @@ __device__ __forceinline__ void fx_axis(long long ufx, int n, int &i0, float &f)
     }
 }
 
+// Packed grid layout (DVGO_LAYOUT_PACKED): 4x4x4-point bricks in row-major brick order
+// (ceil(n/4) bricks per axis), the 64 points of a brick in Morton (bit-interleaved) order, so the
+// 2x2x2 corners of a cell with even base indices are 8 consecutive entries and most cells' corners
+// share a brick.
+__host__ __device__ __forceinline__ long long packed_index(int i, int j, int k, int ny, int nz) {
+    const int nby = (ny + 3) >> 2, nbz = (nz + 3) >> 2;
+    const long long brick = ((long long)(i >> 2) * nby + (j >> 2)) * nbz + (k >> 2);
+    const int m = ((i & 1) << 2) | ((j & 1) << 1) | (k & 1) | ((i & 2) << 4) | ((j & 2) << 3) | ((k & 2) << 2);
+    return brick * 64 + m;
+}
+
+__host__ __device__ __forceinline__ long long grid_index(int i, int j, int k, int ny, int nz, bool packed) {
+    return packed ? packed_index(i, j, k, ny, nz) : ((long long)i * ny + j) * nz + k;
+}
+
 // Corner q (bits x = q>>2, y = (q>>1)&1, z = q&1): flat lattice index and trilinear weight.
-__device__ __forceinline__ long long corner_index(const Cell &c, int q, int ny, int nz) {
-    return ((long long)(c.i0 + ((q >> 2) & 1)) * ny + (c.j0 + ((q >> 1) & 1))) * nz + (c.k0 + (q & 1));
+__device__ __forceinline__ long long corner_index(const Cell &c, int q, int ny, int nz, bool packed) {
+    return grid_index(c.i0 + ((q >> 2) & 1), c.j0 + ((q >> 1) & 1), c.k0 + (q & 1), ny, nz, packed);
+}
+
+// Flat index of corner (bx, by, bz) of the cell whose base corner has canonical index cb.
+__device__ __forceinline__ long long corner_from_base(long long cb, int bx, int by, int bz, int ny, int nz,
+                                                      bool packed) {
+    if (!packed) return cb + (long long)bx * ny * nz + (long long)by * nz + bz;
+    const long long nyz = (long long)ny * nz;
+    const int i0 = (int)(cb / nyz), j0 = (int)((cb / nz) % ny), k0 = (int)(cb % nz);
+    return packed_index(i0 + bx, j0 + by, k0 + bz, ny, nz);
 }
 __device__ __forceinline__ float corner_weight(const Cell &c, int q) {
     float wx = ((q >> 2) & 1) ? c.fx : 1.0f - c.fx;
@@ -288,7 +314,8 @@ __device__ __forceinline__ bool known_free(const RenderArgs &A, const long long 
     const Cell c = cell_from_fx(uc, A.fs_nx, A.fs_ny, A.fs_nz);
     float s = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s = fmaf(corner_weight(c, q), __ldg(A.fs_density + corner_index(c, q, A.fs_ny, A.fs_nz)), s);
+    for (int q = 0; q < 8; ++q)
+        s = fmaf(corner_weight(c, q), __ldg(A.fs_density + corner_index(c, q, A.fs_ny, A.fs_nz, A.fs_packed)), s);
     return -expm1f(-softplusf(s + A.fs_shift_b) * A.fs_step) < A.fs_tau;
 }
 

@@ -52,12 +52,12 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
                         float s = 0.0f;
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
-                            s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz)), s);
+                            s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed)), s);
                         tau = softplusf(s + A.shift_b) * dt;
                     } else {
                         float v[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz));
+                        for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed));
                         tau = tau_pre_in(kOrder, c, v, A.shift_b, dt);
                     }
                     kept = !(-expm1f(-tau) < A.tau_f);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                int idx = (int)corner_index(c, q, A.ny, A.nz);
+                int idx = (int)corner_index(c, q, A.ny, A.nz, A.packed);
                 Seg sg = make_seg(act ? idx : -1 - lane, lane);
                 float gq;
                 if (kOrder == DVGO_ACT_POST) {

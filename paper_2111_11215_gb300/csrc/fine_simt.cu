@@ -90,21 +90,24 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
         float dt;
         Cell c = sample_cell(A, rr, ray, k, dt);
         if (q == 0) {
-            S.cbase[i] = (int)corner_index(c, 0, A.ny, A.nz);
+            S.cbase[i] = (int)grid_index(c.i0, c.j0, c.k0, A.ny, A.nz, false);   // canonical base
             S.frac[3 * i] = c.fx;
             S.frac[3 * i + 1] = c.fy;
             S.frac[3 * i + 2] = c.fz;
             S.slot[i] = slot;
         }
         int qa = q << 1;   // corner bits (x, y, 0)
-        long long idx0 = corner_index(c, qa, A.ny, A.nz);
+        long long idx0 = corner_index(c, qa, A.ny, A.nz, A.packed);
         float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
         const FeatT *g = static_cast<const FeatT *>(A.cgrid) + idx0 * FEAT;
+        // the z + 1 corner: the next point in the canonical layout, located in the packed one
+        const FeatT *gz = A.packed ? static_cast<const FeatT *>(A.cgrid) + corner_index(c, qa | 1, A.ny, A.nz, true) * FEAT
+                                   : g + FEAT;
         if constexpr (sizeof(FeatT) == 4) {
-            const float4 *g4 = reinterpret_cast<const float4 *>(g);
+            const float4 *g4 = reinterpret_cast<const float4 *>(g), *gz4 = reinterpret_cast<const float4 *>(gz);
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                float4 a = __ldg(g4 + v), b = __ldg(g4 + 3 + v);
+                float4 a = __ldg(g4 + v), b = __ldg(gz4 + v);
                 f[4 * v + 0] = fmaf(w0, a.x, w1 * b.x);
                 f[4 * v + 1] = fmaf(w0, a.y, w1 * b.y);
                 f[4 * v + 2] = fmaf(w0, a.z, w1 * b.z);
@@ -112,10 +115,10 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
             }
         } else {
             // BF16 storage: 24 bytes per corner, 8-byte aligned; 48 contiguous bytes for the pair.
-            const uint2 *g2 = reinterpret_cast<const uint2 *>(g);
+            const uint2 *g2 = reinterpret_cast<const uint2 *>(g), *gz2 = reinterpret_cast<const uint2 *>(gz);
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                uint2 a = __ldg(g2 + v), b = __ldg(g2 + 3 + v);
+                uint2 a = __ldg(g2 + v), b = __ldg(gz2 + v);
                 __nv_bfloat162 a0 = *reinterpret_cast<__nv_bfloat162 *>(&a.x), a1 = *reinterpret_cast<__nv_bfloat162 *>(&a.y);
                 __nv_bfloat162 b0 = *reinterpret_cast<__nv_bfloat162 *>(&b.x), b1 = *reinterpret_cast<__nv_bfloat162 *>(&b.y);
                 float2 fa0 = __bfloat1622float2(a0), fa1 = __bfloat1622float2(a1);
@@ -399,14 +402,16 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
                 float fx = S.frac[3 * i], fy = S.frac[3 * i + 1], fz = S.frac[3 * i + 2];
                 float wxy = ((q >> 1) ? fx : 1.0f - fx) * ((q & 1) ? fy : 1.0f - fy);
                 float w0 = wxy * (1.0f - fz), w1 = wxy * fz;
-                long long idx0 = (long long)S.cbase[i] + (long long)(q >> 1) * A.ny * A.nz + (long long)(q & 1) * A.nz;
+                const long long idx0 = corner_from_base(S.cbase[i], q >> 1, q & 1, 0, A.ny, A.nz, A.packed);
+                const long long idx1 = corner_from_base(S.cbase[i], q >> 1, q & 1, 1, A.ny, A.nz, A.packed);
                 float4 *g0 = reinterpret_cast<float4 *>(A.grad_cgrid + idx0 * FEAT);
+                float4 *g1 = reinterpret_cast<float4 *>(A.grad_cgrid + idx1 * FEAT);
                 const float *d = S.de + i * FEAT;
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     float4 dv = make_float4(d[4 * v], d[4 * v + 1], d[4 * v + 2], d[4 * v + 3]);
                     atomicAdd(g0 + v, make_float4(w0 * dv.x, w0 * dv.y, w0 * dv.z, w0 * dv.w));
-                    atomicAdd(g0 + 3 + v, make_float4(w1 * dv.x, w1 * dv.y, w1 * dv.z, w1 * dv.w));
+                    atomicAdd(g1 + v, make_float4(w1 * dv.x, w1 * dv.y, w1 * dv.z, w1 * dv.w));
                 }
             }
         }

@@ -116,7 +116,7 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
     for (int q = 0; q < 8; ++q) {
         const int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
         const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz);
-        const long long idx = cb + (long long)bx * A.ny * A.nz + (long long)by * A.nz + bz;
+        const long long idx = corner_from_base(cb, bx, by, bz, A.ny, A.nz, A.packed);
         float4 *g = reinterpret_cast<float4 *>(A.grad_cgrid + idx * FEAT);
         atomicAdd(g + 0, make_float4(w * e0.x, w * e0.y, w * e0.z, w * e0.w));
         atomicAdd(g + 1, make_float4(w * e1.x, w * e1.y, w * e1.z, w * e1.w));
@@ -138,7 +138,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         float dt;
         const Cell c = sample_cell(A, rr, kv.y, kv.x - rr.off, dt);
         slot = kv.x;
-        cbase = (int)corner_index(c, 0, A.ny, A.nz);
+        cbase = (int)grid_index(c.i0, c.j0, c.k0, A.ny, A.nz, false);   // canonical base
         fx = c.fx;
         fy = c.fy;
         fz = c.fz;
@@ -151,24 +151,28 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
             const int qa = q << 1;
-            const long long idx0 = corner_index(c, qa, A.ny, A.nz);
+            const long long idx0 = corner_index(c, qa, A.ny, A.nz, A.packed);
             const float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
             const FeatT *g = static_cast<const FeatT *>(A.cgrid) + idx0 * FEAT;
+            // the z + 1 corner: the next point in the canonical layout, located in the packed one
+            const FeatT *gz = A.packed ? static_cast<const FeatT *>(A.cgrid) +
+                                             corner_index(c, qa | 1, A.ny, A.nz, true) * FEAT
+                                       : g + FEAT;
             if constexpr (sizeof(FeatT) == 4) {
-                const float4 *g4 = reinterpret_cast<const float4 *>(g);
+                const float4 *g4 = reinterpret_cast<const float4 *>(g), *gz4 = reinterpret_cast<const float4 *>(gz);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float4 a = __ldg(g4 + k), bb = __ldg(g4 + 3 + k);
+                    const float4 a = __ldg(g4 + k), bb = __ldg(gz4 + k);
                     v[4 * k + 0] += w0 * a.x + w1 * bb.x;
                     v[4 * k + 1] += w0 * a.y + w1 * bb.y;
                     v[4 * k + 2] += w0 * a.z + w1 * bb.z;
                     v[4 * k + 3] += w0 * a.w + w1 * bb.w;
                 }
             } else {
-                const uint2 *g2 = reinterpret_cast<const uint2 *>(g);
+                const uint2 *g2 = reinterpret_cast<const uint2 *>(g), *gz2 = reinterpret_cast<const uint2 *>(gz);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    uint2 a = __ldg(g2 + k), bb = __ldg(g2 + 3 + k);
+                    uint2 a = __ldg(g2 + k), bb = __ldg(gz2 + k);
                     const float2 a0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.x));
                     const float2 a1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a.y));
                     const float2 b0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&bb.x));

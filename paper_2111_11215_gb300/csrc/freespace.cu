@@ -23,13 +23,13 @@ __global__ void bbox_init_kernel(int *out) {
 }
 
 __global__ void __launch_bounds__(256) bbox_scan_kernel(const float *__restrict__ v, int nx, int ny, int nz, float b,
-                                                        float step, float tau, int *out) {
+                                                        float step, float tau, int packed, int *out) {
     const long long n = (long long)nx * ny * nz;
     int cnt = 0, lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float alpha = -expm1f(-softplusf(__ldg(v + i) + b) * step);
-        if (alpha < tau) continue;   // known free
         const int k = (int)(i % nz), j = (int)((i / nz) % ny), ii = (int)(i / ((long long)ny * nz));
+        const float alpha = -expm1f(-softplusf(__ldg(v + grid_index(ii, j, k, ny, nz, packed != 0)) + b) * step);
+        if (alpha < tau) continue;   // known free
         const int ijk[3] = {ii, j, k};
         ++cnt;
 #pragma unroll
@@ -76,6 +76,7 @@ extern "C" int dvgo_unknown_bbox(const dvgo_freespace *fs, int *out, void *strea
     if (!fs || !fs->density || !out) return DVGO_ERR_INVALID_ARG;
     const dvgo_grid_desc &g = fs->desc;
     if (g.nx < 2 || g.ny < 2 || g.nz < 2 || g.channels != 1 || g.dtype != DVGO_DTYPE_F32) return DVGO_ERR_INVALID_ARG;
+    if (g.layout != DVGO_LAYOUT_CANONICAL && g.layout != DVGO_LAYOUT_PACKED) return DVGO_ERR_INVALID_ARG;
     if (!(fs->step > 0.0f) || !isfinite(fs->step) || !isfinite(fs->shift_b) || !isfinite(fs->tau))
         return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -86,7 +87,7 @@ extern "C" int dvgo_unknown_bbox(const dvgo_freespace *fs, int *out, void *strea
         ProfScope ps_(DVGO_K_AUX, s);
         bbox_init_kernel<<<1, 32, 0, s>>>(out);
         bbox_scan_kernel<<<(unsigned)blocks, 256, 0, s>>>(fs->density, g.nx, g.ny, g.nz, fs->shift_b, fs->step, fs->tau,
-                                                         out);
+                                                         g.layout == DVGO_LAYOUT_PACKED, out);
         bbox_finish_kernel<<<1, 32, 0, s>>>(g.nx, g.ny, g.nz, out);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;

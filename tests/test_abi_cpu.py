@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_strings(lib):
     import paper_2111_11215_gb300 as dvgo
-    assert dvgo.dvgo_abi_version() == 2
+    assert dvgo.dvgo_abi_version() == 3
     assert dvgo.dvgo_status_string(0) == "ok"
     assert "workspace" in dvgo.dvgo_status_string(-2)
 
@@ -61,3 +61,16 @@ def test_workspace_size_bounds_longest_ray(lib):
     assert n2 > 8192 * 555 * 40 and n2 < 8192 * 600 * 48
     assert n1 > 0
     assert dvgo.dvgo_workspace_size(dvgo.Params(step=0.0), g, 10) == 0
+
+
+def test_grid_elements_per_layout(lib):
+    """Canonical: nx ny nz C; packed: whole 4^3 bricks of 64 points per brick (no GPU needed)."""
+    import paper_2111_11215_gb300 as dvgo
+    for shape, C in (((160, 160, 160), 12), ((13, 6, 9), 1), ((4, 4, 4), 3), ((2, 5, 17), 2)):
+        g = dvgo.GridDesc(shape, C)
+        assert dvgo.dvgo_grid_elements(g) == shape[0] * shape[1] * shape[2] * C
+        bricks = 1
+        for n in shape:
+            bricks *= -(-n // 4)
+        assert dvgo.dvgo_grid_elements(g.with_(layout=dvgo.DVGO_LAYOUT_PACKED)) == bricks * 64 * C
+    assert dvgo.dvgo_grid_elements(dvgo.GridDesc((8, 8, 8), 1, layout=7)) == 0      # invalid layout
