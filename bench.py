@@ -46,6 +46,7 @@ MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                             
 MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 128)   # 80,128
 N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
 ACT_ORDERS = {"post": 0, "pre": 1, "in": 2}   # Sec. 3 interpolation / activation orders
+LAYOUTS = {"canonical": 0, "packed": 1}          # grid storage layouts (dvgo.h)
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -198,6 +199,7 @@ def workload_config(args, form):
     return {"workload": "DVGO fine stage, 160^3 density + 12-ch feature grid, MLP 39-128-128-3, 8192 rays/batch, "
                         "step 0.5 voxel, 8 balls (raw density 50) + smooth albedo, 100 views 800x800",
             "form": form, "global_batch": NRAYS * args.gpus, "grid": RES, "feat_dim": FEAT, "hidden": HID,
+            "layout": getattr(args, "layout", "canonical"),
             "parallelism": f"replicas x{args.gpus} (independent problems)",
             "l2": "inputs larger than L2: Adam sweeps ~1.7 GB of parameters and moments every step"}
 
@@ -209,7 +211,7 @@ def workload_config(args, form):
 class Form:
     """One training form on the benchmark scene: its model, its step, and what it processes."""
 
-    def __init__(self, name, dev, dens, feat, mlp, dvgo, torch):
+    def __init__(self, name, dev, dens, feat, mlp, dvgo, torch, args_layout="canonical"):
         import synth
         self.name, self.dvgo, self.torch = name, dvgo, torch
         chosen = name == "chosen"
@@ -219,7 +221,7 @@ class Form:
                              mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
         self.model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), self.p, NRAYS, bf16_feat=chosen,
-                                    overlap_adam=chosen)
+                                    overlap_adam=chosen, layout=LAYOUTS[args_layout])
         self.trainer = None
         if chosen:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
@@ -239,7 +241,7 @@ class Form:
 
 
 def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, local_rank, peaks):
-    form = Form(name, dev, dens, feat, mlp, dvgo, torch)
+    form = Form(name, dev, dens, feat, mlp, dvgo, torch, args.layout)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
     dbatches = [tuple(t(x) for x in b) for b in batches]
     # samples per batch of the uniform forward (units of the colour kernels)
@@ -617,7 +619,7 @@ def run_stress(args):
     p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * 2.0 / rs, bg=(1.0, 1.0, 1.0), mlp_prec=dvgo.DVGO_MLP_BF16,
                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rs))
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
-    model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p, nr, bf16_feat=True)
+    model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p, nr, bf16_feat=True, layout=LAYOUTS[args.layout])
     batches = []
     for i in range(4):
         o, d = synth.blob_rays(nr, seed=300 + i)
@@ -652,6 +654,7 @@ def run_stress(args):
                       "higher_is_better": True, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
                       "dtype": "bf16", "data": "synthetic", "samples_per_step": samples,
                       "config": {"grid": rs, "feat_dim": FEAT, "rays": nr, "feat_storage": "bf16", "mlp": "bf16 tensor cores",
+                                 "layout": args.layout,
                                  "scene": "one ball r=0.3 raw density 200 at the origin; rays aimed into it"},
                       "kernels_ms_per_step": kernels,
                       "adam_gbs": n_params * (32 + 0) / 1e9 / (adam_ms / 1e3) + rs ** 3 * FEAT * 2 / 1e9 / (adam_ms / 1e3),
@@ -761,6 +764,8 @@ def main():
     ap.add_argument("--prop-eta", type=float, default=PROPOSAL_ETA)
     ap.add_argument("--prop-warmup", type=int, default=0)
     ap.add_argument("--stress-rays", type=int, default=65536, help="rays per batch of the 256^3 stress workload")
+    ap.add_argument("--layout", choices=list(LAYOUTS), default="canonical",
+                    help="grid storage layout of the training-step and stress workloads")
     ap.add_argument("--act-order", choices=list(ACT_ORDERS), default="post",
                     help="time-to-psnr: interpolation / activation order of the density in both stages (Sec. 3)")
     ap.add_argument("--aux-losses", action="store_true",

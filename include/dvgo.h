@@ -45,7 +45,8 @@ extern "C" {
  *              above), channel-last inside a point: ceil(nx/4)*ceil(ny/4)*ceil(nz/4)*64*C
  *              elements, padding points included (they stay 0 under training: they get no
  *              gradient).  The eight corners of a cell share a brick unless the cell straddles
- *              one, and are eight consecutive points when the cell's base indices are even. */
+ *              one, and are eight consecutive points when the cell's base indices are even.
+ *              At most 2048 x 2048 x 1024 points. */
 #define DVGO_LAYOUT_CANONICAL 0
 #define DVGO_LAYOUT_PACKED 1
 

@@ -47,6 +47,7 @@ bool grid_ok(const dvgo_grid_desc *g) {
     if (!g) return false;
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->channels < 1) return false;
     if (g->layout != DVGO_LAYOUT_CANONICAL && g->layout != DVGO_LAYOUT_PACKED) return false;
+    if (g->layout == DVGO_LAYOUT_PACKED && (g->nx > 2048 || g->ny > 2048 || g->nz > 1024)) return false;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(g->xyz_min[a]) || !isfinite(g->xyz_max[a]) || !(g->xyz_max[a] > g->xyz_min[a])) return false;
     long long n = (long long)((g->nx + 3) / 4 * 4) * ((g->ny + 3) / 4 * 4) * ((g->nz + 3) / 4 * 4) * g->channels;

@@ -226,13 +226,17 @@ __device__ __forceinline__ long long corner_index(const Cell &c, int q, int ny, 
     return grid_index(c.i0 + ((q >> 2) & 1), c.j0 + ((q >> 1) & 1), c.k0 + (q & 1), ny, nz, packed);
 }
 
-// Flat index of corner (bx, by, bz) of the cell whose base corner has canonical index cb.
-__device__ __forceinline__ long long corner_from_base(long long cb, int bx, int by, int bz, int ny, int nz,
-                                                      bool packed) {
-    if (!packed) return cb + (long long)bx * ny * nz + (long long)by * nz + bz;
-    const long long nyz = (long long)ny * nz;
-    const int i0 = (int)(cb / nyz), j0 = (int)((cb / nz) % ny), k0 = (int)(cb % nz);
-    return packed_index(i0 + bx, j0 + by, k0 + bz, ny, nz);
+// A cell's base corner as kept in the colour kernels' per-row tables: the canonical flat index, or
+// for the packed layout the lattice indices as bit fields i0 << 21 | j0 << 10 | k0 (the packed
+// layout is limited to 2048 x 2048 x 1024 points).
+__device__ __forceinline__ int cell_base(const Cell &c, int ny, int nz, bool packed) {
+    return packed ? (c.i0 << 21) | (c.j0 << 10) | c.k0 : (int)grid_index(c.i0, c.j0, c.k0, ny, nz, false);
+}
+
+// Flat index of corner (bx, by, bz) of the cell with base `cb` (cell_base).
+__device__ __forceinline__ long long corner_from_base(int cb, int bx, int by, int bz, int ny, int nz, bool packed) {
+    if (!packed) return (long long)cb + (long long)bx * ny * nz + (long long)by * nz + bz;
+    return packed_index(((unsigned)cb >> 21) + bx, ((cb >> 10) & 2047) + by, (cb & 1023) + bz, ny, nz);
 }
 __device__ __forceinline__ float corner_weight(const Cell &c, int q) {
     float wx = ((q >> 2) & 1) ? c.fx : 1.0f - c.fx;

@@ -90,7 +90,7 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
         float dt;
         Cell c = sample_cell(A, rr, ray, k, dt);
         if (q == 0) {
-            S.cbase[i] = (int)grid_index(c.i0, c.j0, c.k0, A.ny, A.nz, false);   // canonical base
+            S.cbase[i] = cell_base(c, A.ny, A.nz, A.packed);
             S.frac[3 * i] = c.fx;
             S.frac[3 * i + 1] = c.fy;
             S.frac[3 * i + 2] = c.fz;

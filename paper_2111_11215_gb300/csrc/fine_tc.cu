@@ -111,7 +111,7 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
     if (slot < 0) return;
     const float4 e0 = *de_slot(S.dout, b, row, 0), e1 = *de_slot(S.dout, b, row, 1), e2 = *de_slot(S.dout, b, row, 2);
     const float fx = S.sm.frac[b][row][0], fy = S.sm.frac[b][row][1], fz = S.sm.frac[b][row][2];
-    const long long cb = S.sm.cbase[b][row];
+    const int cb = S.sm.cbase[b][row];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         float dt;
         const Cell c = sample_cell(A, rr, kv.y, kv.x - rr.off, dt);
         slot = kv.x;
-        cbase = (int)grid_index(c.i0, c.j0, c.k0, A.ny, A.nz, false);   // canonical base
+        cbase = cell_base(c, A.ny, A.nz, A.packed);
         fx = c.fx;
         fy = c.fy;
         fz = c.fz;

@@ -140,18 +140,25 @@ class FineModel:
     def __init__(self, density: torch.Tensor, feat: torch.Tensor, mlp_flat: torch.Tensor, params: B.Params,
                  n_rays: int, bf16_feat: bool = False, box=((-1.0,) * 3, (1.0,) * 3),
                  lr_grid: float = 0.1, lr_mlp: float = 1e-3, decay_steps: float = 20000.0,
-                 overlap_adam: bool = False):
+                 overlap_adam: bool = False, layout: int = B.DVGO_LAYOUT_CANONICAL):
         self.params = params
         res = tuple(density.shape)
         C = feat.shape[-1]
+        self.layout = layout
+        if layout == B.DVGO_LAYOUT_PACKED:
+            # the grids (and with them their gradients and Adam state) live in the packed layout
+            density = B.dvgo_pack_grid(B.GridDesc(res, 1, box[0], box[1]), density.contiguous(),
+                                       B.GridDesc(res, 1, box[0], box[1], layout=layout))
+            feat = B.dvgo_pack_grid(B.GridDesc(res, C, box[0], box[1]), feat.contiguous(),
+                                    B.GridDesc(res, C, box[0], box[1], layout=layout))
         self.density = density.contiguous()
         self._feat = feat.contiguous()
         self.mlp_flat = mlp_flat.contiguous()
         self.mlp = mlp_views(self.mlp_flat, C + 3 + 6 * params.n_freq_dir, params.hidden)
         self.bf16_feat = bf16_feat
         self._feat_bf16 = self._feat.to(torch.bfloat16) if bf16_feat else None
-        self.dd = B.GridDesc(res, 1, box[0], box[1])
-        self.cd = B.GridDesc(res, C, box[0], box[1], B.DVGO_DTYPE_BF16 if bf16_feat else B.DVGO_DTYPE_F32)
+        self.dd = B.GridDesc(res, 1, box[0], box[1], layout=layout)
+        self.cd = B.GridDesc(res, C, box[0], box[1], B.DVGO_DTYPE_BF16 if bf16_feat else B.DVGO_DTYPE_F32, layout=layout)
         self.renderer = Renderer(params, self.dd, self.cd, n_rays, device=density.device)
         self.g_density = torch.zeros_like(self.density)
         self.g_feat = torch.zeros_like(self._feat)
