@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 3
+#define DVGO_ABI_VERSION 4
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -89,6 +89,16 @@ size_t dvgo_grid_elements(const dvgo_grid_desc *g);
  * elements of their descriptors; they must not overlap. */
 int dvgo_pack_grid(const dvgo_grid_desc *src, const void *in, const dvgo_grid_desc *dst, void *out, void *stream);
 
+/* Progressive scaling (Sec. 4.2): resizes a grid by trilinear interpolation onto another lattice.
+ * Point (i, j, k) of the destination sits at x = dst.xyz_min + (i, j, k) (dst.xyz_max -
+ * dst.xyz_min) / (n - 1) and takes interp(x, V_src) (Sec. 3 Eq. interp) of the source grid, x
+ * first clamped into the source box; positions and weights are formed in FP64, the result is
+ * rounded once to FP32.  Both grids FP32 with the same channel count, either layout each (padding
+ * points of a packed destination are set to 0); in / out are device buffers of
+ * dvgo_grid_elements() elements of their descriptors and must not overlap.  Stream-ordered. */
+int dvgo_resize_grid(const dvgo_grid_desc *src, const float *in, const dvgo_grid_desc *dst, float *out,
+                     void *stream);
+
 /*
  * Known free space of the fine stage (Sec. 4.2, "Known free space and unknown space" and "Free
  * space skipping"): the optimised coarse-stage density grid with its own lattice and box
@@ -132,13 +142,18 @@ typedef struct {
     int act_order;       /* Sec. 3 Eq. pre_in_post: DVGO_ACT_POST (the paper's choice),
                             DVGO_ACT_PRE  alpha = interp(x, alpha(softplus(V + b))),
                             DVGO_ACT_IN   alpha = alpha(interp(x, softplus(V + b)))              */
+    int n_freq_pos;      /* fine: positional-encoding frequencies on the query point x (Sec. 4.2
+                            Eq. fine_queries_rgb, Supp. A: k_x = 5); 0 leaves x out of the MLP
+                            input.  This build supports 0 and 5.                                 */
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
- *   in = C + 3 + 6*n_freq_dir  ->  hidden  ->  hidden  ->  3
+ *   in = C + 3 + 6*n_freq_dir (+ 3 + 6*n_freq_pos)  ->  hidden  ->  hidden  ->  3
  *   input row e = [interp(x, V_feat) (C), d (3), sin(2^k d_c) (c-major, k < n_freq_dir),
- *                  cos(2^k d_c) (c-major)],  ReLU after the hidden layers, sigmoid on the output
- *   (Sec. 2 Eq. nerf_mlp output activation, Sec. 4.2, Supp. A). */
+ *                  cos(2^k d_c) (c-major)] and, with n_freq_pos > 0, the same encoding of the
+ *                  world-space query point x appended: [x (3), sin(2^k x_c), cos(2^k x_c)];
+ *   ReLU after the hidden layers, sigmoid on the output (Sec. 2 Eq. nerf_mlp output activation,
+ *   Sec. 4.2 Eq. fine_queries_rgb, Supp. A: C = 12, k_d = 4, k_x = 5, in = 72). */
 typedef struct {
     const float *w1, *b1, *w2, *b2, *w3, *b3;
 } dvgo_mlp;

@@ -68,7 +68,7 @@ class _Params(C.Structure):
                 ("xyz_min", C.c_double * 3), ("xyz_max", C.c_double * 3), ("shift_b", C.c_double),
                 ("delta", C.c_double), ("tau_f", C.c_double), ("t_near", C.c_double),
                 ("t_far", C.c_double), ("bg", C.c_double * 3), ("w_pt", C.c_double), ("w_bg", C.c_double),
-                ("act_order", C.c_int)]
+                ("act_order", C.c_int), ("n_freq_pos", C.c_int)]
 
 
 class _FreeSpace(C.Structure):
@@ -123,6 +123,12 @@ class Params:
     w_pt: float = 0.0            # per-point rgb loss weight (Supp. A w_pt_rgb)
     w_bg: float = 0.0            # background entropy loss weight (Supp. A w_bg)
     act_order: int = 0           # Sec. 3: 0 post- (the paper's), 1 pre-, 2 in-activation
+    n_freq_pos: int = 0          # PE frequencies on the query point x (Supp. A k_x = 5); 0: x not input
+
+    @property
+    def in_dim(self) -> int:
+        """Width of the fine MLP input row (Eq. fine_queries_rgb)."""
+        return self.feat_dim + 3 + 6 * self.n_freq + (3 + 6 * self.n_freq_pos if self.n_freq_pos > 0 else 0)
 
     def _c(self) -> _Params:
         p = _Params()
@@ -135,6 +141,7 @@ class Params:
         p.bg[:] = [float(v) for v in self.bg]
         p.w_pt, p.w_bg = float(self.w_pt), float(self.w_bg)
         p.act_order = int(self.act_order)
+        p.n_freq_pos = int(self.n_freq_pos)
         return p
 
 
@@ -282,6 +289,22 @@ def interp(params: Params, grid, x):
     Cc = 1 if grid.ndim == 3 else grid.shape[-1]
     out = np.zeros(Cc)
     lib().oracle_interp(C.byref(P), _ptr(grid), C.c_int(Cc), _ptr(_f64(x)), _ptr(out))
+    return out
+
+
+def resize_grid(grid, dst_shape, src_box=((-1.0,) * 3, (1.0,) * 3), dst_box=None):
+    """Progressive scaling (Sec. 4.2): trilinear resize of a channel-last grid onto the
+    align-corners lattice of ``dst_shape`` points over ``dst_box`` (default: the source box)."""
+    grid = _f64(grid)
+    n = np.array(grid.shape[:3], dtype=np.int32)
+    Cc = 1 if grid.ndim == 3 else grid.shape[-1]
+    n2 = np.array([int(v) for v in dst_shape], dtype=np.int32)
+    dst_box = src_box if dst_box is None else dst_box
+    out = np.zeros(tuple(n2) + ((Cc,) if grid.ndim == 4 else ()))
+    ip = C.POINTER(C.c_int)
+    lib().oracle_resize_grid(n.ctypes.data_as(ip), _ptr(_f64(src_box[0])), _ptr(_f64(src_box[1])), C.c_int(Cc),
+                             _ptr(grid), n2.ctypes.data_as(ip), _ptr(_f64(dst_box[0])), _ptr(_f64(dst_box[1])),
+                             _ptr(out))
     return out
 
 

@@ -31,7 +31,11 @@
  *   * grid values sit on an align-corners lattice of N points per axis spanning the box;
  *   * a sample whose alpha is below tau_f is removed (alpha := 0, no colour query, no gradient);
  *   * the coarse colour has no activation unless rgb_act = 1 (sigmoid);
- *   * the fine MLP input is [features, d, sin(2^k d_c), cos(2^k d_c)] (c-major blocks, no pi);
+ *   * the fine MLP input is [features, d, sin(2^k d_c), cos(2^k d_c)] (c-major blocks, no pi),
+ *     followed, when positions are encoded too (Supp. A: k_x = 5), by the same encoding of the
+ *     world-space query point x;
+ *   * progressive scaling resizes a grid onto the align-corners lattice of the new dimensions over
+ *     the same box, each new lattice point taking interp(x, V_old) at its position;
  *   * the loss is (1/R) sum_r sum_ch (C_hat - C)^2.
  *
  * The integer decisions (how many samples a ray gets) are taken in FP64 with the operation order
@@ -74,6 +78,9 @@ typedef struct {
      *   1 pre:  alpha = interp(x, alpha(softplus(V + b)))
      *   2 in:   alpha = alpha(interp(x, softplus(V + b)))                                    */
     int act_order;
+    /* Positional-encoding frequencies on the query point x (Sec. 4.2 Eq. fine_queries_rgb, Supp. A
+     * k_x = 5); 0 leaves x out of the MLP input. */
+    int n_freq_pos;
 } og_params;
 
 /* Known free space (Sec. 4.2): the optimised coarse-stage density grid with its own lattice,
@@ -92,7 +99,8 @@ typedef struct {
 typedef struct {
     const double *density;      /* [nx][ny][nz]                                               */
     const double *cgrid;        /* [nx][ny][nz][C]                                             */
-    /* fine MLP, row-major [in][out]: in_dim = C + 3 + 6*n_freq -> hidden -> hidden -> 3       */
+    /* fine MLP, row-major [in][out]: in_dim = C + 3 + 6*n_freq (+ 3 + 6*n_freq_pos) -> hidden
+     * -> hidden -> 3                                                                            */
     const double *w1, *b1, *w2, *b2, *w3, *b3;
     const og_freespace *fs;     /* nullable: no known-free-space test                           */
 } og_model;
@@ -226,6 +234,35 @@ void oracle_interp(const og_params *P, const double *grid, int C, const double x
         for (int ch = 0; ch < C; ++ch) out[ch] += w[c] * grid[idx[c] * C + ch];
 }
 
+/* Progressive scaling (Sec. 4.2): resize a C-channel grid by trilinear interpolation.  The new
+ * grid has n2[0] x n2[1] x n2[2] points on the align-corners lattice of the box [dmin, dmax]; its
+ * point (i, j, k), at x = dmin + (i, j, k) (dmax - dmin) / (n2 - 1), takes interp(x, V) (Eq. interp)
+ * of the source grid (n[3] points on [smin, smax]), with x first clamped into the source box. */
+void oracle_resize_grid(const int n[3], const double smin[3], const double smax[3], int C, const double *src,
+                        const int n2[3], const double dmin[3], const double dmax[3], double *dst) {
+    og_params Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.nx = n[0];
+    Q.ny = n[1];
+    Q.nz = n[2];
+    for (int a = 0; a < 3; ++a) {
+        Q.xyz_min[a] = smin[a];
+        Q.xyz_max[a] = smax[a];
+    }
+    long npts = (long)n2[0] * n2[1] * n2[2];
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < npts; ++p) {
+        int ijk[3] = {(int)(p / ((long)n2[1] * n2[2])), (int)((p / n2[2]) % n2[1]), (int)(p % n2[2])};
+        double x[3];
+        for (int a = 0; a < 3; ++a) {
+            x[a] = dmin[a] + (double)ijk[a] * (dmax[a] - dmin[a]) / (double)(n2[a] - 1);
+            if (x[a] < smin[a]) x[a] = smin[a];
+            if (x[a] > smax[a]) x[a] = smax[a];
+        }
+        oracle_interp(&Q, src, C, x, dst + p * C);
+    }
+}
+
 /* Post-activated alpha at a point (Eq. post_activation): alpha(softplus(interp(x, V) + b), delta). */
 double oracle_alpha_at(const og_params *P, const double *density, const double x[3], double delta) {
     double s;
@@ -288,26 +325,37 @@ long oracle_unknown_bbox(const og_freespace *F, int lo[3], int hi[3]) {
 /* Colour model                                                                                 */
 /* ------------------------------------------------------------------------------------------ */
 
-/* MLP input row (fine stage): [feat(C), d(3), sin(2^k d_c) (c-major), cos(2^k d_c) (c-major)]. */
-static void og_mlp_input(const og_params *P, const double *feat, const double dn[3], double *e) {
-    int C = P->feat_dim, F = P->n_freq;
-    for (int ch = 0; ch < C; ++ch) e[ch] = feat[ch];
-    for (int a = 0; a < 3; ++a) e[C + a] = dn[a];
+/* Positional encoding of a 3-vector v with F frequencies into e:
+ * [v (3), sin(2^k v_c) (c-major, k < F), cos(2^k v_c) (c-major)], 3 + 6F values. */
+static void og_posenc(const double v[3], int F, double *e) {
+    for (int a = 0; a < 3; ++a) e[a] = v[a];
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < F; ++k) {
-            double arg = ldexp(dn[a], k);
-            e[C + 3 + a * F + k] = sin(arg);
-            e[C + 3 + 3 * F + a * F + k] = cos(arg);
+            double arg = ldexp(v[a], k);
+            e[3 + a * F + k] = sin(arg);
+            e[3 + 3 * F + a * F + k] = cos(arg);
         }
 }
 
-int oracle_mlp_in_dim(int feat_dim, int n_freq) { return feat_dim + 3 + 6 * n_freq; }
+/* MLP input row (fine stage, Eq. fine_queries_rgb): [feat (C), PE(d, n_freq)] and, with
+ * n_freq_pos > 0, PE(x, n_freq_pos) of the world-space query point appended. */
+static void og_mlp_input(const og_params *P, const double *feat, const double dn[3], const double x[3],
+                         double *e) {
+    int C = P->feat_dim;
+    for (int ch = 0; ch < C; ++ch) e[ch] = feat[ch];
+    og_posenc(dn, P->n_freq, e + C);
+    if (P->n_freq_pos > 0) og_posenc(x, P->n_freq_pos, e + C + 3 + 6 * P->n_freq);
+}
+
+int oracle_mlp_in_dim(int feat_dim, int n_freq, int n_freq_pos) {
+    return feat_dim + 3 + 6 * n_freq + (n_freq_pos > 0 ? 3 + 6 * n_freq_pos : 0);
+}
 
 /* Forward of the shallow colour MLP, keeping pre-activations for the backward.
  * z1 = e W1 + b1, h1 = relu(z1), z2 = h1 W2 + b2, h2 = relu(z2), o = h2 W3 + b3, c = sigmoid(o). */
 static void og_mlp_fwd(const og_params *P, const og_model *M, const double *e, double *z1,
                        double *h1, double *z2, double *h2, double c[3]) {
-    int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq), H = P->hidden;
+    int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), H = P->hidden;
     for (int j = 0; j < H; ++j) {
         double s = M->b1[j];
         for (int i = 0; i < I; ++i) s += e[i] * M->w1[i * H + j];
@@ -332,7 +380,7 @@ void oracle_mlp_forward(const og_params *P, const og_model *M, int n, const doub
     int H = P->hidden;
     double *buf = (double *)malloc(sizeof(double) * 4 * H);
     for (int r = 0; r < n; ++r)
-        og_mlp_fwd(P, M, e + (long)r * oracle_mlp_in_dim(P->feat_dim, P->n_freq), buf, buf + H,
+        og_mlp_fwd(P, M, e + (long)r * oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), buf, buf + H,
                    buf + 2 * H, buf + 3 * H, c + 3 * r);
     free(buf);
 }
@@ -374,7 +422,7 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
     if (tin) *tin = t_enter;
     if (tout) *tout = t_exit;
     int C = P->feat_dim, H = P->hidden;
-    int I = (P->mode == 1) ? oracle_mlp_in_dim(C, P->n_freq) : 0;
+    int I = (P->mode == 1) ? oracle_mlp_in_dim(C, P->n_freq, P->n_freq_pos) : 0;
     og_sample *S = (og_sample *)calloc(n > 0 ? n : 1, sizeof(og_sample));
     double *act = NULL; /* per-sample MLP activations: e, z1, h1, z2, h2 */
     int stride = I + 4 * H;
@@ -427,7 +475,7 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                 }
             } else {
                 double *e = act + (size_t)k * stride;
-                og_mlp_input(P, feat, dn, e);
+                og_mlp_input(P, feat, dn, s->x, e);
                 og_mlp_fwd(P, M, e, e + I, e + I + H, e + I + 2 * H, e + I + 3 * H, s->c);
             }
         }
@@ -572,7 +620,7 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
                    const double *dts, const double *target, double *rgb, double *tfinal,
                    int *nsamp, double *t_enter, double *t_exit, double *loss, const double *gC,
                    const double *gT, og_grads *G, double *wbins, int nbins) {
-    int H = P->hidden, I = oracle_mlp_in_dim(P->feat_dim, P->n_freq);
+    int H = P->hidden, I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos);
     /* Sizes of the MLP parameter blocks w1, b1, w2, b2, w3, b3. */
     long nw[6] = {(long)I * H, H, (long)H * H, H, (long)H * 3, 3};
     int want_mlp = (gC != NULL) && (P->mode == 1);

@@ -22,7 +22,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
-    "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid",
+    "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
@@ -61,7 +61,7 @@ class _Params(C.Structure):
                 ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
                 ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
-                ("act_order", C.c_int)]
+                ("act_order", C.c_int), ("n_freq_pos", C.c_int)]
 
 
 class _Mlp(C.Structure):
@@ -115,6 +115,8 @@ def lib():
         L.dvgo_grid_elements.argtypes = [vp]
         L.dvgo_pack_grid.restype = i
         L.dvgo_pack_grid.argtypes = [vp, vp, vp, vp, vp]
+        L.dvgo_resize_grid.restype = i
+        L.dvgo_resize_grid.argtypes = [vp, vp, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -195,6 +197,14 @@ class Params:
     w_pt_rgb: float = 0.0        # per-point rgb loss weight (Supp. A)
     w_bg: float = 0.0            # background entropy loss weight (Supp. A)
     act_order: int = 0           # Sec. 3 interpolation / activation order: 0 post, 1 pre, 2 in
+    n_freq_pos: int = 0          # PE frequencies on the query point x (Supp. A: 5); 0: x not an MLP input
+
+    def mlp_in_dim(self, channels: int = 12) -> int:
+        """Width of the fine MLP's input row (Sec. 4.2 Eq. fine_queries_rgb): 39, or 72 with PE(x)."""
+        return channels + 3 + 6 * self.n_freq_dir + (3 + 6 * self.n_freq_pos if self.n_freq_pos > 0 else 0)
+
+    def with_(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
 
     def c(self) -> _Params:
         p = _Params()
@@ -205,6 +215,7 @@ class Params:
         p.bg[:] = [float(v) for v in self.bg]
         p.w_pt_rgb, p.w_bg = float(self.w_pt_rgb), float(self.w_bg)
         p.act_order = int(self.act_order)
+        p.n_freq_pos = int(self.n_freq_pos)
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)
@@ -453,6 +464,19 @@ def dvgo_grid_elements(desc: GridDesc) -> int:
     included)."""
     g = desc.c()
     return int(lib().dvgo_grid_elements(C.byref(g)))
+
+
+def dvgo_resize_grid(src_desc: GridDesc, src, dst_desc: GridDesc, out=None, stream=None):
+    """Progressive scaling (Sec. 4.2): trilinear resize of an FP32 grid onto the lattice of
+    dst_desc; returns the (flat) output tensor."""
+    if out is None:
+        out = torch.empty(dvgo_grid_elements(dst_desc), dtype=torch.float32, device=src.device)
+    if out.numel() != dvgo_grid_elements(dst_desc) or src.numel() != dvgo_grid_elements(src_desc):
+        raise ValueError("dvgo_resize_grid: tensor sizes do not match the descriptors")
+    a, b = src_desc.c(), dst_desc.c()
+    _check(lib().dvgo_resize_grid(C.byref(a), _dev(src, "src", torch.float32), C.byref(b),
+                                  _dev(out, "out", torch.float32), _stream(stream)), "dvgo_resize_grid")
+    return out
 
 
 def dvgo_pack_grid(src_desc: GridDesc, src, dst_desc: GridDesc, out=None, stream=None):

@@ -98,6 +98,7 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
         if (cd->dtype != DVGO_DTYPE_F32 && cd->dtype != DVGO_DTYPE_BF16) return DVGO_ERR_INVALID_ARG;
         if (p->mlp_prec != DVGO_MLP_FP32 && p->mlp_prec != DVGO_MLP_BF16) return DVGO_ERR_INVALID_ARG;
         if (cd->channels != 12 || p->n_freq_dir != 4 || p->hidden != 128) return DVGO_ERR_UNSUPPORTED;
+        if (p->n_freq_pos != 0 && p->n_freq_pos != 5) return DVGO_ERR_UNSUPPORTED;
     } else {
         return DVGO_ERR_INVALID_ARG;
     }
@@ -193,7 +194,15 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
         A.b2 = mlp->b2;
         A.w3 = mlp->w3;
         A.b3 = mlp->b3;
-        A.in_dim = cd->channels + 3 + 6 * p->n_freq_dir;
+        A.in_dim = cd->channels + 3 + 6 * p->n_freq_dir + (p->n_freq_pos > 0 ? 3 + 6 * p->n_freq_pos : 0);
+    }
+    if (p->mode == DVGO_MODE_FINE) {
+        A.nfreq_pos = p->n_freq_pos;
+        const int n[3] = {dd->nx, dd->ny, dd->nz};
+        for (int a = 0; a < 3; ++a) {
+            A.pos0[a] = dd->xyz_min[a];
+            A.posh[a] = (float)(((double)dd->xyz_max[a] - dd->xyz_min[a]) / (n[a] - 1));
+        }
     }
     return A;
 }

@@ -69,6 +69,8 @@ struct WsLayout {
 struct RenderArgs {
     int R;
     int mode, rgb_act, mlp_prec, nfreq, hidden;
+    int nfreq_pos;              // fine: PE frequencies on the query point x (0: x is not an input)
+    float pos0[3], posh[3];     // world position of lattice coordinate u: pos0 + u posh (FP32)
     float step, shift_b, tau_f;
     float bg[3];
     int nx, ny, nz, C;
@@ -268,6 +270,27 @@ __device__ __forceinline__ Cell cell_from_fx(const long long u[3], int nx, int n
     fx_axis(u[1], ny, c.j0, c.fy);
     fx_axis(u[2], nz, c.k0, c.fz);
     return c;
+}
+
+// World-space position of a sample from its cell, x = xyz_min + (i0 + f) h per axis, in FP32 (the
+// input of the positional encoding of x).
+__device__ __forceinline__ void cell_world(const RenderArgs &A, const Cell &c, float x[3]) {
+    x[0] = fmaf(c.fx, A.posh[0], fmaf((float)c.i0, A.posh[0], A.pos0[0]));
+    x[1] = fmaf(c.fy, A.posh[1], fmaf((float)c.j0, A.posh[1], A.pos0[1]));
+    x[2] = fmaf(c.fz, A.posh[2], fmaf((float)c.k0, A.posh[2], A.pos0[2]));
+}
+
+// Positional encoding of one coordinate v with F frequencies: s[k] = sin(2^k v), c[k] = cos(2^k v),
+// k < F, from one sincosf and the double-angle identities sin 2a = 2 sin a cos a,
+// cos 2a = (cos a - sin a)(cos a + sin a).
+template <int F>
+__device__ __forceinline__ void pe_axis(float v, float *s, float *c) {
+    sincosf(v, &s[0], &c[0]);
+#pragma unroll
+    for (int k = 1; k < F; ++k) {
+        s[k] = 2.0f * s[k - 1] * c[k - 1];
+        c[k] = (c[k - 1] - s[k - 1]) * (c[k - 1] + s[k - 1]);
+    }
 }
 
 // Cell and step length of sample k of a ray.

@@ -1,9 +1,11 @@
 // fine_simt.cu -- colour queries of the fine stage with the FP32 (SIMT) shallow MLP.
 //
-// Sec. 4.2 Eq. fine_queries_rgb and Supp. A: c = MLP(interp(x, V_feat), PE(d)) with D = 12 feature
-// channels, k_d = 4 direction frequencies, two hidden layers of 128 and ReLU, sigmoid output.
-// Input row e = [feat (12), d (3), sin(2^k d_c) (12, c-major), cos(2^k d_c) (12)] and a constant 1
-// in column 39 that carries the first-layer bias (W1 row 39 = b1).
+// Sec. 4.2 Eq. fine_queries_rgb and Supp. A: c = MLP(interp(x, V_feat), PE(d)[, PE(x)]) with D = 12
+// feature channels, k_d = 4 direction frequencies, optionally k_x = 5 frequencies on the query
+// point, two hidden layers of 128 and ReLU, sigmoid output.  Input row e = [feat (12), d (3),
+// sin(2^k d_c) (12, c-major), cos(2^k d_c) (12)] (39 inputs), with PE(x) [x (3), sin(2^k x_c)
+// (15), cos(2^k x_c) (15)] appended (72 inputs), and a constant 1 in the next column that carries
+// the first-layer bias (W1 row IN = b1).
 //
 // Persistent CTAs (one per SM, 256 threads) walk tiles of 64 kept samples from the compact
 // list.  Weights stay in shared memory for the whole launch.  Activations are stored
@@ -31,18 +33,29 @@ constexpr int NT = 256;           // threads per CTA
 constexpr int HID = 128;
 constexpr int FEAT = 12;
 constexpr int NF = 4;
-constexpr int IN = FEAT + 3 + 6 * NF;   // 39
-constexpr int K1 = IN + 1;              // 40 with the bias column
+constexpr int NFX = 5;
 constexpr int LDA = TM + 4;             // 68: activation row stride
 constexpr int LDW = HID + 4;            // 132: weight row stride
+constexpr int PX = FEAT + 3 + 6 * NF;   // 39: first input of the PE(x) block
 
+// Input widths: 39 (features + PE(d)) or 72 (+ PE(x)); K1 adds the bias column; the backward
+// splits the K1 (padded to 2 KH) rows of dW1|b1 between two thread halves.
+template <bool PEX>
+struct Dims {
+    static constexpr int IN = PX + (PEX ? 3 + 6 * NFX : 0);
+    static constexpr int K1 = IN + 1;
+    static constexpr int KH = (K1 + 1) / 2;
+};
+
+template <bool PEX>
 struct Smem {
+    static constexpr int K1 = Dims<PEX>::K1, KP = 2 * Dims<PEX>::KH;
     float w1[K1 * LDW];
     float w2[HID * LDW];
     float b2[HID];
     float w3[HID * 3];
     float b3[4];
-    float xt[K1 * LDA];        // X^T
+    float xt[KP * LDA];        // X^T (a zero padding row when K1 is odd)
     float h1[HID * LDA];       // H1^T, later dZ1^T
     float h2[HID * LDA];       // H2^T, later dZ2^T
     float dout[TM * 3];        // dL/do (pre-sigmoid) per sample
@@ -56,7 +69,10 @@ __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
 // Load weights into shared memory (FP32 master weights, row-major [in][out]).
-__device__ void load_weights(Smem &S, const RenderArgs &A) {
+template <bool PEX>
+__device__ void load_weights(Smem<PEX> &S, const RenderArgs &A) {
+    constexpr int IN = Dims<PEX>::IN, K1 = Dims<PEX>::K1;
+    for (int i = threadIdx.x; i < (Smem<PEX>::KP - K1) * LDA; i += NT) S.xt[K1 * LDA + i] = 0.0f;
     for (int i = threadIdx.x; i < K1 * HID; i += NT) {
         int k = i / HID, j = i % HID;
         S.w1[k * LDW + j] = (k < IN) ? A.w1[k * HID + j] : A.b1[j];
@@ -69,8 +85,9 @@ __device__ void load_weights(Smem &S, const RenderArgs &A) {
 
 // Gather the input rows of one tile: 4 threads per sample, thread q handles the corner pair
 // (x bit, y bit) = (q >> 1, q & 1) with z = 0, 1 (adjacent in memory).
-template <typename FeatT>
-__device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) {
+template <typename FeatT, bool PEX>
+__device__ void gather_tile(Smem<PEX> &S, const RenderArgs &A, int tile, int n_kept) {
+    constexpr int IN = Dims<PEX>::IN;
     int tid = threadIdx.x;
     int i = tid >> 2, q = tid & 3;
     int e = tile * TM + i;
@@ -80,6 +97,7 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
     for (int c = 0; c < FEAT; ++c) f[c] = 0.0f;
     const RayRec *rp = nullptr;
     int ray = 0, slot = -1;
+    float xw = 0.0f;   // world coordinate of axis q - 1 (PE(x), threads q = 1..3)
     if (valid) {
         int2 kv = A.kept[e];
         slot = kv.x;
@@ -89,6 +107,11 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
         int k = slot - rr.off;
         float dt;
         Cell c = sample_cell(A, rr, ray, k, dt);
+        if (PEX && q > 0) {
+            float xv[3];
+            cell_world(A, c, xv);
+            xw = xv[q - 1];
+        }
         if (q == 0) {
             S.cbase[i] = cell_base(c, A.ny, A.nz, A.packed);
             S.frac[3 * i] = c.fx;
@@ -156,6 +179,16 @@ __device__ void gather_tile(Smem &S, const RenderArgs &A, int tile, int n_kept) 
             S.xt[(FEAT + 3 + a * NF + k) * LDA + i] = s;
             S.xt[(FEAT + 3 + 3 * NF + a * NF + k) * LDA + i] = cs;
         }
+        if constexpr (PEX) {
+            float sx[NFX], cx[NFX];
+            pe_axis<NFX>(xw, sx, cx);
+            S.xt[(PX + a) * LDA + i] = xw;
+#pragma unroll
+            for (int k = 0; k < NFX; ++k) {
+                S.xt[(PX + 3 + a * NFX + k) * LDA + i] = sx[k];
+                S.xt[(PX + 3 + 3 * NFX + a * NFX + k) * LDA + i] = cx[k];
+            }
+        }
     }
 }
 
@@ -192,23 +225,25 @@ __device__ __forceinline__ void gemm_fwd(const float *InT, const float *W, const
 }
 
 // Output layer for sample s = tid & 63, channel ch = tid >> 6 (< 3): o = h2 . W3[:, ch] + b3.
-__device__ __forceinline__ float out_logit(const Smem &S, int s, int ch) {
+template <bool PEX>
+__device__ __forceinline__ float out_logit(const Smem<PEX> &S, int s, int ch) {
     float o = S.b3[ch];
 #pragma unroll 8
     for (int j = 0; j < HID; ++j) o = fmaf(S.h2[j * LDA + s], S.w3[j * 3 + ch], o);
     return o;
 }
 
-template <typename FeatT>
+template <typename FeatT, bool PEX>
 __global__ void __launch_bounds__(NT, 1) fine_colour_fwd_kernel(RenderArgs A) {
+    constexpr int K1 = Dims<PEX>::K1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<PEX> &S = *reinterpret_cast<Smem<PEX> *>(smem_raw);
     load_weights(S, A);
     const int n_kept = A.hdr->n_kept;
     const int ntiles = (n_kept + TM - 1) / TM;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        gather_tile<FeatT>(S, A, tile, n_kept);
+        gather_tile<FeatT, PEX>(S, A, tile, n_kept);
         __syncthreads();
         gemm_fwd<K1>(S.xt, S.w1, nullptr, S.h1);
         __syncthreads();
@@ -222,10 +257,11 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_fwd_kernel(RenderArgs A) {
     }
 }
 
-template <typename FeatT>
+template <typename FeatT, bool PEX>
 __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
+    constexpr int IN = Dims<PEX>::IN, K1 = Dims<PEX>::K1, KH = Dims<PEX>::KH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<PEX> &S = *reinterpret_cast<Smem<PEX> *>(smem_raw);
     load_weights(S, A);
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -233,7 +269,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
     const int ntiles = (n_kept + TM - 1) / TM;
 
     float gw2[8][8];       // dW2[tx + 16 i][ty + 16 jj]
-    float gw1[20];         // dW1|b1[kh*20 + kk][j], j = tid & 127, kh = tid >> 7
+    float gw1[KH];         // dW1|b1[kh*KH + kk][j], j = tid & 127, kh = tid >> 7
     float gw3[3];          // dW3[tid][ch] (tid < 128)
     float gb2 = 0.0f;      // db2[tid - 128] (tid >= 128)
     float gb3 = 0.0f;      // db3[tid] (tid < 3)
@@ -242,12 +278,12 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) gw2[i][j] = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 20; ++i) gw1[i] = 0.0f;
+    for (int i = 0; i < KH; ++i) gw1[i] = 0.0f;
     gw3[0] = gw3[1] = gw3[2] = 0.0f;
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        gather_tile<FeatT>(S, A, tile, n_kept);
+        gather_tile<FeatT, PEX>(S, A, tile, n_kept);
         __syncthreads();
         gemm_fwd<K1>(S.xt, S.w1, nullptr, S.h1);
         __syncthreads();
@@ -366,14 +402,14 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
             }
         }
         __syncthreads();
-        // dW1|b1 += X^T dZ1 : thread j = tid & 127, rows kh*20 .. kh*20+19
+        // dW1|b1 += X^T dZ1 : thread j = tid & 127, rows kh*KH .. kh*KH+KH-1
         {
             int j = tid & 127, kh = tid >> 7;
             for (int s = 0; s < TM; s += 4) {
                 float4 b = ld4(S.h1 + j * LDA + s);
 #pragma unroll
-                for (int kk = 0; kk < 20; ++kk) {
-                    float4 a = ld4(S.xt + (kh * 20 + kk) * LDA + s);
+                for (int kk = 0; kk < KH; ++kk) {
+                    float4 a = ld4(S.xt + (kh * KH + kk) * LDA + s);
                     gw1[kk] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, gw1[kk]))));
                 }
             }
@@ -426,10 +462,10 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
     {
         int j = tid & 127, kh = tid >> 7;
 #pragma unroll
-        for (int kk = 0; kk < 20; ++kk) {
-            int k = kh * 20 + kk;
+        for (int kk = 0; kk < KH; ++kk) {
+            int k = kh * KH + kk;
             if (k < IN) atomicAdd(gW1 + k * HID + j, gw1[kk]);
-            else atomicAdd(gB1 + j, gw1[kk]);
+            else if (k == IN) atomicAdd(gB1 + j, gw1[kk]);
         }
     }
     if (tid < HID) {
@@ -442,26 +478,33 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
     if (tid < 3) atomicAdd(gB3 + tid, gb3);
 }
 
+template <bool PEX>
 void launch_persistent(void (*kernel)(RenderArgs), int kind, const RenderArgs &A, cudaStream_t s) {
-    ensure_smem(reinterpret_cast<const void *>(kernel), (int)sizeof(Smem));
+    ensure_smem(reinterpret_cast<const void *>(kernel), (int)sizeof(Smem<PEX>));
     ProfScope ps_(kind, s);
-    kernel<<<num_sms(), NT, sizeof(Smem), s>>>(A);
+    kernel<<<num_sms(), NT, sizeof(Smem<PEX>), s>>>(A);
+}
+
+template <bool BWD, bool PEX>
+void launch_colour(const RenderArgs &A, cudaStream_t s) {
+    const int kind = BWD ? DVGO_K_FINE_COLOUR_BWD : DVGO_K_FINE_COLOUR_FWD;
+    if (A.cdtype == DVGO_DTYPE_BF16)
+        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<__nv_bfloat16, PEX> : fine_colour_fwd_kernel<__nv_bfloat16, PEX>,
+                               kind, A, s);
+    else
+        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<float, PEX> : fine_colour_fwd_kernel<float, PEX>, kind, A, s);
 }
 
 }  // namespace
 
 void launch_fine_colour_fwd_simt(const RenderArgs &A, cudaStream_t s) {
-    if (A.cdtype == DVGO_DTYPE_BF16)
-        launch_persistent(fine_colour_fwd_kernel<__nv_bfloat16>, DVGO_K_FINE_COLOUR_FWD, A, s);
-    else
-        launch_persistent(fine_colour_fwd_kernel<float>, DVGO_K_FINE_COLOUR_FWD, A, s);
+    if (A.nfreq_pos > 0) launch_colour<false, true>(A, s);
+    else launch_colour<false, false>(A, s);
 }
 
 void launch_fine_colour_bwd_simt(const RenderArgs &A, cudaStream_t s) {
-    if (A.cdtype == DVGO_DTYPE_BF16)
-        launch_persistent(fine_colour_bwd_kernel<__nv_bfloat16>, DVGO_K_FINE_COLOUR_BWD, A, s);
-    else
-        launch_persistent(fine_colour_bwd_kernel<float>, DVGO_K_FINE_COLOUR_BWD, A, s);
+    if (A.nfreq_pos > 0) launch_colour<true, true>(A, s);
+    else launch_colour<true, false>(A, s);
 }
 
 }  // namespace dvgo

@@ -1,7 +1,8 @@
 // fine_tc.cu -- colour queries of the fine stage with the BF16 tensor-core MLP (tcgen05, sm_103a).
 //
 // Same function as fine_simt.cu (Sec. 4.2 Eq. fine_queries_rgb, Supp. A: 12 features + PE(d, 4)
-// = 39 inputs, two hidden layers of 128 with ReLU, sigmoid output) with the two 128-wide layers
+// = 39 inputs, or 72 with PE(x, 5) appended; two hidden layers of 128 with ReLU, sigmoid output)
+// with the two 128-wide layers
 // and all weight-gradient contractions on the 5th-generation tensor cores: BF16 operands in
 // shared memory (128-byte swizzled panels, see tc_helpers.cuh), FP32 accumulators in TMEM, MMAs
 // issued by one thread, completion signalled through mbarriers.  The 128 -> 3 output layer, the
@@ -15,7 +16,13 @@
 // handles columns 64 (w / 4)..+63 of those rows, so two warps share each row.  full[b] / empty[b]
 // mbarriers hand the X panels over; every wait is bounded.
 //
-// Forward per tile:  X[128x64] (features, PE(d), 1) -> Z1 = X W1|b1 -> H1 = relu(Z1) -> Z2 = H1 W2
+// Inputs beyond the 64 columns of the X panel (PE(x) entries 24-32 of the 72-input row) live in a
+// "tail panel" that also holds W3: columns 0-15 W3 (3 used), 16-31 / 32-47 the tail of X buffer 0 /
+// 1, 48-63 the tail rows of W1 (transposed).  Layer 1 adds one K = 16 MMA over the tails; the
+// backward adds dW1_tail^T += dZ1^T X_tail (an MN-major operand that starts 32 or 64 bytes into
+// the swizzled rows).
+//
+// Forward per tile:  X[128x64] (features, PE(d), [PE(x)], 1) -> Z1 = X W1|b1 -> H1 = relu(Z1) -> Z2 = H1 W2
 //                    -> H2 = relu(Z2 + b2) -> O = H2 W3 (N = 16, 3 used) -> c = sigmoid(O + b3).
 // Backward per tile (recomputes the forward), with dL/dc from the compositing backward:
 //   dout = dL/dc c (1 - c)                                        (epilogue, BF16 panel)
@@ -25,7 +32,7 @@
 //   de = dZ1 W1[0:16]^T;  [dW1 | db1]^T += dZ1^T X                 (MMAs)
 //   de[0:12] -> shared memory -> scattered to the feature grid by the producers
 // TMEM columns: Z1 / O / dH2 [0,128), Z2 / dH1 [128,256), dW2 [256,384), dW1^T [384,448),
-// dW3 [448,464), db2 [464,480), de [480,496).  The weight-gradient accumulators live in TMEM for
+// dW3 [448,464), db2 [464,480), de [480,496), dW1_tail^T [496,512).  The weight-gradient accumulators live in TMEM for
 // the whole launch and are added to global memory once per CTA.
 
 #include <stddef.h>
@@ -46,10 +53,21 @@ constexpr int NP = 128;        // producer threads (one sample row each)
 constexpr int HID = 128;
 constexpr int FEAT = 12;
 constexpr int NF = 4;
-constexpr int IN = FEAT + 3 + 6 * NF;   // 39; column 39 of X carries the first-layer bias
+constexpr int NFX = 5;
+constexpr int PX = FEAT + 3 + 6 * NF;   // 39: first input of the PE(x) block
+
+// Input row of the two widths: IN inputs, NMAIN of them in the X panel, the first-layer bias as
+// the constant-1 column BIAS of the X panel, NTAIL inputs in the tail panel.
+template <bool PEX>
+struct TcDims {
+    static constexpr int IN = PX + (PEX ? 3 + 6 * NFX : 0);   // 39 or 72
+    static constexpr int NMAIN = PEX ? 63 : IN;
+    static constexpr int BIAS = NMAIN;
+    static constexpr int NTAIL = IN - NMAIN;                  // 0 or 9
+};
 
 constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_DH2 = 0, COL_Z2 = 128, COL_DW2 = 256, COL_DW1 = 384, COL_DW3 = 448,
-                   COL_DB2 = 464, COL_DE = 480;
+                   COL_DB2 = 464, COL_DE = 480, COL_DW1T = 496;
 
 // Small per-CTA state, padded to a multiple of 1024 bytes so that the panels after it stay
 // aligned to the 128-byte-swizzle atom.
@@ -69,7 +87,8 @@ struct alignas(1024) SmallTC {
 struct SmemTC {
     unsigned char w1t[kPanelBytes];       // W1|b1 transposed: row = hidden unit, 64 input columns
     unsigned char w2t[2 * kPanelBytes];   // W2 transposed: row = output unit, 128 input columns
-    unsigned char w3p[kPanelBytes];       // W3: row = hidden unit, columns 0-2 (3-63 zero)
+    unsigned char tp[kPanelBytes];        // tail panel: row = hidden unit / sample; W3 in columns 0-2,
+                                          // X tails in 16-31 / 32-47, W1 tail in 48-63
     unsigned char x[2][kPanelBytes];      // X (double-buffered): row = sample
     unsigned char h1[2 * kPanelBytes];    // H1, later dZ1
     unsigned char h2[2 * kPanelBytes];    // H2
@@ -124,12 +143,15 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
     }
 }
 
-// Producer: gather sample row `row` of a tile into X panel b and the per-row tables.
-template <typename FeatT, bool BWD>
+// Producer: gather sample row `row` of a tile into X panel b (and its tail) and the per-row tables.
+template <typename FeatT, bool BWD, bool PEX>
 __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int e, int n_kept, int row) {
-    float v[64];
+    using D = TcDims<PEX>;
+    float v[64], tail[16];
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tail[i] = 0.0f;
     int slot = -1, cbase = 0;
     float fx = 0.0f, fy = 0.0f, fz = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
     if (e < n_kept) {
@@ -193,10 +215,28 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
             if (4 * k + 2 < 27) v[FEAT + 4 * k + 2] = q4.z;
             if (4 * k + 3 < 27) v[FEAT + 4 * k + 3] = q4.w;
         }
-        v[IN] = 1.0f;
+        if constexpr (PEX) {
+            // PE(x) of the world-space sample position: [x (3), sin(2^k x_c) (15), cos(2^k x_c) (15)]
+            float xv[3], pe[3 + 6 * NFX];
+            cell_world(A, c, xv);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                pe[a] = xv[a];
+                pe_axis<NFX>(xv[a], pe + 3 + a * NFX, pe + 3 + 3 * NFX + a * NFX);
+            }
+#pragma unroll
+            for (int j = 0; j < D::NMAIN - PX; ++j) v[PX + j] = pe[j];
+#pragma unroll
+            for (int j = 0; j < D::NTAIL; ++j) tail[j] = pe[D::NMAIN - PX + j];
+        }
+        v[D::BIAS] = 1.0f;
     }
 #pragma unroll
     for (int c = 0; c < 64; c += 8) panel_store8(S.x[b], row, c, v + c);
+    if constexpr (PEX) {
+        panel_store8(S.tp, row, 16 * (1 + b), tail);
+        panel_store8(S.tp, row, 16 * (1 + b) + 8, tail + 8);
+    }
     S.sm.slot[b][row] = slot;
     S.sm.cbase[b][row] = cbase;
     S.sm.frac[b][row][0] = fx;
@@ -209,8 +249,9 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
     }
 }
 
-template <typename FeatT, bool BWD>
+template <typename FeatT, bool BWD, bool PEX>
 __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
+    using D = TcDims<PEX>;
     extern __shared__ unsigned char smem_raw[];
     SmemTC &S = *reinterpret_cast<SmemTC *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -226,10 +267,11 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     }
     if (warp == 0) tmem_alloc(&S.sm.tmem_base, NCOLS);
     if (tid < TM) {
-        // weights: row n = tid of W1^T (64 input columns, bias in column 39), of W2^T and of W3
+        // weights: row n = tid of W1^T (64 input columns, bias in column BIAS), of W2^T and of the
+        // tail panel (W3, and with PE(x) the tail rows of W1)
         float v[64];
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = k < IN ? A.w1[k * HID + tid] : (k == IN ? A.b1[tid] : 0.0f);
+        for (int k = 0; k < 64; ++k) v[k] = k < D::NMAIN ? A.w1[k * HID + tid] : (k == D::BIAS ? A.b1[tid] : 0.0f);
 #pragma unroll
         for (int c = 0; c < 64; c += 8) panel_store8(S.w1t, tid, c, v + c);
 #pragma unroll
@@ -240,9 +282,11 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             for (int c = 0; c < 64; c += 8) panel_store8(S.w2t + pnl * kPanelBytes, tid, c, v + c);
         }
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = k < 3 ? A.w3[3 * tid + k] : 0.0f;
+        for (int k = 0; k < 64; ++k)
+            v[k] = k < 3 ? A.w3[3 * tid + k]
+                         : ((k >= 48 && k - 48 < D::NTAIL) ? A.w1[(D::NMAIN + k - 48) * HID + tid] : 0.0f);
 #pragma unroll
-        for (int c = 0; c < 64; c += 8) panel_store8(S.w3p, tid, c, v + c);
+        for (int c = 0; c < 64; c += 8) panel_store8(S.tp, tid, c, v + c);
         if (BWD) {
 #pragma unroll
             for (int k = 0; k < 64; ++k) v[k] = 0.0f;
@@ -277,7 +321,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 if (BWD) scatter_row(A, S, b, row);   // feature gradients of tile i - 2
             }
             if (*(volatile int *)&S.sm.abort) break;
-            produce_row<FeatT, BWD>(A, S, b, tile * TM + row, n_kept, row);
+            produce_row<FeatT, BWD, PEX>(A, S, b, tile * TM + row, n_kept, row);
             fence_async_smem();
             mbar_arrive(&S.sm.full[b]);
         }
@@ -308,7 +352,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             const int b = i & 1;
             const uint32_t acc_w = i > 0 ? 1u : 0u;   // first tile of this CTA initialises the accumulators
             // opaque copies: keeps the compiler from hoisting every MMA descriptor out of the loop
-            uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.w3p);
+            uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.tp);
             uint32_t h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), dz2_ = smem_u32(S.dz2), dout_ = smem_u32(S.dout);
             asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(h1_), "+r"(h2_), "+r"(dz2_), "+r"(dout_));
             if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1)) ok = false;
@@ -323,6 +367,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 #pragma unroll 1
                 for (int kk = 0; kk < 4; ++kk)
                     mma(tb + COL_Z1, desc_kmajor(x_, kk), desc_kmajor(w1t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                if (PEX)   // the X tail (k-step 1 + b of the tail panel) against the W1 tail (k-step 3)
+                    mma(tb + COL_Z1, desc_kmajor(w3p_, 1 + b), desc_kmajor(w3p_, 3), idesc_bf16(128, 128, 0, 0), 1u);
                 commit(&S.sm.mma);
             }
             if (!wait_mma()) { ok = false; break; }
@@ -459,6 +505,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                     mma(tb + COL_DE, desc_kmajor(h1_, kk), desc_mnmajor(w1t_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
                     mma(tb + COL_DW1, desc_mnmajor(h1_, kk), desc_mnmajor(x_, kk), idesc_bf16(128, 64, 1, 1),
                         acc_w | (kk > 0));
+                    if (PEX)
+                        mma(tb + COL_DW1T, desc_mnmajor(h1_, kk), desc_mnmajor(w3p_ + 32u * (1 + b), kk),
+                            idesc_bf16(128, 16, 1, 1), acc_w | (kk > 0));
                 }
                 commit(&S.sm.mma);
             }
@@ -499,7 +548,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     if (BWD && !failed && tid < NC && ntile_mine > 0) {
         const uint32_t tb = S.sm.tmem_base;
         const int r = tid & (TM - 1), hc = tid >> 7;
-        float *gW1 = A.grad_mlp, *gB1 = gW1 + IN * HID, *gW2 = gB1 + HID, *gB2 = gW2 + HID * HID;
+        float *gW1 = A.grad_mlp, *gB1 = gW1 + D::IN * HID, *gW2 = gB1 + HID, *gB2 = gW2 + HID * HID;
         float *gW3 = gB2 + HID, *gB3 = gW3 + HID * 3;
         // dW2: lane = input unit r, columns = output units (64 per half)
 #pragma unroll 1
@@ -510,16 +559,23 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) atomicAdd(gW2 + r * HID + col + k, v[k]);
         }
-        // [dW1 | db1]^T: lane = hidden unit r, columns = inputs (39 = bias), 32 per half
+        // [dW1 | db1]^T: lane = hidden unit r, columns = X columns (BIAS = bias), 32 per half
         {
             float v[32];
             tmem_ld32(taddr(tb, warp, COL_DW1 + 32 * hc), v);
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int kin = 32 * hc + k;
-                if (kin < IN) atomicAdd(gW1 + kin * HID + r, v[k]);
-                else if (kin == IN) atomicAdd(gB1 + r, v[k]);
+                if (kin < D::NMAIN) atomicAdd(gW1 + kin * HID + r, v[k]);
+                else if (kin == D::BIAS) atomicAdd(gB1 + r, v[k]);
             }
+        }
+        if constexpr (PEX) {   // dW1 tail^T: columns = inputs NMAIN..IN-1
+            float v[16];
+            tmem_ld16(taddr(tb, warp, COL_DW1T), v);
+            if (hc == 0)
+#pragma unroll
+                for (int t = 0; t < D::NTAIL; ++t) atomicAdd(gW1 + (D::NMAIN + t) * HID + r, v[t]);
         }
         float v[16];
         tmem_ld16(taddr(tb, warp, COL_DW3), v);
@@ -538,30 +594,34 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     if (warp == 0) tmem_dealloc(S.sm.tmem_base, NCOLS);
 }
 
-template <typename FeatT, bool BWD>
+template <typename FeatT, bool BWD, bool PEX>
 void launch_tc(const RenderArgs &A, int kind, cudaStream_t s) {
-    auto kern = fine_colour_tc_kernel<FeatT, BWD>;
+    auto kern = fine_colour_tc_kernel<FeatT, BWD, PEX>;
     const int bytes = (int)smem_bytes(BWD);
     ensure_smem(reinterpret_cast<const void *>(kern), bytes);
     ProfScope ps_(kind, s);
     kern<<<num_sms(), NT, bytes, s>>>(A);
 }
 
+template <bool BWD>
+void launch_tc_any(const RenderArgs &A, cudaStream_t s) {
+    const int kind = BWD ? DVGO_K_FINE_COLOUR_BWD : DVGO_K_FINE_COLOUR_FWD;
+    const bool bf = A.cdtype == DVGO_DTYPE_BF16, pex = A.nfreq_pos > 0;
+    if (bf && pex) launch_tc<__nv_bfloat16, BWD, true>(A, kind, s);
+    else if (bf) launch_tc<__nv_bfloat16, BWD, false>(A, kind, s);
+    else if (pex) launch_tc<float, BWD, true>(A, kind, s);
+    else launch_tc<float, BWD, false>(A, kind, s);
+}
+
 }  // namespace
 
 int launch_fine_colour_fwd_tc(const RenderArgs &A, cudaStream_t s) {
-    if (A.cdtype == DVGO_DTYPE_BF16)
-        launch_tc<__nv_bfloat16, false>(A, DVGO_K_FINE_COLOUR_FWD, s);
-    else
-        launch_tc<float, false>(A, DVGO_K_FINE_COLOUR_FWD, s);
+    launch_tc_any<false>(A, s);
     return DVGO_OK;
 }
 
 int launch_fine_colour_bwd_tc(const RenderArgs &A, cudaStream_t s) {
-    if (A.cdtype == DVGO_DTYPE_BF16)
-        launch_tc<__nv_bfloat16, true>(A, DVGO_K_FINE_COLOUR_BWD, s);
-    else
-        launch_tc<float, true>(A, DVGO_K_FINE_COLOUR_BWD, s);
+    launch_tc_any<true>(A, s);
     return DVGO_OK;
 }
 

@@ -92,7 +92,7 @@ class RenderFunction(torch.autograd.Function):
         samples = None if samples_t is None else (samples_t, samples_dt)
         mlp = None
         if renderer.params.mode == B.DVGO_MODE_FINE:
-            mlp = mlp_views(mlp_flat, renderer.cd.channels + 3 + 6 * renderer.params.n_freq_dir, renderer.params.hidden)
+            mlp = mlp_views(mlp_flat, renderer.params.mlp_in_dim(renderer.cd.channels), renderer.params.hidden)
         rgb, tfinal, _ = renderer.forward(density, cgrid, mlp, rays_o, rays_d, jitter, samples)
         renderer._gen = getattr(renderer, "_gen", 0) + 1
         ctx.gen = renderer._gen
@@ -154,7 +154,7 @@ class FineModel:
         self.density = density.contiguous()
         self._feat = feat.contiguous()
         self.mlp_flat = mlp_flat.contiguous()
-        self.mlp = mlp_views(self.mlp_flat, C + 3 + 6 * params.n_freq_dir, params.hidden)
+        self.mlp = mlp_views(self.mlp_flat, params.mlp_in_dim(C), params.hidden)
         self.bf16_feat = bf16_feat
         self._feat_bf16 = self._feat.to(torch.bfloat16) if bf16_feat else None
         self.dd = B.GridDesc(res, 1, box[0], box[1], layout=layout)

@@ -32,7 +32,8 @@ def oracle_params(p, grid_shape, feat_dim, box=((-1.0,) * 3, (1.0,) * 3)):
         grid_shape=tuple(grid_shape), xyz_min=tuple(f32(v) for v in box[0]), xyz_max=tuple(f32(v) for v in box[1]),
         shift_b=f32(p.shift_b), delta=f32(p.step), tau_f=f32(p.tau_f), t_near=f32(p.t_near), t_far=f32(p.t_far),
         bg=tuple(f32(v) for v in p.bg), mode=p.mode, rgb_act=p.rgb_act, feat_dim=feat_dim, n_freq=p.n_freq_dir,
-        hidden=p.hidden, w_pt=f32(p.w_pt_rgb), w_bg=f32(p.w_bg), act_order=p.act_order)
+        hidden=p.hidden, w_pt=f32(p.w_pt_rgb), w_bg=f32(p.w_bg), act_order=p.act_order,
+        n_freq_pos=p.n_freq_pos)
 
 
 def floor_err(got, ref, rtol, floor=FLOOR):
