@@ -430,9 +430,9 @@ def run_time_to_psnr(args):
     with the uniform FP32 renderer every `eval_every` steps on 2 held-out views; the fine-stage time
     excludes evaluation.  The PSNR target is the plain form's final PSNR minus 0.5 dB unless given."""
     import torch
-    import torch.nn.functional as F
     import synth
     import paper_2111_11215_gb300 as dvgo
+    from paper_2111_11215_gb300 import progressive
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
@@ -489,6 +489,9 @@ def run_time_to_psnr(args):
     box = ((-1.0,) * 3, (1.0,) * 3)
     fshape, s_f = (RES,) * 3, 2.0 / RES
     freespace, tau_f, recipe = None, 0.0, {"name": "full-box", "grid": list(fshape), "box": box}
+    pe_pos = 5 if args.pe_x else 0
+    in_dim = 39 + (3 + 6 * pe_pos if pe_pos else 0)
+    pg = sorted(int(c) for c in args.pg_ckpt.split(",") if c.strip())
     if args.fine_recipe == "paper":
         # Sec. 4.2: known free space of the coarse grid (tau_c = 1e-3), the fine grid allocated on the
         # box of the unknown space with M_f = 160^3 voxels, and tau_f = 1e-4 (Supp. A)
@@ -497,31 +500,35 @@ def run_time_to_psnr(args):
         bb = dvgo.dvgo_unknown_bbox(freespace).cpu().numpy()
         h = 2.0 / (rc - 1)
         bmin, bmax = -1.0 + bb[1:4] * h, -1.0 + bb[4:7] * h
-        ext = bmax - bmin
-        s_f = float(np.prod(ext) / RES ** 3) ** (1.0 / 3.0)
-        fshape = tuple(int(v) for v in np.floor(ext / s_f))
+        fshape, s_f = progressive.voxel_grid(RES ** 3, bmax - bmin)
         box = (tuple(float(v) for v in bmin), tuple(float(v) for v in bmax))
         tau_f = 1e-4
         recipe = {"name": "paper (coarse known free space tau_c=1e-3, fine box from the coarse grid, tau_f=1e-4)",
                   "grid": list(fshape), "box": box, "unknown_coarse_points": int(bb[0])}
+    # progressive scaling (Sec. 4.2): M_f / 2^|pg| voxels first, doubled at every checkpoint; b_f from
+    # alpha_init^(f) and the final voxel size
+    sched = progressive.pg_schedule(int(np.prod(fshape)), np.subtract(box[1], box[0]), pg) if pg else \
+        [(0, tuple(fshape), s_f)]
+    fshape0, s0 = sched[0][1], sched[0][2]
     b_f = dvgo.dvgo_shift_from_alpha_init(1e-2, s_f)
     # same activated density on the finer lattice: raw_f = resize(raw_c) + b_c - b_f (trilinear, Sec. 4.2);
     # the fine lattice points are sampled from the coarse grid (whose box is [-1, 1]^3)
-    axes = [torch.linspace(box[0][a], box[1][a], fshape[a], device=dev) for a in range(3)]
-    X, Y, Z = torch.meshgrid(*axes, indexing="ij")
-    where = torch.stack([Z, Y, X], dim=-1)[None]          # grid_sample wants (x = last axis, y, z)
-    dens0 = F.grid_sample(coarse.density[None, None], where, mode="bilinear", align_corners=True)[0, 0]
-    dens0 = (dens0 + (pc.shift_b - b_f)).contiguous()
-    feat0 = torch.as_tensor(synth.normal_grid(fshape, FEAT, 1e-2, seed=11), device=dev)
-    mlp0 = torch.as_tensor(mlp_flat(synth.mlp_weights(39, HID, 3, seed=12)), device=dev)
-    p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
-                         freespace=freespace, act_order=ACT_ORDERS[args.act_order])
-    dd, cd32 = dvgo.GridDesc(fshape, 1, box[0], box[1]), dvgo.GridDesc(fshape, FEAT, box[0], box[1])
-    eval_r = dvgo.Renderer(p_eval, dd, cd32, NRAYS)
+    dens0 = dvgo.dvgo_resize_grid(coarse.dd, coarse.density.reshape(-1), dvgo.GridDesc(fshape0, 1, box[0], box[1]))
+    dens0 = (dens0.view(fshape0) + (pc.shift_b - b_f)).contiguous()
+    feat0 = torch.as_tensor(synth.normal_grid(fshape0, FEAT, 1e-2, seed=11), device=dev)
+    mlp0 = torch.as_tensor(mlp_flat(synth.mlp_weights(in_dim, HID, 3, seed=12)), device=dev)
+    p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s0, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
+                         freespace=freespace, act_order=ACT_ORDERS[args.act_order], n_freq_pos=pe_pos)
+    eval_cache = {}
 
     def psnr(model, n_rays):
+        # the uniform FP32 renderer on the model's current lattice and step
+        if model.shape not in eval_cache:
+            eval_cache[model.shape] = dvgo.Renderer(p_eval.with_(step=model.params.step), model.dd,
+                                                    model.cd.with_(dtype=dvgo.DVGO_DTYPE_F32), NRAYS)
+        eval_r = eval_cache[model.shape]
         se = torch.zeros((), device=dev, dtype=torch.float64)
-        views = dvgo.mlp_views(model.mlp_flat)
+        views = model.mlp
         for s in range(0, n_rays, NRAYS):
             o, d, c = o_te[s:s + NRAYS], d_te[s:s + NRAYS], c_te[s:s + NRAYS]
             if o.shape[0] < NRAYS:
@@ -539,9 +546,9 @@ def run_time_to_psnr(args):
     results = {}
     for form in forms:
         bf16, use_prop = form_defs[form]
-        p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s_f, shift_b=b_f, bg=(1.0, 1.0, 1.0),
+        p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s0, shift_b=b_f, bg=(1.0, 1.0, 1.0),
                         mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace,
-                        w_pt_rgb=aux_f[0], w_bg=aux_f[1], act_order=ACT_ORDERS[args.act_order])
+                        w_pt_rgb=aux_f[0], w_bg=aux_f[1], act_order=ACT_ORDERS[args.act_order], n_freq_pos=pe_pos)
         model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16,
                                overlap_adam=use_prop, box=box)
         prop = trainer = None
@@ -551,8 +558,12 @@ def run_time_to_psnr(args):
             trainer = dvgo.ProposalTrainer(model, prop, n_ps, every, args.prop_warmup, PROPOSAL_TRAIN_RAYS, eta)
             tb, dtb = torch.empty((NRAYS, n_ps), device=dev), torch.empty((NRAYS, n_ps), device=dev)
         st = [0]
+        rescale_at = {start: (dims, s) for start, dims, s in sched[1:]}
 
         def fine_step():
+            if st[0] in rescale_at:
+                dims, s = rescale_at[st[0]]
+                (trainer or model).rescale(dims, 0.5 * s)
             o, d, jit, tgt = batch(st[0], 2)
             if trainer is None:
                 model.train_step(o, d, jit, tgt)
@@ -592,6 +603,7 @@ def run_time_to_psnr(args):
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
             "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
+            "mlp_inputs": in_dim, "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched]},
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
             "forms": results}
@@ -770,6 +782,11 @@ def main():
                     help="time-to-psnr: interpolation / activation order of the density in both stages (Sec. 3)")
     ap.add_argument("--aux-losses", action="store_true",
                     help="time-to-psnr: add the per-point rgb and background entropy losses with the Supp. A weights")
+    ap.add_argument("--pe-x", action="store_true",
+                    help="time-to-psnr: the paper's 72-input MLP, PE(x, 5) of the query point appended (Supp. A)")
+    ap.add_argument("--pg-ckpt", default="",
+                    help="time-to-psnr: progressive-scaling checkpoints of the fine stage, e.g. 1000,2000,3000 "
+                         "(Supp. A); empty = the final grid from the start")
     ap.add_argument("--fine-recipe", choices=["full-box", "paper"], default="full-box",
                     help="time-to-psnr fine stage: 160^3 on the full box, or the paper's Sec. 4.2 recipe "
                          "(fine box from the coarse grid's unknown space, known-free-space and tau_f skipping)")

@@ -171,6 +171,7 @@ class FineModel:
         self.loss = torch.zeros(1, device=dev)
         self.dloss = torch.empty((n_rays, 3), device=dev)
         self.step_count = 0
+        self.grid_t0 = 0               # step count at the last rescale: the grids' Adam restarts there
         self._side = torch.cuda.Stream(device=dev) if overlap_adam else None
         self._ev_bwd = torch.cuda.Event() if overlap_adam else None
         self._ev_after = torch.cuda.Event() if overlap_adam else None
@@ -221,6 +222,39 @@ class FineModel:
         if self._feat_pending:
             self._cur(stream).wait_event(self._ev_feat)
 
+    @property
+    def shape(self):
+        return tuple(self.dd.shape)
+
+    def rescale(self, shape, step: float, stream=None):
+        """Progressive scaling (Sec. 4.2): resize the density and feature grids to `shape` lattice
+        points on the same box by trilinear interpolation (dvgo_resize_grid) and render with the
+        sampling step `step` from now on (the step follows the voxel size).  The shift b stays, so
+        the activated density field is unchanged.  The grids' Adam moments restart from zero, with
+        their bias-correction count; the learning-rate decay and the MLP's Adam state continue."""
+        self.wait_params(stream)
+        shape = tuple(int(v) for v in shape)
+        C = self.cd.channels
+        dd = self.dd.with_(shape=shape)
+        cd32 = self.cd.with_(shape=shape, dtype=B.DVGO_DTYPE_F32)
+        self.density = B.dvgo_resize_grid(self.dd, self.density.reshape(-1), dd, stream=stream)
+        self._feat = B.dvgo_resize_grid(self.cd.with_(dtype=B.DVGO_DTYPE_F32), self._feat.reshape(-1), cd32,
+                                        stream=stream)
+        if self.layout == B.DVGO_LAYOUT_CANONICAL:
+            self.density = self.density.view(shape)
+            self._feat = self._feat.view(shape + (C,))
+        if self.bf16_feat:
+            self._feat_bf16 = B.dvgo_pack_grid(cd32, self._feat.reshape(-1), cd32.with_(dtype=B.DVGO_DTYPE_BF16),
+                                               stream=stream).view(self._feat.shape)
+        self.dd, self.cd = dd, self.cd.with_(shape=shape)
+        self.params = self.params.with_(step=float(step))
+        self.renderer = Renderer(self.params, self.dd, self.cd, self.renderer.n_rays, device=self.density.device)
+        self._expl = None
+        self.g_density = torch.zeros_like(self.density)
+        self.g_feat = torch.zeros_like(self._feat)
+        self.adam["density"], self.adam["feat"] = AdamState(self.density), AdamState(self._feat)
+        self.grid_t0 = self.step_count
+
     def forward(self, rays_o, rays_d, jitter=None, target=None, stream=None):
         self.wait_params(stream)
         return self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
@@ -251,15 +285,16 @@ class FineModel:
                       self.g_density, self.g_feat, self.g_mlp, stream)
         self.step_count += 1
         t = self.step_count
+        tg = t - self.grid_t0          # the grids' Adam count (restarted by rescale)
         lr_g = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
         lr_m = B.dvgo_lr_at(self.lr_mlp, t - 1, self.decay_steps)
         if self._side is not None:
             self._ev_bwd.record(self._cur(stream))
-            self._feat_deferred = (lr_g, t)
+            self._feat_deferred = (lr_g, tg)
         else:
-            B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
+            B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, tg,
                              param_bf16_out=self._feat_bf16, stream=stream)
-        B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, t,
+        B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, tg,
                          stream=stream)
         B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
         return self.loss
@@ -391,6 +426,12 @@ class ProposalTrainer:
         self.dt_buf = torch.empty((R, self.n_samples), device=dev)
         self.i = 0
         self.n_uniform = self.n_proposal = 0
+
+    def rescale(self, shape, step: float, stream=None):
+        """Progressive scaling of the model (FineModel.rescale); the proposal renders and labels on
+        the new lattice and step from then on."""
+        self.model.rescale(shape, step, stream)
+        self.proposal.params, self.proposal.dd = self.model.params, self.model.dd
 
     def is_uniform(self, i: int) -> bool:
         return i < self.warmup or i % self.uniform_every == 0
