@@ -511,10 +511,16 @@ def run_time_to_psnr(args):
         [(0, tuple(fshape), s_f)]
     fshape0, s0 = sched[0][1], sched[0][2]
     b_f = dvgo.dvgo_shift_from_alpha_init(1e-2, s_f)
-    # same activated density on the finer lattice: raw_f = resize(raw_c) + b_c - b_f (trilinear, Sec. 4.2);
-    # the fine lattice points are sampled from the coarse grid (whose box is [-1, 1]^3)
-    dens0 = dvgo.dvgo_resize_grid(coarse.dd, coarse.density.reshape(-1), dvgo.GridDesc(fshape0, 1, box[0], box[1]))
-    dens0 = (dens0.view(fshape0) + (pc.shift_b - b_f)).contiguous()
+    fine_init = args.fine_init if args.fine_init != "auto" else ("zero" if args.fine_recipe == "paper" else "coarse")
+    if fine_init == "zero":
+        # Sec. 4.2 / Supp. A: the fine density grid starts low-density, raw 0 with b_f for
+        # alpha_init^(f) = 1e-2; the known free space of the coarse grid keeps queries off empty space
+        dens0 = torch.zeros(fshape0, device=dev)
+    else:
+        # full box without free-space skipping: the same activated density as the coarse result on the
+        # finer lattice, raw_f = resize(raw_c) + b_c - b_f (trilinear; the coarse box is [-1, 1]^3)
+        dens0 = dvgo.dvgo_resize_grid(coarse.dd, coarse.density.reshape(-1), dvgo.GridDesc(fshape0, 1, box[0], box[1]))
+        dens0 = (dens0.view(fshape0) + (pc.shift_b - b_f)).contiguous()
     feat0 = torch.as_tensor(synth.normal_grid(fshape0, FEAT, 1e-2, seed=11), device=dev)
     mlp0 = torch.as_tensor(mlp_flat(synth.mlp_weights(in_dim, HID, 3, seed=12)), device=dev)
     p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s0, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
@@ -563,7 +569,7 @@ def run_time_to_psnr(args):
         def fine_step():
             if st[0] in rescale_at:
                 dims, s = rescale_at[st[0]]
-                (trainer or model).rescale(dims, 0.5 * s)
+                (trainer or model).rescale(dims, 0.5 * s, adam=args.pg_adam)
             o, d, jit, tgt = batch(st[0], 2)
             if trainer is None:
                 model.train_step(o, d, jit, tgt)
@@ -603,7 +609,8 @@ def run_time_to_psnr(args):
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
             "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
-            "mlp_inputs": in_dim, "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched]},
+            "fine_density_init": fine_init, "mlp_inputs": in_dim, "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched],
+                                                  "adam": args.pg_adam},
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
             "forms": results}
@@ -787,6 +794,11 @@ def main():
     ap.add_argument("--pg-ckpt", default="",
                     help="time-to-psnr: progressive-scaling checkpoints of the fine stage, e.g. 1000,2000,3000 "
                          "(Supp. A); empty = the final grid from the start")
+    ap.add_argument("--pg-adam", choices=["reset", "resize"], default="reset",
+                    help="time-to-psnr: the grids' Adam moments at a progressive-scaling checkpoint")
+    ap.add_argument("--fine-init", choices=["auto", "zero", "coarse"], default="auto",
+                    help="time-to-psnr: fine density from raw 0 at alpha_init 1e-2 (the paper's, default of the paper "
+                         "recipe) or the coarse result resized onto the fine lattice (default of the full-box recipe)")
     ap.add_argument("--fine-recipe", choices=["full-box", "paper"], default="full-box",
                     help="time-to-psnr fine stage: 160^3 on the full box, or the paper's Sec. 4.2 recipe "
                          "(fine box from the coarse grid's unknown space, known-free-space and tau_f skipping)")

@@ -226,23 +226,35 @@ class FineModel:
     def shape(self):
         return tuple(self.dd.shape)
 
-    def rescale(self, shape, step: float, stream=None):
+    def rescale(self, shape, step: float, stream=None, adam: str = "reset"):
         """Progressive scaling (Sec. 4.2): resize the density and feature grids to `shape` lattice
         points on the same box by trilinear interpolation (dvgo_resize_grid) and render with the
         sampling step `step` from now on (the step follows the voxel size).  The shift b stays, so
-        the activated density field is unchanged.  The grids' Adam moments restart from zero, with
-        their bias-correction count; the learning-rate decay and the MLP's Adam state continue."""
+        the activated density field is unchanged.  The grids' Adam state: adam="reset" restarts the
+        moments from zero with their bias-correction count; adam="resize" resizes both moments with
+        the grids (trilinear, so the second moment stays >= 0) and keeps the count.  The
+        learning-rate decay and the MLP's Adam state continue either way."""
+        if adam not in ("reset", "resize"):
+            raise ValueError("rescale: adam must be 'reset' or 'resize'")
         self.wait_params(stream)
         shape = tuple(int(v) for v in shape)
         C = self.cd.channels
         dd = self.dd.with_(shape=shape)
         cd32 = self.cd.with_(shape=shape, dtype=B.DVGO_DTYPE_F32)
-        self.density = B.dvgo_resize_grid(self.dd, self.density.reshape(-1), dd, stream=stream)
-        self._feat = B.dvgo_resize_grid(self.cd.with_(dtype=B.DVGO_DTYPE_F32), self._feat.reshape(-1), cd32,
-                                        stream=stream)
-        if self.layout == B.DVGO_LAYOUT_CANONICAL:
-            self.density = self.density.view(shape)
-            self._feat = self._feat.view(shape + (C,))
+        cd32_old = self.cd.with_(dtype=B.DVGO_DTYPE_F32)
+
+        def grid_shape(t, channels):
+            if self.layout != B.DVGO_LAYOUT_CANONICAL:
+                return t
+            return t.view(shape + ((channels,) if channels > 1 else ()))
+        moments = None
+        if adam == "resize":
+            moments = {"density": [grid_shape(B.dvgo_resize_grid(self.dd, x.reshape(-1), dd, stream=stream), 1)
+                                   for x in (self.adam["density"].m, self.adam["density"].v)],
+                       "feat": [grid_shape(B.dvgo_resize_grid(cd32_old, x.reshape(-1), cd32, stream=stream), C)
+                                for x in (self.adam["feat"].m, self.adam["feat"].v)]}
+        self.density = grid_shape(B.dvgo_resize_grid(self.dd, self.density.reshape(-1), dd, stream=stream), 1)
+        self._feat = grid_shape(B.dvgo_resize_grid(cd32_old, self._feat.reshape(-1), cd32, stream=stream), C)
         if self.bf16_feat:
             self._feat_bf16 = B.dvgo_pack_grid(cd32, self._feat.reshape(-1), cd32.with_(dtype=B.DVGO_DTYPE_BF16),
                                                stream=stream).view(self._feat.shape)
@@ -253,7 +265,11 @@ class FineModel:
         self.g_density = torch.zeros_like(self.density)
         self.g_feat = torch.zeros_like(self._feat)
         self.adam["density"], self.adam["feat"] = AdamState(self.density), AdamState(self._feat)
-        self.grid_t0 = self.step_count
+        if moments is None:
+            self.grid_t0 = self.step_count
+        else:
+            for k, (m, v) in moments.items():
+                self.adam[k].m, self.adam[k].v = m, v
 
     def forward(self, rays_o, rays_d, jitter=None, target=None, stream=None):
         self.wait_params(stream)
@@ -427,10 +443,10 @@ class ProposalTrainer:
         self.i = 0
         self.n_uniform = self.n_proposal = 0
 
-    def rescale(self, shape, step: float, stream=None):
+    def rescale(self, shape, step: float, stream=None, adam: str = "reset"):
         """Progressive scaling of the model (FineModel.rescale); the proposal renders and labels on
         the new lattice and step from then on."""
-        self.model.rescale(shape, step, stream)
+        self.model.rescale(shape, step, stream, adam)
         self.proposal.params, self.proposal.dd = self.model.params, self.model.dd
 
     def is_uniform(self, i: int) -> bool:

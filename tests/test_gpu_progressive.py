@@ -56,6 +56,27 @@ def test_rescale_grids_match_the_oracle_resize(bf16):
     assert m.g_density.shape == m.density.shape and m.density.abs().sum() > 0
 
 
+def test_rescale_can_resize_the_adam_moments():
+    m, _, _ = _model(20, False)
+    o, d, jit, tgt = (cuda(a) for a in synth.fine_batch(512, 153))
+    for _ in range(3):
+        m.train_step(o, d, jit, tgt)
+    m.wait_params()
+    mv = {k: (m.adam[k].m.cpu().numpy().astype(np.float64), m.adam[k].v.cpu().numpy().astype(np.float64))
+          for k in ("density", "feat")}
+    m.rescale((23, 26, 21), 0.04, adam="resize")
+    torch.cuda.synchronize()
+    for k, (mo, vo) in mv.items():
+        np.testing.assert_allclose(m.adam[k].m.cpu().numpy(), oracle.resize_grid(mo, (23, 26, 21)), rtol=2 ** -23,
+                                   atol=1e-12)
+        np.testing.assert_allclose(m.adam[k].v.cpu().numpy(), oracle.resize_grid(vo, (23, 26, 21)), rtol=2 ** -23,
+                                   atol=1e-20)
+        assert m.adam[k].v.min() >= 0
+    assert m.grid_t0 == 0                              # the bias-correction count continues
+    loss = m.train_step(o, d, jit, tgt)
+    assert np.isfinite(float(loss.item()))
+
+
 @pytest.mark.parametrize("layout", [dvgo.DVGO_LAYOUT_CANONICAL, dvgo.DVGO_LAYOUT_PACKED])
 def test_rescale_onto_the_same_lattice_renders_the_same(layout):
     m, _, _ = _model(24, True, n_freq_pos=5, layout=layout)
