@@ -42,9 +42,24 @@ N_PROP_SAMPLES = 48
 PROPOSAL_EVERY = 4
 PROPOSAL_TRAIN_RAYS = 2048
 PROPOSAL_ETA = 0.05
-MLP_FWD_FLOP = 2 * (39 * 128 + 128 * 128 + 128 * 3)                                    # 43,520
-MLP_BWD_FLOP = 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + 39 * 128 + 12 * 128)   # 80,128
-N_PARAMS = RES ** 3 * (1 + FEAT) + 22019
+# Colour-MLP input width: 39 (features + PE(d), the benchmark's model) or 72 (+ PE(x, 5), --pe-x)
+MLP_IN = 39
+
+
+def mlp_fwd_flop():
+    return 2 * (MLP_IN * 128 + 128 * 128 + 128 * 3)                                      # 43,520 at 39
+
+
+def mlp_bwd_flop():
+    return 2 * (128 * 3 + 128 * 3 + 128 * 128 + 128 * 128 + MLP_IN * 128 + 12 * 128)     # 80,128 at 39
+
+
+def n_params():
+    return RES ** 3 * (1 + FEAT) + (MLP_IN + 1) * 128 + 129 * 128 + 129 * 3              # 22,019 MLP at 39
+
+
+def n_freq_pos():
+    return 5 if MLP_IN == 72 else 0
 ACT_ORDERS = {"post": 0, "pre": 1, "in": 2}   # Sec. 3 interpolation / activation orders
 LAYOUTS = {"canonical": 0, "packed": 1}          # grid storage layouts (dvgo.h)
 
@@ -69,7 +84,7 @@ def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
 def workload(seed=0):
     import synth
     dens, feat = synth.fine_scene(seed=seed, res=RES, feat_dim=FEAT)
-    mlp = synth.mlp_weights(39, HID, 3, seed=3)
+    mlp = synth.mlp_weights(MLP_IN, HID, 3, seed=3)
     batches = [synth.fine_batch(NRAYS, seed=100 + i) for i in range(N_BATCHES)]
     return dens, feat, mlp, batches
 
@@ -147,10 +162,10 @@ class OracleStep:
         self.P = oracle.Params(grid_shape=(RES,) * 3,
                                shift_b=float(np.float32(oracle.shift_from_alpha_init(1e-6, 2.0 / RES))),
                                delta=float(np.float32(step)), bg=(1.0, 1.0, 1.0), mode=1, feat_dim=FEAT, n_freq=4,
-                               hidden=HID)
+                               hidden=HID, n_freq_pos=n_freq_pos())
         self.dens64, self.feat64 = dens.astype(np.float64), feat.astype(np.float64)
         self.mlp64 = {k: v.astype(np.float64) for k, v in mlp.items()}
-        self.adam_arrays = [np.zeros(N_PARAMS), np.ones(N_PARAMS), np.zeros(N_PARAMS), np.zeros(N_PARAMS)]
+        self.adam_arrays = [np.zeros(n_params()), np.ones(n_params()), np.zeros(n_params()), np.zeros(n_params())]
         self.t = 0
 
     def run(self, batch, n):
@@ -170,7 +185,7 @@ class OracleStep:
         step_s = t_render * NRAYS / n + t_adam
         return {"value": NRAYS / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(), "kind": "oracle",
                 "sample": f"{n} of 8192 rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam sweep over "
-                          f"all {N_PARAMS} parameters ({t_adam:.2f} s), projected to a full step"}
+                          f"all {n_params()} parameters ({t_adam:.2f} s), projected to a full step"}
 
 
 def run_reference(args, rank, world):
@@ -196,7 +211,7 @@ def run_reference(args, rank, world):
 
 
 def workload_config(args, form):
-    return {"workload": "DVGO fine stage, 160^3 density + 12-ch feature grid, MLP 39-128-128-3, 8192 rays/batch, "
+    return {"workload": f"DVGO fine stage, 160^3 density + 12-ch feature grid, MLP {MLP_IN}-128-128-3, 8192 rays/batch, "
                         "step 0.5 voxel, 8 balls (raw density 50) + smooth albedo, 100 views 800x800",
             "form": form, "global_batch": NRAYS * args.gpus, "grid": RES, "feat_dim": FEAT, "hidden": HID,
             "layout": getattr(args, "layout", "canonical"),
@@ -218,7 +233,7 @@ class Form:
         step = 2.0 / RES * 0.5
         self.p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step,
                              shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES), bg=(1.0, 1.0, 1.0),
-                             mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32)
+                             mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32, n_freq_pos=n_freq_pos())
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
         self.model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), self.p, NRAYS, bf16_feat=chosen,
                                     overlap_adam=chosen, layout=LAYOUTS[args_layout])
@@ -334,7 +349,7 @@ def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
     hbm = peaks.get("hbm_gbs")
     if kind in ("fine_colour_bwd", "fine_colour_fwd"):
         units = bwd_units if kind == "fine_colour_bwd" else fwd_units
-        flop = units * (MLP_FWD_FLOP + (MLP_BWD_FLOP if kind == "fine_colour_bwd" else 0))
+        flop = units * (mlp_fwd_flop() + (mlp_bwd_flop() if kind == "fine_colour_bwd" else 0))
         achieved = flop / (avg_ms * 1e-3) / 1e12
         if chosen:
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -347,7 +362,7 @@ def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
                 "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz"}
     if kind == "adam":
         # three launches per step (density, features, MLP); per-launch average of the step's bytes
-        byts = N_PARAMS * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
+        byts = n_params() * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
         achieved = byts / 3.0 / (avg_ms * 1e-3) / 1e9
         peak = hbm or 6800.0
         return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -384,7 +399,7 @@ def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
     step = 2.0 / RES * 0.5
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
     mk = lambda prec: dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=step, bg=(1.0, 1.0, 1.0), mlp_prec=prec,
-                                  shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES))
+                                  shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / RES), n_freq_pos=n_freq_pos())
     p32 = mk(dvgo.DVGO_MLP_FP32)
     m32 = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), p32, NRAYS)
     prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p32, m32.dd, NRAYS,
@@ -790,7 +805,8 @@ def main():
     ap.add_argument("--aux-losses", action="store_true",
                     help="time-to-psnr: add the per-point rgb and background entropy losses with the Supp. A weights")
     ap.add_argument("--pe-x", action="store_true",
-                    help="time-to-psnr: the paper's 72-input MLP, PE(x, 5) of the query point appended (Supp. A)")
+                    help="time-to-psnr and step: the paper's 72-input MLP, PE(x, 5) of the query point appended "
+                         "(Supp. A); the step workload's default is the 39-input model")
     ap.add_argument("--pg-ckpt", default="",
                     help="time-to-psnr: progressive-scaling checkpoints of the fine stage, e.g. 1000,2000,3000 "
                          "(Supp. A); empty = the final grid from the start")
@@ -806,6 +822,9 @@ def main():
     ap.add_argument("--psnr-target", type=float, default=28.891)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global MLP_IN
+    if args.pe_x and args.workload == "step":
+        MLP_IN = 72
     if args.steps is None:
         args.steps = 5 if args.impl == "reference" else (50 if args.workload == "stress" else 1000)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -85,7 +85,7 @@ __device__ void load_weights(Smem<PEX> &S, const RenderArgs &A) {
 
 // Gather the input rows of one tile: 4 threads per sample, thread q handles the corner pair
 // (x bit, y bit) = (q >> 1, q & 1) with z = 0, 1 (adjacent in memory).
-template <typename FeatT, bool PEX>
+template <typename FeatT, bool PEX, bool PK>
 __device__ void gather_tile(Smem<PEX> &S, const RenderArgs &A, int tile, int n_kept) {
     constexpr int IN = Dims<PEX>::IN;
     int tid = threadIdx.x;
@@ -113,18 +113,18 @@ __device__ void gather_tile(Smem<PEX> &S, const RenderArgs &A, int tile, int n_k
             xw = xv[q - 1];
         }
         if (q == 0) {
-            S.cbase[i] = cell_base(c, A.ny, A.nz, A.packed);
+            S.cbase[i] = cell_base(c, A.ny, A.nz, PK);
             S.frac[3 * i] = c.fx;
             S.frac[3 * i + 1] = c.fy;
             S.frac[3 * i + 2] = c.fz;
             S.slot[i] = slot;
         }
         int qa = q << 1;   // corner bits (x, y, 0)
-        long long idx0 = corner_index(c, qa, A.ny, A.nz, A.packed);
+        long long idx0 = corner_index(c, qa, A.ny, A.nz, PK);
         float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
         const FeatT *g = static_cast<const FeatT *>(A.cgrid) + idx0 * FEAT;
         // the z + 1 corner: the next point in the canonical layout, located in the packed one
-        const FeatT *gz = A.packed ? static_cast<const FeatT *>(A.cgrid) + corner_index(c, qa | 1, A.ny, A.nz, true) * FEAT
+        const FeatT *gz = PK ? static_cast<const FeatT *>(A.cgrid) + corner_index(c, qa | 1, A.ny, A.nz, true) * FEAT
                                    : g + FEAT;
         if constexpr (sizeof(FeatT) == 4) {
             const float4 *g4 = reinterpret_cast<const float4 *>(g), *gz4 = reinterpret_cast<const float4 *>(gz);
@@ -233,7 +233,7 @@ __device__ __forceinline__ float out_logit(const Smem<PEX> &S, int s, int ch) {
     return o;
 }
 
-template <typename FeatT, bool PEX>
+template <typename FeatT, bool PEX, bool PK>
 __global__ void __launch_bounds__(NT, 1) fine_colour_fwd_kernel(RenderArgs A) {
     constexpr int K1 = Dims<PEX>::K1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_fwd_kernel(RenderArgs A) {
     const int ntiles = (n_kept + TM - 1) / TM;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        gather_tile<FeatT, PEX>(S, A, tile, n_kept);
+        gather_tile<FeatT, PEX, PK>(S, A, tile, n_kept);
         __syncthreads();
         gemm_fwd<K1>(S.xt, S.w1, nullptr, S.h1);
         __syncthreads();
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_fwd_kernel(RenderArgs A) {
     }
 }
 
-template <typename FeatT, bool PEX>
+template <typename FeatT, bool PEX, bool PK>
 __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
     constexpr int IN = Dims<PEX>::IN, K1 = Dims<PEX>::K1, KH = Dims<PEX>::KH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        gather_tile<FeatT, PEX>(S, A, tile, n_kept);
+        gather_tile<FeatT, PEX, PK>(S, A, tile, n_kept);
         __syncthreads();
         gemm_fwd<K1>(S.xt, S.w1, nullptr, S.h1);
         __syncthreads();
@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_bwd_kernel(RenderArgs A) {
                 float fx = S.frac[3 * i], fy = S.frac[3 * i + 1], fz = S.frac[3 * i + 2];
                 float wxy = ((q >> 1) ? fx : 1.0f - fx) * ((q & 1) ? fy : 1.0f - fy);
                 float w0 = wxy * (1.0f - fz), w1 = wxy * fz;
-                const long long idx0 = corner_from_base(S.cbase[i], q >> 1, q & 1, 0, A.ny, A.nz, A.packed);
-                const long long idx1 = corner_from_base(S.cbase[i], q >> 1, q & 1, 1, A.ny, A.nz, A.packed);
+                const long long idx0 = corner_from_base(S.cbase[i], q >> 1, q & 1, 0, A.ny, A.nz, PK);
+                const long long idx1 = corner_from_base(S.cbase[i], q >> 1, q & 1, 1, A.ny, A.nz, PK);
                 float4 *g0 = reinterpret_cast<float4 *>(A.grad_cgrid + idx0 * FEAT);
                 float4 *g1 = reinterpret_cast<float4 *>(A.grad_cgrid + idx1 * FEAT);
                 const float *d = S.de + i * FEAT;
@@ -485,26 +485,34 @@ void launch_persistent(void (*kernel)(RenderArgs), int kind, const RenderArgs &A
     kernel<<<num_sms(), NT, sizeof(Smem<PEX>), s>>>(A);
 }
 
-template <bool BWD, bool PEX>
+template <bool BWD, bool PEX, bool PK>
 void launch_colour(const RenderArgs &A, cudaStream_t s) {
     const int kind = BWD ? DVGO_K_FINE_COLOUR_BWD : DVGO_K_FINE_COLOUR_FWD;
     if (A.cdtype == DVGO_DTYPE_BF16)
-        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<__nv_bfloat16, PEX> : fine_colour_fwd_kernel<__nv_bfloat16, PEX>,
+        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<__nv_bfloat16, PEX, PK>
+                                   : fine_colour_fwd_kernel<__nv_bfloat16, PEX, PK>,
                                kind, A, s);
     else
-        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<float, PEX> : fine_colour_fwd_kernel<float, PEX>, kind, A, s);
+        launch_persistent<PEX>(BWD ? fine_colour_bwd_kernel<float, PEX, PK> : fine_colour_fwd_kernel<float, PEX, PK>,
+                               kind, A, s);
+}
+
+template <bool BWD>
+void launch_colour_any(const RenderArgs &A, cudaStream_t s) {
+    const bool pex = A.nfreq_pos > 0;
+    if (A.packed) {
+        if (pex) launch_colour<BWD, true, true>(A, s);
+        else launch_colour<BWD, false, true>(A, s);
+    } else {
+        if (pex) launch_colour<BWD, true, false>(A, s);
+        else launch_colour<BWD, false, false>(A, s);
+    }
 }
 
 }  // namespace
 
-void launch_fine_colour_fwd_simt(const RenderArgs &A, cudaStream_t s) {
-    if (A.nfreq_pos > 0) launch_colour<false, true>(A, s);
-    else launch_colour<false, false>(A, s);
-}
+void launch_fine_colour_fwd_simt(const RenderArgs &A, cudaStream_t s) { launch_colour_any<false>(A, s); }
 
-void launch_fine_colour_bwd_simt(const RenderArgs &A, cudaStream_t s) {
-    if (A.nfreq_pos > 0) launch_colour<true, true>(A, s);
-    else launch_colour<true, false>(A, s);
-}
+void launch_fine_colour_bwd_simt(const RenderArgs &A, cudaStream_t s) { launch_colour_any<true>(A, s); }
 
 }  // namespace dvgo

@@ -125,6 +125,7 @@ __device__ __forceinline__ float4 *de_slot(unsigned char *dout, int b, int r, in
 }
 
 // Producer: add a tile's feature gradients (de rows staged in the dout panel) to the grid.
+template <bool PK>
 __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int b, int row) {
     const int slot = S.sm.slot[b][row];
     if (slot < 0) return;
@@ -135,7 +136,7 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
     for (int q = 0; q < 8; ++q) {
         const int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
         const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz);
-        const long long idx = corner_from_base(cb, bx, by, bz, A.ny, A.nz, A.packed);
+        const long long idx = corner_from_base(cb, bx, by, bz, A.ny, A.nz, PK);
         float4 *g = reinterpret_cast<float4 *>(A.grad_cgrid + idx * FEAT);
         atomicAdd(g + 0, make_float4(w * e0.x, w * e0.y, w * e0.z, w * e0.w));
         atomicAdd(g + 1, make_float4(w * e1.x, w * e1.y, w * e1.z, w * e1.w));
@@ -144,7 +145,7 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
 }
 
 // Producer: gather sample row `row` of a tile into X panel b (and its tail) and the per-row tables.
-template <typename FeatT, bool BWD, bool PEX>
+template <typename FeatT, bool BWD, bool PEX, bool PK>
 __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int e, int n_kept, int row) {
     using D = TcDims<PEX>;
     float v[64], tail[16];
@@ -160,7 +161,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         float dt;
         const Cell c = sample_cell(A, rr, kv.y, kv.x - rr.off, dt);
         slot = kv.x;
-        cbase = cell_base(c, A.ny, A.nz, A.packed);
+        cbase = cell_base(c, A.ny, A.nz, PK);
         fx = c.fx;
         fy = c.fy;
         fz = c.fz;
@@ -173,11 +174,11 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
             const int qa = q << 1;
-            const long long idx0 = corner_index(c, qa, A.ny, A.nz, A.packed);
+            const long long idx0 = corner_index(c, qa, A.ny, A.nz, PK);
             const float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
             const FeatT *g = static_cast<const FeatT *>(A.cgrid) + idx0 * FEAT;
             // the z + 1 corner: the next point in the canonical layout, located in the packed one
-            const FeatT *gz = A.packed ? static_cast<const FeatT *>(A.cgrid) +
+            const FeatT *gz = PK ? static_cast<const FeatT *>(A.cgrid) +
                                              corner_index(c, qa | 1, A.ny, A.nz, true) * FEAT
                                        : g + FEAT;
             if constexpr (sizeof(FeatT) == 4) {
@@ -249,7 +250,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
     }
 }
 
-template <typename FeatT, bool BWD, bool PEX>
+template <typename FeatT, bool BWD, bool PEX, bool PK>
 __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     using D = TcDims<PEX>;
     extern __shared__ unsigned char smem_raw[];
@@ -318,10 +319,10 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                     ok = false;
                     break;
                 }
-                if (BWD) scatter_row(A, S, b, row);   // feature gradients of tile i - 2
+                if (BWD) scatter_row<PK>(A, S, b, row);   // feature gradients of tile i - 2
             }
             if (*(volatile int *)&S.sm.abort) break;
-            produce_row<FeatT, BWD, PEX>(A, S, b, tile * TM + row, n_kept, row);
+            produce_row<FeatT, BWD, PEX, PK>(A, S, b, tile * TM + row, n_kept, row);
             fence_async_smem();
             mbar_arrive(&S.sm.full[b]);
         }
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             // the last (up to) two tiles: wait until the consumers are done with them, then scatter
             for (int j = (i >= 2 ? i - 2 : 0); j < i && ok; ++j) {
                 if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1)) ok = false;
-                else if (!*(volatile int *)&S.sm.abort) scatter_row(A, S, j & 1, row);
+                else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, row);
             }
         }
         if (!ok) atomicExch(&S.sm.abort, 1);
@@ -594,9 +595,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     if (warp == 0) tmem_dealloc(S.sm.tmem_base, NCOLS);
 }
 
-template <typename FeatT, bool BWD, bool PEX>
+template <typename FeatT, bool BWD, bool PEX, bool PK>
 void launch_tc(const RenderArgs &A, int kind, cudaStream_t s) {
-    auto kern = fine_colour_tc_kernel<FeatT, BWD, PEX>;
+    auto kern = fine_colour_tc_kernel<FeatT, BWD, PEX, PK>;
     const int bytes = (int)smem_bytes(BWD);
     ensure_smem(reinterpret_cast<const void *>(kern), bytes);
     ProfScope ps_(kind, s);
@@ -607,10 +608,17 @@ template <bool BWD>
 void launch_tc_any(const RenderArgs &A, cudaStream_t s) {
     const int kind = BWD ? DVGO_K_FINE_COLOUR_BWD : DVGO_K_FINE_COLOUR_FWD;
     const bool bf = A.cdtype == DVGO_DTYPE_BF16, pex = A.nfreq_pos > 0;
-    if (bf && pex) launch_tc<__nv_bfloat16, BWD, true>(A, kind, s);
-    else if (bf) launch_tc<__nv_bfloat16, BWD, false>(A, kind, s);
-    else if (pex) launch_tc<float, BWD, true>(A, kind, s);
-    else launch_tc<float, BWD, false>(A, kind, s);
+    if (A.packed) {
+        if (bf && pex) launch_tc<__nv_bfloat16, BWD, true, true>(A, kind, s);
+        else if (bf) launch_tc<__nv_bfloat16, BWD, false, true>(A, kind, s);
+        else if (pex) launch_tc<float, BWD, true, true>(A, kind, s);
+        else launch_tc<float, BWD, false, true>(A, kind, s);
+    } else {
+        if (bf && pex) launch_tc<__nv_bfloat16, BWD, true, false>(A, kind, s);
+        else if (bf) launch_tc<__nv_bfloat16, BWD, false, false>(A, kind, s);
+        else if (pex) launch_tc<float, BWD, true, false>(A, kind, s);
+        else launch_tc<float, BWD, false, false>(A, kind, s);
+    }
 }
 
 }  // namespace
