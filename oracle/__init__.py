@@ -308,6 +308,22 @@ def resize_grid(grid, dst_shape, src_box=((-1.0,) * 3, (1.0,) * 3), dst_box=None
     return out
 
 
+def fit2d(grid, target, order: int = 0, shift_b: float = 0.0, delta: float = 1.0, grad: bool = False):
+    """Image-fitting toy of Sec. 3 (Fig. exdv_poc): the grid's predicted image (bilinear
+    interpolation under the pre- / in- / post-activation order, order 1 / 2 / 0), the mean squared
+    error to the target and, with grad, dL/dgrid.  Returns (image, loss, grad or None)."""
+    V = _f64(grid)
+    T = _f64(target)
+    (gh, gw), (H, W) = V.shape, T.shape
+    img = np.zeros((H, W))
+    g = np.zeros_like(V) if grad else None
+    f = lib().oracle_fit2d
+    f.restype = C.c_double
+    loss = f(C.c_int(H), C.c_int(W), C.c_int(gh), C.c_int(gw), C.c_int(order), C.c_double(shift_b),
+             C.c_double(delta), _ptr(V), _ptr(T), _ptr(img), _ptr(g))
+    return img, float(loss), g
+
+
 def alpha_at(params: Params, density, x, delta: float) -> float:
     """Eq. post_activation: alpha(softplus(interp(x, V) + b), delta) at one point."""
     P = params._c()

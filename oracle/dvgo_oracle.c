@@ -682,6 +682,73 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
 /* Adam (Kingma & Ba) with the exponential decay lr_t = lr0 * 0.1^(t / 20000) (Supp. A)         */
 /* ------------------------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------------------------ */
+/* Image-fitting toy of Sec. 3 (Fig. exdv_poc)                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * A binary image of H x W pixels is regressed by a gh x gw grid V queried with bilinear
+ * interpolation under the pre-, in- or post-activation order of Eq. pre_in_post.  Readings: the
+ * image covers [0, 1]^2 with pixel (i, j) (row i) at ((i + 0.5) / H, (j + 0.5) / W); the grid's
+ * points sit on the align-corners lattice of [0, 1]^2 (u = x (g - 1), i0 = clamp(floor(u), 0,
+ * g - 2), f = u - i0); the predicted pixel is the alpha of the order with softplus(v + b) and
+ * alpha(sigma) = 1 - exp(-sigma delta); the loss is the mean squared error over all pixels.
+ * Writes the predicted image (nullable), adds dL/dV into grad (nullable) and returns L.
+ */
+double oracle_fit2d(int H, int W, int gh, int gw, int order, double b, double delta, const double *V,
+                    const double *target, double *image, double *grad) {
+    double loss = 0.0;
+    double scale = 1.0 / ((double)H * (double)W);
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double u[2] = {(i + 0.5) / H * (gh - 1), (j + 0.5) / W * (gw - 1)};
+            int g[2] = {gh, gw}, c0[2];
+            double f[2];
+            for (int a = 0; a < 2; ++a) {
+                double fl = floor(u[a]);
+                if (fl < 0.0) fl = 0.0;
+                if (fl > (double)(g[a] - 2)) fl = (double)(g[a] - 2);
+                c0[a] = (int)fl;
+                f[a] = u[a] - fl;
+            }
+            long idx[4];
+            double w[4], v[4];
+            for (int q = 0; q < 4; ++q) {
+                int bi = (q >> 1) & 1, bj = q & 1;
+                idx[q] = (long)(c0[0] + bi) * gw + (c0[1] + bj);
+                w[q] = (bi ? f[0] : 1.0 - f[0]) * (bj ? f[1] : 1.0 - f[1]);
+                v[q] = V[idx[q]];
+            }
+            double alpha, dadv[4];
+            if (order == 1) {            /* pre: interpolate the corners' alphas */
+                alpha = 0.0;
+                for (int q = 0; q < 4; ++q) {
+                    double e = exp(-og_softplus(v[q] + b) * delta);
+                    alpha += w[q] * (1.0 - e);
+                    dadv[q] = w[q] * delta * e * og_sigmoid(v[q] + b);
+                }
+            } else if (order == 2) {     /* in: interpolate the corners' densities */
+                double sigma = 0.0;
+                for (int q = 0; q < 4; ++q) sigma += w[q] * og_softplus(v[q] + b);
+                double e = exp(-sigma * delta);
+                alpha = 1.0 - e;
+                for (int q = 0; q < 4; ++q) dadv[q] = delta * e * w[q] * og_sigmoid(v[q] + b);
+            } else {                     /* post: activate the interpolated raw value */
+                double z = b;
+                for (int q = 0; q < 4; ++q) z += w[q] * v[q];
+                double e = exp(-og_softplus(z) * delta);
+                alpha = 1.0 - e;
+                for (int q = 0; q < 4; ++q) dadv[q] = delta * e * og_sigmoid(z) * w[q];
+            }
+            double r = alpha - target[(long)i * W + j];
+            loss += r * r * scale;
+            if (image) image[(long)i * W + j] = alpha;
+            if (grad)
+                for (int q = 0; q < 4; ++q) grad[idx[q]] += 2.0 * r * scale * dadv[q];
+        }
+    return loss;
+}
+
 double oracle_lr_decay(double lr0, int step, double decay_steps) {
     return lr0 * pow(0.1, (double)step / decay_steps);
 }
