@@ -89,6 +89,27 @@ size_t dvgo_grid_elements(const dvgo_grid_desc *g);
  * elements of their descriptors; they must not overlap. */
 int dvgo_pack_grid(const dvgo_grid_desc *src, const void *in, const dvgo_grid_desc *dst, void *out, void *stream);
 
+/* Image-fitting toy of Sec. 3 (Fig. exdv_poc): a binary image regressed by a low-resolution 2D grid
+ * queried with bilinear interpolation under the pre-, in- or post-activation order of
+ * Eq. pre_in_post.  The image covers [0, 1]^2, pixel (i, j) (row i) at ((i + 0.5) / height,
+ * (j + 0.5) / width); the grid's grid_h x grid_w points sit on the align-corners lattice of
+ * [0, 1]^2; the predicted pixel is alpha = 1 - exp(-sigma delta) with sigma from
+ * softplus(v + shift_b) in the given order; the loss is the mean squared error over all pixels. */
+typedef struct {
+    int height, width;   /* target image, row-major [height][width]                              */
+    int grid_h, grid_w;  /* lattice points of the 2D grid (row-major [grid_h][grid_w]), each >= 2  */
+    int act_order;       /* DVGO_ACT_POST / DVGO_ACT_PRE / DVGO_ACT_IN                             */
+    float shift_b;       /* b of Eq. density_activation                                           */
+    float delta;         /* the alpha function's step                                             */
+} dvgo_fit2d_desc;
+
+/* One evaluation of the toy on device buffers: image_out [height*width] gets the predicted image
+ * (nullable); with a target [height*width], loss_out[0] is set to the mean squared error and
+ * grad_grid [grid_h*grid_w] accumulates (+=) its gradient (each nullable).  Pixel cells and
+ * fractions come from exact integer arithmetic; the activations run in FP32.  Stream-ordered. */
+int dvgo_fit2d(const dvgo_fit2d_desc *d, const float *grid, const float *target, float *image_out, float *grad_grid,
+               float *loss_out, void *stream);
+
 /* Progressive scaling (Sec. 4.2): resizes a grid by trilinear interpolation onto another lattice.
  * Point (i, j, k) of the destination sits at x = dst.xyz_min + (i, j, k) (dst.xyz_max -
  * dst.xyz_min) / (n - 1) and takes interp(x, V_src) (Sec. 3 Eq. interp) of the source grid, x

@@ -22,7 +22,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
-    "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid",
+    "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid", "dvgo_fit2d",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
@@ -62,6 +62,11 @@ class _Params(C.Structure):
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
                 ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
                 ("act_order", C.c_int), ("n_freq_pos", C.c_int)]
+
+
+class _Fit2d(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("grid_h", C.c_int), ("grid_w", C.c_int),
+                ("act_order", C.c_int), ("shift_b", C.c_float), ("delta", C.c_float)]
 
 
 class _Mlp(C.Structure):
@@ -117,6 +122,8 @@ def lib():
         L.dvgo_pack_grid.argtypes = [vp, vp, vp, vp, vp]
         L.dvgo_resize_grid.restype = i
         L.dvgo_resize_grid.argtypes = [vp, vp, vp, vp, vp]
+        L.dvgo_fit2d.restype = i
+        L.dvgo_fit2d.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -464,6 +471,28 @@ def dvgo_grid_elements(desc: GridDesc) -> int:
     included)."""
     g = desc.c()
     return int(lib().dvgo_grid_elements(C.byref(g)))
+
+
+def dvgo_fit2d(grid, target=None, act_order: int = DVGO_ACT_POST, shift_b: float = 0.0, delta: float = 1.0,
+               image_out=None, grad_out=None, loss_out=None, stream=None, image_shape=None):
+    """Image-fitting toy of Sec. 3: grid [gh, gw] and target [H, W] (CUDA FP32).  Writes the
+    predicted image (image_out), the MSE (loss_out[0]) and accumulates dL/dgrid (grad_out), each
+    optional.  Without a target, image_shape (H, W) gives the image size."""
+    H, W = (target.shape if target is not None else image_shape)
+    for t, n, name in ((target, H * W, "target"), (image_out, H * W, "image_out"),
+                       (grad_out, grid.numel(), "grad_out")):
+        if t is not None and t.numel() != n:
+            raise ValueError(f"dvgo_fit2d: {name} has {t.numel()} elements, expected {n}")
+    if grid.dim() != 2 or (loss_out is not None and loss_out.numel() < 1):
+        raise ValueError("dvgo_fit2d: grid must be [grid_h, grid_w] and loss_out hold one element")
+    d = _Fit2d()
+    d.height, d.width, d.grid_h, d.grid_w = int(H), int(W), int(grid.shape[0]), int(grid.shape[1])
+    d.act_order, d.shift_b, d.delta = int(act_order), float(shift_b), float(delta)
+    _check(lib().dvgo_fit2d(C.byref(d), _dev(grid, "grid", torch.float32),
+                            _dev(target, "target", torch.float32, allow_none=True),
+                            _dev(image_out, "image_out", torch.float32, allow_none=True),
+                            _dev(grad_out, "grad_out", torch.float32, allow_none=True),
+                            _dev(loss_out, "loss_out", torch.float32, allow_none=True), _stream(stream)), "dvgo_fit2d")
 
 
 def dvgo_resize_grid(src_desc: GridDesc, src, dst_desc: GridDesc, out=None, stream=None):

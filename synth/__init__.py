@@ -140,6 +140,29 @@ def random_spheres(n: int, seed: int, lo=-0.7, hi=0.7, rmin=0.1, rmax=0.3):
     return g.uniform(lo, hi, size=(n, 3)), g.uniform(rmin, rmax, size=n)
 
 
+def binary_image(height: int, width: int, seed: int, n_shapes: int = 24):
+    """A binary image ({0, 1} float32, [height, width]) standing in for the target of the
+    image-fitting toy (Sec. 3, Fig. exdv_poc): the union of seeded discs, rotated rectangles and thin
+    strokes -- large occupied and free regions with sharp, curved and straight boundaries."""
+    g = rng(seed)
+    y, x = np.meshgrid((np.arange(height) + 0.5) / height, (np.arange(width) + 0.5) / width, indexing="ij")
+    img = np.zeros((height, width), dtype=bool)
+    for _ in range(n_shapes):
+        kind = g.integers(3)
+        cy, cx = g.uniform(0.05, 0.95, size=2)
+        if kind == 0:
+            r = g.uniform(0.03, 0.15)
+            img |= (y - cy) ** 2 + (x - cx) ** 2 < r * r
+        else:
+            th = g.uniform(0, np.pi)
+            a, b = (g.uniform(0.04, 0.2), g.uniform(0.02, 0.1)) if kind == 1 else (g.uniform(0.1, 0.35),
+                                                                                   g.uniform(0.002, 0.008))
+            u = (x - cx) * np.cos(th) + (y - cy) * np.sin(th)
+            v = -(x - cx) * np.sin(th) + (y - cy) * np.cos(th)
+            img |= (np.abs(u) < a) & (np.abs(v) < b)
+    return img.astype(np.float32)
+
+
 def smooth_features(res: int, channels: int, seed: int, n_waves: int = 4, max_freq: float = 2.0):
     """Per channel, the mean of n_waves random low-frequency sinusoids: values in [-1, 1]."""
     g = rng(seed)
