@@ -1,11 +1,16 @@
 // fit2d.cu -- the image-fitting toy of Sec. 3 (Fig. exdv_poc): a binary image regressed by a 2D
 // grid under the pre-, in- or post-activation order of Eq. pre_in_post (forward, MSE, gradient).
 //
-// Blocks of 256 threads own 32 x 32-pixel tiles.  A pixel's cell and fraction come from integer
-// arithmetic, u = (2i + 1)(g - 1) / (2 H): i0 = the quotient (clamped to g - 2), f = the remainder /
-// (2 H) rounded once to FP32, so cell choices are exact.  The gradient of a tile's pixels is summed
-// in a shared-memory patch of the grid points the tile touches and added to global memory once per
-// point; tiles wider than the patch (grids finer than the image) add straight to global memory.
+// Blocks of 256 threads own 32 x 32-pixel tiles; a warp takes one 32-pixel row of the tile at a
+// time.  A pixel's cell and fraction come from integer arithmetic, u = (2i + 1)(g - 1) / (2 H):
+// i0 = the quotient (clamped to g - 2), f = the remainder / (2 H) rounded once to FP32, so cell
+// choices are exact; the tile's 32 rows and 32 columns are resolved once into shared memory.
+// Gradients: the derivative of a pixel's alpha with respect to corner q factors into a per-pixel
+// term, the row weight (shared by the warp) and a per-corner term (shared by the pixels of a cell),
+// so the column weights are summed over runs of lanes with the same column cell by a segmented
+// warp scan and the run's last lane adds the four corners' sums -- into a shared-memory patch of
+// the grid points the tile touches, added to global memory once per point, or, for grids finer
+// than the image, straight to global memory.
 
 #include "dvgo_internal.cuh"
 
@@ -41,24 +46,32 @@ __global__ void __launch_bounds__(256) fit2d_kernel(dvgo_fit2d_desc d, const flo
                                                     float *__restrict__ grad, float *__restrict__ loss) {
     __shared__ float patch[PATCH ? kPatch * kPatch : 1];
     __shared__ float red[8];
+    __shared__ Axis rows[kTile], cols[kTile];
     const int ti = blockIdx.y * kTile, tj = blockIdx.x * kTile;
-    const int pr0 = pixel_axis(ti, d.height, d.grid_h).c0, pc0 = pixel_axis(tj, d.width, d.grid_w).c0;
+    if (threadIdx.x < kTile)
+        rows[threadIdx.x] = pixel_axis(min(ti + (int)threadIdx.x, d.height - 1), d.height, d.grid_h);
+    else if (threadIdx.x < 2 * kTile)
+        cols[threadIdx.x - kTile] = pixel_axis(min(tj + (int)threadIdx.x - kTile, d.width - 1), d.width, d.grid_w);
     if (PATCH && grad)
         for (int k = threadIdx.x; k < kPatch * kPatch; k += blockDim.x) patch[k] = 0.0f;
-    if (PATCH) __syncthreads();
+    __syncthreads();
+    const int pr0 = rows[0].c0, pc0 = cols[0].c0;
     const float gscale = 2.0f / ((float)d.height * (float)d.width);
+    const int lane = threadIdx.x & 31;
     float lsum = 0.0f;
+    // every lane runs the same iterations (kTile^2 is a multiple of the block size), so the warp
+    // scans below see all 32 lanes; pixels outside the image are inactive lanes
     for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
         const int i = ti + k / kTile, j = tj + k % kTile;
-        if (i >= d.height || j >= d.width) continue;
-        const Axis ay = pixel_axis(i, d.height, d.grid_h), ax = pixel_axis(j, d.width, d.grid_w);
-        float w[4], v[4], dadv[4], alpha;
+        const bool on = i < d.height && j < d.width;
+        const Axis ay = rows[k / kTile], ax = cols[k % kTile];
+        const float wy[2] = {1.0f - ay.f, ay.f}, wx[2] = {1.0f - ax.f, ax.f};
+        // dalpha / dv_q = L wy[bi] wx[bj] K[q]: L varies per pixel, K[q] only with the corner's value
+        float v[4], K[4], L, alpha;
         int idx[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int bi = (q >> 1) & 1, bj = q & 1;
-            idx[q] = (ay.c0 + bi) * d.grid_w + ax.c0 + bj;
-            w[q] = (bi ? ay.f : 1.0f - ay.f) * (bj ? ax.f : 1.0f - ax.f);
+            idx[q] = (ay.c0 + ((q >> 1) & 1)) * d.grid_w + ax.c0 + (q & 1);
             v[q] = __ldg(V + idx[q]);
         }
         if (ORDER == DVGO_ACT_PRE) {
@@ -66,41 +79,53 @@ __global__ void __launch_bounds__(256) fit2d_kernel(dvgo_fit2d_desc d, const flo
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float e = expf(-softplusf(v[q] + d.shift_b) * d.delta);
-                alpha = fmaf(w[q], 1.0f - e, alpha);
-                dadv[q] = w[q] * d.delta * e * sigmoidf_(v[q] + d.shift_b);
+                alpha = fmaf(wy[(q >> 1) & 1] * wx[q & 1], 1.0f - e, alpha);
+                K[q] = d.delta * e * sigmoidf_(v[q] + d.shift_b);
             }
+            L = 1.0f;
         } else if (ORDER == DVGO_ACT_IN) {
             float sigma = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sigma = fmaf(w[q], softplusf(v[q] + d.shift_b), sigma);
-            const float e = expf(-sigma * d.delta);
+            for (int q = 0; q < 4; ++q) {
+                sigma = fmaf(wy[(q >> 1) & 1] * wx[q & 1], softplusf(v[q] + d.shift_b), sigma);
+                K[q] = sigmoidf_(v[q] + d.shift_b);
+            }
             alpha = -expm1f(-sigma * d.delta);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dadv[q] = d.delta * e * w[q] * sigmoidf_(v[q] + d.shift_b);
+            L = d.delta * expf(-sigma * d.delta);
         } else {
             float z = d.shift_b;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) z = fmaf(w[q], v[q], z);
-            const float sigma = softplusf(z), e = expf(-sigma * d.delta);
+            for (int q = 0; q < 4; ++q) z = fmaf(wy[(q >> 1) & 1] * wx[q & 1], v[q], z);
+            // softplus and sigmoid from one exponential: t = exp(-|z|)
+            const float t = expf(-fabsf(z));
+            const float sigma = fmaxf(z, 0.0f) + log1pf(t), sg = (z >= 0.0f ? 1.0f : t) / (1.0f + t);
             alpha = -expm1f(-sigma * d.delta);
-            const float s = d.delta * e * sigmoidf_(z);
+            L = d.delta * expf(-sigma * d.delta) * sg;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dadv[q] = s * w[q];
+            for (int q = 0; q < 4; ++q) K[q] = 1.0f;
         }
-        if (img) img[(long long)i * d.width + j] = alpha;
+        if (on && img) img[(long long)i * d.width + j] = alpha;
         if (T) {
-            const float r = alpha - __ldg(T + (long long)i * d.width + j);
+            const float r = on ? alpha - __ldg(T + (long long)i * d.width + j) : 0.0f;
             lsum = fmaf(r, r, lsum);
             if (grad) {
-                const float g = gscale * r;
+                // the warp's lanes share the pixel row (hence wy and the corner rows); runs of lanes
+                // with the same column cell share all four corners: sum L wx over each run, one
+                // atomic per corner and run (inactive lanes get a key of their own and add nothing)
+                const float gl = on ? gscale * r * L : 0.0f;
+                const Seg sg = make_seg(on ? ax.c0 : -1 - lane, lane);
+                const float a0 = seg_sum(gl * wx[0], sg, lane), a1 = seg_sum(gl * wx[1], sg, lane);
+                if (sg.tail) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (dadv[q] == 0.0f) continue;
-                    if (PATCH) {
-                        const int pi = ay.c0 + ((q >> 1) & 1) - pr0, pj = ax.c0 + (q & 1) - pc0;
-                        atomicAdd(&patch[pi * kPatch + pj], g * dadv[q]);
-                    } else {
-                        atomicAdd(grad + idx[q], g * dadv[q]);
+                    for (int q = 0; q < 4; ++q) {
+                        const float val = wy[(q >> 1) & 1] * K[q] * ((q & 1) ? a1 : a0);
+                        if (val == 0.0f) continue;
+                        if (PATCH) {
+                            const int pi = ay.c0 + ((q >> 1) & 1) - pr0, pj = ax.c0 + (q & 1) - pc0;
+                            atomicAdd(&patch[pi * kPatch + pj], val);
+                        } else {
+                            atomicAdd(grad + idx[q], val);
+                        }
                     }
                 }
             }
