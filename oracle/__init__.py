@@ -79,7 +79,7 @@ class _FreeSpace(C.Structure):
 
 class _Model(C.Structure):
     _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")] + \
-        [("fs", C.POINTER(_FreeSpace))]
+        [("fs", C.POINTER(_FreeSpace)), ("mark_density", C.POINTER(C.c_ubyte)), ("mark_cgrid", C.POINTER(C.c_ubyte))]
 
 
 class _Grads(C.Structure):
@@ -155,6 +155,7 @@ class RenderResult:
     loss: float | None = None
     grads: dict = field(default_factory=dict)
     wbins: np.ndarray | None = None
+    touched: dict | None = None
 
 
 MLP_KEYS = ("w1", "b1", "w2", "b2", "w3", "b3")
@@ -215,13 +216,14 @@ def unknown_bbox(fs: FreeSpace):
 
 def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dict | None = None,
            target=None, grad_rgb=None, grad_tfinal=None, explicit_t=None, explicit_dt=None,
-           n_bins: int = 0, freespace: FreeSpace | None = None) -> RenderResult:
+           n_bins: int = 0, freespace: FreeSpace | None = None, touched: bool = False) -> RenderResult:
     """Render a ray batch forward and, if ``grad_rgb`` is given, backward (Sec. 2-4).
 
     density: [nx, ny, nz]; cgrid: [nx, ny, nz, C] (coarse colour or fine features);
     rays_o, rays_d: [R, 3]; jitter: [R] in [0, 1) or None (0.5); mlp: dict of w1..b3 (fine);
     grad_rgb: [R, 3] upstream dL/dC_hat; grad_tfinal: [R] or None; freespace: the known-free-space
-    test of Sec. 4.2 (skips points where the coarse grid's alpha is below tau_c).
+    test of Sec. 4.2 (skips points where the coarse grid's alpha is below tau_c); touched: also
+    return the lattice points the render reads (boolean [nx, ny, nz] per grid, in ``touched``).
     Returns colours, final transmittances, sample counts, clip bounds, loss and gradients.
     """
     P = params._c()
@@ -236,6 +238,11 @@ def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dic
     if freespace is not None:
         fs_c, fs_keep = freespace._c()
         M.fs = C.pointer(fs_c)
+    marks = None
+    if touched:
+        marks = {k: np.zeros(tuple(params.grid_shape), dtype=np.uint8) for k in ("density", "cgrid")}
+        M.mark_density = marks["density"].ctypes.data_as(C.POINTER(C.c_ubyte))
+        M.mark_cgrid = marks["cgrid"].ctypes.data_as(C.POINTER(C.c_ubyte))
     mlp_arrs = {}
     if params.mode == 1:
         for k in MLP_KEYS:
@@ -268,8 +275,11 @@ def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dic
                         ns.ctypes.data_as(C.POINTER(C.c_int)), _ptr(t0), _ptr(t1), C.byref(loss),
                         _ptr(gC), _ptr(gT), C.byref(G) if gC is not None else None, _ptr(wb),
                         C.c_int(n_bins))
-    return RenderResult(rgb=rgb, tfinal=tf, n_samples=ns, t_enter=t0, t_exit=t1,
-                        loss=float(loss.value) if tgt is not None else None, grads=grads, wbins=wb)
+    res = RenderResult(rgb=rgb, tfinal=tf, n_samples=ns, t_enter=t0, t_exit=t1,
+                       loss=float(loss.value) if tgt is not None else None, grads=grads, wbins=wb)
+    if marks is not None:
+        res.touched = {k: v.astype(bool) for k, v in marks.items()}
+    return res
 
 
 def ray_bounds(params: Params, o, d, p: float = 0.5):

@@ -103,6 +103,10 @@ typedef struct {
      * -> hidden -> 3                                                                            */
     const double *w1, *b1, *w2, *b2, *w3, *b3;
     const og_freespace *fs;     /* nullable: no known-free-space test                           */
+    /* Optional marks (nullable, [nx*ny*nz], set to 1) of the lattice points a render reads: the
+     * 8 corners of every sample that queries the density grid (every sample not in the known free
+     * space), and the 8 corners of every kept sample for the colour / feature grid. */
+    unsigned char *mark_density, *mark_cgrid;
 } og_model;
 
 typedef struct {
@@ -447,6 +451,11 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             continue;
         }
         og_corners(P, s->x, s->idx, s->cw);
+        if (M->mark_density)
+            for (int c = 0; c < 8; ++c) {
+#pragma omp atomic write
+                M->mark_density[s->idx[c]] = 1;
+            }
         if (P->act_order == 1) {            /* pre: interpolate the corners' alphas */
             s->alpha = 0.0;
             for (int c = 0; c < 8; ++c)
@@ -463,6 +472,11 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             s->alpha = -expm1(-sigma * s->dt);
         }
         s->kept = !(s->alpha < P->tau_f);
+        if (s->kept && M->mark_cgrid)
+            for (int c = 0; c < 8; ++c) {
+#pragma omp atomic write
+                M->mark_cgrid[s->idx[c]] = 1;
+            }
         if (!s->kept) s->alpha = 0.0;
         if (s->kept) {
             for (int ch = 0; ch < C; ++ch) feat[ch] = 0.0;
