@@ -215,6 +215,8 @@ def workload_config(args, form):
                         "step 0.5 voxel, 8 balls (raw density 50) + smooth albedo, 100 views 800x800",
             "form": form, "global_batch": NRAYS * args.gpus, "grid": RES, "feat_dim": FEAT, "hidden": HID,
             "layout": getattr(args, "layout", "canonical"),
+            "grid_adam": "lazy (skips zero gradients)" if (form == "chosen" and getattr(args, "lazy_adam", False))
+            else "dense",
             "parallelism": f"replicas x{args.gpus} (independent problems)",
             "l2": "inputs larger than L2: Adam sweeps ~1.7 GB of parameters and moments every step"}
 
@@ -226,7 +228,7 @@ def workload_config(args, form):
 class Form:
     """One training form on the benchmark scene: its model, its step, and what it processes."""
 
-    def __init__(self, name, dev, dens, feat, mlp, dvgo, torch, args_layout="canonical"):
+    def __init__(self, name, dev, dens, feat, mlp, dvgo, torch, args_layout="canonical", lazy_adam=False):
         import synth
         self.name, self.dvgo, self.torch = name, dvgo, torch
         chosen = name == "chosen"
@@ -236,7 +238,8 @@ class Form:
                              mlp_prec=dvgo.DVGO_MLP_BF16 if chosen else dvgo.DVGO_MLP_FP32, n_freq_pos=n_freq_pos())
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
         self.model = dvgo.FineModel(t(dens), t(feat), t(mlp_flat(mlp)), self.p, NRAYS, bf16_feat=chosen,
-                                    overlap_adam=chosen, layout=LAYOUTS[args_layout])
+                                    overlap_adam=chosen, layout=LAYOUTS[args_layout],
+                                    lazy_grid_adam=chosen and lazy_adam)
         self.trainer = None
         if chosen:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), self.p, self.model.dd, NRAYS,
@@ -256,7 +259,7 @@ class Form:
 
 
 def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, local_rank, peaks):
-    form = Form(name, dev, dens, feat, mlp, dvgo, torch, args.layout)
+    form = Form(name, dev, dens, feat, mlp, dvgo, torch, args.layout, args.lazy_adam)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)
     dbatches = [tuple(t(x) for x in b) for b in batches]
     # samples per batch of the uniform forward (units of the colour kernels)
@@ -334,15 +337,49 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
         fwd_units = bwd_units = ((args.steps - n_dense) * expl + n_dense * dense_samples) / args.steps
     dom_name, (dom_ms, dom_n) = max(per_kind.items(), key=lambda kv: kv[1][0])
     roof = roofline(dom_name, dom_ms / max(dom_n, 1), fwd_units, bwd_units, name == "chosen", peaks)
+    step_roof = step_hbm_minimum(form, dbatches[0], ms / args.steps, dvgo, torch, peaks)
     return {"value": value, "ms_per_step": ms / args.steps, "dtype": "bf16" if name == "chosen" else "f32",
             "config": workload_config(args, name) | {"dense_samples_per_batch": dense_samples,
                                                      "hit_rays_per_batch": hit_rays,
                                                      "samples_per_hit_ray": N_PROP_SAMPLES if name == "chosen" else None},
-            "roofline": roof,
+            "roofline": roof, "step_roofline": step_roof,
             "kernels_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in per_kind.items() if v[1]},
             "e2e": {"value": whole_job_rate(NRAYS * args.steps, world, e2e_ms), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": clk}
+
+
+def step_hbm_minimum(form, batch, ms_per_step, dvgo, torch, peaks):
+    """The whole step against the HBM roofline: the minimum DRAM bytes of one step -- every touched
+    lattice point's density (4 B) and features (48 B FP32 / 24 B BF16) read once and its FP32
+    gradients read and written once, the dense Adam sweep (32 B per parameter, plus the 2-byte BF16
+    feature copy), 48 B of ray input per ray -- with the touched points counted exactly
+    (dvgo_touched_points) on one batch; the chosen form weights a uniform step and a proposal step
+    by how often each runs."""
+    m = form.model
+    o, d, jit, _ = batch
+    counts = {}
+    m.forward(o, d, jit)
+    counts["uniform"] = dvgo.dvgo_touched_points(m.params, m.dd, NRAYS, None, m.renderer.workspace)[1]
+    mix = {"uniform": 1.0}
+    if form.trainer is not None:
+        tr = form.trainer
+        ts, dts = tr.proposal.sample(o, d, jit, tr.n_samples, eta=tr.eta)
+        rend = m.explicit_renderer(tr.n_samples)
+        rend.forward(m.density, m.cgrid, m.mlp, o, d, jit, (ts, dts))
+        counts["proposal"] = dvgo.dvgo_touched_points(m.params, m.dd, NRAYS, (ts, dts), rend.workspace)[1]
+        mix = {"uniform": 1.0 / tr.uniform_every, "proposal": 1.0 - 1.0 / tr.uniform_every}
+    torch.cuda.synchronize()
+    counts = {k: [int(x) for x in v.cpu()] for k, v in counts.items()}
+    feat_b = 24 if m.bf16_feat else 48
+    render = sum(w * (counts[k][0] * 4 * 3 + counts[k][1] * (feat_b + 2 * 48)) for k, w in mix.items())
+    adam = n_params() * 32 + (RES ** 3 * FEAT * 2 if m.bf16_feat else 0)
+    byts = render + adam + 48 * NRAYS
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    achieved = byts / (ms_per_step * 1e-3) / 1e9
+    return {"bound": "hbm", "hbm_min_bytes_per_step": int(byts), "render_bytes": int(render), "adam_bytes": int(adam),
+            "touched_points": counts, "achieved": achieved, "unit": "GB/s", "peak": hbm, "frac": achieved / hbm,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
 
 
 def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
@@ -571,7 +608,7 @@ def run_time_to_psnr(args):
                         mlp_prec=dvgo.DVGO_MLP_BF16 if bf16 else dvgo.DVGO_MLP_FP32, tau_f=tau_f, freespace=freespace,
                         w_pt_rgb=aux_f[0], w_bg=aux_f[1], act_order=ACT_ORDERS[args.act_order], n_freq_pos=pe_pos)
         model = dvgo.FineModel(dens0.clone(), feat0.clone(), mlp0.clone(), p, NRAYS, bf16_feat=bf16,
-                               overlap_adam=use_prop, box=box)
+                               overlap_adam=use_prop, box=box, lazy_grid_adam=use_prop and args.lazy_adam)
         prop = trainer = None
         if use_prop:
             prop = dvgo.Proposal(synth.proposal_weights(39, 64, seed=5), p, model.dd, NRAYS,
@@ -624,7 +661,8 @@ def run_time_to_psnr(args):
             "eval_every": args.eval_every, "ground_truth_render_s": t_gt, "data": "synthetic (analytic 20-primitive "
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
             "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
-            "fine_density_init": fine_init, "mlp_inputs": in_dim, "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched],
+            "fine_density_init": fine_init, "lazy_grid_adam_chosen": args.lazy_adam, "mlp_inputs": in_dim,
+            "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched],
                                                   "adam": args.pg_adam},
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
                          "train_rays": PROPOSAL_TRAIN_RAYS, "eta": eta},
@@ -841,7 +879,8 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": head["value"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic", "config": head["config"],
-            "roofline": head["roofline"], "kernels_ms_per_step": head["kernels_ms_per_step"], "e2e": head["e2e"],
+            "roofline": head["roofline"], "step_roofline": head["step_roofline"],
+            "kernels_ms_per_step": head["kernels_ms_per_step"], "e2e": head["e2e"],
             "gpu_launches": sum(r["gpu_launches"] for r in res.values()), "clocks": head["clocks"],
             "forms": res}
     if not args.no_proposal_eval and world == 1:
@@ -892,6 +931,9 @@ def main():
     ap.add_argument("--pg-ckpt", default="",
                     help="time-to-psnr: progressive-scaling checkpoints of the fine stage, e.g. 1000,2000,3000 "
                          "(Supp. A); empty = the final grid from the start")
+    ap.add_argument("--lazy-adam", action="store_true",
+                    help="step and time-to-psnr: the chosen form's grid Adam skips elements with a zero gradient "
+                         "(lazy variant, this library's option; the paper's Adam is dense)")
     ap.add_argument("--pg-adam", choices=["reset", "resize"], default="reset",
                     help="time-to-psnr: the grids' Adam moments at a progressive-scaling checkpoint")
     ap.add_argument("--fine-init", choices=["auto", "zero", "coarse"], default="auto",

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 4
+#define DVGO_ABI_VERSION 5
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -244,6 +244,9 @@ typedef struct {
     float lr;            /* already-decayed learning rate for this step                        */
     float beta1, beta2, eps;
     int step;            /* 1-based step count t (bias correction 1 - beta^t)                  */
+    int skip_zero_grad;  /* 1: lazy variant -- an element whose gradient is exactly 0 keeps its
+                            parameter and moments (reads 4 B instead of 32 B there); this
+                            library's option, the paper's Adam is dense (0)                     */
 } dvgo_adam_hparams;
 
 /*
@@ -269,6 +272,17 @@ int dvgo_workspace_status(void *workspace, void *stream);
  * from a workspace into counts_out [n_rays] (device int32), and the batch total into
  * total_out[0] (device, nullable).  n_rays must be the forward's ray count. */
 int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *total_out, void *stream);
+
+/* Lattice points one fine-stage render read (the sizes behind the minimum HBM bytes of a step):
+ * bitmaps[0 .. W) marks the density grid's points at the 8 corners of every sample outside the known
+ * free space, bitmaps[W .. 2W) the feature grid's points at the 8 corners of every kept sample
+ * (W = ceil(nx*ny*nz / 32) uint32 words, bit p of the canonical index p = (i ny + j) nz + k, whatever
+ * the storage layout); counts[0], counts[1] = their populations.  Call after dvgo_render_fwd with the
+ * same parameters, grid descriptor, ray count, explicit samples and workspace; bitmaps and counts
+ * are device buffers, overwritten.  Fine stage only.  Stream-ordered. */
+int dvgo_touched_points(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
+                        const dvgo_samples *explicit_samples, void *workspace, size_t workspace_bytes,
+                        uint32_t *bitmaps, unsigned long long *counts, void *stream);
 
 /*
  * Allocation-free variant of the coarse-stage forward (dvgo_render_fwd with mode

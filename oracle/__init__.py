@@ -354,13 +354,16 @@ def mlp_forward(params: Params, mlp: dict, e):
     return out
 
 
-def adam(param, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None, zero_grad=True):
-    """One Adam step (Kingma & Ba), in place on float64 arrays; lr already decayed."""
+def adam(param, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None, zero_grad=True,
+         skip_zero_grad=False):
+    """One Adam step (Kingma & Ba), in place on float64 arrays; lr already decayed.  skip_zero_grad:
+    the lazy variant, elements with an exactly zero gradient keep parameter and moments."""
     for a in (param, grad, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().oracle_adam(C.c_long(param.size), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), C.c_double(lr),
                       C.c_double(beta1), C.c_double(beta2), C.c_double(eps), C.c_int(t),
-                      _ptr(None if lr_scale is None else _f64(lr_scale)), C.c_int(int(zero_grad)))
+                      _ptr(None if lr_scale is None else _f64(lr_scale)), C.c_int(int(zero_grad)),
+                      C.c_int(int(skip_zero_grad)))
 
 
 PROP_KEYS = ("w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3")

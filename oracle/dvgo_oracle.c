@@ -769,12 +769,15 @@ double oracle_lr_decay(double lr0, int step, double decay_steps) {
 
 /* One Adam step at 1-based step t with learning rate lr (already decayed).  lr_scale nullable
  * (per-element scale, Sec. 4.1 Prior 2).  If zero_grad, g is cleared afterwards. */
+/* One Adam step.  skip_zero_grad != 0 selects the lazy variant (this library's option, not the
+ * paper's): an element whose gradient is exactly 0 keeps its parameter and both moments. */
 void oracle_adam(long n, double *param, double *grad, double *m, double *v, double lr,
                  double beta1, double beta2, double eps, int t, const double *lr_scale,
-                 int zero_grad) {
+                 int zero_grad, int skip_zero_grad) {
     double bc1 = 1.0 - pow(beta1, t), bc2 = 1.0 - pow(beta2, t);
     for (long i = 0; i < n; ++i) {
         double g = grad[i];
+        if (skip_zero_grad && g == 0.0) continue;
         m[i] = beta1 * m[i] + (1.0 - beta1) * g;
         v[i] = beta2 * v[i] + (1.0 - beta2) * g * g;
         double mhat = m[i] / bc1, vhat = v[i] / bc2;

@@ -23,6 +23,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
     "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid", "dvgo_fit2d",
+    "dvgo_touched_points",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
@@ -79,7 +80,7 @@ class _Samples(C.Structure):
 
 class _AdamH(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("step", C.c_int)]
+                ("step", C.c_int), ("skip_zero_grad", C.c_int)]
 
 
 def lib():
@@ -124,6 +125,8 @@ def lib():
         L.dvgo_resize_grid.argtypes = [vp, vp, vp, vp, vp]
         L.dvgo_fit2d.restype = i
         L.dvgo_fit2d.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.dvgo_touched_points.restype = i
+        L.dvgo_touched_points.argtypes = [vp, vp, i, vp, vp, sz, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -298,6 +301,22 @@ def dvgo_lr_at(lr0: float, step: int, decay_steps: float = 20000.0) -> float:
     return float(lib().dvgo_lr_at(lr0, step, decay_steps))
 
 
+def dvgo_touched_points(params: Params, density_desc: GridDesc, n_rays: int, samples, workspace, stream=None):
+    """Lattice points the last fine forward on `workspace` read: returns (bitmaps [2, W] int32 view of
+    the uint32 words -- density, then features -- and counts [2] int64, both on the device)."""
+    n = int(density_desc.shape[0]) * int(density_desc.shape[1]) * int(density_desc.shape[2])
+    words = (n + 31) // 32
+    bm = torch.empty((2, words), dtype=torch.int32, device=workspace.device)
+    counts = torch.empty(2, dtype=torch.int64, device=workspace.device)
+    p, g = params.c(), density_desc.c()
+    s = _samples_struct(samples)
+    _check(lib().dvgo_touched_points(C.byref(p), C.byref(g), int(n_rays), _ref(s),
+                                     _dev(workspace, "workspace", torch.uint8), workspace.numel(),
+                                     C.c_void_p(bm.data_ptr()), C.c_void_p(counts.data_ptr()), _stream(stream)),
+           "dvgo_touched_points")
+    return bm, counts
+
+
 def dvgo_workspace_size(params: Params, density_desc: GridDesc, n_rays: int, samples=None) -> int:
     p, g = params.c(), density_desc.c()
     s = _samples_struct(samples) if samples is not None else None
@@ -339,9 +358,10 @@ def dvgo_render_bwd(params: Params, density_desc: GridDesc, density, cgrid_desc:
 
 
 def dvgo_adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8,
-                   lr_scale=None, param_bf16_out=None, zero_grad=True, stream=None):
+                   lr_scale=None, param_bf16_out=None, zero_grad=True, stream=None, skip_zero_grad=False):
     h = _AdamH()
     h.lr, h.beta1, h.beta2, h.eps, h.step = float(lr), float(beta1), float(beta2), float(eps), int(step)
+    h.skip_zero_grad = int(bool(skip_zero_grad))
     st = lib().dvgo_adam_step(
         _dev(param, "param", torch.float32), _dev(grad, "grad", torch.float32), _dev(m, "m", torch.float32),
         _dev(v, "v", torch.float32), param.numel(), C.byref(h), _dev(lr_scale, "lr_scale", torch.float32, True),

@@ -4,7 +4,9 @@
 //
 // HBM-bound: per element it reads p, g, m, v (16 B) and writes p, m, v and, with zero_grad, g
 // (12-16 B), plus 2 B for the optional BF16 copy.  16-byte vector loads/stores, grid-stride
-// loop over a grid sized to fill every SM.
+// loop over a grid sized to fill every SM.  The lazy variant reads the gradient first and leaves
+// a 4-element vector whose gradients are all zero untouched (4 B of traffic per element there);
+// inside a vector it updates only the elements with a nonzero gradient.
 
 #include "dvgo_internal.cuh"
 
@@ -23,6 +25,11 @@ __device__ __forceinline__ void adam_one(float &p, float &m, float &v, float g, 
     p -= k.lr * s * mhat / (sqrtf(vhat) + k.eps);
 }
 
+__device__ __forceinline__ void adam_lazy(float &p, float &m, float &v, float g, float s, const AdamK &k) {
+    if (g != 0.0f) adam_one(p, m, v, g, s, k);
+}
+
+template <bool LAZY>
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                                                     float *__restrict__ v, size_t n, AdamK k,
                                                     const float *__restrict__ scale, uint16_t *__restrict__ pb,
@@ -30,15 +37,23 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     size_t n4 = n / 4;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 G = reinterpret_cast<const float4 *>(g)[i];
+        if (LAZY && G.x == 0.0f && G.y == 0.0f && G.z == 0.0f && G.w == 0.0f) continue;
         float4 P = reinterpret_cast<float4 *>(p)[i];
-        float4 G = reinterpret_cast<const float4 *>(g)[i];
         float4 M = reinterpret_cast<float4 *>(m)[i];
         float4 V = reinterpret_cast<float4 *>(v)[i];
         float4 S = scale ? reinterpret_cast<const float4 *>(scale)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
-        adam_one(P.x, M.x, V.x, G.x, S.x, k);
-        adam_one(P.y, M.y, V.y, G.y, S.y, k);
-        adam_one(P.z, M.z, V.z, G.z, S.z, k);
-        adam_one(P.w, M.w, V.w, G.w, S.w, k);
+        if (LAZY) {
+            adam_lazy(P.x, M.x, V.x, G.x, S.x, k);
+            adam_lazy(P.y, M.y, V.y, G.y, S.y, k);
+            adam_lazy(P.z, M.z, V.z, G.z, S.z, k);
+            adam_lazy(P.w, M.w, V.w, G.w, S.w, k);
+        } else {
+            adam_one(P.x, M.x, V.x, G.x, S.x, k);
+            adam_one(P.y, M.y, V.y, G.y, S.y, k);
+            adam_one(P.z, M.z, V.z, G.z, S.z, k);
+            adam_one(P.w, M.w, V.w, G.w, S.w, k);
+        }
         reinterpret_cast<float4 *>(p)[i] = P;
         reinterpret_cast<float4 *>(m)[i] = M;
         reinterpret_cast<float4 *>(v)[i] = V;
@@ -53,6 +68,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     }
     // scalar tail
     for (size_t i = n4 * 4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (LAZY && g[i] == 0.0f) continue;
         float P = p[i], M = m[i], V = v[i];
         adam_one(P, M, V, g[i], scale ? scale[i] : 1.0f, k);
         p[i] = P;
@@ -84,7 +100,10 @@ void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const 
     if (blocks < 1) blocks = 1;
     {
         ProfScope ps_(DVGO_K_ADAM, s);
-        adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, k, lr_scale, bf16_out, zero_grad);
+        if (h.skip_zero_grad)
+            adam_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, k, lr_scale, bf16_out, zero_grad);
+        else
+            adam_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, k, lr_scale, bf16_out, zero_grad);
     }
 }
 

@@ -332,7 +332,7 @@ int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n, cons
                    const float *lr_scale, uint16_t *param_bf16_out, int zero_grad, void *stream) {
     if (!h || (n > 0 && (!param || !grad || !m || !v))) return DVGO_ERR_INVALID_ARG;
     if (h->step < 1 || !isfinite(h->lr) || !(h->beta1 >= 0.0f && h->beta1 < 1.0f) ||
-        !(h->beta2 >= 0.0f && h->beta2 < 1.0f) || !(h->eps >= 0.0f))
+        !(h->beta2 >= 0.0f && h->beta2 < 1.0f) || !(h->eps >= 0.0f) || (h->skip_zero_grad & ~1) != 0)
         return DVGO_ERR_INVALID_ARG;
     const void *ptrs[6] = {param, grad, m, v, lr_scale, param_bf16_out};
     for (int i = 0; i < 6; ++i)
@@ -354,6 +354,22 @@ int dvgo_sample_counts(const void *ws, int n_rays, int *counts_out, int *total_o
     sample_counts_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(
         reinterpret_cast<const RayRec *>(b + L.rays), reinterpret_cast<const WsHeader *>(b + L.header), n_rays,
         counts_out, total_out);
+    return launch_status();
+}
+
+int dvgo_touched_points(const dvgo_params *p, const dvgo_grid_desc *dd, int R, const dvgo_samples *ex, void *ws,
+                        size_t ws_bytes, uint32_t *bitmaps, unsigned long long *counts, void *stream) {
+    if (!p || !dd || !bitmaps || !counts || R < 0 || p->mode != DVGO_MODE_FINE || !grid_ok(dd) || dd->channels != 1)
+        return DVGO_ERR_INVALID_ARG;
+    if (!finite_pos(p->step)) return DVGO_ERR_INVALID_ARG;
+    if (ex && (!ex->t || !ex->dt || ex->n_per_ray < 1)) return DVGO_ERR_INVALID_ARG;
+    if (p->freespace && p->freespace->density && !grid_ok(&p->freespace->desc)) return DVGO_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode);
+    int st = check_ws(L, ws, ws_bytes);
+    if (st) return st;
+    RenderArgs A = make_args(p, dd, nullptr, dd, nullptr, nullptr, R, ex, ws, L);
+    launch_touched(A, bitmaps, counts, s);
     return launch_status();
 }
 

@@ -417,6 +417,8 @@ void launch_fine_colour_bwd(const RenderArgs &A, cudaStream_t s);
 void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
                  const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s);
 
+void launch_touched(const RenderArgs &A, uint32_t *bitmaps, unsigned long long *counts, cudaStream_t s);
+
 int num_sms();
 void ensure_smem(const void *kernel, int bytes);
 

@@ -140,7 +140,7 @@ class FineModel:
     def __init__(self, density: torch.Tensor, feat: torch.Tensor, mlp_flat: torch.Tensor, params: B.Params,
                  n_rays: int, bf16_feat: bool = False, box=((-1.0,) * 3, (1.0,) * 3),
                  lr_grid: float = 0.1, lr_mlp: float = 1e-3, decay_steps: float = 20000.0,
-                 overlap_adam: bool = False, layout: int = B.DVGO_LAYOUT_CANONICAL):
+                 overlap_adam: bool = False, layout: int = B.DVGO_LAYOUT_CANONICAL, lazy_grid_adam: bool = False):
         self.params = params
         res = tuple(density.shape)
         C = feat.shape[-1]
@@ -165,6 +165,7 @@ class FineModel:
         self.g_mlp = torch.zeros_like(self.mlp_flat)
         self.adam = {k: AdamState(t) for k, t in (("density", self.density), ("feat", self._feat), ("mlp", self.mlp_flat))}
         self.lr_grid, self.lr_mlp, self.decay_steps = lr_grid, lr_mlp, decay_steps
+        self.lazy_grid_adam = lazy_grid_adam   # grids' Adam skips elements with a zero gradient
         dev = density.device
         self.rgb = torch.empty((n_rays, 3), device=dev)
         self.tfinal = torch.empty(n_rays, device=dev)
@@ -211,7 +212,7 @@ class FineModel:
         self._side.wait_event(self._ev_bwd)
         self._side.wait_event(self._ev_after)
         B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, t,
-                         param_bf16_out=self._feat_bf16, stream=self._side)
+                         param_bf16_out=self._feat_bf16, stream=self._side, skip_zero_grad=self.lazy_grid_adam)
         self._ev_feat.record(self._side)
         self._feat_pending = True
 
@@ -309,9 +310,9 @@ class FineModel:
             self._feat_deferred = (lr_g, tg)
         else:
             B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, tg,
-                             param_bf16_out=self._feat_bf16, stream=stream)
+                             param_bf16_out=self._feat_bf16, stream=stream, skip_zero_grad=self.lazy_grid_adam)
         B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, tg,
-                         stream=stream)
+                         stream=stream, skip_zero_grad=self.lazy_grid_adam)
         B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
         return self.loss
 
