@@ -153,39 +153,50 @@ class ClockSampler:
 
 class OracleStep:
     """The FP64 oracle on n rays of a batch (fwd + bwd) plus one oracle Adam sweep over all
-    parameters, projected to a full 8192-ray step."""
+    parameters, projected to a full batch of `batch_rays` rays.  Defaults: the config-2 step (160^3
+    on [-1, 1]^3, b for alpha_init 1e-6, step 0.5 voxel)."""
 
-    def __init__(self, dens, feat, mlp):
+    def __init__(self, dens, feat, mlp, shape=None, box=((-1.0,) * 3, (1.0,) * 3), shift_b=None, step=None,
+                 pe_pos=None, batch_rays=NRAYS, params=None, **_):
         import oracle
         self.oracle = oracle
-        step = 2.0 / RES * 0.5
-        self.P = oracle.Params(grid_shape=(RES,) * 3,
-                               shift_b=float(np.float32(oracle.shift_from_alpha_init(1e-6, 2.0 / RES))),
-                               delta=float(np.float32(step)), bg=(1.0, 1.0, 1.0), mode=1, feat_dim=FEAT, n_freq=4,
-                               hidden=HID, n_freq_pos=n_freq_pos())
+        shape = tuple(dens.shape[:3]) if shape is None else tuple(shape)
+        step = 2.0 / RES * 0.5 if step is None else step
+        shift_b = oracle.shift_from_alpha_init(1e-6, 2.0 / RES) if shift_b is None else shift_b
+        pe_pos = n_freq_pos() if pe_pos is None else pe_pos
+        self.P = params if params is not None else oracle.Params(
+            grid_shape=shape, xyz_min=tuple(float(np.float32(v)) for v in box[0]),
+            xyz_max=tuple(float(np.float32(v)) for v in box[1]), shift_b=float(np.float32(shift_b)),
+            delta=float(np.float32(step)), bg=(1.0, 1.0, 1.0), mode=1, feat_dim=FEAT, n_freq=4, hidden=HID,
+            n_freq_pos=pe_pos)
         self.dens64, self.feat64 = dens.astype(np.float64), feat.astype(np.float64)
-        self.mlp64 = {k: v.astype(np.float64) for k, v in mlp.items()}
-        self.adam_arrays = [np.zeros(n_params()), np.ones(n_params()), np.zeros(n_params()), np.zeros(n_params())]
+        self.mlp64 = {k: np.asarray(v).astype(np.float64) for k, v in mlp.items()}
+        n_par = int(np.prod(shape)) * (1 + FEAT) + sum(v.size for v in self.mlp64.values())
+        self.n_par = n_par
+        self.adam_arrays = [np.zeros(n_par), np.ones(n_par), np.zeros(n_par), np.zeros(n_par)]
+        self.batch_rays = batch_rays
+        self.freespace = None      # oracle.FreeSpace of the known-free-space test, when the recipe has one
         self.t = 0
 
     def run(self, batch, n):
-        o, d, jit, tgt = batch
+        o, d, jit, tgt = (np.asarray(x) for x in batch)
         t0 = time.perf_counter()
         fwd = self.oracle.render(self.P, self.dens64, self.feat64, o[:n], d[:n], jitter=jit[:n], mlp=self.mlp64,
-                                 target=tgt[:n])
+                                 target=tgt[:n], freespace=self.freespace)
         gC = 2.0 * (fwd.rgb - tgt[:n]) / n
         self.oracle.render(self.P, self.dens64, self.feat64, o[:n], d[:n], jitter=jit[:n], mlp=self.mlp64,
-                           grad_rgb=gC)
+                           grad_rgb=gC, freespace=self.freespace)
         t_render = time.perf_counter() - t0
         self.t += 1
         p, g, m, v = self.adam_arrays
         t1 = time.perf_counter()
         self.oracle.adam(p, g, m, v, 0.1, self.t, zero_grad=False)
         t_adam = time.perf_counter() - t1
-        step_s = t_render * NRAYS / n + t_adam
-        return {"value": NRAYS / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(), "kind": "oracle",
-                "sample": f"{n} of 8192 rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam sweep over "
-                          f"all {n_params()} parameters ({t_adam:.2f} s), projected to a full step"}
+        step_s = t_render * self.batch_rays / n + t_adam
+        return {"value": self.batch_rays / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(),
+                "kind": "oracle", "step_s": step_s,
+                "sample": f"{n} of {self.batch_rays} rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam "
+                          f"sweep over all {self.n_par} parameters ({t_adam:.2f} s), projected to a full step"}
 
 
 def run_reference(args, rank, world):
@@ -578,6 +589,25 @@ def run_time_to_psnr(args):
     p_eval = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.5 * s0, shift_b=b_f, bg=(1.0, 1.0, 1.0), tau_f=tau_f,
                          freespace=freespace, act_order=ACT_ORDERS[args.act_order], n_freq_pos=pe_pos)
     eval_cache = {}
+    oracle_proj = None
+    if not args.no_cpu_baseline:
+        # the FP64 oracle's rate on 256 rays of a fine-stage batch (fwd + bwd + Adam, the first
+        # grid of the schedule, the recipe's skipping), projected to the fine stage's steps
+        import oracle
+        Po = oracle.Params(grid_shape=fshape0, xyz_min=tuple(float(np.float32(v)) for v in box[0]),
+                           xyz_max=tuple(float(np.float32(v)) for v in box[1]), shift_b=float(np.float32(b_f)),
+                           delta=float(np.float32(0.5 * s0)), tau_f=float(np.float32(tau_f)), bg=(1.0, 1.0, 1.0),
+                           mode=1, feat_dim=FEAT, n_freq=4, hidden=HID, n_freq_pos=pe_pos,
+                           w_pt=float(np.float32(aux_f[0])), w_bg=float(np.float32(aux_f[1])))
+        mv = {k: v.cpu().numpy() for k, v in dvgo.mlp_views(mlp0, in_dim, HID).items()}
+        ost = OracleStep(dens0.cpu().numpy(), feat0.cpu().numpy(), mv, params=Po)
+        if freespace is not None:
+            ost.freespace = oracle.FreeSpace(density=coarse.density.cpu().numpy().astype(np.float64),
+                                             shift_b=float(np.float32(pc.shift_b)), delta=float(np.float32(pc.step)),
+                                             tau=float(np.float32(1e-3)))
+        r0 = ost.run(tuple(x.cpu().numpy() for x in batch(0, 2)), 256)
+        oracle_proj = {"rays_per_s": r0["value"], "cores": r0["cores"], "step_s": r0["step_s"],
+                       "projected_fine_stage_s": r0["step_s"] * args.fine_steps, "sample": r0["sample"]}
 
     def psnr(model, n_rays):
         # the uniform FP32 renderer on the model's current lattice and step
@@ -662,6 +692,7 @@ def run_time_to_psnr(args):
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
             "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
             "fine_density_init": fine_init, "lazy_grid_adam_chosen": args.lazy_adam, "mlp_inputs": in_dim,
+            "cpu_baseline": oracle_proj,
             "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched],
                                                   "adam": args.pg_adam},
             "proposal": {"samples_per_ray": n_ps, "uniform_every": every, "uniform_warmup": args.prop_warmup,
@@ -719,6 +750,12 @@ def run_stress(args):
     dvgo.dvgo_profile_enable(False)
     per_kind = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
     ms = e0.elapsed_time(e1) / args.steps
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on 256 of the batch's rays (fwd + bwd, the FP32-feature model), projected
+        hb = tuple(x.cpu().numpy() for x in batches[0])
+        cpu = OracleStep(dens, feat, mlp, step=0.5 * 2.0 / rs, shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rs),
+                         pe_pos=0, batch_rays=nr).run(hb, 256)
     n_params = rs ** 3 * (1 + FEAT) + 22019
     adam_ms = per_kind["adam"][0] / args.steps
     kernels = {k: round(v[0] / args.steps, 4) for k, v in per_kind.items() if v[1]}
@@ -731,7 +768,7 @@ def run_stress(args):
                       "kernels_ms_per_step": kernels,
                       "adam_gbs": n_params * (32 + 0) / 1e9 / (adam_ms / 1e3) + rs ** 3 * FEAT * 2 / 1e9 / (adam_ms / 1e3),
                       "colour_bwd_samples_per_s": samples / (kernels.get("fine_colour_bwd", 1e9) / 1e3),
-                      "clocks": clk}), flush=True)
+                      "clocks": clk, "cpu_baseline": cpu}), flush=True)
 
 
 def run_render(args):
