@@ -157,7 +157,7 @@ class OracleStep:
     on [-1, 1]^3, b for alpha_init 1e-6, step 0.5 voxel)."""
 
     def __init__(self, dens, feat, mlp, shape=None, box=((-1.0,) * 3, (1.0,) * 3), shift_b=None, step=None,
-                 pe_pos=None, batch_rays=NRAYS, params=None, **_):
+                 pe_pos=None, batch_rays=NRAYS, params=None, adam_sample=None, **_):
         import oracle
         self.oracle = oracle
         shape = tuple(dens.shape[:3]) if shape is None else tuple(shape)
@@ -173,7 +173,10 @@ class OracleStep:
         self.mlp64 = {k: np.asarray(v).astype(np.float64) for k, v in mlp.items()}
         n_par = int(np.prod(shape)) * (1 + FEAT) + sum(v.size for v in self.mlp64.values())
         self.n_par = n_par
-        self.adam_arrays = [np.zeros(n_par), np.ones(n_par), np.zeros(n_par), np.zeros(n_par)]
+        # the Adam sweep is timed on adam_sample parameters (all by default) and scaled to n_par
+        # (its cost is linear in the parameter count)
+        self.n_adam = n_par if adam_sample is None else min(int(adam_sample), n_par)
+        self.adam_arrays = [np.zeros(self.n_adam), np.ones(self.n_adam), np.zeros(self.n_adam), np.zeros(self.n_adam)]
         self.batch_rays = batch_rays
         self.freespace = None      # oracle.FreeSpace of the known-free-space test, when the recipe has one
         self.t = 0
@@ -191,12 +194,13 @@ class OracleStep:
         p, g, m, v = self.adam_arrays
         t1 = time.perf_counter()
         self.oracle.adam(p, g, m, v, 0.1, self.t, zero_grad=False)
-        t_adam = time.perf_counter() - t1
+        t_adam = (time.perf_counter() - t1) * self.n_par / self.n_adam
         step_s = t_render * self.batch_rays / n + t_adam
         return {"value": self.batch_rays / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(),
                 "kind": "oracle", "step_s": step_s,
                 "sample": f"{n} of {self.batch_rays} rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam "
-                          f"sweep over all {self.n_par} parameters ({t_adam:.2f} s), projected to a full step"}
+                          f"sweep over {self.n_adam} of the {self.n_par} parameters (projected: {t_adam:.2f} s), "
+                          f"projected to a full step"}
 
 
 def run_reference(args, rank, world):
@@ -204,7 +208,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     dens, feat, mlp, batches = workload()
-    ostep = OracleStep(dens, feat, mlp)
+    # per step: args.ref_rays rays fwd + bwd and an Adam sweep timed on 2 M parameters, both
+    # projected -- ~0.15 s of CPU work, so even a long --steps run ends within minutes
+    ostep = OracleStep(dens, feat, mlp, adam_sample=2_000_000)
     vals = []
     for i in range(args.warmup + args.steps):
         r = ostep.run(batches[i % N_BATCHES], args.ref_rays)
@@ -943,7 +949,7 @@ def main():
     ap.add_argument("--form", choices=["both", "plain", "chosen"], default="both")
     ap.add_argument("--cpu-rays", type=int, default=8192, help="rays of the oracle's CPU baseline sample")
     ap.add_argument("--cpu-reps", type=int, default=3, help="repetitions of the oracle's CPU baseline sample")
-    ap.add_argument("--ref-rays", type=int, default=64)
+    ap.add_argument("--ref-rays", type=int, default=256, help="--impl reference: rays per oracle step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal-eval", action="store_true")
     ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d"], default="step")
