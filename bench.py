@@ -153,7 +153,7 @@ class ClockSampler:
 
 class OracleStep:
     """The FP64 oracle on n rays of a batch (fwd + bwd) plus one oracle Adam sweep over all
-    parameters, projected to a full batch of `batch_rays` rays.  Defaults: the config-2 step (160^3
+    parameters, projected to a full batch of `batch_rays` rays.  Defaults: the 160^3 training step (160^3
     on [-1, 1]^3, b for alpha_init 1e-6, step 0.5 voxel)."""
 
     def __init__(self, dens, feat, mlp, shape=None, box=((-1.0,) * 3, (1.0,) * 3), shift_b=None, step=None,
@@ -492,7 +492,7 @@ def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
 
 
 def run_time_to_psnr(args):
-    """Full per-scene optimisation on the analytic scene (config 3): ground truth for 100 training and
+    """Full per-scene optimisation on the analytic 20-primitive scene: ground truth for 100 training and
     20 held-out 800x800 views, coarse stage (100^3 density + RGB, 5k steps), fine stage (160^3 density
     + 12-channel features + MLP, 20k steps, Adam 0.1 / 1e-3 with the decay of Supp. A, 8192 rays per
     step) for the plain and the chosen form from the same coarse result.  Held-out PSNR is measured
@@ -711,7 +711,7 @@ def run_time_to_psnr(args):
 
 
 def run_stress(args):
-    """Large-grid stress (config 5): 256^3 density (one ball of raw density 200, radius 0.3, at the
+    """Large-grid stress: 256^3 density (one ball of raw density 200, radius 0.3, at the
     origin) + 12-channel BF16 feature grid, BF16 tensor-core MLP, 65,536 rays per batch from the
     radius-4 sphere all aimed into the ball (maximal gradient-scatter contention), uniform 0.5-voxel
     steps, fused backward with recomputation, Adam on all ~218 M parameters."""
@@ -778,7 +778,7 @@ def run_stress(args):
 
 
 def run_render(args):
-    """Test-time rendering (forward only) of full 800x800 frames of the config-2 scene (160^3 density
+    """Test-time rendering (forward only) of full 800x800 frames of the 160^3 eight-ball scene (160^3 density
     of 8 balls, 12-channel features, MLP 39-128-128-3, 0.5-voxel steps) in 65,536-ray chunks, FP32 and
     BF16 MLP, without skipping and with the paper's test-time skipping of samples below
     tau_f = 1e-4 (Sec. 4.2).  The paper's figure for context: 0.64 s per 800x800 frame on an
@@ -819,7 +819,7 @@ def run_render(args):
                      "mean_rgb": float(rgb.mean().item())}
     print(json.dumps({"metric": "test-time render, 800x800 frames", "workload": "render", "unit": "s/frame",
                       "higher_is_better": False, "value": out["bf16_skip"]["s_per_frame"], "frames": args.frames,
-                      "chunk_rays": 65536, "data": "synthetic (config-2 scene: 8 balls of raw density 50, smooth albedo)",
+                      "chunk_rays": 65536, "data": "synthetic (160^3 scene: 8 balls of raw density 50, smooth albedo)",
                       "forms": out, "paper_context": "0.64 s/frame on an RTX 2080 Ti (trained Synthetic-NeRF scenes)"}),
           flush=True)
 

@@ -60,7 +60,7 @@ def _run_coarse(case, p, jitter=None):
 
 
 @pytest.mark.parametrize("b_kind,rgb_act", [("alpha_init", 0), ("zero", 0), ("zero", 1)])
-def test_coarse_parity_config1(b_kind, rgb_act):
+def test_coarse_parity_32cube_4096rays(b_kind, rgb_act):
     case = synth.coarse_case(seed=0)
     b = dvgo.dvgo_shift_from_alpha_init(1e-6, 0.0625) if b_kind == "alpha_init" else 0.0
     p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.03125, shift_b=b, bg=(1.0, 1.0, 1.0), rgb_act=rgb_act)
@@ -236,7 +236,7 @@ def test_fine_explicit_samples_parity():
     assert_close(g_f.cpu().numpy(), ref.grads["cgrid"], RTOL_GRAD, "grad_feat")
 
 
-def test_fine_config2_full_size_sampled_rays():
+def test_fine_160cube_8192rays_sampled():
     """160^3 density (8 spheres of 50) + 12-channel smooth features, 8192 camera rays, the launch
     the benchmark times; colours checked on a seeded sample of rays, gradients on a 192-ray batch
     over the full-size grids."""
