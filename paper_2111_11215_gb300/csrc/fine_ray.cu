@@ -8,6 +8,11 @@
 //                 alpha_k = 1 - exp(-tau_k) < tau_f (Sec. 4.2 free space skipping).
 //                 Writes tau_k to the sample slot and appends kept samples to a compact list
 //                 (one atomic per warp chunk, lane order kept) for the colour kernel.
+//                 Early ray termination, exact: the compositing pass forms T_k = exp(-(sum_{j<k}
+//                 tau_j)) with the same chunked warp scan; a sample where that is exactly 0 in
+//                 FP32 has weight 0 and no gradient through it, so it is not kept, its slot gets
+//                 tau = +inf (alpha 1, every later T and T_K stay exactly 0), and the rest of the
+//                 ray is written the same way without density queries.
 // fine_composite: warp per ray.  T_k = exp(-sum_{j<k} tau_j), w_k = T_k alpha_k,
 //                 C_hat = sum w_k c_k + T_K bg (Eq. volume_rendering), loss (Eq. photo_loss).
 // fine_comp_bwd:  warp per ray.  dC/dc_k = w_k -> stored for the colour backward;
@@ -37,11 +42,16 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
+        float carry = 0.0f;          // optical depth before this chunk, as the compositing pass forms it
         for (int base = 0; base < rr.n; base += 32) {
             int k = base + lane;
             bool valid = k < rr.n;
             float tau = 0.0f;
             bool kept = false;
+            if (isinf(carry)) {      // terminated: T = 0 from here on
+                if (valid) A.samp[rr.off + k] = make_float4(INFINITY, 0.0f, 0.0f, 0.0f);
+                continue;
+            }
             if (valid) {
                 float dt;
                 long long u[3];
@@ -63,8 +73,18 @@ __global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
                     kept = !(-expm1f(-tau) < A.tau_f);
                     if (!kept) tau = 0.0f;
                 }
-                A.samp[rr.off + k] = make_float4(tau, 0.0f, 0.0f, 0.0f);
             }
+            // T_k of the compositing pass; exactly 0 -> terminated (the scan sees tau of lanes below only)
+            const float incl = warp_incl_scan(tau, lane);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 0.0f;
+            if (expf(-(carry + excl)) == 0.0f) {
+                kept = false;
+                tau = INFINITY;
+            }
+            const bool any_dead = __any_sync(FULL, isinf(tau));
+            carry = any_dead ? INFINITY : carry + __shfl_sync(FULL, incl, 31);
+            if (valid) A.samp[rr.off + k] = make_float4(tau, 0.0f, 0.0f, 0.0f);
             unsigned m = __ballot_sync(FULL, kept);
             int cnt = __popc(m);
             int base_slot = 0;
@@ -239,7 +259,7 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
                     gq = act ? dtau * dtau_dv_pre_in(kOrder, c, q, __ldg(A.density + idx), A.shift_b, dt, sv.x) : 0.0f;
                 }
                 float v = seg_sum(gq, sg, lane);
-                if (act && sg.tail) atomicAdd(A.grad_density + idx, v);
+                if (act && sg.tail && v != 0.0f) atomicAdd(A.grad_density + idx, v);   // terminated samples add 0
             }
         }
         __syncwarp();
