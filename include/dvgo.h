@@ -275,7 +275,8 @@ int dvgo_sample_counts(const void *workspace, int n_rays, int *counts_out, int *
 
 /* Lattice points one fine-stage render read (the sizes behind the minimum HBM bytes of a step):
  * bitmaps[0 .. W) marks the density grid's points at the 8 corners of every sample outside the known
- * free space, bitmaps[W .. 2W) the feature grid's points at the 8 corners of every kept sample
+ * free space and not removed by early ray termination, bitmaps[W .. 2W) the feature grid's points
+ * at the 8 corners of every kept sample
  * (W = ceil(nx*ny*nz / 32) uint32 words, bit p of the canonical index p = (i ny + j) nz + k, whatever
  * the storage layout); counts[0], counts[1] = their populations.  Call after dvgo_render_fwd with the
  * same parameters, grid descriptor, ray count, explicit samples and workspace; bitmaps and counts

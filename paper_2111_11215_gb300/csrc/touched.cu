@@ -1,6 +1,7 @@
 // touched.cu -- exact counts of the lattice points one fine-stage render reads: the density grid's
-// points at the corners of every sample outside the known free space, and the feature grid's
-// points at the corners of every kept sample (the sizes behind the minimum HBM bytes of a step).
+// points at the corners of every sample outside the known free space that the density pass did
+// not terminate (a terminated sample's slot holds tau = +inf), and the feature grid's points at
+// the corners of every kept sample (the sizes behind the minimum HBM bytes of a step).
 //
 // Runs after a forward on its workspace: the per-ray records give every sample's fixed-point
 // position (uniform or explicit), the compact list gives the kept samples.  One bit per lattice
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(256) touched_density_kernel(RenderArgs A, uint
         for (int k = lane; k < rr.n; k += 32) {
             long long u[3];
             float dt;
+            if (isinf(A.samp[rr.off + k].x)) break;   // terminated: this and every later sample
             sample_fx(A, rr, ray, k, dt, u);
             if (A.fs_density && known_free(A, u)) continue;
             mark_cell(bm, cell_from_fx(u, A.nx, A.ny, A.nz), A.ny, A.nz);
