@@ -403,3 +403,37 @@ def sample_pdf(probs, t0: float, t1: float, n_samples: int, jit: float = 0.5, et
     lib().oracle_sample_pdf(C.c_int(probs.size), _ptr(probs), C.c_double(t0), C.c_double(t1),
                             C.c_int(n_samples), C.c_double(jit), C.c_double(eta), _ptr(t), _ptr(dt))
     return t, dt
+
+
+def _rig_args(c2w, height, width, fx, fy=None, cx=None, cy=None, near=0.0):
+    c2w = np.ascontiguousarray(_f64(c2w).reshape(-1, 3, 4))
+    fy = fx if fy is None else fy
+    cx = 0.5 * width if cx is None else cx
+    cy = 0.5 * height if cy is None else cy
+    return c2w, (C.c_int(c2w.shape[0]), _ptr(c2w), C.c_int(height), C.c_int(width), C.c_double(fx), C.c_double(fy),
+                 C.c_double(cx), C.c_double(cy), C.c_double(near))
+
+
+def view_counts_points(points, c2w, height: int, width: int, fx: float, fy=None, cx=None, cy=None, near=0.0):
+    """Sec. 4.1 Prior 2: the number of pinhole views (camera-to-world [V, 3, 4], OpenGL axes) whose
+    image rectangle a world point projects into, in front of the camera beyond ``near``."""
+    pts = np.ascontiguousarray(_f64(points).reshape(-1, 3))
+    out = np.zeros(pts.shape[0], dtype=np.uint32)
+    keep, a = _rig_args(c2w, height, width, fx, fy, cx, cy, near)
+    lib().oracle_view_counts_points(C.c_long(pts.shape[0]), _ptr(pts), *a, out.ctypes.data_as(C.POINTER(C.c_uint)))
+    return out
+
+
+def view_counts(shape, c2w, height: int, width: int, fx: float, fy=None, cx=None, cy=None, near=0.0,
+                box=((-1.0,) * 3, (1.0,) * 3)):
+    """Sec. 4.1 Prior 2 on the align-corners lattice of ``shape`` over ``box``: (counts n_j as a
+    uint32 grid, learning-rate scale n_j / n_max, n_max)."""
+    n = np.array([int(s) for s in shape], dtype=np.int32)
+    counts = np.zeros(tuple(n), dtype=np.uint32)
+    scale = np.zeros(tuple(n))
+    keep, a = _rig_args(c2w, height, width, fx, fy, cx, cy, near)
+    f = lib().oracle_view_counts
+    f.restype = C.c_uint
+    n_max = f(n.ctypes.data_as(C.POINTER(C.c_int)), _ptr(_f64(box[0])), _ptr(_f64(box[1])), *a,
+              counts.ctypes.data_as(C.POINTER(C.c_uint)), _ptr(scale))
+    return counts, scale, int(n_max)

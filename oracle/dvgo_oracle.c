@@ -980,3 +980,68 @@ void oracle_sample_pdf(int nb, const double *probs, double t0, double t1, int ns
     if (ns > 0) dt[ns - 1] = w / (ns * q[last_b] / Q[nb]);
     free(q);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Prior 2: view-count-based learning rate (Sec. 4.1)                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Number of training views that see each of n_pts world points x[3 n_pts] (Sec. 4.1 Prior 2: the
+ * view count n_j of grid point j).  View v is the pinhole camera c2w[12 v ...], a row-major 3x4
+ * camera-to-world matrix [R | c] whose columns R_0, R_1, R_2 are the camera's x (right), y (up) and
+ * z (backward) axes in world space (the camera looks along -z), with focal lengths fx, fy and
+ * principal point (cx, cy) in pixels of an image W pixels wide and H high (rows run downward).
+ *
+ * Reading of "visible" (the paper gives no definition): the camera-frame position
+ * q = R^T (x - c) lies in front of the camera beyond the near distance (-q_z > near) and projects
+ * into the closed image rectangle, 0 <= cx + fx q_x / (-q_z) <= W and 0 <= cy - fy q_y / (-q_z) <= H.
+ * Occlusion is not considered (the grid holds no geometry when the counts are taken).  The sums are
+ * taken left to right in the order written.
+ */
+static int og_sees(const double *P, int H, int W, double fx, double fy, double cx, double cy, double near,
+                   const double x[3]) {
+    double d[3], q[3];
+    for (int i = 0; i < 3; ++i) d[i] = x[i] - P[4 * i + 3];
+    for (int k = 0; k < 3; ++k) q[k] = P[k] * d[0] + P[4 + k] * d[1] + P[8 + k] * d[2];
+    double depth = -q[2];
+    if (!(depth > near)) return 0;
+    double u = cx + fx * q[0] / depth;
+    double v = cy - fy * q[1] / depth;
+    return u >= 0.0 && u <= (double)W && v >= 0.0 && v <= (double)H;
+}
+
+void oracle_view_counts_points(long n_pts, const double *x, int V, const double *c2w, int H, int W, double fx,
+                               double fy, double cx, double cy, double near, unsigned *counts) {
+#pragma omp parallel for schedule(static)
+    for (long j = 0; j < n_pts; ++j) {
+        unsigned n = 0;
+        for (int v = 0; v < V; ++v) n += (unsigned)og_sees(c2w + 12 * (long)v, H, W, fx, fy, cx, cy, near, x + 3 * j);
+        counts[j] = n;
+    }
+}
+
+/*
+ * View counts of the points of an align-corners lattice of n[0] x n[1] x n[2] points over the box
+ * [xmin, xmax] (point (i, j, k), canonical index (i n1 + j) n2 + k, sits at
+ * xmin + (i, j, k) (xmax - xmin) / (n - 1)), and the learning-rate scale n_j / n_max of Prior 2
+ * (n_max: the largest count; when no point is seen at all the scale is 1, i.e. no prior).
+ * scale is nullable.  Returns n_max.
+ */
+unsigned oracle_view_counts(const int n[3], const double xmin[3], const double xmax[3], int V, const double *c2w,
+                            int H, int W, double fx, double fy, double cx, double cy, double near,
+                            unsigned *counts, double *scale) {
+    long npts = (long)n[0] * n[1] * n[2];
+    double *x = (double *)malloc(sizeof(double) * 3 * (size_t)(npts > 0 ? npts : 1));
+    for (long p = 0; p < npts; ++p) {
+        long ijk[3] = {p / ((long)n[1] * n[2]), (p / n[2]) % n[1], p % n[2]};
+        for (int a = 0; a < 3; ++a) x[3 * p + a] = xmin[a] + (double)ijk[a] * (xmax[a] - xmin[a]) / (double)(n[a] - 1);
+    }
+    oracle_view_counts_points(npts, x, V, c2w, H, W, fx, fy, cx, cy, near, counts);
+    free(x);
+    unsigned n_max = 0;
+    for (long p = 0; p < npts; ++p)
+        if (counts[p] > n_max) n_max = counts[p];
+    if (scale)
+        for (long p = 0; p < npts; ++p) scale[p] = n_max ? (double)counts[p] / (double)n_max : 1.0;
+    return n_max;
+}
