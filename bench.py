@@ -547,6 +547,37 @@ def run_time_to_psnr(args):
                      shift_b=dvgo.dvgo_shift_from_alpha_init(1e-6, 2.0 / rc), w_pt_rgb=aux_c[0], w_bg=aux_c[1],
                      act_order=ACT_ORDERS[args.act_order])
     coarse = dvgo.CoarseModel(torch.zeros((rc,) * 3, device=dev), torch.zeros((rc,) * 3 + (3,), device=dev), pc, NRAYS)
+    prior2 = None
+    if args.prior2:
+        # Sec. 4.1 Prior 2: the coarse density's learning rate scaled by n_j / n_max (view counts of
+        # the training rig); the setup call is timed once cold and then over repeats (the kernel's
+        # roofline: 27 FP32 flops per (point, view) pair against the FP32 FMA peak)
+        c2w = torch.as_tensor(rig_tr.c2w, dtype=torch.float64).to(dev).contiguous()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n_max = coarse.set_view_counts(c2w, rig_tr.height, rig_tr.width, rig_tr.focal)
+        e1.record()
+        torch.cuda.synchronize()
+        t_first = e0.elapsed_time(e1)
+        for _ in range(3):
+            dvgo.dvgo_view_counts(coarse.dd, c2w, rig_tr.height, rig_tr.width, rig_tr.focal, with_scale=False)
+        reps = 20
+        e0.record()
+        for _ in range(reps):
+            dvgo.dvgo_view_counts(coarse.dd, c2w, rig_tr.height, rig_tr.width, rig_tr.focal, with_scale=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t_ms = e0.elapsed_time(e1) / reps
+        pairs = rc ** 3 * rig_tr.c2w.shape[0]
+        achieved = 27.0 * pairs / (t_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        cnt = coarse.view_counts
+        prior2 = {"n_max": n_max, "min_count": int(cnt.min().item()),
+                  "points_below_half": int((cnt * 2 < n_max).sum().item()), "setup_ms_first_call": round(t_first, 4),
+                  "roofline": {"bound": "alu", "kernel": "view_count_kernel", "ms_per_launch": round(t_ms, 4),
+                               "pairs": pairs, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                               "frac": achieved / peak,
+                               "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz"}}
     it = [0]
 
     def coarse_step():
@@ -698,6 +729,7 @@ def run_time_to_psnr(args):
             "scene, 100 train + 20 held-out 800x800 views, radius 4, focal 1111)",
             "fine_recipe": recipe, "aux_losses": {"coarse": aux_c, "fine": aux_f}, "act_order": args.act_order,
             "fine_density_init": fine_init, "lazy_grid_adam_chosen": args.lazy_adam, "mlp_inputs": in_dim,
+            "prior2_view_count_lr": prior2,
             "cpu_baseline": oracle_proj,
             "progressive": {"pg_ckpt": pg, "grids": [list(g) for _, g, _ in sched],
                                                   "adam": args.pg_adam},
@@ -972,6 +1004,9 @@ def main():
                     help="grid storage layout of the training-step and stress workloads")
     ap.add_argument("--act-order", choices=list(ACT_ORDERS), default="post",
                     help="time-to-psnr: interpolation / activation order of the density in both stages (Sec. 3)")
+    ap.add_argument("--prior2", action="store_true",
+                    help="time-to-psnr: Sec. 4.1 Prior 2, the coarse density's learning rate scaled by n_j / n_max "
+                         "(per-point view counts of the training views)")
     ap.add_argument("--aux-losses", action="store_true",
                     help="time-to-psnr: add the per-point rgb and background entropy losses with the Supp. A weights")
     ap.add_argument("--pe-x", action="store_true",

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 5
+#define DVGO_ABI_VERSION 6
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -261,6 +261,39 @@ int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n,
                    const dvgo_adam_hparams *h, const float *lr_scale, uint16_t *param_bf16_out,
                    int zero_grad, void *stream);
 
+/* Pinhole training views for the view counts below: image size, intrinsics and near distance
+ * shared by all views. */
+typedef struct {
+    int n_views;             /* V >= 0                                                           */
+    int height, width;       /* image size in pixels, each >= 1; rows run downward                */
+    double fx, fy;           /* focal lengths in pixels, > 0                                      */
+    double cx, cy;           /* principal point in pixels (finite)                                */
+    double near;             /* a point must lie further than this (>= 0) along the viewing axis  */
+} dvgo_view_rig;
+
+/*
+ * Sec. 4.1 Prior 2 (view-count-based learning rate): for every point j of the lattice of g
+ * (channels 1, FP32), the number n_j of views that see it, and the scale n_j / n_max of its base
+ * learning rate (n_max = max_j n_j), for lr_scale of dvgo_adam_step on that grid.
+ *   c2w      device, [n_views][3][4] FP64 row-major camera-to-world matrices [R | c]: columns
+ *            R_0, R_1, R_2 are the camera's x (right), y (up) and z (backward) axes in world space,
+ *            c its centre; the camera looks along -z.
+ *   A point x is seen by a view when q = R^T (x - c) has depth -q_z > near and projects into the
+ *   closed image rectangle: 0 <= cx + fx q_x / (-q_z) <= width, 0 <= cy - fy q_y / (-q_z) <= height.
+ *   Occlusion is not considered.  The decision equals that of the FP64 arithmetic written in that
+ *   order, each operation correctly rounded, the lattice point at xyz_min + i (xyz_max - xyz_min) /
+ *   (n - 1) (FP32 box corners taken exactly).
+ *   counts   device uint32 [dvgo_grid_elements(g)], overwritten in g's storage layout (packed
+ *            padding: 0).
+ *   lr_scale device float [dvgo_grid_elements(g)], nullable: counts / n_max correctly rounded, or 1
+ *            everywhere when no point is seen (n_max = 0).
+ *   n_max    device uint32 [1], overwritten with n_max.
+ * Device pointers 4-byte aligned (c2w 8-byte).  Stream-ordered; returns DVGO_ERR_INVALID_ARG on a
+ * bad descriptor, rig or pointer before launching anything.
+ */
+int dvgo_view_counts(const dvgo_grid_desc *g, const dvgo_view_rig *rig, const double *c2w, uint32_t *counts,
+                     float *lr_scale, uint32_t *n_max, void *stream);
+
 /* Learning rate of Supp. A at 0-based step t: lr0 * 0.1^(t / decay_steps). */
 float dvgo_lr_at(float lr0, int step, float decay_steps);
 
@@ -390,7 +423,7 @@ enum {
     DVGO_K_FINE_DENSITY = 4, DVGO_K_FINE_COLOUR_FWD = 5, DVGO_K_FINE_COMPOSITE = 6,
     DVGO_K_FINE_COMP_BWD = 7, DVGO_K_FINE_COLOUR_BWD = 8, DVGO_K_ADAM = 9, DVGO_K_AUX = 10,
     DVGO_K_WEIGHT_BINS = 11, DVGO_K_PROPOSAL_FWD = 12, DVGO_K_PROPOSAL_BWD = 13, DVGO_K_SAMPLE_PDF = 14,
-    DVGO_K_COUNT = 15
+    DVGO_K_VIEW_COUNTS = 15, DVGO_K_COUNT = 16
 };
 
 /* Benchmarking aid.  While enabled (on != 0), every kernel launch of this library is bracketed

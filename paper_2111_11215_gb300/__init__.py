@@ -14,7 +14,7 @@ from .binding import (  # noqa: F401
     dvgo_profile_read, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
     dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS, FreeSpace, dvgo_unknown_bbox, DVGO_ACT_POST, DVGO_ACT_PRE,
     DVGO_ACT_IN, DVGO_LAYOUT_CANONICAL, DVGO_LAYOUT_PACKED, dvgo_grid_elements, dvgo_pack_grid, dvgo_resize_grid,
-    dvgo_fit2d, dvgo_touched_points,
+    dvgo_fit2d, dvgo_touched_points, dvgo_view_counts,
 )
 from .render import (  # noqa: F401
     AdamState, CoarseModel, FineModel, FrameRenderer, Proposal, ProposalTrainer, Renderer, RenderFunction,

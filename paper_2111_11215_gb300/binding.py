@@ -23,7 +23,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
     "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid", "dvgo_fit2d",
-    "dvgo_touched_points",
+    "dvgo_touched_points", "dvgo_view_counts",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
@@ -31,7 +31,7 @@ DVGO_LAYOUT_CANONICAL, DVGO_LAYOUT_PACKED = 0, 1     # grid storage layouts
 
 KERNEL_KINDS = ("ray_setup", "scan", "coarse_fwd", "coarse_bwd", "fine_density", "fine_colour_fwd",
                 "fine_composite", "fine_comp_bwd", "fine_colour_bwd", "adam", "aux", "weight_bins", "proposal_fwd",
-                "proposal_bwd", "sample_pdf")
+                "proposal_bwd", "sample_pdf", "view_counts")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -76,6 +76,11 @@ class _Mlp(C.Structure):
 
 class _Samples(C.Structure):
     _fields_ = [("t", C.c_void_p), ("dt", C.c_void_p), ("n_per_ray", C.c_int)]
+
+
+class _ViewRig(C.Structure):
+    _fields_ = [("n_views", C.c_int), ("height", C.c_int), ("width", C.c_int), ("fx", C.c_double),
+                ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double), ("near", C.c_double)]
 
 
 class _AdamH(C.Structure):
@@ -127,6 +132,8 @@ def lib():
         L.dvgo_fit2d.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_touched_points.restype = i
         L.dvgo_touched_points.argtypes = [vp, vp, i, vp, vp, sz, vp, vp, vp]
+        L.dvgo_view_counts.restype = i
+        L.dvgo_view_counts.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_render_fwd_noalloc.restype = i
         L.dvgo_render_fwd_noalloc.argtypes = [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dvgo_profile_enable.restype = i
@@ -315,6 +322,31 @@ def dvgo_touched_points(params: Params, density_desc: GridDesc, n_rays: int, sam
                                      C.c_void_p(bm.data_ptr()), C.c_void_p(counts.data_ptr()), _stream(stream)),
            "dvgo_touched_points")
     return bm, counts
+
+
+def dvgo_view_counts(desc: GridDesc, c2w, height: int, width: int, fx: float, fy=None, cx=None, cy=None,
+                     near: float = 0.0, with_scale: bool = True, stream=None):
+    """Sec. 4.1 Prior 2 on the lattice of `desc`: per point the number of views (camera-to-world CUDA
+    float64 [V, 3, 4], OpenGL axes) that see it, and the learning-rate scale n_j / n_max.  Returns
+    (counts int32 view of the uint32 grid in desc's storage layout, scale float32 or None, n_max
+    int32 [1]), all on the device; fy defaults to fx, (cx, cy) to the image centre."""
+    c2w = c2w.reshape(-1, 3, 4)
+    r = _ViewRig()
+    r.n_views, r.height, r.width = int(c2w.shape[0]), int(height), int(width)
+    r.fx = float(fx)
+    r.fy = float(fx if fy is None else fy)
+    r.cx = float(0.5 * width if cx is None else cx)
+    r.cy = float(0.5 * height if cy is None else cy)
+    r.near = float(near)
+    g = desc.c()
+    n = int(dvgo_grid_elements(desc))
+    counts = torch.empty(n, dtype=torch.int32, device=c2w.device)
+    scale = torch.empty(n, dtype=torch.float32, device=c2w.device) if with_scale else None
+    n_max = torch.empty(1, dtype=torch.int32, device=c2w.device)
+    _check(lib().dvgo_view_counts(C.byref(g), C.byref(r), _dev(c2w, "c2w", torch.float64),
+                                  C.c_void_p(counts.data_ptr()), _dev(scale, "lr_scale", torch.float32, True),
+                                  C.c_void_p(n_max.data_ptr()), _stream(stream)), "dvgo_view_counts")
+    return counts, scale, n_max
 
 
 def dvgo_workspace_size(params: Params, density_desc: GridDesc, n_rays: int, samples=None) -> int:

@@ -373,6 +373,22 @@ int dvgo_touched_points(const dvgo_params *p, const dvgo_grid_desc *dd, int R, c
     return launch_status();
 }
 
+int dvgo_view_counts(const dvgo_grid_desc *g, const dvgo_view_rig *rig, const double *c2w, uint32_t *counts,
+                     float *lr_scale, uint32_t *n_max, void *stream) {
+    if (!g || !rig || !counts || !n_max || !grid_ok(g) || g->channels != 1 || g->dtype != DVGO_DTYPE_F32)
+        return DVGO_ERR_INVALID_ARG;
+    if (rig->n_views < 0 || rig->n_views > (1 << 24) || rig->height < 1 || rig->width < 1) return DVGO_ERR_INVALID_ARG;
+    if (!(isfinite(rig->fx) && rig->fx > 0.0) || !(isfinite(rig->fy) && rig->fy > 0.0) || !isfinite(rig->cx) ||
+        !isfinite(rig->cy) || !(isfinite(rig->near) && rig->near >= 0.0))
+        return DVGO_ERR_INVALID_ARG;
+    if (rig->n_views > 0 && (!c2w || reinterpret_cast<uintptr_t>(c2w) % 8)) return DVGO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(counts) % 4 || reinterpret_cast<uintptr_t>(lr_scale) % 4 ||
+        reinterpret_cast<uintptr_t>(n_max) % 4)
+        return DVGO_ERR_INVALID_ARG;
+    launch_view_counts(*g, *rig, c2w, counts, lr_scale, n_max, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
 int dvgo_workspace_status(void *ws, void *stream) {
     if (!ws) return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

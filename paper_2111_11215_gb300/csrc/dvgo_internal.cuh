@@ -418,6 +418,8 @@ void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const 
                  const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s);
 
 void launch_touched(const RenderArgs &A, uint32_t *bitmaps, unsigned long long *counts, cudaStream_t s);
+void launch_view_counts(const dvgo_grid_desc &g, const dvgo_view_rig &rig, const double *c2w, uint32_t *counts,
+                        float *lr_scale, uint32_t *n_max, cudaStream_t s);
 
 int num_sms();
 void ensure_smem(const void *kernel, int bytes);

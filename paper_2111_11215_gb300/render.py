@@ -339,6 +339,15 @@ class CoarseModel:
         self.loss = torch.zeros(1, device=dev)
         self.dloss = torch.empty((n_rays, 3), device=dev)
         self.step_count = 0
+        self.lr_scale = None        # Prior 2: per-point density learning-rate scale n_j / n_max
+
+    def set_view_counts(self, c2w: torch.Tensor, height: int, width: int, fx: float, fy=None, cx=None, cy=None,
+                        near: float = 0.0, stream=None) -> int:
+        """Sec. 4.1 Prior 2: scale each density point's learning rate by n_j / n_max, n_j the number
+        of training views (camera-to-world CUDA float64 [V, 3, 4]) that see it.  Returns n_max."""
+        counts, scale, n_max = B.dvgo_view_counts(self.dd, c2w, height, width, fx, fy, cx, cy, near, stream=stream)
+        self.view_counts, self.lr_scale = counts.view(self.density.shape), scale.view(self.density.shape)
+        return int(n_max.item())
 
     def forward(self, rays_o, rays_d, jitter=None, stream=None):
         return self.renderer.forward(self.density, self.rgb_grid, None, rays_o, rays_d, jitter, None, None,
@@ -353,7 +362,7 @@ class CoarseModel:
         t = self.step_count
         lr = B.dvgo_lr_at(self.lr_grid, t - 1, self.decay_steps)
         B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr, t,
-                         stream=stream)
+                         lr_scale=self.lr_scale, stream=stream)
         B.dvgo_adam_step(self.rgb_grid, self.g_rgb, self.adam["rgb"].m, self.adam["rgb"].v, lr, t, stream=stream)
         return self.loss
 
