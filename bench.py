@@ -934,6 +934,78 @@ def run_toy2d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_view_counts(args):
+    """Prior 2 of Sec. 4.1 on its own: the view counts n_j and the scale n_j / n_max of a lattice of
+    vc_res^3 points over [-1, 1]^3 under vc_views inward 800x800 views (radius 4, focal 1111; the
+    default 100^3 x 100 is the coarse stage of the per-scene optimisation).  The kernel is timed with
+    CUDA events over repeated launches; the roofline counts 27 FP32 flops per (point, view) pair (the
+    projection of the definition: 3 sub, 9 mul + 6 add, 4 image bounds as mul + add, 1 sub) against
+    the FP32 FMA peak.  The FP64 oracle runs the same problem on the host cores (cpu_baseline) and
+    its counts are compared with the GPU's."""
+    import torch
+    import synth
+    import paper_2111_11215_gb300 as dvgo
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    res, nv = args.vc_res, args.vc_views
+    rig = synth.hemisphere_rig(nv, seed=2024)
+    c2w = torch.as_tensor(rig.c2w, dtype=torch.float64).to(dev).contiguous()
+    desc = dvgo.GridDesc((res,) * 3, 1)
+
+    def call():
+        return dvgo.dvgo_view_counts(desc, c2w, rig.height, rig.width, rig.focal)
+    for _ in range(max(args.warmup, 3)):
+        counts, scale, n_max = call()
+    torch.cuda.synchronize()
+    reps = args.vc_reps
+    launches0 = dvgo.dvgo_launch_counter()
+    clk = ClockSampler(0)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        counts, scale, n_max = call()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = dvgo.dvgo_launch_counter() - launches0
+    t_ms = e0.elapsed_time(e1) / reps
+    # the count kernel alone (no scale pass), for the roofline
+    e0.record()
+    for _ in range(reps):
+        dvgo.dvgo_view_counts(desc, c2w, rig.height, rig.width, rig.focal, with_scale=False)
+    e1.record()
+    torch.cuda.synchronize()
+    k_ms = e0.elapsed_time(e1) / reps
+    pairs = res ** 3 * nv
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    line = {"metric": "Prior 2 view counts: (point, view) visibility decisions per second", "workload": "view-counts",
+            "value": pairs / (t_ms * 1e-3), "unit": "pairs/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": reps, "warmup": max(args.warmup, 3), "ms_per_call": round(t_ms, 5), "dtype": "f32 (+f64 at ties)",
+            "data": "synthetic (seeded hemisphere rig)",
+            "config": {"workload": f"view counts + lr scale, {res}^3 lattice over [-1,1]^3, {nv} inward 800x800 views "
+                                   "(radius 4, focal 1111)", "output_bytes": int(8 * res ** 3),
+                       "l2": "output 8 B/point; repeated calls on the same buffers (the camera data stays in L2)"},
+            "n_max": int(n_max.item()), "gpu_launches": int(launches), "clocks": clocks}
+    achieved = 27.0 * pairs / (k_ms * 1e-3) / 1e12
+    line["roofline"] = {"bound": "alu", "kernel": "view_count_kernel", "ms_per_launch": round(k_ms, 5),
+                        "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "algorithmic_flops_per_pair": 27, "pairs_per_call": pairs,
+                        "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz"}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref_c, _, ref_max = oracle.view_counts((res,) * 3, rig.c2w, rig.height, rig.width, rig.focal)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"the whole problem ({pairs} pairs), FP64"}
+        line["matches_oracle"] = bool(np.array_equal(counts.cpu().numpy().reshape((res,) * 3), ref_c.astype(np.int32))
+                                      and ref_max == int(n_max.item()))
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2111_11215_gb300 as dvgo
@@ -984,7 +1056,11 @@ def main():
     ap.add_argument("--ref-rays", type=int, default=256, help="--impl reference: rays per oracle step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal-eval", action="store_true")
-    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d"], default="step")
+    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d", "view-counts"],
+                    default="step")
+    ap.add_argument("--vc-res", type=int, default=100, help="view-counts: lattice points per axis")
+    ap.add_argument("--vc-views", type=int, default=100, help="view-counts: number of views")
+    ap.add_argument("--vc-reps", type=int, default=2000, help="view-counts: timed calls")
     ap.add_argument("--toy-res", type=int, default=512, help="toy2d: image side in pixels")
     ap.add_argument("--toy-steps", type=int, default=2000, help="toy2d: Adam steps per fit")
     ap.add_argument("--toy-strides", default="2,3,4,5,6,8,10,12,16", help="toy2d: grid strides")
@@ -1063,6 +1139,10 @@ def main():
     if args.workload == "toy2d":
         if rank == 0:
             run_toy2d(args)
+        return
+    if args.workload == "view-counts":
+        if rank == 0:
+            run_view_counts(args)
         return
     run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -6,19 +6,28 @@
 // not considered).  That is an integer decision per (point, view) pair, taken exactly as the FP64
 // definition takes it:
 //
-//   * fast test, FP32: with depth = -q_z > 0 the image conditions are the signs of four linear forms
-//     (fx q_x + cx depth, (W - cx) depth - fx q_x, cy depth - fy q_y, fy q_y + (H - cy) depth) and
-//     of depth - near.  Each is a short sum whose FP32 rounding error is below 20 u M (u = 2^-24,
-//     M the sum of the magnitudes of its terms over the whole box, bounded per view); a value
-//     further than the guard 2^-16 M from zero has the sign of the exact value, and so the FP64
-//     decision;
-//   * the rare pair inside a guard band is decided again in FP64 with the definition's operations
-//     in the definition's order, each correctly rounded (no contraction), which reproduces the
-//     FP64 decision bit for bit.
+//   * with depth = -q_z > 0 the decision is the sign test of five forms, each affine in the point:
+//     F1 = fx q_x + cx depth (u >= 0), F2 = (W - cx) depth - fx q_x (u <= W),
+//     F3 = cy depth - fy q_y (v >= 0), F4 = fy q_y + (H - cy) depth (v <= H), F5 = depth - near;
+//     the point is seen iff all five are >= 0 (F5 > 0).  On the lattice, x = min + (i, j, k) step,
+//     so each form is b + i w_i + j w_j + k w_k with per-view coefficients;
+//   * fast test, FP32: every coefficient, the evaluation and the step along k round with an error
+//     below 40 u M (u = 2^-24, M the sum over the box of the magnitudes of the form's terms,
+//     bounded per view).  A value further than the guard G = 2^-15 3 M from zero has the sign of the
+//     exact form, and so gives the FP64 decision.  Each form is scaled by the power of two that
+//     brings its guard into (1/2, 1] (exact), so one minimum over the five decides: > 1 seen,
+//     < -1 not seen;
+//   * the rare pair in between is decided again in FP64 with the definition's operations in the
+//     definition's order, each correctly rounded (no contraction), which reproduces the FP64
+//     decision bit for bit.
 //
-// Layout: one thread per lattice point (4 points per thread, strided by the block size so that the
-// writes coalesce), the views' FP32 constants in shared memory (read as broadcasts), built by each
-// block from the FP64 camera matrices.  ALU-bound: ~30 FP32 flops per pair, 4 output bytes per point.
+// Layout: a thread takes 8 consecutive points along k of one lattice row (the forms step by w_k),
+// the views' scaled coefficients sit in shared memory (read as broadcasts), built by each block from
+// the FP64 camera matrices.  Guard-band pairs are queued in shared memory and decided after the
+// block's pass over the views, 32 to a warp: this GPU's FP64 pipe issues a warp instruction at the
+// same cost whether one lane or all are active, so deciding them where they arise (one lane of a
+// warp at a time) made the few blocks that meet many of them several times slower than the rest.
+// ALU-bound: ~14 instructions per (point, view) pair, 4 output bytes per point.
 
 #include "dvgo_internal.cuh"
 
@@ -27,14 +36,15 @@ namespace dvgo {
 namespace {
 
 constexpr int kVcThreads = 256;
-constexpr int kVcPts = 4;           // lattice points per thread
-constexpr int kVcChunk = 512;       // views held in shared memory at a time (32 KB)
-constexpr float kVcGuard = 1.52587890625e-05f;   // 2^-16
+constexpr int kVcK = 8;             // consecutive lattice points along k per thread
+constexpr int kVcChunk = 384;       // views held in shared memory at a time (30 KB)
+constexpr int kVcQueue = 1024;      // guard-band pairs a block defers to its FP64 pass per tile
+constexpr float kVcGuard = 3.0517578125e-05f;    // 2^-15
 
 struct VcArgs {
     int nx, ny, nz;
     bool packed;
-    float fmin[3], fstep[3];        // FP32 lattice: fmin + i fstep
+    float fmin[3], fstep[3];        // FP32 lattice: fmin + i fstep (box corners exact, step rounded)
     double dmin[3], dmax[3];        // the box corners (FP64 lattice of the definition)
     float bmax[3];                  // max(|min|, |max|) per axis
     int V, H, W;
@@ -68,9 +78,8 @@ __device__ __noinline__ unsigned sees_fp64(const VcArgs &A, int v, int i, int j,
     return (u >= 0.0 && u <= (double)A.W && w >= 0.0 && w <= (double)A.H) ? 1u : 0u;
 }
 
-// FP32 constants of views [v0, v0 + nv) into shared memory, 4 float4 per view:
-//   s[0] = (c, guard of the x forms), s[1] = (fx R_:,0, guard of the y forms),
-//   s[2] = (fy R_:,1, guard of the depth form), s[3] = (R_:,2, 0).
+// Scaled FP32 coefficients of views [v0, v0 + nv) into shared memory: 5 float4 (b, w_i, w_j, w_k)
+// per view, one per form F1..F5, each multiplied by the power of two that puts its guard in (1/2, 1].
 __device__ void load_views(const VcArgs &A, float4 *s, int v0, int nv) {
     for (int t = threadIdx.x; t < nv; t += blockDim.x) {
         const double *P = A.c2w + 12 * (long long)(v0 + t);
@@ -83,49 +92,80 @@ __device__ void load_views(const VcArgs &A, float4 *s, int v0, int nv) {
             amp[a] = A.bmax[a] + fabsf(c[a]);     // bounds |x_a - c_a| over the box
         }
         const float fx = (float)A.fx, fy = (float)A.fy;
-        float mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            mx += fx * fabsf(R[a][0]) * amp[a];
-            my += fy * fabsf(R[a][1]) * amp[a];
-            mz += fabsf(R[a][2]) * amp[a];
+        for (int m = 0; m < 5; ++m) {
+            float al[3], mag = m == 4 ? A.f_near : 0.0f;
+            float bsum = m == 4 ? -A.f_near : 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float t0, t1;             // the two terms of the form's coefficient on axis a
+                switch (m) {
+                    case 0: t0 = fx * R[a][0]; t1 = -A.f_cx * R[a][2]; break;
+                    case 1: t0 = -fx * R[a][0]; t1 = -A.f_wcx * R[a][2]; break;
+                    case 2: t0 = -fy * R[a][1]; t1 = -A.f_cy * R[a][2]; break;
+                    case 3: t0 = fy * R[a][1]; t1 = -A.f_hcy * R[a][2]; break;
+                    default: t0 = 0.0f; t1 = -R[a][2]; break;
+                }
+                al[a] = t0 + t1;
+                mag += (fabsf(t0) + fabsf(t1)) * amp[a];
+                bsum = fmaf(al[a], A.fmin[a] - c[a], bsum);
+            }
+            int e;
+            frexpf(kVcGuard * 3.0f * mag, &e);
+            const float sc = ldexpf(1.0f, -e);
+            s[5 * t + m] = make_float4(bsum * sc, al[0] * A.fstep[0] * sc, al[1] * A.fstep[1] * sc,
+                                       al[2] * A.fstep[2] * sc);
         }
-        const float gx = kVcGuard * (mx + fmaxf(fabsf(A.f_cx), fabsf(A.f_wcx)) * mz);
-        const float gy = kVcGuard * (my + fmaxf(fabsf(A.f_cy), fabsf(A.f_hcy)) * mz);
-        const float ga = kVcGuard * (mz + A.f_near);
-        s[4 * t + 0] = make_float4(c[0], c[1], c[2], gx);
-        s[4 * t + 1] = make_float4(fx * R[0][0], fx * R[1][0], fx * R[2][0], gy);
-        s[4 * t + 2] = make_float4(fy * R[0][1], fy * R[1][1], fy * R[2][1], ga);
-        s[4 * t + 3] = make_float4(R[0][2], R[1][2], R[2][2], 0.0f);
     }
 }
 
-__global__ void __launch_bounds__(kVcThreads) view_count_kernel(const __grid_constant__ VcArgs A) {
-    __shared__ float4 sv[kVcChunk * 4];
-    const long long npts = (long long)A.nx * A.ny * A.nz;
-    const long long tile = (long long)kVcThreads * kVcPts;
+// Point (i, j, k0) of work item it: rows of the lattice in canonical order, kb items of kVcK points
+// per row.
+__device__ __forceinline__ void vc_item(const VcArgs &A, long long it, int kb, long long &row, int &i, int &j,
+                                        int &k0) {
+    row = it / kb;
+    k0 = (int)(it - row * kb) * kVcK;
+    i = (int)(row / A.ny);
+    j = (int)(row - (long long)i * A.ny);
+}
+
+// The smallest of the five scaled forms at point k0 + r of a thread's run.
+__device__ __forceinline__ float vc_min_form(const float (&f0)[5], const float (&wk)[5], float r) {
+    return fminf(fminf(fminf(fmaf(r, wk[0], f0[0]), fmaf(r, wk[1], f0[1])),
+                       fminf(fmaf(r, wk[2], f0[2]), fmaf(r, wk[3], f0[3]))),
+                 fmaf(r, wk[4], f0[4]));
+}
+
+__global__ void __launch_bounds__(kVcThreads, 4) view_count_kernel(const __grid_constant__ VcArgs A) {
+    __shared__ float4 sv[kVcChunk * 5];
+    // pairs inside a guard band: the FP64 test runs once per tile with every lane of a warp busy
+    // (the FP64 pipe is narrow, so a lone lane costs a whole warp's issue slots)
+    __shared__ uint32_t q_view[kVcQueue];
+    __shared__ uint16_t q_point[kVcQueue];          // threadIdx.x * kVcK + r
+    __shared__ uint32_t q_extra[kVcThreads * kVcK];  // FP64 verdicts per point of the tile
+    __shared__ unsigned q_n;
+    const int kb = (A.nz + kVcK - 1) / kVcK;
+    const long long items = (long long)A.nx * A.ny * kb;
     const bool resident = A.V <= kVcChunk;
-    if (resident) {
-        load_views(A, sv, 0, A.V);
-        __syncthreads();
-    }
+    if (resident) load_views(A, sv, 0, A.V);
+    const bool vec_store = !A.packed && (A.nz % 4) == 0 && (reinterpret_cast<uintptr_t>(A.counts) & 15u) == 0;
     unsigned local_max = 0;
-    for (long long base = (long long)blockIdx.x * tile; base < npts; base += (long long)gridDim.x * tile) {
-        float px[kVcPts], py[kVcPts], pz[kVcPts];
-        int li[kVcPts], lj[kVcPts], lk[kVcPts];
-        unsigned cnt[kVcPts];
+    // block-granular stride, so every thread of a block runs the same iterations (uniform barriers)
+    for (long long base = (long long)blockIdx.x * kVcThreads; base < items; base += (long long)gridDim.x * kVcThreads) {
+        const long long it = base + threadIdx.x;
+        const bool live = it < items;
+        long long row;
+        int i, j, k0;
+        vc_item(A, live ? it : items - 1, kb, row, i, j, k0);
+        const float fi = (float)i, fj = (float)j, fk = (float)k0;
+        unsigned cnt[kVcK];
 #pragma unroll
-        for (int r = 0; r < kVcPts; ++r) {
-            const long long p = base + r * kVcThreads + threadIdx.x;
-            const long long pc = p < npts ? p : npts - 1;
-            lk[r] = (int)(pc % A.nz);
-            lj[r] = (int)((pc / A.nz) % A.ny);
-            li[r] = (int)(pc / ((long long)A.ny * A.nz));
-            px[r] = fmaf((float)li[r], A.fstep[0], A.fmin[0]);
-            py[r] = fmaf((float)lj[r], A.fstep[1], A.fmin[1]);
-            pz[r] = fmaf((float)lk[r], A.fstep[2], A.fmin[2]);
+        for (int r = 0; r < kVcK; ++r) {
             cnt[r] = 0u;
+            q_extra[threadIdx.x * kVcK + r] = 0u;
         }
+        if (threadIdx.x == 0) q_n = 0u;
+        __syncthreads();
         for (int v0 = 0; v0 < A.V; v0 += kVcChunk) {
             const int nv = min(kVcChunk, A.V - v0);
             if (!resident) {
@@ -134,33 +174,61 @@ __global__ void __launch_bounds__(kVcThreads) view_count_kernel(const __grid_con
                 __syncthreads();
             }
             for (int t = 0; t < nv; ++t) {
-                const float4 s0 = sv[4 * t], s1 = sv[4 * t + 1], s2 = sv[4 * t + 2], s3 = sv[4 * t + 3];
+                float f0[5], wk[5];
 #pragma unroll
-                for (int r = 0; r < kVcPts; ++r) {
-                    const float dx = px[r] - s0.x, dy = py[r] - s0.y, dz = pz[r] - s0.z;
-                    const float qx = fmaf(s1.z, dz, fmaf(s1.y, dy, s1.x * dx));      // fx q_x
-                    const float qy = fmaf(s2.z, dz, fmaf(s2.y, dy, s2.x * dx));      // fy q_y
-                    const float dep = -fmaf(s3.z, dz, fmaf(s3.y, dy, s3.x * dx));    // -q_z
-                    const float mx = fminf(fmaf(A.f_cx, dep, qx), fmaf(A.f_wcx, dep, -qx));
-                    const float my = fminf(fmaf(A.f_cy, dep, -qy), fmaf(A.f_hcy, dep, qy));
-                    const float a = dep - A.f_near;
-                    const bool in = (mx > s0.w) & (my > s1.w) & (a > s2.w);
-                    const bool out = (mx < -s0.w) | (my < -s1.w) | (a < -s2.w);
-                    if (in) {
-                        ++cnt[r];
-                    } else if (!out && base + r * kVcThreads + threadIdx.x < npts) {
-                        cnt[r] += sees_fp64(A, v0 + t, li[r], lj[r], lk[r]);
+                for (int m = 0; m < 5; ++m) {
+                    const float4 q = sv[5 * t + m];
+                    f0[m] = fmaf(fk, q.w, fmaf(fj, q.z, fmaf(fi, q.y, q.x)));
+                    wk[m] = q.w;
+                }
+                float amin = INFINITY;    // the smallest |min form| of this view's points
+#pragma unroll
+                for (int r = 0; r < kVcK; ++r) {
+                    const float mn = vc_min_form(f0, wk, (float)r);
+                    cnt[r] += mn > 1.0f ? 1u : 0u;
+                    amin = fminf(amin, fabsf(mn));
+                }
+                if (amin <= 1.0f && live) {   // rare: queue for the FP64 pass (decide now if the queue is full)
+#pragma unroll
+                    for (int r = 0; r < kVcK; ++r) {
+                        if (fabsf(vc_min_form(f0, wk, (float)r)) <= 1.0f && k0 + r < A.nz) {
+                            const unsigned slot = atomicAdd(&q_n, 1u);
+                            if (slot < (unsigned)kVcQueue) {
+                                q_view[slot] = (uint32_t)(v0 + t);
+                                q_point[slot] = (uint16_t)(threadIdx.x * kVcK + r);
+                            } else {
+                                cnt[r] += sees_fp64(A, v0 + t, i, j, k0 + r);
+                            }
+                        }
                     }
                 }
             }
         }
+        __syncthreads();
+        const unsigned nq = min(q_n, (unsigned)kVcQueue);
+        for (unsigned e = threadIdx.x; e < nq; e += kVcThreads) {
+            const unsigned lp = q_point[e];
+            long long orow;
+            int oi, oj, ok0;
+            vc_item(A, base + lp / kVcK, kb, orow, oi, oj, ok0);
+            if (sees_fp64(A, (int)q_view[e], oi, oj, ok0 + (int)(lp % kVcK))) atomicAdd(&q_extra[lp], 1u);
+        }
+        __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kVcPts; ++r) {
-            const long long p = base + r * kVcThreads + threadIdx.x;
-            if (p < npts) {
-                A.counts[grid_index(li[r], lj[r], lk[r], A.ny, A.nz, A.packed)] = cnt[r];
-                local_max = max(local_max, cnt[r]);
+        for (int r = 0; r < kVcK; ++r) cnt[r] += q_extra[threadIdx.x * kVcK + r];
+        if (live) {
+            if (vec_store && k0 + kVcK <= A.nz) {
+                uint4 *dst = reinterpret_cast<uint4 *>(A.counts + row * A.nz + k0);
+                dst[0] = make_uint4(cnt[0], cnt[1], cnt[2], cnt[3]);
+                dst[1] = make_uint4(cnt[4], cnt[5], cnt[6], cnt[7]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < kVcK; ++r)
+                    if (k0 + r < A.nz) A.counts[grid_index(i, j, k0 + r, A.ny, A.nz, A.packed)] = cnt[r];
             }
+#pragma unroll
+            for (int r = 0; r < kVcK; ++r)
+                if (k0 + r < A.nz) local_max = max(local_max, cnt[r]);
         }
     }
 #pragma unroll
@@ -212,10 +280,12 @@ void launch_view_counts(const dvgo_grid_desc &g, const dvgo_view_rig &rig, const
     const long long elems = A.packed ? (long long)dvgo_grid_elements(&g) : npts;
     cudaMemsetAsync(n_max, 0, sizeof(uint32_t), s);
     if (A.packed) cudaMemsetAsync(counts, 0, (size_t)elems * sizeof(uint32_t), s);
-    const long long tiles = (npts + kVcThreads * kVcPts - 1) / (kVcThreads * kVcPts);
+    const long long items = (long long)g.nx * g.ny * ((g.nz + kVcK - 1) / kVcK);
     {
         ProfScope ps_(DVGO_K_VIEW_COUNTS, s);
-        view_count_kernel<<<(unsigned)std::min<long long>(tiles, (long long)num_sms() * 64), kVcThreads, 0, s>>>(A);
+        view_count_kernel<<<(unsigned)std::min<long long>((items + kVcThreads - 1) / kVcThreads,
+                                                          (long long)num_sms() * 64),
+                            kVcThreads, 0, s>>>(A);
     }
     if (lr_scale) {
         ProfScope ps_(DVGO_K_VIEW_COUNTS, s);
