@@ -19,6 +19,7 @@
  *   - volume-rendering quadrature and photometric MSE      (Sec. 2 Eq. volume_rendering, Eq. photo_loss)
  *   - hand-derived reverse-mode gradient of all the above  (chain rule of the same equations)
  *   - Adam with exponential learning-rate decay            (Sec. 5.2 / Supp. A; Kingma & Ba)
+ *   - view counts of grid points and the learning-rate scale of Prior 2   (Sec. 4.1 Prior 2)
  *   - the learned sample proposal (64-bin PDF, 48 inverse-CDF samples).  The paper leaves
  *     hierarchical sampling to future work (Supp. B, step-size ablation); the proposal is this
  *     library's addition and is defined here by the readings listed in the design notes.
@@ -36,7 +37,9 @@
  *     world-space query point x;
  *   * progressive scaling resizes a grid onto the align-corners lattice of the new dimensions over
  *     the same box, each new lattice point taking interp(x, V_old) at its position;
- *   * the loss is (1/R) sum_r sum_ch (C_hat - C)^2.
+ *   * the loss is (1/R) sum_r sum_ch (C_hat - C)^2;
+ *   * a grid point is visible to a view when it lies in front of the camera beyond the near
+ *     distance and projects into the closed image rectangle (no occlusion test).
  *
  * The integer decisions (how many samples a ray gets) are taken in FP64 with the operation order
  * written in oracle_ray_bounds(); the file is compiled with -ffp-contract=off so that no fused
