@@ -339,6 +339,7 @@ class CoarseModel:
         self.loss = torch.zeros(1, device=dev)
         self.dloss = torch.empty((n_rays, 3), device=dev)
         self.step_count = 0
+        self.view_counts = None     # Prior 2: per-point view counts n_j (int32 view of the uint32 grid)
         self.lr_scale = None        # Prior 2: per-point density learning-rate scale n_j / n_max
 
     def set_view_counts(self, c2w: torch.Tensor, height: int, width: int, fx: float, fy=None, cx=None, cy=None,
