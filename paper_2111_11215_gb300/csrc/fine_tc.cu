@@ -27,12 +27,13 @@
 // Backward per tile (recomputes the forward), with dL/dc from the compositing backward:
 //   dout = dL/dc c (1 - c)                                        (epilogue, BF16 panel)
 //   dH2 = dout W3^T;  dZ2 = dH2 [Z2 + b2 > 0]                      (MMA, epilogue)
-//   dH1 = dZ2 W2^T;  dW2 += H1^T dZ2;  dW3 += H2^T dout;  db2 += dZ2^T 1     (MMAs)
+//   dH1 = dZ2 W2^T;  [dW2^T | db2] += dZ2^T [H1 | dout];  dW3 += H2^T dout   (MMAs; dout's
+//   column 3 is 1, so one N = 144 MMA gives dW2^T and db2)
 //   dZ1 = dH1 [Z1 > 0]                                             (epilogue)
 //   de = dZ1 W1[0:16]^T;  [dW1 | db1]^T += dZ1^T X                 (MMAs)
 //   de[0:12] -> shared memory -> scattered to the feature grid by the producers
-// TMEM columns: Z1 / O / dH2 [0,128), Z2 / dH1 [128,256), dW2 [256,384), dW1^T [384,448),
-// dW3 [448,464), db2 [464,480), de [480,496), dW1_tail^T [496,512).  The weight-gradient accumulators live in TMEM for
+// TMEM columns: Z1 / O / dH2 [0,128), Z2 / dH1 [128,256), [dW2^T | db2] [256,400), dW1^T [400,464),
+// dW3 [464,480), de [480,496), dW1_tail^T [496,512).  The weight-gradient accumulators live in TMEM for
 // the whole launch and are added to global memory once per CTA.
 
 #include <stddef.h>
@@ -66,8 +67,8 @@ struct TcDims {
     static constexpr int NTAIL = IN - NMAIN;                  // 0 or 9
 };
 
-constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_DH2 = 0, COL_Z2 = 128, COL_DW2 = 256, COL_DW1 = 384, COL_DW3 = 448,
-                   COL_DB2 = 464, COL_DE = 480, COL_DW1T = 496;
+constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_DH2 = 0, COL_Z2 = 128, COL_DW2T = 256, COL_DW1 = 400, COL_DW3 = 464,
+                   COL_DE = 480, COL_DW1T = 496;
 
 // Small per-CTA state, padded to a multiple of 1024 bytes so that the panels after it stay
 // aligned to the 128-byte-swizzle atom.
@@ -91,14 +92,16 @@ struct SmemTC {
                                           // X tails in 16-31 / 32-47, W1 tail in 48-63
     unsigned char x[2][kPanelBytes];      // X (double-buffered): row = sample
     unsigned char h1[2 * kPanelBytes];    // H1, later dZ1
+    // backward: columns 0-15: [dout_r, dout_g, dout_b, 1, ...] (MMA operand); bytes 32-79 and 80-127
+    // of every row (16-byte chunks 2-4 and 5-7): de[0:12] in FP32 for X buffer 0 and 1.  It follows
+    // H1 directly, so [H1 | dout] is one MN-major operand of N = 144 (panels 16 KiB apart)
+    unsigned char dout[kPanelBytes];
     unsigned char h2[2 * kPanelBytes];    // H2
     SmallTC sm;
     // backward only (the forward allocates the struct up to here)
     unsigned char dz2[2 * kPanelBytes];   // dZ2
-    // columns 0-15: [dout_r, dout_g, dout_b, 1, 0, ...] (MMA operand); bytes 32-79 and 80-127 of
-    // every row (16-byte chunks 2-4 and 5-7): de[0:12] in FP32 for X buffer 0 and 1
-    unsigned char dout[kPanelBytes];
 };
+static_assert(offsetof(SmemTC, dout) == offsetof(SmemTC, h1) + 2 * kPanelBytes, "[H1 | dout] must be contiguous");
 
 constexpr size_t smem_bytes(bool bwd) { return (bwd ? sizeof(SmemTC) : offsetof(SmemTC, dz2)) + 1024; }
 
@@ -478,11 +481,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 #pragma unroll 1
                 for (int kk = 0; kk < 8; ++kk) {
                     mma(tb + COL_Z2, desc_kmajor(dz2_, kk), desc_mnmajor(w2t_, kk), idesc_bf16(128, 128, 0, 1), kk > 0);  // dH1
-                    mma(tb + COL_DW2, desc_mnmajor(h1_, kk), desc_mnmajor(dz2_, kk), idesc_bf16(128, 128, 1, 1),
-                        acc_w | (kk > 0));
+                    mma(tb + COL_DW2T, desc_mnmajor(dz2_, kk), desc_mnmajor(h1_, kk), idesc_bf16(128, 144, 1, 1),
+                        acc_w | (kk > 0));   // [dW2^T | db2]: B = [H1 | dout]
                     mma(tb + COL_DW3, desc_mnmajor(h2_, kk), desc_mnmajor(dout_, kk), idesc_bf16(128, 16, 1, 1),
-                        acc_w | (kk > 0));
-                    mma(tb + COL_DB2, desc_mnmajor(dz2_, kk), desc_mnmajor(dout_, kk), idesc_bf16(128, 16, 1, 1),
                         acc_w | (kk > 0));
                 }
                 commit(&S.sm.mma);
@@ -551,14 +552,14 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         const int r = tid & (TM - 1), hc = tid >> 7;
         float *gW1 = A.grad_mlp, *gB1 = gW1 + D::IN * HID, *gW2 = gB1 + HID, *gB2 = gW2 + HID * HID;
         float *gW3 = gB2 + HID, *gB3 = gW3 + HID * 3;
-        // dW2: lane = input unit r, columns = output units (64 per half)
+        // dW2^T: lane = output unit r, columns = input units (64 per half); column 128 + 3 = db2
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
             const int col = 64 * hc + 32 * c;
             float v[32];
-            tmem_ld32(taddr(tb, warp, COL_DW2 + col), v);
+            tmem_ld32(taddr(tb, warp, COL_DW2T + col), v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) atomicAdd(gW2 + r * HID + col + k, v[k]);
+            for (int k = 0; k < 32; ++k) atomicAdd(gW2 + (col + k) * HID + r, v[k]);
         }
         // [dW1 | db1]^T: lane = hidden unit r, columns = X columns (BIAS = bias), 32 per half
         {
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             atomicAdd(gW3 + r * 3 + 1, v[1]);
             atomicAdd(gW3 + r * 3 + 2, v[2]);
         }
-        tmem_ld16(taddr(tb, warp, COL_DB2), v);
+        tmem_ld16(taddr(tb, warp, COL_DW2T + 128), v);
         if (hc == 0) atomicAdd(gB2 + r, v[3]);
         if (tid < 3) atomicAdd(gB3 + tid, S.sm.db3[tid]);
     }
