@@ -24,8 +24,9 @@
 //
 // Forward per tile:  X[128x64] (features, PE(d), [PE(x)], 1) -> Z1 = X W1|b1 -> H1 = relu(Z1) -> Z2 = H1 W2
 //                    -> H2 = relu(Z2 + b2) -> O = H2 W3 (N = 16, 3 used) -> c = sigmoid(O + b3).
-// Backward per tile (recomputes the forward), with dL/dc from the compositing backward:
-//   dout = dL/dc c (1 - c)                                        (epilogue, BF16 panel)
+// Backward per tile (recomputes layers 1 and 2; the colour c is the one the forward stored in the
+// sample record, so layer 3 is not recomputed), with dL/dc from the compositing backward:
+//   dout = dL/dc c (1 - c)                                        (producers; epilogue, BF16 panel)
 //   dH2 = dout W3^T;  dZ2 = dH2 [Z2 + b2 > 0]                      (MMA, epilogue)
 //   dH1 = dZ2 W2^T;  [dW2^T | db2] += dZ2^T [H1 | dout];  dW3 += H2^T dout   (MMAs; dout's
 //   column 3 is 1, so one N = 144 MMA gives dW2^T and db2)
@@ -169,10 +170,12 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         fy = c.fy;
         fz = c.fz;
         if (BWD) {
-            const float4 gc = A.sgrad[slot];
-            d0 = gc.y;
-            d1 = gc.z;
-            d2 = gc.w;
+            // dout = dL/dc c (1 - c) with the colour c the forward left in the sample record
+            // (the same kernel arithmetic on the same operands, so the layer-3 recompute is skipped)
+            const float4 gc = A.sgrad[slot], cv = A.samp[slot];
+            d0 = gc.y * cv.y * (1.0f - cv.y);
+            d1 = gc.z * cv.z * (1.0f - cv.z);
+            d2 = gc.w * cv.w * (1.0f - cv.w);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
@@ -364,8 +367,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             if (!ok || *(volatile int *)&S.sm.abort) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers
             const int slot = S.sm.slot[b][r];
-            const float dc0 = BWD ? S.sm.dc[b][r][0] : 0.0f, dc1 = BWD ? S.sm.dc[b][r][1] : 0.0f,
-                        dc2 = BWD ? S.sm.dc[b][r][2] : 0.0f;
+            const float d0 = BWD ? S.sm.dc[b][r][0] : 0.0f, d1 = BWD ? S.sm.dc[b][r][1] : 0.0f,
+                        d2 = BWD ? S.sm.dc[b][r][2] : 0.0f;
             // ---- layer 1: Z1 = X W1 ----
             if (tid == 0) {
 #pragma unroll 1
@@ -422,20 +425,21 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 #pragma unroll
                 for (int k = 0; k < 32; k += 8) panel_store8(S.h2 + hc * kPanelBytes, r, 32 * g + k, z + k);
             }
-            consumer_publish();
-            // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used) ----
-            if (tid == 0) {
-#pragma unroll 1
-                for (int kk = 0; kk < 8; ++kk)
-                    mma(tb + COL_O, desc_kmajor(h2_, kk), desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
-                commit(&S.sm.mma);
-            }
-            if (!wait_mma()) { ok = false; break; }
-            float o[16];
-            tmem_ld16(taddr(tb, warp, COL_O), o);
-            const float c0 = sigmoidf_(o[0] + S.sm.b3[0]), c1 = sigmoidf_(o[1] + S.sm.b3[1]),
-                        c2 = sigmoidf_(o[2] + S.sm.b3[2]);
             if (!BWD) {
+                consumer_publish();
+                // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used) ----
+                if (tid == 0) {
+#pragma unroll 1
+                    for (int kk = 0; kk < 8; ++kk)
+                        mma(tb + COL_O, desc_kmajor(h2_, kk), desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1),
+                            kk > 0);
+                    commit(&S.sm.mma);
+                }
+                if (!wait_mma()) { ok = false; break; }
+                float o[16];
+                tmem_ld16(taddr(tb, warp, COL_O), o);
+                const float c0 = sigmoidf_(o[0] + S.sm.b3[0]), c1 = sigmoidf_(o[1] + S.sm.b3[1]),
+                            c2 = sigmoidf_(o[2] + S.sm.b3[2]);
                 if (slot >= 0 && hc == 0) {
                     float *sp = reinterpret_cast<float *>(A.samp + slot);
                     sp[1] = c0;
@@ -445,10 +449,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 consumer_sync();   // TMEM reads done before the next tile's MMAs
                 continue;
             }
-            // ---- backward: dout = dL/dc c (1 - c) ----
-            const float d0 = dc0 * c0 * (1.0f - c0);
-            const float d1 = dc1 * c1 * (1.0f - c1);
-            const float d2 = dc2 * c2 * (1.0f - c2);
+            // ---- backward: dout = dL/dc c (1 - c), formed by the producers; the publish below
+            //      also covers H2 ----
             if (hc == 0) {
                 db3_part[0] += d0;
                 db3_part[1] += d1;
