@@ -227,7 +227,8 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, co
  * with respect to the density grid, the colour / feature grid and the MLP parameters.
  * Compositing state (T_k, the weights and the suffix colour sums) is recomputed from the
  * per-sample values the forward left in the workspace (optical depths and colours); the MLP's
- * hidden activations are recomputed, its output colour is the forward's.
+ * activations are recomputed (the BF16 tensor-core backward takes the output colour from the
+ * forward instead of recomputing the last layer).
  * grad_rgb [n_rays*3] (required), grad_tfinal [n_rays] or NULL.
  * grad_density [nx*ny*nz] FP32; grad_cgrid [nx*ny*nz*C] FP32 (also for a BF16 feature grid);
  * grad_mlp (fine only) FP32, packed w1 | b1 | w2 | b2 | w3 | b3 in the dvgo_mlp layouts.
