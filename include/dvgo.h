@@ -277,9 +277,10 @@ typedef struct {
  * Sec. 4.1 Prior 2 (view-count-based learning rate): for every point j of the lattice of g
  * (channels 1, FP32), the number n_j of views that see it, and the scale n_j / n_max of its base
  * learning rate (n_max = max_j n_j), for lr_scale of dvgo_adam_step on that grid.
- *   c2w      device, [n_views][3][4] FP64 row-major camera-to-world matrices [R | c]: columns
- *            R_0, R_1, R_2 are the camera's x (right), y (up) and z (backward) axes in world space,
- *            c its centre; the camera looks along -z.
+ *   c2w      device, [n_views][3][4] FP64 row-major camera-to-world matrices [R | c], finite:
+ *            columns R_0, R_1, R_2 are the camera's x (right), y (up) and z (backward) axes in
+ *            world space, c its centre; the camera looks along -z (R need not be orthonormal:
+ *            q = R^T (x - c) is used as given).
  *   A point x is seen by a view when q = R^T (x - c) has depth -q_z > near and projects into the
  *   closed image rectangle: 0 <= cx + fx q_x / (-q_z) <= width, 0 <= cy - fy q_y / (-q_z) <= height.
  *   Occlusion is not considered.  The decision equals that of the FP64 arithmetic written in that
