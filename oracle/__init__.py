@@ -68,7 +68,7 @@ class _Params(C.Structure):
                 ("xyz_min", C.c_double * 3), ("xyz_max", C.c_double * 3), ("shift_b", C.c_double),
                 ("delta", C.c_double), ("tau_f", C.c_double), ("t_near", C.c_double),
                 ("t_far", C.c_double), ("bg", C.c_double * 3), ("w_pt", C.c_double), ("w_bg", C.c_double),
-                ("act_order", C.c_int), ("n_freq_pos", C.c_int)]
+                ("act_order", C.c_int), ("n_freq_pos", C.c_int), ("mlp_operands", C.c_int)]
 
 
 class _FreeSpace(C.Structure):
@@ -84,6 +84,10 @@ class _Model(C.Structure):
 
 class _Grads(C.Structure):
     _fields_ = [(n, _dp) for n in ("density", "cgrid", "w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+class _Bound(C.Structure):
+    _fields_ = [("u_op", C.c_double), ("u_acc", C.c_double), ("E", _Grads)]
 
 
 class _Prop(C.Structure):
@@ -124,6 +128,7 @@ class Params:
     w_bg: float = 0.0            # background entropy loss weight (Supp. A w_bg)
     act_order: int = 0           # Sec. 3: 0 post- (the paper's), 1 pre-, 2 in-activation
     n_freq_pos: int = 0          # PE frequencies on the query point x (Supp. A k_x = 5); 0: x not input
+    mlp_operands: int = 0        # colour-MLP contractions: 0 exact; 1 BF16 operands (the chosen form's arithmetic)
 
     @property
     def in_dim(self) -> int:
@@ -142,6 +147,7 @@ class Params:
         p.w_pt, p.w_bg = float(self.w_pt), float(self.w_bg)
         p.act_order = int(self.act_order)
         p.n_freq_pos = int(self.n_freq_pos)
+        p.mlp_operands = int(self.mlp_operands)
         return p
 
 
@@ -156,6 +162,7 @@ class RenderResult:
     grads: dict = field(default_factory=dict)
     wbins: np.ndarray | None = None
     touched: dict | None = None
+    bounds: dict = field(default_factory=dict)
 
 
 MLP_KEYS = ("w1", "b1", "w2", "b2", "w3", "b3")
@@ -216,7 +223,8 @@ def unknown_bbox(fs: FreeSpace):
 
 def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dict | None = None,
            target=None, grad_rgb=None, grad_tfinal=None, explicit_t=None, explicit_dt=None,
-           n_bins: int = 0, freespace: FreeSpace | None = None, touched: bool = False) -> RenderResult:
+           n_bins: int = 0, freespace: FreeSpace | None = None, touched: bool = False,
+           error_bound: tuple | None = None) -> RenderResult:
     """Render a ray batch forward and, if ``grad_rgb`` is given, backward (Sec. 2-4).
 
     density: [nx, ny, nz]; cgrid: [nx, ny, nz, C] (coarse colour or fine features);
@@ -224,6 +232,10 @@ def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dic
     grad_rgb: [R, 3] upstream dL/dC_hat; grad_tfinal: [R] or None; freespace: the known-free-space
     test of Sec. 4.2 (skips points where the coarse grid's alpha is below tau_c); touched: also
     return the lattice points the render reads (boolean [nx, ny, nz] per grid, in ``touched``).
+    error_bound: (u_op, u_acc) -- fine stage with grad_rgb: also return in ``bounds`` (keys as
+    ``grads``) a first-order bound on |finite-precision gradient - this gradient| per element for MLP
+    operands rounded to relative u_op (BF16: 2^-8) and accumulation with unit roundoff u_acc (FP32:
+    2^-24); test infrastructure, defined in dvgo_oracle.c (og_bound).
     Returns colours, final transmittances, sample counts, clip bounds, loss and gradients.
     """
     P = params._c()
@@ -270,16 +282,57 @@ def render(params: Params, density, cgrid, rays_o, rays_d, jitter=None, mlp: dic
         dts = _f64(explicit_dt).reshape(R, -1)
         n_expl = ts.shape[1]
     wb = np.zeros((R, n_bins)) if n_bins > 0 else None
+    Bd, bounds = None, {}
+    if error_bound is not None and gC is not None and params.mode == 1:
+        Bd = _Bound()
+        Bd.u_op, Bd.u_acc = float(error_bound[0]), float(error_bound[1])
+        for k, v in grads.items():
+            bounds[k] = np.zeros_like(v)
+            setattr(Bd.E, k, _ptr(bounds[k]))
     lib().oracle_render(C.byref(P), C.byref(M), C.c_int(R), _ptr(rays_o), _ptr(rays_d), _ptr(jit),
                         C.c_int(n_expl), _ptr(ts), _ptr(dts), _ptr(tgt), _ptr(rgb), _ptr(tf),
                         ns.ctypes.data_as(C.POINTER(C.c_int)), _ptr(t0), _ptr(t1), C.byref(loss),
                         _ptr(gC), _ptr(gT), C.byref(G) if gC is not None else None, _ptr(wb),
-                        C.c_int(n_bins))
+                        C.c_int(n_bins), C.byref(Bd) if Bd is not None else None)
     res = RenderResult(rgb=rgb, tfinal=tf, n_samples=ns, t_enter=t0, t_exit=t1,
-                       loss=float(loss.value) if tgt is not None else None, grads=grads, wbins=wb)
+                       loss=float(loss.value) if tgt is not None else None, grads=grads, wbins=wb, bounds=bounds)
     if marks is not None:
         res.touched = {k: v.astype(bool) for k, v in marks.items()}
     return res
+
+
+def bf16(v) -> np.ndarray:
+    """Values rounded to BF16 (8 significant bits, to nearest, ties to even), as FP64."""
+    v = _f64(v)
+    f = lib().oracle_bf16
+    f.restype = C.c_double
+    f.argtypes = [C.c_double]
+    return np.array([f(float(x)) for x in v.reshape(-1)]).reshape(v.shape)
+
+
+def mlp_sample_bound(params: Params, mlp: dict, e_in, e_err, dc, rho_dc: float, u_op: float, u_acc: float):
+    """One fine-MLP sample with its running error bound (og_bound in dvgo_oracle.c; test
+    infrastructure): input row e_in [I] with absolute errors e_err [I], upstream dL/dc [3] with
+    relative error rho_dc.  Returns (c, bound of c, dL/de, its bound, per-sample weight gradients,
+    their bounds), the last two as dicts w1..b3."""
+    P = params._c()
+    M = _Model()
+    arrs = {k: _f64(mlp[k]) for k in MLP_KEYS}
+    for k in MLP_KEYS:
+        setattr(M, k, _ptr(arrs[k]))
+    e_in, e_err, dc = _f64(e_in), _f64(e_err), _f64(dc)
+    I = params.in_dim
+    c, ec, de, ede = np.zeros(3), np.zeros(3), np.zeros(I), np.zeros(I)
+    g = {k: np.zeros_like(v) for k, v in arrs.items()}
+    eb = {k: np.zeros_like(v) for k, v in arrs.items()}
+    G, Eb = _Grads(), _Grads()
+    for k in MLP_KEYS:
+        setattr(G, k, _ptr(g[k]))
+        setattr(Eb, k, _ptr(eb[k]))
+    lib().oracle_mlp_sample_bound(C.byref(P), C.byref(M), _ptr(e_in), _ptr(e_err), _ptr(dc), C.c_double(rho_dc),
+                                  C.c_double(u_op), C.c_double(u_acc), _ptr(c), _ptr(ec), _ptr(de), _ptr(ede),
+                                  C.byref(G), C.byref(Eb))
+    return c, ec, de, ede, g, eb
 
 
 def ray_bounds(params: Params, o, d, p: float = 0.5):

@@ -13,7 +13,7 @@
  *   - trilinear interpolation of a voxel grid              (Sec. 3 Eq. interp)
  *   - shifted softplus and alpha, applied after interp     (Sec. 3 Eq. density_activation,
  *                                                             Eq. post_activation, Eq. density_2_alpha)
- *   - low-density initialisation shift b                   (Sec. 4.1 Eq. low_density_init, Supp. D)
+ *   - low-density initialisation shift b                   (Sec. 4.1 Eq. low_density_init, Supp. F)
  *   - coarse colour grid / fine feature grid + shallow MLP (Sec. 4.1 Eq. coarse_queries,
  *                                                             Sec. 4.2 Eq. fine_queries, Supp. A)
  *   - volume-rendering quadrature and photometric MSE      (Sec. 2 Eq. volume_rendering, Eq. photo_loss)
@@ -84,6 +84,14 @@ typedef struct {
     /* Positional-encoding frequencies on the query point x (Sec. 4.2 Eq. fine_queries_rgb, Supp. A
      * k_x = 5); 0 leaves x out of the MLP input. */
     int n_freq_pos;
+    /* Arithmetic of the colour MLP's contractions:
+     *   0  exact (FP64 throughout: the definition);
+     *   1  BF16 operands -- the chosen form's statement that the colour MLP runs in BF16 with wider
+     *      accumulation: every operand of a contraction is rounded to BF16 (round to nearest, ties
+     *      to even) -- the input row X, H1 and H2 in the forward; dL/do, dZ2 and dZ1 in the
+     *      backward -- and the products are accumulated exactly; the weights are used as given (a
+     *      caller passes them rounded), biases b2, b3 and the sum of dL/do into db3 unrounded. */
+    int mlp_operands;
 } og_params;
 
 /* Known free space (Sec. 4.2): the optimised coarse-stage density grid with its own lattice,
@@ -358,8 +366,23 @@ int oracle_mlp_in_dim(int feat_dim, int n_freq, int n_freq_pos) {
     return feat_dim + 3 + 6 * n_freq + (n_freq_pos > 0 ? 3 + 6 * n_freq_pos : 0);
 }
 
+/* v rounded to BF16 (8 significant bits, round to nearest, ties to even); the exponent range of
+ * the values met here is FP32's, so no overflow or subnormal handling is needed. */
+double oracle_bf16(double v) {
+    if (v == 0.0 || !isfinite(v)) return v;
+    int ex;
+    frexp(v, &ex);                        /* |v| = m 2^ex, 0.5 <= m < 1 */
+    double sc = ldexp(1.0, 8 - ex);       /* v sc in [128, 256): the 8 significant bits */
+    return nearbyint(v * sc) / sc;        /* default rounding mode: to nearest, ties to even */
+}
+
+/* An MLP operand as the contraction uses it: rounded to BF16 in the BF16-operand arithmetic. */
+static double og_op(const og_params *P, double v) { return P->mlp_operands ? oracle_bf16(v) : v; }
+
 /* Forward of the shallow colour MLP, keeping pre-activations for the backward.
- * z1 = e W1 + b1, h1 = relu(z1), z2 = h1 W2 + b2, h2 = relu(z2), o = h2 W3 + b3, c = sigmoid(o). */
+ * z1 = e W1 + b1, h1 = relu(z1), z2 = h1 W2 + b2, h2 = relu(z2), o = h2 W3 + b3, c = sigmoid(o).
+ * With BF16 operands, e must already be rounded and h1, h2 are stored rounded (as the next
+ * contraction and the weight gradients use them); z1, z2 stay exact (they decide the masks). */
 static void og_mlp_fwd(const og_params *P, const og_model *M, const double *e, double *z1,
                        double *h1, double *z2, double *h2, double c[3]) {
     int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), H = P->hidden;
@@ -367,13 +390,13 @@ static void og_mlp_fwd(const og_params *P, const og_model *M, const double *e, d
         double s = M->b1[j];
         for (int i = 0; i < I; ++i) s += e[i] * M->w1[i * H + j];
         z1[j] = s;
-        h1[j] = s > 0 ? s : 0.0;
+        h1[j] = og_op(P, s > 0 ? s : 0.0);
     }
     for (int j = 0; j < H; ++j) {
         double s = M->b2[j];
         for (int i = 0; i < H; ++i) s += h1[i] * M->w2[i * H + j];
         z2[j] = s;
-        h2[j] = s > 0 ? s : 0.0;
+        h2[j] = og_op(P, s > 0 ? s : 0.0);
     }
     for (int j = 0; j < 3; ++j) {
         double s = M->b3[j];
@@ -384,11 +407,13 @@ static void og_mlp_fwd(const og_params *P, const og_model *M, const double *e, d
 
 /* Public MLP forward on a batch of rows (test of the MLP alone against a matmul chain). */
 void oracle_mlp_forward(const og_params *P, const og_model *M, int n, const double *e, double *c) {
-    int H = P->hidden;
-    double *buf = (double *)malloc(sizeof(double) * 4 * H);
-    for (int r = 0; r < n; ++r)
-        og_mlp_fwd(P, M, e + (long)r * oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), buf, buf + H,
-                   buf + 2 * H, buf + 3 * H, c + 3 * r);
+    int H = P->hidden, I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos);
+    double *buf = (double *)malloc(sizeof(double) * (4 * H + I));
+    double *row = buf + 4 * H;
+    for (int r = 0; r < n; ++r) {
+        for (int i = 0; i < I; ++i) row[i] = og_op(P, e[(long)r * I + i]);
+        og_mlp_fwd(P, M, row, buf, buf + H, buf + 2 * H, buf + 3 * H, c + 3 * r);
+    }
     free(buf);
 }
 
@@ -408,6 +433,267 @@ typedef struct {
     double craw[3];      /* coarse: interpolated colour before the activation                   */
 } og_sample;
 
+/* ------------------------------------------------------------------------------------------ */
+/* Running error bound of the fine-stage gradients (test infrastructure)                         */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Not part of the method: a first-order bound on how far a finite-precision evaluation of the
+ * fine-stage render and its gradient can lie from the exact values computed here, used by the
+ * tests as a per-element tolerance.  The arithmetic it describes is the one the north-star
+ * precision statement fixes for the colour MLP: each contraction takes its operands rounded to a
+ * format of relative rounding u_op (BF16: 2^-8; 0 when the operands are used as they are) and
+ * accumulates with unit roundoff u_acc (FP32: 2^-24), as do the per-sample interpolation, the
+ * positional encoding and the compositing.
+ *
+ * The rounded operands are, in the forward, the layer inputs X (the MLP input row), H1 and H2,
+ * and, in the backward, dL/do (= dL/dc c (1 - c)), dZ2 and dZ1 (after the ReLU masks).  Each
+ * quantity v carries a bound e(v) on |computed - exact|, propagated with absolute values
+ * (standard running error analysis): a dot product sum_i a_i b_i with errors e(a_i) in one factor
+ * gets sum_i |b_i| e(a_i) + n u_acc sum_i |a_i b_i|, and a rounding to the operand format adds
+ * u_op |v|.  A ReLU whose input z satisfies |z| <= e(z) may take either branch in finite
+ * precision; the bound then allows both (the output error is at most |z| + e(z), and the masked
+ * backward quantity's error at most |dh| + e(dh)).  Gradient bounds add over the samples that
+ * contribute to an element.  The density gradient's bound propagates the colour bounds e(c_j)
+ * through dC/dtau_k = T_{k+1} c_k - S_k (Eq. volume_rendering) term by term,
+ * sum_ch |gC_ch| (T_{k+1} e(c_k) + sum_{j>k} w_j e(c_j)), plus the FP32 compositing itself
+ * (prefix sums of the optical depth and the exponential: relative u_acc (k P + k + 6) on T_k, with
+ * P the optical depth).  Fine stage only; the summation of contributions into one element is not
+ * included (the tests' relative tolerance covers it).
+ */
+typedef struct {
+    double u_op;     /* relative rounding of each MLP operand (see above); 0: none              */
+    double u_acc;    /* unit roundoff of accumulation and per-sample arithmetic                  */
+    og_grads E;      /* the bounds, accumulated like the gradients (members nullable)            */
+} og_bound;
+
+/* Errors of the MLP input row before any rounding to the operand format: the interpolated
+ * features (8 weighted corners, FP32 weights), then the positional encodings (sin / cos of 2^k v). */
+static void og_input_err(const og_params *P, const og_model *M, const og_sample *s, double u_acc, double *ex) {
+    int C = P->feat_dim, F = P->n_freq, Fp = P->n_freq_pos;
+    for (int ch = 0; ch < C; ++ch) {
+        double a = 0.0;
+        for (int c = 0; c < 8; ++c) a += s->cw[c] * fabs(M->cgrid[s->idx[c] * C + ch]);
+        ex[ch] = 12.0 * u_acc * a;
+    }
+    int b = C;
+    for (int a = 0; a < 3; ++a) ex[b + a] = 2.0 * u_acc;
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < F; ++k) {
+            ex[b + 3 + a * F + k] = u_acc * ldexp(4.0, k);
+            ex[b + 3 + 3 * F + a * F + k] = u_acc * ldexp(4.0, k);
+        }
+    if (Fp > 0) {
+        b = C + 3 + 6 * F;
+        for (int a = 0; a < 3; ++a) {
+            double sc = 1.0 + fabs(s->x[a]);
+            ex[b + a] = 4.0 * u_acc * sc;
+            for (int k = 0; k < Fp; ++k) {
+                ex[b + 3 + a * Fp + k] = u_acc * ldexp(4.0, k) * sc;
+                ex[b + 3 + 3 * Fp + a * Fp + k] = u_acc * ldexp(4.0, k) * sc;
+            }
+        }
+    }
+}
+
+/* Error of a ReLU output given its input z with error ez: both branches allowed when |z| <= ez. */
+static double og_relu_err(double z, double ez) {
+    if (fabs(z) <= ez) return fabs(z) + ez;
+    return z > 0 ? ez : 0.0;
+}
+
+/* Error of a masked backward quantity dz = [z > 0] dh given dh's error edh. */
+static double og_mask_err(double z, double ez, double dh, double edh) {
+    if (fabs(z) <= ez) return fabs(dh) + edh;
+    return z > 0 ? edh : 0.0;
+}
+
+/* Spacing of BF16 numbers in the binade of |v| (v != 0). */
+static double og_bf16_ulp(double v) {
+    int ex;
+    frexp(v, &ex);
+    return ldexp(1.0, ex - 8);
+}
+
+/* Error of a BF16 operand rounded from a value v that finite precision computes within ev of its
+ * exact value.  Both round to nearest, so the two operands are the same BF16 number unless a
+ * rounding midpoint lies within ev of v; then they differ by at most ev plus twice the spacing. */
+static double og_bf16_err(double v, double ev) {
+    if (ev <= 0.0) return 0.0;
+    double a = fabs(v);
+    if (a == 0.0) return ev + 2.0 * og_bf16_ulp(ev);
+    double sp = og_bf16_ulp(a);
+    double lo = floor(a / sp) * sp, hi = ceil(a / sp) * sp;
+    int ambiguous;
+    if (lo == hi) ambiguous = ev >= 0.25 * sp;                     /* v itself representable */
+    else ambiguous = ev >= fabs(a - 0.5 * (lo + hi)) || ev >= (a - lo) + 0.25 * sp || ev >= (hi - a) + 0.5 * sp;
+    return ambiguous ? ev + 2.0 * og_bf16_ulp(a + ev) : 0.0;
+}
+
+/* Error of an MLP operand formed from a value v with error ev: rounded to BF16 with the same
+ * rounding on both sides (BF16-operand arithmetic), or by a format of relative rounding u_op on
+ * one side only (exact arithmetic with the rounding as the error's source). */
+static double og_operand_err(const og_params *P, double v, double ev, double u_op) {
+    return P->mlp_operands ? og_bf16_err(v, ev) : ev + u_op * fabs(v);
+}
+
+/* Forward errors of the MLP given the activations of og_mlp_fwd (e: the input row as the
+ * contraction uses it; e_pre: before its rounding to the operand format, ex: e_pre's errors). */
+static void og_mlp_err_fwd(const og_params *P, const og_model *M, const double *e, const double *e_pre,
+                           const double *ex, const double *z1, const double *h1, const double *z2, const double *h2,
+                           const double c[3], double u_op, double u_acc, double *exo, double *ez1, double *eh1,
+                           double *ez2, double *eh2, double ec[3]) {
+    int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), H = P->hidden;
+    for (int i = 0; i < I; ++i) exo[i] = og_operand_err(P, e_pre[i], ex[i], u_op);
+    for (int j = 0; j < H; ++j) {
+        double a = fabs(M->b1[j]), pe = 0.0;
+        for (int i = 0; i < I; ++i) {
+            a += fabs(e[i] * M->w1[i * H + j]);
+            pe += fabs(M->w1[i * H + j]) * exo[i];
+        }
+        ez1[j] = pe + (I + 1) * u_acc * a;
+        eh1[j] = og_operand_err(P, z1[j] > 0 ? z1[j] : 0.0, og_relu_err(z1[j], ez1[j]), u_op);
+    }
+    for (int j = 0; j < H; ++j) {
+        double a = fabs(M->b2[j]), pe = 0.0;
+        for (int i = 0; i < H; ++i) {
+            a += fabs(h1[i] * M->w2[i * H + j]);
+            pe += fabs(M->w2[i * H + j]) * eh1[i];
+        }
+        ez2[j] = pe + (H + 1) * u_acc * a;
+        eh2[j] = og_operand_err(P, z2[j] > 0 ? z2[j] : 0.0, og_relu_err(z2[j], ez2[j]), u_op);
+    }
+    for (int j = 0; j < 3; ++j) {
+        double a = fabs(M->b3[j]), pe = 0.0;
+        for (int i = 0; i < H; ++i) {
+            a += fabs(h2[i] * M->w3[i * 3 + j]);
+            pe += fabs(M->w3[i * 3 + j]) * eh2[i];
+        }
+        double eo = pe + (H + 1) * u_acc * a;
+        ec[j] = c[j] * (1.0 - c[j]) * eo + 4.0 * u_acc * c[j];
+    }
+}
+
+/* Backward errors of one sample's MLP gradient contributions.  dc: dL/dc with relative error
+ * rho_dc; dout: dL/do before its rounding to the operand format (db3 sums it unrounded);
+ * dout_op, dz2, dz1: the operands of the backward contractions.  Adds the weight-gradient bounds
+ * into LE (members nullable) and writes the bound of dL/de into ede[0 .. I) (nullable).
+ * exo: the input operand errors of og_mlp_err_fwd.  work: 4H doubles. */
+static void og_mlp_err_bwd(const og_params *P, const og_model *M, const double *e, const double *exo,
+                           const double *z1, const double *h1, const double *z2, const double *h2,
+                           const double *ez1, const double *eh1, const double *ez2, const double *eh2,
+                           const double c[3], const double ec[3], const double dc[3], double rho_dc,
+                           const double dout[3], const double dout_op[3], const double *dz2, const double *dz1,
+                           double u_op, double u_acc, double *work, double *ede, og_grads *LE) {
+    int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), H = P->hidden;
+    double *edz2 = work, *edz1 = work + H;
+    double edout[3], edout_op[3];
+    for (int j = 0; j < 3; ++j) {
+        edout[j] = fabs(dc[j]) * fabs(1.0 - 2.0 * c[j]) * ec[j] + rho_dc * fabs(dc[j]) * c[j] * (1.0 - c[j]) +
+                   3.0 * u_acc * fabs(dout[j]);
+        edout_op[j] = og_operand_err(P, dout[j], edout[j], u_op);
+    }
+    for (int i = 0; i < H; ++i) {
+        double dh = 0.0, a = 0.0, pe = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            dh += M->w3[i * 3 + j] * dout_op[j];
+            a += fabs(M->w3[i * 3 + j] * dout_op[j]);
+            pe += fabs(M->w3[i * 3 + j]) * edout_op[j];
+        }
+        double edh = pe + 3.0 * u_acc * a;
+        edz2[i] = og_operand_err(P, z2[i] > 0 ? dh : 0.0, og_mask_err(z2[i], ez2[i], dh, edh), u_op);
+    }
+    for (int i = 0; i < H; ++i) {
+        double dh = 0.0, a = 0.0, pe = 0.0;
+        for (int j = 0; j < H; ++j) {
+            dh += M->w2[i * H + j] * dz2[j];
+            a += fabs(M->w2[i * H + j] * dz2[j]);
+            pe += fabs(M->w2[i * H + j]) * edz2[j];
+        }
+        double edh = pe + H * u_acc * a;
+        edz1[i] = og_operand_err(P, z1[i] > 0 ? dh : 0.0, og_mask_err(z1[i], ez1[i], dh, edh), u_op);
+    }
+    if (ede)
+        for (int i = 0; i < I; ++i) {
+            double a = 0.0, pe = 0.0;
+            for (int j = 0; j < H; ++j) {
+                a += fabs(M->w1[i * H + j] * dz1[j]);
+                pe += fabs(M->w1[i * H + j]) * edz1[j];
+            }
+            ede[i] = pe + H * u_acc * a;
+        }
+    if (LE->w1)
+        for (int i = 0; i < I; ++i)
+            for (int j = 0; j < H; ++j) LE->w1[i * H + j] += fabs(e[i]) * edz1[j] + exo[i] * fabs(dz1[j]);
+    if (LE->b1)
+        for (int j = 0; j < H; ++j) LE->b1[j] += edz1[j];
+    if (LE->w2)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < H; ++j) LE->w2[i * H + j] += fabs(h1[i]) * edz2[j] + eh1[i] * fabs(dz2[j]);
+    if (LE->b2)
+        for (int j = 0; j < H; ++j) LE->b2[j] += edz2[j];
+    if (LE->w3)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < 3; ++j) LE->w3[i * 3 + j] += fabs(h2[i]) * edout_op[j] + eh2[i] * fabs(dout_op[j]);
+    if (LE->b3)
+        for (int j = 0; j < 3; ++j) LE->b3[j] += edout[j];
+}
+
+/*
+ * The bound of one MLP sample on its own (for the bound's own pins): input row e_in [I] (before
+ * any rounding to the operand format) with errors ex [I], upstream dL/dc (relative error rho_dc).
+ * Writes c, its bound ec, dL/de and its bound, and ADDS the sample's weight-gradient
+ * contributions into G and their bounds into Eb (members nullable).
+ */
+void oracle_mlp_sample_bound(const og_params *P, const og_model *M, const double *e_in, const double *ex,
+                             const double dc[3], double rho_dc, double u_op, double u_acc, double c[3], double ec[3],
+                             double *de, double *ede, og_grads *G, og_grads *Eb) {
+    int I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos), H = P->hidden;
+    double *buf = (double *)calloc((size_t)12 * H + 2 * (size_t)I, sizeof(double));
+    double *z1 = buf, *h1 = buf + H, *z2 = buf + 2 * H, *h2 = buf + 3 * H;
+    double *ez1 = buf + 4 * H, *eh1 = buf + 5 * H, *ez2 = buf + 6 * H, *eh2 = buf + 7 * H;
+    double *dz2 = buf + 8 * H, *dz1 = buf + 9 * H, *work = buf + 10 * H;
+    double *e = buf + 12 * H, *exo = e + I;
+    for (int i = 0; i < I; ++i) e[i] = og_op(P, e_in[i]);
+    og_mlp_fwd(P, M, e, z1, h1, z2, h2, c);
+    og_mlp_err_fwd(P, M, e, e_in, ex, z1, h1, z2, h2, c, u_op, u_acc, exo, ez1, eh1, ez2, eh2, ec);
+    /* the sample's backward: dout = dc c (1 - c); dZ2 = [z2 > 0] dout W3^T; dZ1 = [z1 > 0] dZ2 W2^T,
+     * each operand as the contractions use it */
+    double dout[3], dout_op[3];
+    for (int j = 0; j < 3; ++j) {
+        dout[j] = dc[j] * c[j] * (1.0 - c[j]);
+        dout_op[j] = og_op(P, dout[j]);
+    }
+    for (int i = 0; i < H; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < 3; ++j) a += M->w3[i * 3 + j] * dout_op[j];
+        dz2[i] = og_op(P, z2[i] > 0 ? a : 0.0);
+    }
+    for (int i = 0; i < H; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < H; ++j) a += M->w2[i * H + j] * dz2[j];
+        dz1[i] = og_op(P, z1[i] > 0 ? a : 0.0);
+    }
+    for (int i = 0; i < I; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < H; ++j) a += M->w1[i * H + j] * dz1[j];
+        de[i] = a;
+    }
+    if (G) {
+        if (G->w1) for (int i = 0; i < I; ++i) for (int j = 0; j < H; ++j) G->w1[i * H + j] += e[i] * dz1[j];
+        if (G->b1) for (int j = 0; j < H; ++j) G->b1[j] += dz1[j];
+        if (G->w2) for (int i = 0; i < H; ++i) for (int j = 0; j < H; ++j) G->w2[i * H + j] += h1[i] * dz2[j];
+        if (G->b2) for (int j = 0; j < H; ++j) G->b2[j] += dz2[j];
+        if (G->w3) for (int i = 0; i < H; ++i) for (int j = 0; j < 3; ++j) G->w3[i * 3 + j] += h2[i] * dout_op[j];
+        if (G->b3) for (int j = 0; j < 3; ++j) G->b3[j] += dout[j];
+    }
+    og_grads none;
+    memset(&none, 0, sizeof(none));
+    og_mlp_err_bwd(P, M, e, exo, z1, h1, z2, h2, ez1, eh1, ez2, eh2, c, ec, dc, rho_dc, dout, dout_op, dz2, dz1, u_op,
+                   u_acc, work, ede, Eb ? Eb : &none);
+    free(buf);
+}
+
 /*
  * Shared per-ray renderer.  Samples come either from uniform stepping (ts == NULL) or from an
  * explicit list (t, dt) of n_expl samples (the proposal path).  Outputs the composite colour,
@@ -420,7 +706,7 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                           const double *dts, double rgb[3], double *tfinal, int *nsamp,
                           double *tin, double *tout, const double *gC, double gT, og_grads *G,
                           og_grads *L, double *wbins, int nbins, const double *tgt, double aux_scale,
-                          double *aux_loss) {
+                          double *aux_loss, const og_bound *B, og_grads *LE) {
     double dn[3], t_enter, t_exit;
     int n;
     oracle_ray_bounds(P, o, d, p, &t_enter, &t_exit, dn, &n);
@@ -435,6 +721,12 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
     int stride = I + 4 * H;
     if (P->mode == 1 && n > 0) act = (double *)malloc(sizeof(double) * (size_t)n * stride);
     double *feat = (double *)malloc(sizeof(double) * (C > 0 ? C : 1));
+    /* error bounds (fine stage, with B): per sample the input row before its rounding to the
+     * operand format e_pre [I], its errors ex [I], the operand errors exo [I], ez1, eh1, ez2, eh2
+     * [H each] and ec [3] */
+    int want_bound = B && gC && P->mode == 1 && n > 0;
+    int sb = 3 * I + 4 * H + 3;
+    double *eb = want_bound ? (double *)malloc(sizeof(double) * (size_t)n * sb) : NULL;
 
     /* Forward: sample, query, composite (Eq. volume_rendering). */
     double T = 1.0, acc[3] = {0, 0, 0}, pt = 0.0;
@@ -493,7 +785,17 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
             } else {
                 double *e = act + (size_t)k * stride;
                 og_mlp_input(P, feat, dn, s->x, e);
+                double *q = want_bound ? eb + (size_t)k * sb : NULL;
+                if (want_bound) {
+                    memcpy(q, e, sizeof(double) * I);
+                    og_input_err(P, M, s, B->u_acc, q + I);
+                }
+                for (int i = 0; i < I; ++i) e[i] = og_op(P, e[i]);    /* the input row as layer 1 uses it */
                 og_mlp_fwd(P, M, e, e + I, e + I + H, e + I + 2 * H, e + I + 3 * H, s->c);
+                if (want_bound)
+                    og_mlp_err_fwd(P, M, e, q, q + I, e + I, e + I + H, e + I + 2 * H, e + I + 3 * H, s->c, B->u_op,
+                                   B->u_acc, q + 2 * I, q + 3 * I, q + 3 * I + H, q + 3 * I + 2 * H,
+                                   q + 3 * I + 3 * H, q + 3 * I + 4 * H);
             }
         }
         double w = T * s->alpha;
@@ -533,6 +835,17 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
         for (int ch = 0; ch < 3; ++ch) Ssuf[ch] = Tk[n] * P->bg[ch];
         double *dh2 = (double *)malloc(sizeof(double) * 3 * (H > 0 ? H : 1));
         double *dz2 = dh2 + H, *dz1 = dh2 + 2 * H;
+        /* bound state: suffix sums of w_j e(c_j) and of T_{j+1} (|c_j| + cmax) over later kept
+         * samples, the compositing's relative error on T_n, and per-sample scratch */
+        double Esuf[3] = {0, 0, 0}, Asuf[3] = {0, 0, 0}, cmax[3], rho_n = 0.0;
+        double *bwork = NULL, *ede = NULL;
+        if (want_bound) {
+            for (int ch = 0; ch < 3; ++ch) cmax[ch] = fabs(P->bg[ch]) > 1.0 ? fabs(P->bg[ch]) : 1.0;
+            double Pn = Tk[n] > 0 ? -log(Tk[n]) : 745.0;
+            rho_n = B->u_acc * (n * Pn + n + 6.0);
+            bwork = (double *)malloc(sizeof(double) * (4 * (size_t)H + I));
+            ede = bwork + 4 * H;
+        }
         for (int k = n - 1; k >= 0; --k) {
             og_sample *s = &S[k];
             double w = Tk[k] * s->alpha;
@@ -541,6 +854,32 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                 double gTe = gT + (tgt ? P->w_bg * aux_scale * og_bg_entropy_dT(Tk[n]) : 0.0);
                 double dtau = -gTe * Tk[n];
                 for (int ch = 0; ch < 3; ++ch) dtau += gC[ch] * (Tk[k + 1] * s->c[ch] - Ssuf[ch]);
+                double edtau = 0.0;
+                const double *q = want_bound ? eb + (size_t)k * sb : NULL;
+                if (want_bound) {
+                    const double *ec = q + 3 * I + 4 * H;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        Asuf[ch] += Tk[k + 1] * (fabs(s->c[ch]) + cmax[ch]);
+                        edtau += fabs(gC[ch]) * (Tk[k + 1] * ec[ch] + Esuf[ch] + rho_n * Asuf[ch]);
+                    }
+                    edtau += fabs(gTe) * Tk[n] * rho_n;
+                    for (int c = 0; c < 8; ++c) {
+                        double f;
+                        if (P->act_order == 1) {
+                            double sp = og_softplus(M->density[s->idx[c]] + P->shift_b);
+                            f = 1.0 / (1.0 - s->alpha) * s->cw[c] * exp(-sp * s->dt) * s->dt *
+                                og_sigmoid(M->density[s->idx[c]] + P->shift_b);
+                        } else if (P->act_order == 2) {
+                            f = s->dt * s->cw[c] * og_sigmoid(M->density[s->idx[c]] + P->shift_b);
+                        } else {
+                            f = s->dt * og_sigmoid(s->z) * s->cw[c];
+                        }
+                        if (B->E.density) {
+#pragma omp atomic
+                            B->E.density[s->idx[c]] += edtau * fabs(f);
+                        }
+                    }
+                }
                 /* dL/dV_q = dL/dtau dtau/dV_q, tau = -log(1 - alpha) */
                 for (int c = 0; c < 8; ++c) {
                     double g;
@@ -574,17 +913,20 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                 } else {
                     const double *e = act + (size_t)k * stride;
                     const double *z1 = e + I, *h1 = z1 + H, *z2 = h1 + H, *h2 = z2 + H;
-                    double dout[3];
-                    for (int j = 0; j < 3; ++j) dout[j] = dc[j] * s->c[j] * (1.0 - s->c[j]);
+                    double dout[3], dout_op[3];
+                    for (int j = 0; j < 3; ++j) {
+                        dout[j] = dc[j] * s->c[j] * (1.0 - s->c[j]);
+                        dout_op[j] = og_op(P, dout[j]);       /* the operand of the contractions */
+                    }
                     for (int j = 0; j < 3; ++j) L->b3[j] += dout[j];
                     for (int i = 0; i < H; ++i) {
                         double acc2 = 0.0;
                         for (int j = 0; j < 3; ++j) {
-                            L->w3[i * 3 + j] += h2[i] * dout[j];
-                            acc2 += M->w3[i * 3 + j] * dout[j];
+                            L->w3[i * 3 + j] += h2[i] * dout_op[j];
+                            acc2 += M->w3[i * 3 + j] * dout_op[j];
                         }
                         dh2[i] = acc2;
-                        dz2[i] = z2[i] > 0 ? acc2 : 0.0;
+                        dz2[i] = og_op(P, z2[i] > 0 ? acc2 : 0.0);
                     }
                     for (int j = 0; j < H; ++j) L->b2[j] += dz2[j];
                     for (int i = 0; i < H; ++i) {
@@ -593,7 +935,7 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                             L->w2[i * H + j] += h1[i] * dz2[j];
                             acc1 += M->w2[i * H + j] * dz2[j];
                         }
-                        dz1[i] = z1[i] > 0 ? acc1 : 0.0;
+                        dz1[i] = og_op(P, z1[i] > 0 ? acc1 : 0.0);
                     }
                     for (int j = 0; j < H; ++j) L->b1[j] += dz1[j];
                     for (int i = 0; i < I; ++i) {
@@ -609,13 +951,30 @@ static void og_render_ray(const og_params *P, const og_model *M, const double o[
                             }
                         }
                     }
+                    if (want_bound) {
+                        double Pk = Tk[k] > 0 ? -log(Tk[k]) : 745.0;
+                        double rho_dc = B->u_acc * (k * Pk + k + 6.0);
+                        og_mlp_err_bwd(P, M, e, q + 2 * I, z1, h1, z2, h2, q + 3 * I, q + 3 * I + H, q + 3 * I + 2 * H,
+                                       q + 3 * I + 3 * H, s->c, q + 3 * I + 4 * H, dc, rho_dc, dout, dout_op, dz2, dz1,
+                                       B->u_op, B->u_acc, bwork, ede, LE);
+                        if (B->E.cgrid)
+                            for (int i = 0; i < C; ++i)
+                                for (int c = 0; c < 8; ++c) {
+#pragma omp atomic
+                                    B->E.cgrid[s->idx[c] * C + i] += ede[i] * s->cw[c];
+                                }
+                    }
                 }
                 for (int ch = 0; ch < 3; ++ch) Ssuf[ch] += w * s->c[ch];
+                if (want_bound)
+                    for (int ch = 0; ch < 3; ++ch) Esuf[ch] += w * q[3 * I + 4 * H + ch];
             }
         }
+        free(bwork);
         free(dh2);
         free(Tk);
     }
+    free(eb);
     free(feat);
     free(act);
     free(S);
@@ -636,7 +995,7 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
                    const double *rays_d, const double *jitter, int n_expl, const double *ts,
                    const double *dts, const double *target, double *rgb, double *tfinal,
                    int *nsamp, double *t_enter, double *t_exit, double *loss, const double *gC,
-                   const double *gT, og_grads *G, double *wbins, int nbins) {
+                   const double *gT, og_grads *G, double *wbins, int nbins, og_bound *B) {
     int H = P->hidden, I = oracle_mlp_in_dim(P->feat_dim, P->n_freq, P->n_freq_pos);
     /* Sizes of the MLP parameter blocks w1, b1, w2, b2, w3, b3. */
     long nw[6] = {(long)I * H, H, (long)H * H, H, (long)H * 3, 3};
@@ -646,9 +1005,10 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
     {
         /* Thread-local MLP gradient buffers (summed into G at the end); grid gradients are
          * scattered with atomics. */
-        og_grads L;
-        double *lbuf = NULL;
+        og_grads L, LE;
+        double *lbuf = NULL, *lebuf = NULL;
         memset(&L, 0, sizeof(L));
+        memset(&LE, 0, sizeof(LE));
         if (want_mlp) {
             long tot = 0;
             for (int i = 0; i < 6; ++i) tot += nw[i];
@@ -658,6 +1018,15 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
             for (int i = 0; i < 6; ++i) {
                 *dst[i] = q;
                 q += nw[i];
+            }
+            if (B) {      /* thread-local bounds of the MLP gradients, like L */
+                lebuf = (double *)calloc((size_t)tot, sizeof(double));
+                q = lebuf;
+                double **dste[6] = {&LE.w1, &LE.b1, &LE.w2, &LE.b2, &LE.w3, &LE.b3};
+                for (int i = 0; i < 6; ++i) {
+                    *dste[i] = q;
+                    q += nw[i];
+                }
             }
         }
         long r;
@@ -671,7 +1040,7 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
                           nsamp ? nsamp + r : NULL, t_enter ? t_enter + r : NULL,
                           t_exit ? t_exit + r : NULL, gC ? gC + 3 * r : NULL, gT ? gT[r] : 0.0,
                           G, &L, wbins ? wbins + (size_t)r * nbins : NULL, nbins,
-                          target ? target + 3 * r : NULL, R > 0 ? 1.0 / R : 0.0, aux ? aux + r : NULL);
+                          target ? target + 3 * r : NULL, R > 0 ? 1.0 / R : 0.0, aux ? aux + r : NULL, B, &LE);
             if (tfinal) tfinal[r] = tf;
         }
         if (want_mlp) {
@@ -680,8 +1049,17 @@ void oracle_render(const og_params *P, const og_model *M, int R, const double *r
 #pragma omp critical
             for (int i = 0; i < 6; ++i)
                 for (long j = 0; j < nw[i]; ++j) dst[i][j] += src[i][j];
+            if (B) {
+                double *srce[6] = {LE.w1, LE.b1, LE.w2, LE.b2, LE.w3, LE.b3};
+                double *dste[6] = {B->E.w1, B->E.b1, B->E.w2, B->E.b2, B->E.w3, B->E.b3};
+#pragma omp critical
+                for (int i = 0; i < 6; ++i)
+                    if (dste[i])
+                        for (long j = 0; j < nw[i]; ++j) dste[i][j] += srce[i][j];
+            }
         }
         free(lbuf);
+        free(lebuf);
     }
     if (target && loss) {
         double Ls = 0.0;
