@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 6
+#define DVGO_ABI_VERSION 7
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -61,7 +61,8 @@ typedef enum {
     DVGO_ERR_WORKSPACE = -2,     /* workspace NULL, misaligned or smaller than required       */
     DVGO_ERR_UNSUPPORTED = -3,   /* a combination this build does not implement               */
     DVGO_ERR_CUDA = -4,          /* a kernel launch failed (cudaGetLastError)                 */
-    DVGO_ERR_DEVICE = -5,        /* device-side flag: a ray had a zero / non-finite direction */
+    DVGO_ERR_DEVICE = -5,        /* device-side flag: a ray had a zero / non-finite direction,
+                                    or a tensor-core kernel's bounded wait ran out              */
     DVGO_ERR_CAPACITY = -6       /* batch larger than the static scratch of dvgo_render_fwd_noalloc */
 } dvgo_status;
 
@@ -166,6 +167,18 @@ typedef struct {
     int n_freq_pos;      /* fine: positional-encoding frequencies on the query point x (Sec. 4.2
                             Eq. fine_queries_rgb, Supp. A: k_x = 5); 0 leaves x out of the MLP
                             input.  This build supports 0 and 5.                                 */
+    /* Failure detection of the tensor-core colour kernels (DVGO_MLP_BF16; not part of the method).
+     * Every device-side wait of those kernels (an mbarrier phase: the producers' tile, the
+     * consumers' release of a buffer, the completion of an MMA batch) gives up after
+     * wait_limit_us microseconds (0: the default, 2 s); the kernel then stops its CTA's work, waits
+     * (bounded) for MMAs it issued, releases its tensor memory, sets bit 1 of the workspace flag
+     * word (dvgo_workspace_status then returns DVGO_ERR_DEVICE until the next forward) and returns;
+     * the gradients or colours of that call are incomplete.  Range 0 .. 60,000,000.
+     * test_withhold_tile (testing aid, 0 in normal use): k > 0 makes one producer thread of the
+     * colour kernels withhold its arrival on tile k - 1, so that the consumers' wait for that tile
+     * runs out -- the failure path above, taken on purpose. */
+    int wait_limit_us;
+    int test_withhold_tile;
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
@@ -300,8 +313,10 @@ int dvgo_view_counts(const dvgo_grid_desc *g, const dvgo_view_rig *rig, const do
 /* Learning rate of Supp. A at 0-based step t: lr0 * 0.1^(t / decay_steps). */
 float dvgo_lr_at(float lr0, int step, float decay_steps);
 
-/* Reads (synchronously, on `stream`) the device-side flag word that the last forward left:
- * returns DVGO_OK or DVGO_ERR_DEVICE when a ray had a zero or non-finite direction. */
+/* Reads (synchronously, on `stream`) the device-side flag word of the workspace: returns DVGO_OK,
+ * or DVGO_ERR_DEVICE when a ray of the last forward had a zero or non-finite direction (bit 0) or
+ * a tensor-core colour kernel of the last forward or backward gave up a wait (bit 1, see
+ * dvgo_params.wait_limit_us).  Each forward clears the word. */
 int dvgo_workspace_status(void *workspace, void *stream);
 
 /* Copies the per-ray sample counts that the last forward computed (step 2 of dvgo_render_fwd)
@@ -330,20 +345,23 @@ int dvgo_touched_points(const dvgo_params *p, const dvgo_grid_desc *density, int
  * counterpart; this is a deployment convenience.
  *
  * Scratch memory: instead of a caller workspace it uses one static device array of
- * DVGO_NOALLOC_SCRATCH_BYTES (about 2.4 MB) inside the library, which every GPU that loads the
+ * DVGO_NOALLOC_SCRATCH_BYTES (about 2.6 MB) inside the library, which every GPU that loads the
  * library holds until the process exits.  The caller still passes all inputs and outputs, with the
  * meaning, layout and nullability of dvgo_render_fwd.  The call itself allocates nothing (no
  * cudaMalloc / cudaFree or allocating library routine).
  *   - n_rays may be at most DVGO_NOALLOC_MAX_RAYS; a larger batch returns DVGO_ERR_CAPACITY and
  *     enqueues nothing.  Any mode other than DVGO_MODE_COARSE returns DVGO_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture.
+ *     that device current, and keeps it for the life of the process; make that first call before
+ *     any stream capture.  A device reset (cudaDeviceReset) or any other teardown of the device's
+ *     primary context unloads the library's device code, after which this entry point must not be
+ *     called again in that process.
  *   - Every call, on every stream, shares the one array and overwrites what the previous call left
  *     there.  Calls whose execution overlaps on the GPU (different streams without ordering between
  *     them) race and give undefined results: order them on one stream or with events.
  */
 #define DVGO_NOALLOC_MAX_RAYS 16384
-#define DVGO_NOALLOC_SCRATCH_BYTES 2359552
+#define DVGO_NOALLOC_SCRATCH_BYTES 2621696
 int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_desc *density_desc, const float *density,
                             const dvgo_grid_desc *cgrid_desc, const void *cgrid, int n_rays,
                             const float *rays_o, const float *rays_d, const float *jitter,

@@ -13,6 +13,8 @@ from dataclasses import dataclass
 import torch
 
 DVGO_OK = 0
+DVGO_ERR_INVALID_ARG, DVGO_ERR_WORKSPACE, DVGO_ERR_UNSUPPORTED = -1, -2, -3
+DVGO_ERR_CUDA, DVGO_ERR_DEVICE, DVGO_ERR_CAPACITY = -4, -5, -6
 DVGO_DTYPE_F32, DVGO_DTYPE_BF16 = 0, 1
 DVGO_MODE_COARSE, DVGO_MODE_FINE = 0, 1
 DVGO_MLP_FP32, DVGO_MLP_BF16 = 0, 1
@@ -26,6 +28,7 @@ EXPORTED_SYMBOLS = (
     "dvgo_touched_points", "dvgo_view_counts",
 )
 DVGO_NOALLOC_MAX_RAYS = 16384
+DVGO_NOALLOC_SCRATCH_BYTES = 2621696
 DVGO_ACT_POST, DVGO_ACT_PRE, DVGO_ACT_IN = 0, 1, 2   # Sec. 3 interpolation / activation orders
 DVGO_LAYOUT_CANONICAL, DVGO_LAYOUT_PACKED = 0, 1     # grid storage layouts
 
@@ -62,7 +65,8 @@ class _Params(C.Structure):
                 ("hidden", C.c_int), ("step", C.c_float), ("shift_b", C.c_float), ("tau_f", C.c_float),
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
                 ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
-                ("act_order", C.c_int), ("n_freq_pos", C.c_int)]
+                ("act_order", C.c_int), ("n_freq_pos", C.c_int), ("wait_limit_us", C.c_int),
+                ("test_withhold_tile", C.c_int)]
 
 
 class _Fit2d(C.Structure):
@@ -215,6 +219,8 @@ class Params:
     w_bg: float = 0.0            # background entropy loss weight (Supp. A)
     act_order: int = 0           # Sec. 3 interpolation / activation order: 0 post, 1 pre, 2 in
     n_freq_pos: int = 0          # PE frequencies on the query point x (Supp. A: 5); 0: x not an MLP input
+    wait_limit_us: int = 0       # tensor-core kernels: bound on every device wait (0: 2 s)
+    test_withhold_tile: int = 0  # testing aid: k > 0 withholds one producer arrival on tile k - 1
 
     def mlp_in_dim(self, channels: int = 12) -> int:
         """Width of the fine MLP's input row (Sec. 4.2 Eq. fine_queries_rgb): 39, or 72 with PE(x)."""
@@ -233,6 +239,8 @@ class Params:
         p.w_pt_rgb, p.w_bg = float(self.w_pt_rgb), float(self.w_bg)
         p.act_order = int(self.act_order)
         p.n_freq_pos = int(self.n_freq_pos)
+        p.wait_limit_us = int(self.wait_limit_us)
+        p.test_withhold_tile = int(self.test_withhold_tile)
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)

@@ -90,6 +90,7 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
         return DVGO_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
         if (!isfinite(p->bg[c])) return DVGO_ERR_INVALID_ARG;
+    if (p->wait_limit_us < 0 || p->wait_limit_us > 60000000 || p->test_withhold_tile < 0) return DVGO_ERR_INVALID_ARG;
     if (p->mode == DVGO_MODE_COARSE) {
         if (cd->channels != 3 || cd->dtype != DVGO_DTYPE_F32) return DVGO_ERR_INVALID_ARG;
         if (p->rgb_act != 0 && p->rgb_act != 1) return DVGO_ERR_INVALID_ARG;
@@ -160,6 +161,8 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
     A.w_bg = p->w_bg;
     A.act_order = p->act_order;
     A.packed = dd->layout == DVGO_LAYOUT_PACKED;
+    A.wait_ns = p->wait_limit_us > 0 ? 1000ull * (unsigned long long)p->wait_limit_us : kDefaultWaitNs;
+    A.withhold_tile = p->test_withhold_tile;
     if (p->mode == DVGO_MODE_FINE) {
         A.pe = reinterpret_cast<float *>(b + L.pe);
         A.texit = reinterpret_cast<double *>(b + L.texit);

@@ -111,7 +111,13 @@ struct RenderArgs {
     int fs_nx, fs_ny, fs_nz;
     float fs_shift_b, fs_step, fs_tau;
     long long fs_scale[3], fs_off[3];
+    // failure detection of the tensor-core kernels: bound on every device wait (ns), and the
+    // testing aid that withholds one producer arrival on tile withhold_tile - 1 (0: none)
+    unsigned long long wait_ns;
+    int withhold_tile;
 };
+
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;   // 2 s
 
 constexpr int kFsScaleBits = 48;
 

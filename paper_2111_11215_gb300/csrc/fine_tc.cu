@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int b = i & 1;
             if (i >= 2) {
-                if (!mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1)) {
+                if (!mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1, A.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -330,12 +330,13 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             if (*(volatile int *)&S.sm.abort) break;
             produce_row<FeatT, BWD, PEX, PK>(A, S, b, tile * TM + row, n_kept, row);
             fence_async_smem();
-            mbar_arrive(&S.sm.full[b]);
+            // (testing aid: one arrival withheld on a chosen tile makes the consumers' wait run out)
+            if (!(row == 0 && tile + 1 == A.withhold_tile)) mbar_arrive(&S.sm.full[b]);
         }
         if (BWD && ok) {
             // the last (up to) two tiles: wait until the consumers are done with them, then scatter
             for (int j = (i >= 2 ? i - 2 : 0); j < i && ok; ++j) {
-                if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1)) ok = false;
+                if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1, A.wait_ns)) ok = false;
                 else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, row);
             }
         }
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         int i = 0;
         // waits for the current MMA batch; on a timeout every consumer leaves the loop
         auto wait_mma = [&]() -> bool {
-            bool w = mbar_wait(&S.sm.mma, mphase);
+            bool w = mbar_wait(&S.sm.mma, mphase, A.wait_ns);
             mphase ^= 1;
             fence_after();
             return w;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.tp);
             uint32_t h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), dz2_ = smem_u32(S.dz2), dout_ = smem_u32(S.dout);
             asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(h1_), "+r"(h2_), "+r"(dz2_), "+r"(dout_));
-            if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1)) ok = false;
+            if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
             fence_after();
             if (!ok || *(volatile int *)&S.sm.abort) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     if (failed) {
         if (tid == 0) atomicOr(&A.hdr->flags, 2);
         // an MMA batch whose completion timed out may still be running: wait (bounded) once more
-        if (tid < NC) mbar_wait(&S.sm.mma, 0);
+        if (tid < NC) mbar_wait(&S.sm.mma, 0, A.wait_ns);
     }
     if (BWD && !failed && tid < NC && ntile_mine > 0) {
         const uint32_t tb = S.sm.tmem_base;

@@ -136,8 +136,10 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// Wait for the mbarrier phase with the given parity; gives up after ~2 s (returns false).
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Wait for the mbarrier phase with the given parity; gives up after limit_ns nanoseconds of the
+// global timer (default 2 s) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
+                                          unsigned long long limit_ns = 2000000000ull) {
     uint32_t addr = smem_u32(mbar);
     uint64_t t0 = globaltimer();
     for (;;) {
@@ -150,7 +152,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (globaltimer() - t0 > 2000000000ull) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 
