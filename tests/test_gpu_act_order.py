@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import FLOOR_FINE_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from helpers import BOUND_FP32, RTOL_COLOUR, RTOL_GRAD, assert_close, assert_within_bound, oracle_params
 from test_gpu_parity import _fine_inputs, _run_coarse, _run_fine
 
 pytestmark = pytest.mark.gpu
@@ -41,11 +41,11 @@ def test_fine_orders_fp32(order):
     gT = g.normal(scale=1e-2, size=R)
     got = _run_fine(p, res, dens, feat, mlp, o, d, jit, gC, gT)
     ref = oracle.render(oracle_params(p, (res,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC,
-                        grad_tfinal=gT)
+                        grad_tfinal=gT, error_bound=BOUND_FP32)
     assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
     assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
-    assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
-    assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
+    assert_within_bound(got["g_d"], ref.grads["density"], ref.bounds["density"], "grad_density")
+    assert_within_bound(got["g_f"], ref.grads["cgrid"], ref.bounds["cgrid"], "grad_feat")
 
 
 def test_pre_order_saturated_corners_stay_finite():

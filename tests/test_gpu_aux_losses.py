@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from helpers import FLOOR_FINE_GRAD, RTOL_GRAD, assert_close, oracle_params
+from helpers import BOUND_FP32, RTOL_GRAD, assert_close, assert_within_bound, mlp_flat, oracle_params
 from test_gpu_parity import _fine_inputs, _mlp_flat, cuda
 
 pytestmark = pytest.mark.gpu
@@ -62,18 +62,17 @@ def test_fine_aux_losses_fp32():
     P = oracle_params(p, (res,) * 3, 12)
     ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, target=tgt)
     gC = 2.0 * (ref.rgb - tgt) / R
-    refb = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, target=tgt, grad_rgb=gC)
+    refb = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, target=tgt, grad_rgb=gC, error_bound=BOUND_FP32)
     assert float(loss.item()) == pytest.approx(ref.loss, rel=1e-5)
-    assert_close(g_d.cpu().numpy(), refb.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
-    assert_close(g_f.cpu().numpy(), refb.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
-    ref_m = np.concatenate([refb.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
-    assert_close(g_m.cpu().numpy(), ref_m, RTOL_GRAD, "grad_mlp", floor=FLOOR_FINE_GRAD)
+    assert_within_bound(g_d.cpu().numpy(), refb.grads["density"], refb.bounds["density"], "grad_density")
+    assert_within_bound(g_f.cpu().numpy(), refb.grads["cgrid"], refb.bounds["cgrid"], "grad_feat")
+    assert_within_bound(g_m.cpu().numpy(), mlp_flat(refb.grads), mlp_flat(refb.bounds), "grad_mlp")
     # a forward without a target leaves no auxiliary gradient behind
     r.forward(D, F, views, ro, rd, jt)
     g2 = torch.zeros_like(D)
     r.backward(D, F, views, ro, rd, jt, None, dloss, None, g2, torch.zeros_like(F), torch.zeros_like(flat))
-    plain = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC)
-    assert_close(g2.cpu().numpy(), plain.grads["density"], RTOL_GRAD, "grad_density_no_target", floor=FLOOR_FINE_GRAD)
+    plain = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, error_bound=BOUND_FP32)
+    assert_within_bound(g2.cpu().numpy(), plain.grads["density"], plain.bounds["density"], "grad_density_no_target")
 
 
 def test_allocation_free_forward_rejects_aux_weights():

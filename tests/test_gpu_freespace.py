@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import FLOOR_FINE_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from helpers import BOUND_FP32, RTOL_COLOUR, assert_close, assert_within_bound, mlp_flat, oracle_params
 from test_gpu_parity import _fine_inputs, _mlp_flat, _run_fine, cuda
 from test_oracle_freespace import _coarse
 
@@ -61,14 +61,14 @@ def test_fine_freespace_parity(feat_dtype):
     g = np.random.default_rng(31)
     gC = g.normal(scale=1e-2, size=(len(idx), 3))
     got = _run_fine(p, res, dens, feat, mlp, o, d, jit, gC, np.zeros(len(idx)), feat_dtype)
-    ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, freespace=fs_ora)
+    ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, freespace=fs_ora,
+                        error_bound=BOUND_FP32)
     np.testing.assert_array_equal(got["counts"], ref.n_samples)     # skipping keeps the sample grid
     assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
     assert_close(got["tfinal"], ref.tfinal, RTOL_COLOUR, "tfinal")
-    assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
-    assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
-    ref_m = np.concatenate([ref.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
-    assert_close(got["g_m"], ref_m, RTOL_GRAD, "grad_mlp", floor=FLOOR_FINE_GRAD)
+    assert_within_bound(got["g_d"], ref.grads["density"], ref.bounds["density"], "grad_density")
+    assert_within_bound(got["g_f"], ref.grads["cgrid"], ref.bounds["cgrid"], "grad_feat")
+    assert_within_bound(got["g_m"], mlp_flat(ref.grads), mlp_flat(ref.bounds), "grad_mlp")
     # the test is not vacuous: skipping changes the render
     no_fs = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC)
     assert np.abs(no_fs.rgb - ref.rgb).max() > 1e-3

@@ -9,7 +9,8 @@ import torch
 
 import oracle
 import synth
-from helpers import FLOOR_FINE_GRAD, NORM_RTOL_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from helpers import (BOUND_FP32, NORM_RTOL_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, assert_within_bound,
+                     mlp_flat, oracle_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -258,12 +259,12 @@ def test_fine_160cube_8192rays_sampled():
     o2, d2, j2 = o[:192].copy(), d[:192].copy(), jit[:192].copy()
     gC = np.random.default_rng(8).normal(scale=1e-2, size=(192, 3))
     g2 = _run_fine(p, res, dens, feat, mlp, o2, d2, j2, gC, np.zeros(192))
-    ref2 = oracle.render(P, dens, feat, o2, d2, jitter=j2, mlp=mlp, grad_rgb=gC)
+    ref2 = oracle.render(P, dens, feat, o2, d2, jitter=j2, mlp=mlp, grad_rgb=gC, error_bound=BOUND_FP32)
     assert_close(g2["rgb"], ref2.rgb, RTOL_COLOUR, "rgb_sub")
-    ref_m = np.concatenate([ref2.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
-    for name, got_g, ref_g in (("grad_density", g2["g_d"], ref2.grads["density"]),
-                               ("grad_feat", g2["g_f"], ref2.grads["cgrid"]), ("grad_mlp", g2["g_m"], ref_m)):
-        _, rel2 = assert_close(got_g, ref_g, RTOL_GRAD, name, floor=FLOOR_FINE_GRAD)
+    for name, got_g, ref_g, bnd in (("grad_density", g2["g_d"], ref2.grads["density"], ref2.bounds["density"]),
+                                    ("grad_feat", g2["g_f"], ref2.grads["cgrid"], ref2.bounds["cgrid"]),
+                                    ("grad_mlp", g2["g_m"], mlp_flat(ref2.grads), mlp_flat(ref2.bounds))):
+        _, rel2 = assert_within_bound(got_g, ref_g, bnd, name)
         assert rel2 <= NORM_RTOL_GRAD, f"{name}: relative L2 {rel2:.3g}"
     assert len(sub) == 48
 

@@ -21,7 +21,7 @@ import torch
 
 import oracle
 import synth
-from helpers import FLOOR_FINE_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from helpers import BOUND_BF16_OPERANDS, BOUND_FP32, RTOL_COLOUR, assert_close, assert_within_bound, oracle_params
 from test_gpu_parity import _counts, _mlp_flat, cuda
 
 pytestmark = pytest.mark.gpu
@@ -85,16 +85,16 @@ def test_pe_x_fp32_mlp_parity(feat_dtype):
     got = _run(p, res, dens, feat, mlp, o, d, jit, gC, gT, feat_dtype)
     P = oracle_params(p, (res,) * 3, 12)
     assert P.in_dim == IN72
-    ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, grad_tfinal=gT)
+    ref = oracle.render(P, dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC, grad_tfinal=gT, error_bound=BOUND_FP32)
     np.testing.assert_array_equal(got["counts"], ref.n_samples)
     assert got["total"] % 64 != 0 and got["total"] > 64 * 10
     assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
-    assert_close(got["g_d"], ref.grads["density"], RTOL_GRAD, "grad_density", floor=FLOOR_FINE_GRAD)
-    assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
-    ref_m, off = _ref_flat(ref), 0
+    assert_within_bound(got["g_d"], ref.grads["density"], ref.bounds["density"], "grad_density")
+    assert_within_bound(got["g_f"], ref.grads["cgrid"], ref.bounds["cgrid"], "grad_feat")
+    off = 0
     for k in MLP_KEYS:
         n = mlp[k].size
-        assert_close(got["g_m"][off:off + n], ref_m[off:off + n], RTOL_GRAD, f"grad_{k}", floor=FLOOR_FINE_GRAD)
+        assert_within_bound(got["g_m"][off:off + n], ref.grads[k], ref.bounds[k], f"grad_{k}")
         off += n
 
 
@@ -158,13 +158,14 @@ def test_pe_x_explicit_samples(prec):
     dts = np.diff(np.concatenate([ts, ts[:, -1:] + 0.01], axis=1), axis=1).astype(np.float32)
     gC = g.normal(scale=1e-2, size=(R, 3))
     got = _run(p, res, dens, feat, mlp, o, d, None, gC, None, samples=(ts, dts))
-    ref = oracle.render(P, dens, feat, o, d, mlp=mlp, explicit_t=ts, explicit_dt=dts, grad_rgb=gC)
-    if prec == dvgo.DVGO_MLP_BF16:
-        ref = oracle.render(P, dens, feat, o, d, mlp=_bf16_operands(mlp), explicit_t=ts, explicit_dt=dts, grad_rgb=gC)
-    if prec == dvgo.DVGO_MLP_FP32:
+    bf = prec == dvgo.DVGO_MLP_BF16
+    ref = oracle.render(oracle_params(p, (res,) * 3, 12, bf16_operands=bf), dens, feat, o, d,
+                        mlp=_bf16_operands(mlp) if bf else mlp, explicit_t=ts, explicit_dt=dts, grad_rgb=gC,
+                        error_bound=BOUND_BF16_OPERANDS if bf else BOUND_FP32)
+    assert_within_bound(got["g_f"], ref.grads["cgrid"], ref.bounds["cgrid"], "grad_feat")
+    assert_within_bound(got["g_m"][:IN72 * 128], ref.grads["w1"], ref.bounds["w1"], "grad_w1")
+    if not bf:
         assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
-        assert_close(got["g_f"], ref.grads["cgrid"], RTOL_GRAD, "grad_feat", floor=FLOOR_FINE_GRAD)
-        assert_close(got["g_m"][:IN72 * 128], ref.grads["w1"].reshape(-1), RTOL_GRAD, "grad_w1", floor=FLOOR_FINE_GRAD)
     else:
         errs = {"rgb_max_abs": float(np.abs(got["rgb"] - ref.rgb).max()),
                 "grad_feat_rel_l2": _rel_l2(got["g_f"], ref.grads["cgrid"]),

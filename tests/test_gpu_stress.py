@@ -8,7 +8,8 @@ import torch
 
 import oracle
 import synth
-from helpers import FLOOR_FINE_GRAD, NORM_RTOL_GRAD, RTOL_COLOUR, RTOL_GRAD, assert_close, oracle_params
+from helpers import (BOUND_FP32, NORM_RTOL_GRAD, RTOL_COLOUR, assert_close, assert_within_bound, mlp_flat,
+                     oracle_params)
 from test_gpu_parity import _mlp_flat, _run_fine
 
 pytestmark = pytest.mark.gpu
@@ -66,10 +67,11 @@ def test_stress_gradients_fp32(scene):
     p = _params(dvgo.DVGO_MLP_FP32)
     gC = np.random.default_rng(6).normal(scale=1e-2, size=(R, 3))
     got = _run_fine(p, RES, dens, feat, mlp, o, d, jit, gC, np.zeros(R))
-    ref = oracle.render(oracle_params(p, (RES,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC)
+    ref = oracle.render(oracle_params(p, (RES,) * 3, 12), dens, feat, o, d, jitter=jit, mlp=mlp, grad_rgb=gC,
+                        error_bound=BOUND_FP32)
     assert_close(got["rgb"], ref.rgb, RTOL_COLOUR, "rgb")
-    ref_m = np.concatenate([ref.grads[k].reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
-    for name, g, r in (("grad_density", got["g_d"], ref.grads["density"]), ("grad_feat", got["g_f"], ref.grads["cgrid"]),
-                       ("grad_mlp", got["g_m"], ref_m)):
-        _, rel2 = assert_close(g, r, RTOL_GRAD, name, floor=FLOOR_FINE_GRAD)
+    for name, g, r, b in (("grad_density", got["g_d"], ref.grads["density"], ref.bounds["density"]),
+                          ("grad_feat", got["g_f"], ref.grads["cgrid"], ref.bounds["cgrid"]),
+                          ("grad_mlp", got["g_m"], mlp_flat(ref.grads), mlp_flat(ref.bounds))):
+        _, rel2 = assert_within_bound(g, r, b, name)
         assert rel2 <= NORM_RTOL_GRAD, (name, rel2)

@@ -21,11 +21,11 @@ def _coarse_params(res=4, **kw):
 
 
 # ------------------------------------------------------------------------------------------
-# Low-density initialisation (Sec. 4.1 Eq. low_density_init, Supp. D)
+# Low-density initialisation (Sec. 4.1 Eq. low_density_init, Supp. F)
 # ------------------------------------------------------------------------------------------
 
 def test_shift_b_closed_form_values():
-    # Supp. D: with all raw densities 0, passing a distance s decays transmittance by 1 - alpha_init.
+    # Supp. F: with all raw densities 0, passing a distance s decays transmittance by 1 - alpha_init.
     for a_init, s in [(1e-6, 0.0625), (1e-2, 2 / 160), (0.3, 0.5)]:
         b = oracle.shift_from_alpha_init(a_init, s)
         sigma = math.log1p(math.exp(b))
@@ -133,20 +133,20 @@ def test_trilinear_hits_lattice_values():
 
 
 # ------------------------------------------------------------------------------------------
-# Post-activation worked examples (Supp. E)
+# Post-activation worked examples (Supp. G)
 # ------------------------------------------------------------------------------------------
 
 EPS, DELTA_RENDER = 1e-4, 0.5
 
 
 def _a_upper(c, Dl, eps=EPS, delta=DELTA_RENDER):
-    # Supp. E.1, Eq. 1d_a_upper_bound, branch delta < 1
+    # Supp. G.1, Eq. 1d_a_upper_bound, branch delta < 1
     return (math.log(2 ** (1 / delta) - 1) * (c + Dl) / Dl
             - math.log(1 / eps ** (1 / delta) - 1) * c / Dl)
 
 
 def _b_of_a(a, c, delta=DELTA_RENDER):
-    # Supp. E.1, Eq. 1d_b_linear_to_a
+    # Supp. G.1, Eq. 1d_b_linear_to_a
     return a * (c - 1) / c + math.log(2 ** (1 / delta) - 1) / c
 
 
@@ -216,7 +216,7 @@ def test_constant_grid_closed_form(x0, b):
     o, d = synth.sphere_rays(64, seed=3, jitter_sd=0.3)
     p = synth.jitter(64, 4)
     r = oracle.render(P, dens, rgb, o, d, jitter=p)
-    alpha = 1 - (1 + math.exp(x0 + b)) ** (-delta)   # Supp. E, Eq. supp_post_activation
+    alpha = 1 - (1 + math.exp(x0 + b)) ** (-delta)   # Supp. G, Eq. supp_post_activation
     for i in range(64):
         K = r.n_samples[i]
         T = (1 - alpha) ** K

@@ -64,6 +64,23 @@ def test_no_alloc_forward_matches_workspace_forward_twice():
             assert_close(g.cpu().numpy(), r.cpu().numpy(), RTOL_COLOUR, name)
 
 
+def test_no_alloc_at_capacity_matches_workspace_forward():
+    """A batch of exactly DVGO_NOALLOC_MAX_RAYS rays fits the static scratch (every block of the
+    coarse workspace layout for that many rays, the unused target block included)."""
+    R = dvgo.binding.DVGO_NOALLOC_MAX_RAYS
+    case = synth.coarse_case(seed=42, res=16, n_rays=R)
+    dd, cd = dvgo.GridDesc((16,) * 3, 1), dvgo.GridDesc((16,) * 3, 3)
+    p = dvgo.Params(mode=dvgo.DVGO_MODE_COARSE, step=0.0625, shift_b=0.1, bg=(1.0, 1.0, 1.0))
+    assert dvgo.dvgo_workspace_size(p, dd, R) <= dvgo.binding.DVGO_NOALLOC_SCRATCH_BYTES
+    args = (_dev(case["density"]), _dev(case["rgb"]), _dev(case["rays_o"]), _dev(case["rays_d"]),
+            _dev(synth.jitter(R, 4)), _dev(case["target"]))
+    ref = _with_workspace(p, dd, cd, *args)
+    got = _no_alloc(p, dd, cd, *args)
+    torch.cuda.synchronize()
+    for name, g, r in zip(("rgb", "tfinal", "loss", "dloss"), got, ref):
+        assert_close(g.cpu().numpy(), r.cpu().numpy(), RTOL_COLOUR, name)
+
+
 def test_no_alloc_rejects_batches_above_capacity():
     res = 8
     dd, cd = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 3)
