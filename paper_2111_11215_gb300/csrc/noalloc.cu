@@ -21,10 +21,13 @@ namespace dvgo {
 
 namespace {
 
-// Workspace of a coarse forward of up to DVGO_NOALLOC_MAX_RAYS rays: header + per-ray records +
-// per-ray outputs, each block 256-byte aligned (the layout of ws_layout()).
+// Workspace of a coarse forward of up to DVGO_NOALLOC_MAX_RAYS rays, block for block as ws_layout()
+// lays it out (each block 256-byte aligned): header, per-ray records, per-ray outputs and the
+// per-ray target block.  This forward never writes the target block (it rejects the auxiliary
+// losses), but the workspace check counts it, so the array holds it too.
 constexpr size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kNoallocScratchBytes = up256(sizeof(WsHeader)) + up256(sizeof(RayRec) * DVGO_NOALLOC_MAX_RAYS) +
+                                        up256(sizeof(float4) * DVGO_NOALLOC_MAX_RAYS) +
                                         up256(sizeof(float4) * DVGO_NOALLOC_MAX_RAYS);
 static_assert(kNoallocScratchBytes == DVGO_NOALLOC_SCRATCH_BYTES, "scratch size in dvgo.h");
 
@@ -59,6 +62,7 @@ extern "C" int dvgo_render_fwd_noalloc(const dvgo_params *p, const dvgo_grid_des
     if (!p || p->mode != DVGO_MODE_COARSE) return DVGO_ERR_UNSUPPORTED;
     if (p->w_pt_rgb != 0.0f || p->w_bg != 0.0f) return DVGO_ERR_UNSUPPORTED;   // no room for the targets
     if (n_rays > DVGO_NOALLOC_MAX_RAYS) return DVGO_ERR_CAPACITY;
+    if (dvgo::ws_layout(n_rays, 0, DVGO_MODE_COARSE).total > dvgo::kNoallocScratchBytes) return DVGO_ERR_CAPACITY;
     void *scratch = nullptr;
     int st = dvgo::scratch_address(&scratch);
     if (st != DVGO_OK) return st;

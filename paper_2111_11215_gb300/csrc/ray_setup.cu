@@ -175,8 +175,10 @@ WsLayout ws_layout(int R, long long max_samples, int mode) {
     } else {
         L.samp = L.sgrad = L.kept = 0;
     }
-    L.rtarget = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));   // last: the allocation-free
-    L.total = o;                                                       // forward does not reach it
+    // last; counted in total, so the allocation-free forward's static scratch includes it even
+    // though that forward (no auxiliary losses) never writes it
+    L.rtarget = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));
+    L.total = o;
     L.max_samples = max_samples;
     return L;
 }
