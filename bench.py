@@ -196,33 +196,37 @@ class OracleStep:
         self.oracle.adam(p, g, m, v, 0.1, self.t, zero_grad=False)
         t_adam = (time.perf_counter() - t1) * self.n_par / self.n_adam
         step_s = t_render * self.batch_rays / n + t_adam
+        whole = n == self.batch_rays and self.n_adam == self.n_par
         return {"value": self.batch_rays / step_s, "unit": "rays/s", "cores": self.oracle.num_threads(),
                 "kind": "oracle", "step_s": step_s,
                 "sample": f"{n} of {self.batch_rays} rays of one batch, fwd+bwd ({t_render:.2f} s), plus one Adam "
-                          f"sweep over {self.n_adam} of the {self.n_par} parameters (projected: {t_adam:.2f} s), "
-                          f"projected to a full step"}
+                          f"sweep over {self.n_adam} of the {self.n_par} parameters ({t_adam:.2f} s)"
+                          + ("" if whole else ", projected to a full step")}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle on the host cores, rank 0 only."""
+    """--impl reference: the FP64 oracle on the host cores, rank 0 only.  Each step is the whole
+    step of the plain form: forward + backward of all args.ref_rays (default: all 8192) rays of a
+    batch and one Adam sweep over every parameter, so ms_per_step is the measured time of a step."""
     if rank != 0:
         return
     dens, feat, mlp, batches = workload()
-    # per step: args.ref_rays rays fwd + bwd and an Adam sweep timed on 2 M parameters, both
-    # projected -- ~0.15 s of CPU work, so even a long --steps run ends within minutes
-    ostep = OracleStep(dens, feat, mlp, adam_sample=2_000_000)
+    ostep = OracleStep(dens, feat, mlp, batch_rays=args.ref_rays)
     vals = []
     for i in range(args.warmup + args.steps):
         r = ostep.run(batches[i % N_BATCHES], args.ref_rays)
         if i >= args.warmup:
             vals.append(r)
-    value = statistics.median(v["value"] for v in vals)
+    step_s = statistics.median(v["step_s"] for v in vals)
+    total_s = sum(v["step_s"] for v in vals)
+    value = args.ref_rays * len(vals) / total_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": NRAYS / value * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, "plain"),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / len(vals) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, "plain") | {"global_batch": args.ref_rays},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+                             "sample": f"every step whole: {args.ref_rays} rays fwd + bwd and one Adam sweep over all "
+                                       f"{ostep.n_par} parameters (median step {step_s:.2f} s)"},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -296,18 +300,15 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     torch.cuda.synchronize()
     assert np.isfinite(form.model.loss.item())
 
+    # the timed region: per-kernel profiling off
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    dvgo.dvgo_profile_enable(True)
-    for k in dvgo.KERNEL_KINDS:
-        dvgo.dvgo_profile_read(k)
     launches0 = dvgo.dvgo_launch_counter()
     clocks = ClockSampler(local_rank)
     clocks.start()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_first = form.trainer.i if form.trainer is not None else 0
     e0.record(s)
     for i in range(args.steps):
         form.step(dbatches[i % N_BATCHES])
@@ -316,10 +317,25 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = dvgo.dvgo_launch_counter() - launches0
-    dvgo.dvgo_profile_enable(False)
-    per_kind = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     value = whole_job_rate(NRAYS * args.steps, world, ms)
+
+    # a separate pass of the same number of steps with per-kernel CUDA-event timing switched on
+    # (each launch bracketed by events on its own stream): where the step's time goes
+    prof_steps = max(args.steps, 20)
+    t_first = form.trainer.i if form.trainer is not None else 0
+    n_prop_train0 = form.trainer.n_uniform if form.trainer is not None else 0
+    torch.cuda.synchronize()
+    dvgo.dvgo_profile_enable(True)
+    for k in dvgo.KERNEL_KINDS:
+        dvgo.dvgo_profile_read(k)
+    for i in range(prof_steps):
+        form.step(dbatches[i % N_BATCHES])
+    form.finish()
+    torch.cuda.synchronize()
+    dvgo.dvgo_profile_enable(False)
+    per_kind = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
+    n_prop_train = (form.trainer.n_uniform - n_prop_train0) if form.trainer is not None else 0
 
     # end to end through the public API with host buffers: H2D of each step's rays / jitter /
     # targets from pinned memory, the step, and a D2H read of its loss
@@ -345,22 +361,30 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     e2e_ms = max_over_ranks(max(e2.elapsed_time(e3), (time.perf_counter() - t_host0) * 1e3), world, dev)
     assert np.all(np.isfinite(loss_host.numpy()))
 
-    # units processed per launch of the colour kernels (uniform and proposal steps of the timed region)
+    # units processed per launch of the colour kernels (uniform and proposal steps of the profiled pass)
     if name == "plain":
         fwd_units = bwd_units = dense_samples
     else:
         expl = hit_rays * N_PROP_SAMPLES
-        n_dense = sum(form.trainer.is_uniform(i) for i in range(t_first, t_first + args.steps))
-        fwd_units = bwd_units = ((args.steps - n_dense) * expl + n_dense * dense_samples) / args.steps
+        n_dense = sum(form.trainer.is_uniform(i) for i in range(t_first, t_first + prof_steps))
+        fwd_units = bwd_units = ((prof_steps - n_dense) * expl + n_dense * dense_samples) / prof_steps
+    # algorithmic bytes of every Adam launch of the profiled pass: per step the density, feature and
+    # MLP sweeps (32 B per parameter, + the 2-byte BF16 feature copy), plus one proposal Adam per
+    # proposal training step (chosen form)
+    prop_params = int(form.trainer.proposal.flat.numel()) if form.trainer is not None else 0
+    adam_bytes = prof_steps * adam_step_bytes(name == "chosen") + n_prop_train * 32 * prop_params
     dom_name, (dom_ms, dom_n) = max(per_kind.items(), key=lambda kv: kv[1][0])
-    roof = roofline(dom_name, dom_ms / max(dom_n, 1), fwd_units, bwd_units, name == "chosen", peaks)
+    roof = roofline(dom_name, dom_ms, dom_n, fwd_units, bwd_units, name == "chosen", peaks, adam_bytes,
+                    (prof_steps, adam_step_bytes(name == "chosen")))
     step_roof = step_hbm_minimum(form, dbatches[0], ms / args.steps, dvgo, torch, peaks)
     return {"value": value, "ms_per_step": ms / args.steps, "dtype": "bf16" if name == "chosen" else "f32",
             "config": workload_config(args, name) | {"dense_samples_per_batch": dense_samples,
                                                      "hit_rays_per_batch": hit_rays,
                                                      "samples_per_hit_ray": N_PROP_SAMPLES if name == "chosen" else None},
             "roofline": roof, "step_roofline": step_roof,
-            "kernels_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in per_kind.items() if v[1]},
+            "kernels_ms_per_step": {k: round(v[0] / prof_steps, 4) for k, v in per_kind.items() if v[1]},
+            "kernels_timing": f"a separate pass of {prof_steps} steps with per-launch CUDA events; the timed region "
+                              f"runs without them",
             "e2e": {"value": whole_job_rate(NRAYS * args.steps, world, e2e_ms), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": clk}
@@ -399,8 +423,19 @@ def step_hbm_minimum(form, batch, ms_per_step, dvgo, torch, peaks):
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
 
 
-def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
+def adam_step_bytes(chosen):
+    """Algorithmic bytes of one step's Adam sweeps: 32 B per parameter (read p, g, m, v; write p, m,
+    v and the zeroed g) and, in the chosen form, the 2-byte BF16 copy of each feature."""
+    return n_params() * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
+
+
+def roofline(kind, total_ms, launches, fwd_units, bwd_units, chosen, peaks, adam_bytes=None,
+             adam_step_launch_bytes=None):
+    """The dominant kernel against its roofline: achieved = algorithmic work per launch / average
+    launch time (CUDA events), i.e. the work of all its launches over their summed time."""
     hbm = peaks.get("hbm_gbs")
+    launches = max(int(launches), 1)
+    avg_ms = total_ms / launches
     if kind in ("fine_colour_bwd", "fine_colour_fwd"):
         units = bwd_units if kind == "fine_colour_bwd" else fwd_units
         flop = units * (mlp_fwd_flop() + (mlp_bwd_flop() if kind == "fine_colour_bwd" else 0))
@@ -409,19 +444,29 @@ def roofline(kind, avg_ms, fwd_units, bwd_units, chosen, peaks):
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
             return {"bound": "tensor", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen), "units_per_launch": units,
+                    "flop_per_launch": flop, "ms_per_launch": avg_ms, "launches": launches,
                     "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         return {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen), "units_per_launch": units,
+                "flop_per_launch": flop, "ms_per_launch": avg_ms, "launches": launches,
                 "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz"}
     if kind == "adam":
-        # three launches per step (density, features, MLP); per-launch average of the step's bytes
-        byts = n_params() * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
-        achieved = byts / 3.0 / (avg_ms * 1e-3) / 1e9
+        byts = adam_bytes / launches
+        achieved = byts / (avg_ms * 1e-3) / 1e9
         peak = hbm or 6800.0
+        # the ncu summary gives the DRAM bytes per launch averaged over one step's three grid / MLP
+        # launches; the proposal's small launches (chosen form) are counted at their algorithmic bytes
+        tr = traffic_from_profiles(kind, chosen)
+        if tr is not None and adam_step_launch_bytes is not None:
+            n_step, step_b = adam_step_launch_bytes
+            tr = (tr * 3 * n_step + (adam_bytes - n_step * step_b)) / launches
         return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_from_profiles(kind, chosen),
-                "algorithmic_bytes_per_launch": byts / 3.0, "peak_source": "measured" if hbm else "fallback"}
+                "frac": achieved / peak, "traffic": tr,
+                "algorithmic_bytes_per_launch": byts, "ms_per_launch": avg_ms, "launches": launches,
+                "note": "launches of the density, feature-grid and MLP sweeps of every step (and of the "
+                        "proposal's, chosen form) averaged: their bytes over their summed time",
+                "peak_source": "measured" if hbm else "fallback"}
     return {"bound": "hbm", "kernel": kind, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
             "traffic": None}
 
@@ -492,6 +537,10 @@ def proposal_eval(dev, dens, feat, mlp, dvgo, torch, n_train=400):
 
 
 def run_time_to_psnr(args):
+    print(json.dumps(time_to_psnr(args)), flush=True)
+
+
+def time_to_psnr(args):
     """Full per-scene optimisation on the analytic 20-primitive scene: ground truth for 100 training and
     20 held-out 800x800 views, coarse stage (100^3 density + RGB, 5k steps), fine stage (160^3 density
     + 12-channel features + MLP, 20k steps, Adam 0.1 / 1e-3 with the decay of Supp. A, 8192 rays per
@@ -739,7 +788,42 @@ def run_time_to_psnr(args):
     if "chosen" in results and "plain" in results:
         line["chosen_minus_plain_final_psnr_db"] = (results["chosen"]["final_psnr_20views"]
                                                     - results["plain"]["final_psnr_20views"])
-    print(json.dumps(line), flush=True)
+    return line
+
+
+# the recipe of the time-to-PSNR entry of the default line: the paper's whole fine stage (Sec. 4.2,
+# Supp. A) -- fine density from raw 0 at alpha_init^(f) = 1e-2, known free space of the coarse grid
+# (tau_c = 1e-3) and the fine box from it, tau_f = 1e-4, the auxiliary losses, the 72-input MLP with
+# PE(x, 5), progressive scaling at 1k / 2k / 3k steps
+PAPER_RECIPE = {"fine_recipe": "paper", "aux_losses": True, "pe_x": True, "pg_ckpt": "1000,2000,3000",
+                "fine_init": "auto", "act_order": "post", "prior2": False, "lazy_adam": False, "pg_adam": "reset",
+                "ttp_forms": "plain,chosen", "no_cpu_baseline": True}
+
+
+def time_to_psnr_summary(args):
+    """Both forms' wall time to the frozen PSNR target on the analytic scene with the paper's recipe
+    (the second half of the benchmark's metric), for the default line."""
+    ns = argparse.Namespace(**(vars(args) | PAPER_RECIPE))
+    t0 = time.perf_counter()
+    r = time_to_psnr(ns)
+    wall = time.perf_counter() - t0
+    f = r["forms"]
+    return {"unit": "s", "higher_is_better": False, "target_psnr_db": r["psnr_target"],
+            "plain_s": f["plain"]["secs_to_target"], "chosen_s": f["chosen"]["secs_to_target"],
+            "plain_steps_to_target": f["plain"]["steps_to_target"],
+            "chosen_steps_to_target": f["chosen"]["steps_to_target"],
+            "final_psnr_20views_db": {"plain": f["plain"]["final_psnr_20views"],
+                                      "chosen": f["chosen"]["final_psnr_20views"]},
+            "chosen_minus_plain_db": r["chosen_minus_plain_final_psnr_db"],
+            "ms_per_step": {"plain": f["plain"]["ms_per_step"], "chosen": f["chosen"]["ms_per_step"]},
+            "fine_steps": r["fine_steps"], "coarse_steps": r["coarse_steps"], "coarse_s": r["coarse_s"],
+            "ground_truth_render_s": r["ground_truth_render_s"], "wall_s": wall,
+            "timing": "fine-stage training time (CUDA events); evaluation (held-out PSNR on 2 views every "
+                      f"{r['eval_every']} steps with the uniform FP32 renderer) excluded",
+            "recipe": "paper: " + r["fine_recipe"]["name"] + ", auxiliary losses, 72-input MLP with PE(x, 5), "
+                      "progressive scaling at " + ",".join(str(c) for c in r["progressive"]["pg_ckpt"]),
+            "fine_grids": r["progressive"]["grids"], "data": r["data"],
+            "curves": {k: [(c["step"], c["train_s"], c["psnr"]) for c in v["curve"]] for k, v in f.items()}}
 
 
 def run_stress(args):
@@ -1025,11 +1109,21 @@ def run_ours(args, rank, world, local_rank):
     head = res["chosen" if "chosen" in res else forms[0]]
     line = {"metric": METRIC, "value": head["value"], "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic", "config": head["config"],
+            "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic", "config": head["config"]}
+    if "plain" in res and head is not res["plain"]:
+        pl = res["plain"]
+        line["plain"] = {"value": pl["value"], "unit": "rays/s", "ms_per_step": pl["ms_per_step"], "dtype": pl["dtype"],
+                         "e2e": pl["e2e"]["value"], "roofline_frac": pl["roofline"]["frac"],
+                         "roofline_kernel": pl["roofline"]["kernel"]}
+    if not args.no_time_to_psnr and world == 1:
+        line["time_to_psnr"] = None        # filled in below; placed early so that a cut tail keeps it
+    line.update({
             "roofline": head["roofline"], "step_roofline": head["step_roofline"],
             "kernels_ms_per_step": head["kernels_ms_per_step"], "e2e": head["e2e"],
-            "gpu_launches": sum(r["gpu_launches"] for r in res.values()), "clocks": head["clocks"],
-            "forms": res}
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "forms": res})
+    if not args.no_time_to_psnr and world == 1:
+        line["time_to_psnr"] = time_to_psnr_summary(args)
     if not args.no_proposal_eval and world == 1:
         line["proposal_eval"] = proposal_eval(dev, dens, feat, mlp, dvgo, torch)
     if not args.no_cpu_baseline and world == 1:
@@ -1053,9 +1147,11 @@ def main():
     ap.add_argument("--form", choices=["both", "plain", "chosen"], default="both")
     ap.add_argument("--cpu-rays", type=int, default=8192, help="rays of the oracle's CPU baseline sample")
     ap.add_argument("--cpu-reps", type=int, default=3, help="repetitions of the oracle's CPU baseline sample")
-    ap.add_argument("--ref-rays", type=int, default=256, help="--impl reference: rays per oracle step")
+    ap.add_argument("--ref-rays", type=int, default=NRAYS, help="--impl reference: rays per oracle step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposal-eval", action="store_true")
+    ap.add_argument("--no-time-to-psnr", action="store_true",
+                    help="step workload: leave out the time-to-PSNR run of both forms (paper recipe) from the line")
     ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d", "view-counts"],
                     default="step")
     ap.add_argument("--vc-res", type=int, default=100, help="view-counts: lattice points per axis")
