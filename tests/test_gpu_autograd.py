@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 
 dvgo = pytest.importorskip("paper_2111_11215_gb300")
 
-RES, R = 8, 24
+RES, R = 8, 160
 MLP_KEYS = ("w1", "b1", "w2", "b2", "w3", "b3")
 
 
@@ -35,9 +35,11 @@ def _case():
     dens, feat, mlp, o, d, jit, _ = _fine_inputs(RES, R, seed=70, value=6.0, n_spheres=3)
     p = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=2.0 / RES * 0.5, bg=(1.0, 1.0, 1.0),
                     shift_b=dvgo.dvgo_shift_from_alpha_init(1e-2, 2.0 / RES))
+    # loss weights of one sign, so that the rays' contributions add up and the gradients stand well
+    # above the FP32 rounding of the forward that the finite differences see
     g = np.random.default_rng(71)
-    A = g.normal(size=(R, 3))
-    b = g.normal(size=R)
+    A = g.uniform(0.5, 1.5, size=(R, 3))
+    b = g.uniform(0.5, 1.5, size=R)
     return p, dens, feat, mlp, o, d, jit, A, b
 
 
@@ -84,7 +86,7 @@ def test_render_function_backward_matches_oracle_and_finite_differences():
     off = 0
     for k in MLP_KEYS:
         n = mlp[k].size
-        checks.append((k, M0, off, n, 1e-3))
+        checks.append((k, M0, off, n, 3e-3))
         off += n
     flat_grad = {"density": got["density"].reshape(-1), "cgrid": got["cgrid"].reshape(-1), "mlp": got["mlp"]}
     for name, base, start, n, h in checks:
@@ -103,6 +105,8 @@ def test_render_function_backward_matches_oracle_and_finite_differences():
             args_p[slot], args_m[slot] = plus, minus
             fd = (loss_at(*args_p) - loss_at(*args_m)) / (2 * h)
             an = flat_grad[key][i]
+            # central differences of an FP32 forward: truncation O(h^2) and the FP32 rounding of
+            # the loss (~1e-7 of it) over 2h; a wrong tensor, sign or scale is off by far more
             assert abs(fd - an) <= 2e-2 * abs(an) + 2e-3 * scale, (name, int(i), fd, an)
 
 

@@ -72,11 +72,12 @@ def test_bounded_wait_runs_out_reports_and_leaves_the_context_usable():
     # the next clean forward clears the flag, and a clean backward gives the clean gradients
     again = _step(dvgo.Renderer(p, dd, cd, R), t)
     for k in ("g_d", "g_f", "g_m"):
-        torch.testing.assert_close(again[k], ref[k], rtol=1e-5, atol=1e-7 * float(ref[k].abs().max()))
+        # (FP32 atomics add in a different order from run to run)
+        torch.testing.assert_close(again[k], ref[k], rtol=1e-4, atol=1e-5 * float(ref[k].abs().max()))
     faulty.params = p
     reuse = _step(faulty, t)
     assert dvgo.dvgo_workspace_status(faulty.workspace) == 0
-    torch.testing.assert_close(reuse["g_m"], ref["g_m"], rtol=1e-5, atol=1e-7 * float(ref["g_m"].abs().max()))
+    torch.testing.assert_close(reuse["g_m"], ref["g_m"], rtol=1e-4, atol=1e-5 * float(ref["g_m"].abs().max()))
 
 
 def test_bounded_wait_in_the_forward_colour_kernel():
