@@ -25,6 +25,8 @@
  *   - Grids are channel-last on an align-corners lattice: value (ix, iy, iz, ch) of an
  *     nx*ny*nz*C grid is at ((ix*ny + iy)*nz + iz)*C + ch; lattice point (ix, iy, iz) sits at
  *     xyz_min + (ix, iy, iz) * (xyz_max - xyz_min) / (n - 1)   (Sec. 3 Eq. interp).
+ *     The render calls read the colour / feature grid with 16-byte loads: its pointer must be
+ *     16-byte aligned (DVGO_ERR_INVALID_ARG otherwise).
  */
 #ifndef DVGO_H
 #define DVGO_H

@@ -80,6 +80,7 @@ int check_common(const dvgo_params *p, const dvgo_grid_desc *dd, const float *de
                  const void *cgrid, const dvgo_mlp *mlp, int R, const float *ro, const float *rd,
                  const dvgo_samples *ex) {
     if (!p || !dd || !cd || !density || !cgrid || R < 0) return DVGO_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(cgrid) & 15u) != 0) return DVGO_ERR_INVALID_ARG;   // 16-byte loads
     if (R > 0 && (!ro || !rd)) return DVGO_ERR_INVALID_ARG;
     if (!grid_ok(dd) || !grid_ok(cd) || dd->channels != 1 || dd->dtype != DVGO_DTYPE_F32) return DVGO_ERR_INVALID_ARG;
     if (!same_lattice(dd, cd)) return DVGO_ERR_INVALID_ARG;

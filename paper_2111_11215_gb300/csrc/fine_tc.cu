@@ -68,12 +68,13 @@ struct TcDims {
     static constexpr int NTAIL = IN - NMAIN;                  // 0 or 9
 };
 
-constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_DH2 = 0, COL_Z2 = 128, COL_DW2T = 256, COL_DW1 = 400, COL_DW3 = 464,
+constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_Z2 = 128, COL_DW2T = 256, COL_DW1 = 400, COL_DW3 = 464,
                    COL_DE = 480, COL_DW1T = 496;
 
 // Small per-CTA state, padded to a multiple of 1024 bytes so that the panels after it stay
 // aligned to the 128-byte-swizzle atom.
 struct alignas(1024) SmallTC {
+    float4 w3[HID];           // W3 row per hidden unit (3 used), BF16-rounded: dH2 = dout W3^T on the CUDA cores
     float b2[HID];
     float b3[4];
     float db3[4];
@@ -81,7 +82,7 @@ struct alignas(1024) SmallTC {
     int cbase[2][TM];         // flat index of the base lattice corner
     float frac[2][TM][3];     // fractional offsets
     float dc[2][TM][3];       // dL/dc (backward)
-    uint64_t full[2], empty[2], mma;
+    uint64_t full[2], empty[2], mma, mma1;   // mma1: the forward's second consumer group
     uint32_t tmem_base;
     int abort;
 };
@@ -148,9 +149,49 @@ __device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int 
     }
 }
 
-// Producer: gather sample row `row` of a tile into X panel b (and its tail) and the per-row tables.
+// The ray data a producer needs to place a sample, fetched a tile ahead: uniform steps, the first
+// sample and the per-step increment (fixed point); explicit samples, the entry point (fixed point),
+// the direction in lattice units (FP64 bits) and t_enter; and the ray's first sample slot.
+struct RayPre {
+    long long f0[3], f1[3];
+    double t_enter;
+    int off;
+};
+
+__device__ __forceinline__ RayPre ray_pre(const RenderArgs &A, int ray) {
+    RayPre p;
+    const RayRec &r = A.rays[ray];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p.f0[a] = A.ts ? r.uefx[a] : r.u0fx[a];
+        p.f1[a] = A.ts ? __double_as_longlong(r.e[a]) : r.dfx[a];
+    }
+    p.t_enter = A.ts ? r.t_enter : 0.0;
+    p.off = r.off;
+    return p;
+}
+
+// sample_cell() from prefetched ray data (the same arithmetic).
+__device__ __forceinline__ Cell cell_pre(const RenderArgs &A, const RayPre &p, int ray, int k, float &dt) {
+    long long u[3];
+    if (A.ts) {
+        const double t = (double)A.ts[(long long)ray * A.n_expl + k];
+        dt = A.dts[(long long)ray * A.n_expl + k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = p.f0[a] + to_fx((t - p.t_enter) * __longlong_as_double(p.f1[a]));
+    } else {
+        dt = A.step;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = p.f0[a] + (long long)k * p.f1[a];
+    }
+    return cell_from_fx(u, A.nx, A.ny, A.nz);
+}
+
+// Producer: gather sample row `row` of a tile (kept entry kv, kv.y < 0 for a padding row; its ray's
+// prefetched data rp) into X panel b (and its tail) and the per-row tables.
 template <typename FeatT, bool BWD, bool PEX, bool PK>
-__device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int e, int n_kept, int row) {
+__device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int2 kv, const RayPre &rp,
+                                            int row) {
     using D = TcDims<PEX>;
     float v[64], tail[16];
 #pragma unroll
@@ -159,11 +200,9 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
     for (int i = 0; i < 16; ++i) tail[i] = 0.0f;
     int slot = -1, cbase = 0;
     float fx = 0.0f, fy = 0.0f, fz = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
-    if (e < n_kept) {
-        const int2 kv = A.kept[e];
-        const RayRec &rr = A.rays[kv.y];
+    if (kv.y >= 0) {
         float dt;
-        const Cell c = sample_cell(A, rr, kv.y, kv.x - rr.off, dt);
+        const Cell c = cell_pre(A, rp, kv.y, kv.x - rp.off, dt);
         slot = kv.x;
         cbase = cell_base(c, A.ny, A.nz, PK);
         fx = c.fx;
@@ -196,6 +235,26 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
                     v[4 * k + 1] += w0 * a.y + w1 * bb.y;
                     v[4 * k + 2] += w0 * a.z + w1 * bb.z;
                     v[4 * k + 3] += w0 * a.w + w1 * bb.w;
+                }
+            } else if constexpr (!PK) {
+                // canonical BF16: the pair is 48 contiguous bytes at offset 0 or 8 mod 16 (the grid is
+                // 16-byte aligned, a point is 24 bytes): three aligned 16-byte loads from the pair's
+                // 16-byte granule and, at offset 8, one 8-byte load for its last word pair -- no byte
+                // outside the grid (at offset 8 the first 8 bytes loaded belong to the point before)
+                const uintptr_t ad = reinterpret_cast<uintptr_t>(g);
+                const uint4 *q = reinterpret_cast<const uint4 *>(ad & ~(uintptr_t)15);
+                const bool off8 = (ad & 15u) != 0u;
+                const uint4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+                const uint2 q3 = off8 ? __ldg(reinterpret_cast<const uint2 *>(q + 3)) : make_uint2(0u, 0u);
+                const uint32_t wd[14] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                                         q2.x, q2.y, q2.z, q2.w, q3.x, q3.y};
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {   // channels 2m, 2m + 1 of the corners z (word m) and z + 1
+                    uint32_t ua = off8 ? wd[m + 2] : wd[m], ub = off8 ? wd[m + 8] : wd[m + 6];
+                    const float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&ua));
+                    const float2 bz = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&ub));
+                    v[2 * m + 0] += w0 * a.x + w1 * bz.x;
+                    v[2 * m + 1] += w0 * a.y + w1 * bz.y;
                 }
             } else {
                 const uint2 *g2 = reinterpret_cast<const uint2 *>(g), *gz2 = reinterpret_cast<const uint2 *>(gz);
@@ -262,7 +321,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     extern __shared__ unsigned char smem_raw[];
     SmemTC &S = *reinterpret_cast<SmemTC *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
-    constexpr uint32_t NCOLS = BWD ? 512 : 256;
+    constexpr uint32_t NCOLS = 512;   // backward: activations + weight gradients; forward: 256 per consumer group
 
     if (tid == 0) {
         mbar_init(&S.sm.full[0], NP);
@@ -270,9 +329,15 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         mbar_init(&S.sm.empty[0], 1);
         mbar_init(&S.sm.empty[1], 1);
         mbar_init(&S.sm.mma, 1);
+        mbar_init(&S.sm.mma1, 1);
         S.sm.abort = 0;
     }
     if (warp == 0) tmem_alloc(&S.sm.tmem_base, NCOLS);
+    // barriers initialised and TMEM allocated: the producers start gathering the first tile while
+    // consumer warps 0-3 stage the weights (published to the consumers and the tensor core below)
+    fence_before();
+    __syncthreads();
+    fence_after();
     if (tid < TM) {
         // weights: row n = tid of W1^T (64 input columns, bias in column BIAS), of W2^T and of the
         // tail panel (W3, and with PE(x) the tail rows of W1)
@@ -292,8 +357,12 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         for (int k = 0; k < 64; ++k)
             v[k] = k < 3 ? A.w3[3 * tid + k]
                          : ((k >= 48 && k - 48 < D::NTAIL) ? A.w1[(D::NMAIN + k - 48) * HID + tid] : 0.0f);
-#pragma unroll
-        for (int c = 0; c < 64; c += 8) panel_store8(S.tp, tid, c, v + c);
+        // only the weight columns (0-15: W3, 48-63: W1 tail): columns 16-47 hold the X tails, which
+        // the producers are already writing
+        panel_store8(S.tp, tid, 0, v);
+        panel_store8(S.tp, tid, 8, v + 8);
+        panel_store8(S.tp, tid, 48, v + 48);
+        panel_store8(S.tp, tid, 56, v + 56);
         if (BWD) {
 #pragma unroll
             for (int k = 0; k < 64; ++k) v[k] = 0.0f;
@@ -301,13 +370,12 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             for (int c = 0; c < 64; c += 8) panel_store8(S.dout, tid, c, v + c);
         }
         S.sm.b2[tid] = A.b2[tid];
+        S.sm.w3[tid] = make_float4(bf16_round(A.w3[3 * tid]), bf16_round(A.w3[3 * tid + 1]),
+                                   bf16_round(A.w3[3 * tid + 2]), 0.0f);
         if (tid < 3) S.sm.b3[tid] = A.b3[tid];
         if (tid < 4) S.sm.db3[tid] = 0.0f;
     }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
+    if (tid < NC) consumer_publish();
 
     const int n_kept = A.hdr->n_kept;
     const int ntiles = (n_kept + TM - 1) / TM;
@@ -316,10 +384,22 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 
     if (tid >= NC) {
         // ------------------------------- producers -------------------------------
+        // Software-pipelined a tile deep: while producing a tile, a producer already has the next
+        // tile's kept entry and fetches that tile's ray data and the kept entry of the tile after, so
+        // that only the corner-feature loads of a tile wait on memory when it is produced.
         const int row = tid - NC;   // 0 .. NP-1
+        auto kept_at = [&](int t) -> int2 {
+            const int e = t * TM + row;
+            return (t < ntiles && e < n_kept) ? A.kept[e] : make_int2(-1, -1);
+        };
+        int2 kv_cur = kept_at(blockIdx.x);
+        RayPre rp_cur = kv_cur.y >= 0 ? ray_pre(A, kv_cur.y) : RayPre{};
+        int2 kv_next = kept_at(blockIdx.x + gridDim.x);
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int b = i & 1;
+            const RayPre rp_next = kv_next.y >= 0 ? ray_pre(A, kv_next.y) : RayPre{};
+            const int2 kv_after = kept_at(tile + 2 * gridDim.x);
             if (i >= 2) {
                 if (!mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1, A.wait_ns)) {
                     ok = false;
@@ -328,10 +408,13 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 if (BWD) scatter_row<PK>(A, S, b, row);   // feature gradients of tile i - 2
             }
             if (*(volatile int *)&S.sm.abort) break;
-            produce_row<FeatT, BWD, PEX, PK>(A, S, b, tile * TM + row, n_kept, row);
+            produce_row<FeatT, BWD, PEX, PK>(A, S, b, kv_cur, rp_cur, row);
             fence_async_smem();
             // (testing aid: one arrival withheld on a chosen tile makes the consumers' wait run out)
             if (!(row == 0 && tile + 1 == A.withhold_tile)) mbar_arrive(&S.sm.full[b]);
+            kv_cur = kv_next;
+            rp_cur = rp_next;
+            kv_next = kv_after;
         }
         if (BWD && ok) {
             // the last (up to) two tiles: wait until the consumers are done with them, then scatter
@@ -339,6 +422,106 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1, A.wait_ns)) ok = false;
                 else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, row);
             }
+        }
+        if (!ok) atomicExch(&S.sm.abort, 1);
+    } else if constexpr (!BWD) {
+        // --------------------------- forward consumers: two groups ---------------------------
+        // Group grp = warp / 4 takes every other tile of this CTA (the CTA's tiles i = grp, grp + 2,
+        // ..., so always X buffer grp), so that one group's epilogues run while the other group's
+        // MMAs do.  Thread r = tid % 128 owns row r (its TMEM lane) and all 128 columns; the group
+        // has its own 256 TMEM columns (Z1 and O at +0, Z2 at +128), its own H panel pair (h1 for
+        // group 0, h2 for group 1; H2 overwrites H1 once layer 2 has read it), MMA barrier and
+        // named barrier (2 + grp, 128 threads).
+        const int grp = warp >> 2, r = tid & (TM - 1);
+        const uint32_t tb = S.sm.tmem_base + 256u * (uint32_t)grp;
+        uint64_t *mbar = grp ? &S.sm.mma1 : &S.sm.mma;
+        unsigned char *hp = grp ? S.h2 : S.h1;
+        uint32_t mphase = 0;
+        auto wait_mma = [&]() -> bool {
+            bool w = mbar_wait(mbar, mphase, A.wait_ns);
+            mphase ^= 1;
+            fence_after();
+            return w;
+        };
+        auto group_sync = [&]() {
+            fence_before();
+            if (grp) asm volatile("bar.sync 3, 128;" ::: "memory");
+            else asm volatile("bar.sync 2, 128;" ::: "memory");
+            fence_after();
+        };
+        int i = grp;
+        for (int tile = blockIdx.x + grp * gridDim.x; tile < ntiles; tile += 2 * gridDim.x, i += 2) {
+            const int b = grp;
+            uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.tp);
+            uint32_t hp_ = smem_u32(hp);
+            asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(hp_));
+            // (no abort-flag test here: two warps of a group could read it on either side of its
+            // setting and part at the group barrier; a failed producer instead leaves this wait
+            // unsatisfied for every thread of the group alike)
+            if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
+            fence_after();
+            if (!ok) break;
+            const int slot = S.sm.slot[b][r];
+            // ---- layer 1: Z1 = X W1 ----
+            if (r == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tb + COL_Z1, desc_kmajor(x_, kk), desc_kmajor(w1t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                if (PEX)
+                    mma(tb + COL_Z1, desc_kmajor(w3p_, 1 + b), desc_kmajor(w3p_, 3), idesc_bf16(128, 128, 0, 0), 1u);
+                commit(mbar);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            if (r == 0) mbar_arrive(&S.sm.empty[b]);   // X[b] is free once layer 1 is done
+            // ---- epilogue 1: H1 = relu(Z1), all 128 columns of my row ----
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_Z1 + 32 * g), z);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k], 0.0f);
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) panel_store8(hp + (g >> 1) * kPanelBytes, r, 32 * (g & 1) + k, z + k);
+            }
+            fence_async_smem();
+            group_sync();
+            // ---- layer 2: Z2 = H1 W2 ----
+            if (r == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tb + COL_Z2, desc_kmajor(hp_, kk), desc_kmajor(w2t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                commit(mbar);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            // ---- epilogue 2: H2 = relu(Z2 + b2) over H1 ----
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                float z[32];
+                tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * g), z);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k] + S.sm.b2[32 * g + k], 0.0f);
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) panel_store8(hp + (g >> 1) * kPanelBytes, r, 32 * (g & 1) + k, z + k);
+            }
+            fence_async_smem();
+            group_sync();
+            // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used) ----
+            if (r == 0) {
+#pragma unroll 1
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tb + COL_O, desc_kmajor(hp_, kk), desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
+                commit(mbar);
+            }
+            if (!wait_mma()) { ok = false; break; }
+            float o[16];
+            tmem_ld16(taddr(tb, warp, COL_O), o);
+            if (slot >= 0) {
+                float *sp = reinterpret_cast<float *>(A.samp + slot);
+                sp[1] = sigmoidf_(o[0] + S.sm.b3[0]);
+                sp[2] = sigmoidf_(o[1] + S.sm.b3[1]);
+                sp[3] = sigmoidf_(o[2] + S.sm.b3[2]);
+            }
+            group_sync();   // TMEM reads and panel reads done before this group's next MMAs
         }
         if (!ok) atomicExch(&S.sm.abort, 1);
     } else {
@@ -363,9 +546,11 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.tp);
             uint32_t h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), dz2_ = smem_u32(S.dz2), dout_ = smem_u32(S.dout);
             asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(h1_), "+r"(h2_), "+r"(dz2_), "+r"(dout_));
+            // (no abort-flag test: consumers reading it on either side of its setting would part at
+            // their named barrier; a failed producer leaves this wait unsatisfied for all of them)
             if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
             fence_after();
-            if (!ok || *(volatile int *)&S.sm.abort) break;
+            if (!ok) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers
             const int slot = S.sm.slot[b][r];
             const float d0 = BWD ? S.sm.dc[b][r][0] : 0.0f, d1 = BWD ? S.sm.dc[b][r][1] : 0.0f,
@@ -407,24 +592,31 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 commit(&S.sm.mma);
             }
             if (!wait_mma()) { ok = false; break; }
-            // ---- epilogue 2: H2 = relu(Z2 + b2), my 64 columns ----
-            uint32_t m2lo = 0u, m2hi = 0u;
+            // ---- epilogue 2: H2 = relu(Z2 + b2), my 64 columns; in the backward also
+            //      dZ2 = (dout W3^T) [Z2 + b2 > 0] on the CUDA cores, from the BF16 operands the MMA
+            //      would take (dout rounded, W3 rounded; the three products are exact in FP32) ----
+            const float e0 = BWD ? bf16_round(d0) : 0.0f, e1 = BWD ? bf16_round(d1) : 0.0f,
+                        e2 = BWD ? bf16_round(d2) : 0.0f;
 #pragma unroll 1
             for (int g = 0; g < 2; ++g) {
                 const int col = 64 * hc + 32 * g;
-                float z[32];
+                float z[32], dz[32];
                 tmem_ld32(taddr(tb, warp, COL_Z2 + col), z);
-                uint32_t bits = 0;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
                     const float h = z[k] + S.sm.b2[col + k];
-                    bits |= (h > 0.0f ? 1u : 0u) << k;
                     z[k] = fmaxf(h, 0.0f);
+                    if (BWD) {
+                        const float4 w = S.sm.w3[col + k];
+                        dz[k] = h > 0.0f ? fmaf(e0, w.x, fmaf(e1, w.y, e2 * w.z)) : 0.0f;
+                    }
                 }
-                if (g == 0) m2lo = bits;
-                else m2hi = bits;
 #pragma unroll
                 for (int k = 0; k < 32; k += 8) panel_store8(S.h2 + hc * kPanelBytes, r, 32 * g + k, z + k);
+                if (BWD) {
+#pragma unroll
+                    for (int k = 0; k < 32; k += 8) panel_store8(S.dz2 + hc * kPanelBytes, r, 32 * g + k, dz + k);
+                }
             }
             if (!BWD) {
                 consumer_publish();
@@ -450,8 +642,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 consumer_sync();   // TMEM reads done before the next tile's MMAs
                 continue;
             }
-            // ---- backward: dout = dL/dc c (1 - c), formed by the producers; the publish below
-            //      also covers H2 ----
+            // ---- backward: dout = dL/dc c (1 - c), formed by the producers, into the dout panel
+            //      (the operand of dW3 and, through its constant-1 column, of db2); the publish
+            //      covers H2, dZ2 and dout ----
             if (hc == 0) {
                 db3_part[0] += d0;
                 db3_part[1] += d1;
@@ -460,24 +653,6 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 q.x = pack_bf16(d0, d1);
                 q.y = pack_bf16(d2, 1.0f);
                 *reinterpret_cast<uint2 *>(S.dout + panel_offset(r, 0)) = q;
-            }
-            consumer_publish();
-            // ---- dH2 = dout W3^T (K = 16) ----
-            if (tid == 0) {
-                mma(tb + COL_DH2, desc_kmajor(dout_, 0), desc_kmajor(w3p_, 0), idesc_bf16(128, 128, 0, 0), 0u);
-                commit(&S.sm.mma);
-            }
-            if (!wait_mma()) { ok = false; break; }
-            // ---- dZ2 = dH2 [Z2 + b2 > 0] ----
-#pragma unroll 1
-            for (int g = 0; g < 2; ++g) {
-                const uint32_t bits = g == 0 ? m2lo : m2hi;
-                float z[32];
-                tmem_ld32(taddr(tb, warp, COL_DH2 + 64 * hc + 32 * g), z);
-#pragma unroll
-                for (int k = 0; k < 32; ++k) z[k] = ((bits >> k) & 1u) ? z[k] : 0.0f;
-#pragma unroll
-                for (int k = 0; k < 32; k += 8) panel_store8(S.dz2 + hc * kPanelBytes, r, 32 * g + k, z + k);
             }
             consumer_publish();
             if (tid == 0) {
@@ -548,7 +723,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
     if (failed) {
         if (tid == 0) atomicOr(&A.hdr->flags, 2);
         // an MMA batch whose completion timed out may still be running: wait (bounded) once more
-        if (tid < NC) mbar_wait(&S.sm.mma, 0, A.wait_ns);
+        if (tid < NC) mbar_wait((!BWD && tid >= TM) ? &S.sm.mma1 : &S.sm.mma, 0, A.wait_ns);
     }
     if (BWD && !failed && tid < NC && ntile_mine > 0) {
         const uint32_t tb = S.sm.tmem_base;

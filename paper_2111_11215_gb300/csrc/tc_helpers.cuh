@@ -156,6 +156,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
     }
 }
 
+// v rounded to BF16 (to nearest, ties to even) and back to FP32.
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&v);
