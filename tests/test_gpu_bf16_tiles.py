@@ -27,6 +27,7 @@ import pytest
 import torch
 
 import oracle
+import synth
 from helpers import BOUND_BF16_OPERANDS, assert_within_bound, mlp_flat, oracle_params
 from test_gpu_parity import _fine_inputs, _run_fine
 from test_gpu_pe_x import _bf16_operands
@@ -126,3 +127,59 @@ def test_bf16_backward_explicit_samples_many_tiles_per_cta(capsys):
                         error_bound=BOUND_BF16_OPERANDS)
     got = {"rgb": rgb.cpu().numpy(), "g_d": g_d.cpu().numpy(), "g_f": g_f.cpu().numpy(), "g_m": g_m.cpu().numpy()}
     _check(got, ref, capsys, f"explicit, {hit * K} samples")
+
+
+def _pack(a, desc, dtype):
+    return dvgo.dvgo_pack_grid(desc, a.reshape(-1).contiguous(),
+                               desc.with_(layout=dvgo.DVGO_LAYOUT_PACKED, dtype=dtype))
+
+
+def _unpack(a, desc):
+    return dvgo.dvgo_pack_grid(desc.with_(layout=dvgo.DVGO_LAYOUT_PACKED), a, desc).reshape(
+        tuple(desc.shape) + ((desc.channels,) if desc.channels > 1 else ()))
+
+
+@pytest.mark.parametrize("pex", [False, True], ids=["39in", "72in"])
+@pytest.mark.parametrize("feat_bf16", [True, False], ids=["bf16feat", "f32feat"])
+@pytest.mark.parametrize("packed", [False, True], ids=["canonical", "packed"])
+def test_bf16_backward_every_kernel_variant_many_tiles_per_cta(pex, feat_bf16, packed, capsys):
+    """Every compiled variant of the tensor-core colour kernels (feature storage FP32 / BF16, 39 or
+    72 inputs -- PE(x, 5) with its tail panel --, canonical or packed grid layout) at >= 8 tiles per
+    CTA, against the BF16-operand oracle within its rounding bound."""
+    res, R = 64, 3000
+    seed = 520 + 4 * pex + 2 * feat_bf16 + packed
+    dens, feat, mlp, o, d, jit, _ = _fine_inputs(res, R, seed=seed)
+    if pex:
+        mlp = synth.mlp_weights(72, 128, 3, seed + 3)
+        mlp["b3"] = np.random.default_rng(seed + 4).normal(scale=0.3, size=3).astype(np.float32)
+    if feat_bf16:
+        feat = _bf16(feat)
+    p = _params(res).with_(n_freq_pos=5 if pex else 0)
+    fdt = dvgo.DVGO_DTYPE_BF16 if feat_bf16 else dvgo.DVGO_DTYPE_F32
+    lay = dvgo.DVGO_LAYOUT_PACKED if packed else dvgo.DVGO_LAYOUT_CANONICAL
+    dd0, cd0 = dvgo.GridDesc((res,) * 3, 1), dvgo.GridDesc((res,) * 3, 12)
+    dd, cd = dd0.with_(layout=lay), cd0.with_(layout=lay, dtype=fdt)
+    cu = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)  # noqa: E731
+    if packed:
+        D = _pack(cu(dens), dd0, dvgo.DVGO_DTYPE_F32)
+        F = _pack(cu(feat), cd0, fdt)
+    else:
+        D, F = cu(dens), cu(feat, torch.bfloat16 if feat_bf16 else torch.float32)
+    flat = cu(mlp_flat(mlp))
+    views = dvgo.render.mlp_views(flat, 72 if pex else 39)
+    r = dvgo.Renderer(p, dd, cd, R)
+    g = np.random.default_rng(seed + 9)
+    gC = g.normal(scale=1e-2, size=(R, 3))
+    rgb, _, _ = r.forward(D, F, views, cu(o), cu(d), cu(jit))
+    g_d, g_f, g_m = torch.zeros_like(D), torch.zeros(F.shape, device="cuda"), torch.zeros_like(flat)
+    r.backward(D, F, views, cu(o), cu(d), cu(jit), None, cu(gC), None, g_d, g_f, g_m)
+    torch.cuda.synchronize()
+    kept = int(r.workspace[8:12].view(torch.int32).item())
+    assert kept / TILE / N_SM >= 8, kept
+    if packed:
+        g_d, g_f = _unpack(g_d, dd0), _unpack(g_f, cd0)
+    ref = oracle.render(oracle_params(p, (res,) * 3, 12, bf16_operands=True), dens, feat, o, d, jitter=jit,
+                        mlp=_bf16_operands(mlp), grad_rgb=gC, error_bound=BOUND_BF16_OPERANDS)
+    got = {"rgb": rgb.cpu().numpy(), "g_d": g_d.cpu().numpy(), "g_f": g_f.cpu().numpy(), "g_m": g_m.cpu().numpy()}
+    _check(got, ref, capsys, f"{'72' if pex else '39'} inputs, {'BF16' if feat_bf16 else 'FP32'} features, "
+                             f"{'packed' if packed else 'canonical'}, {kept} samples")
