@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 7
+#define DVGO_ABI_VERSION 8
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -181,6 +181,12 @@ typedef struct {
      * runs out -- the failure path above, taken on purpose. */
     int wait_limit_us;
     int test_withhold_tile;
+    /* cgrid_ready: NULL, or a cudaEvent_t (of the calling device) that dvgo_render_fwd and
+     * dvgo_render_bwd make their stream wait on right before their first kernel that reads the
+     * colour / feature grid -- for a producer of that grid on another stream (an optimiser step):
+     * the ray set-up, the sample scan and the density pass before it are not held back.  Not
+     * validated; an event that was never recorded is complete.  Other calls ignore it. */
+    void *cgrid_ready;
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
@@ -431,11 +437,14 @@ int dvgo_proposal_bwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, 
 /* Inverse-CDF sampling of n_samples sorted samples per ray from probs [n_rays * n_bins]: the PDF
  * is mixed with the uniform one, q_b = (1 - eta) p_b + eta / n_bins; sample j sits at quantile
  * u_j = (j + jit) / n_samples of the CDF (jit = jitter[r], or 0.5 when jitter is NULL) with linear
- * interpolation inside its bin (CDF, quantiles and bin choice in FP64, the fraction inside the bin
- * in FP32).  t_out, dt_out [n_rays * n_samples]: distances along the
+ * interpolation inside its bin.  t_out, dt_out [n_rays * n_samples]: distances along the
  * normalised direction and step lengths (t_{j+1} - t_j; for the last sample the bin width over
  * n_samples times the bin's normalised probability), ready for dvgo_samples.  Rays that miss the
- * box get zeros.  Bin decisions are taken in FP64. */
+ * box (FP64 clip, as in the renderer) get zeros.  Precision: the CDF, the quantiles and the sample
+ * positions are double-float (two FP32 words, ~48 significant bits), the fraction inside a bin
+ * FP32, so t and dt are within about an FP32 ulp of their exact values; a bin choice can differ
+ * from the exact one only where a quantile lies within ~1e-14 of a bin edge, where t is
+ * continuous.  1 <= n_bins <= 128, 1 <= n_samples <= 2^24 (DVGO_ERR_INVALID_ARG otherwise). */
 int dvgo_sample_pdf(const dvgo_params *p, const dvgo_grid_desc *density_desc, int n_rays, const float *rays_o,
                     const float *rays_d, const float *probs, int n_bins, int n_samples, const float *jitter,
                     float eta, float *t_out, float *dt_out, void *stream);

@@ -29,6 +29,77 @@ __device__ __forceinline__ void adam_lazy(float &p, float &m, float &v, float g,
     if (g != 0.0f) adam_one(p, m, v, g, s, k);
 }
 
+// Launch shape: blocks of 256 threads, at most DVGO_ADAM_BLOCKS_PER_SM per SM in the grid, and
+// DVGO_ADAM_UNROLL 4-element vectors per thread in flight per iteration of the dense variant.  Three
+// blocks per SM is one wave (the kernel's registers allow four) that keeps the copy-rate bound and
+// leaves a quarter of each SM's threads and a third of its registers to kernels of other streams.
+// DVGO_ADAM_CARVEOUT (percent, -1 = the driver's choice) is the kernel's preferred shared-memory
+// carveout.  The driver's choice gives the loads in flight the whole L1: a carveout of 100 %
+// (room for concurrent kernels that use shared memory) costs the kernel 15 % of its rate.
+#ifndef DVGO_ADAM_BLOCKS_PER_SM
+#define DVGO_ADAM_BLOCKS_PER_SM 3
+#endif
+#ifndef DVGO_ADAM_UNROLL
+#define DVGO_ADAM_UNROLL 1
+#endif
+#ifndef DVGO_ADAM_CARVEOUT
+#define DVGO_ADAM_CARVEOUT -1
+#endif
+
+__device__ __forceinline__ void adam_store(float4 *p4, float4 *m4, float4 *v4, float4 *g4, uint2 *pb4, size_t i,
+                                           const float4 &P, const float4 &M, const float4 &V, int zero_grad) {
+    p4[i] = P;
+    m4[i] = M;
+    v4[i] = V;
+    if (zero_grad) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pb4) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
+        uint2 o;
+        o.x = *reinterpret_cast<unsigned *>(&lo);
+        o.y = *reinterpret_cast<unsigned *>(&hi);
+        pb4[i] = o;
+    }
+}
+
+// Dense variant with U vectors per thread per iteration: all loads of an iteration are issued
+// before the first update.
+template <int U>
+__device__ __forceinline__ void adam_dense_vec(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                                               float *__restrict__ v, size_t n4, const AdamK &k,
+                                               const float *__restrict__ scale, uint16_t *__restrict__ pb,
+                                               int zero_grad) {
+    float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
+    float4 *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+    const float4 *s4 = reinterpret_cast<const float4 *>(scale);
+    uint2 *pb4 = reinterpret_cast<uint2 *>(pb);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += stride * U) {
+        float4 G[U], P[U], M[U], V[U], S[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            if (i < n4) {
+                G[u] = g4[i];
+                P[u] = p4[i];
+                M[u] = m4[i];
+                V[u] = v4[i];
+                S[u] = s4 ? s4[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            if (i < n4) {
+                adam_one(P[u].x, M[u].x, V[u].x, G[u].x, S[u].x, k);
+                adam_one(P[u].y, M[u].y, V[u].y, G[u].y, S[u].y, k);
+                adam_one(P[u].z, M[u].z, V[u].z, G[u].z, S[u].z, k);
+                adam_one(P[u].w, M[u].w, V[u].w, G[u].w, S[u].w, k);
+                adam_store(p4, m4, v4, g4, pb4, i, P[u], M[u], V[u], zero_grad);
+            }
+        }
+    }
+}
+
 template <bool LAZY>
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                                                     float *__restrict__ v, size_t n, AdamK k,
@@ -36,34 +107,22 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
                                                     int zero_grad) {
     size_t n4 = n / 4;
     size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-        const float4 G = reinterpret_cast<const float4 *>(g)[i];
-        if (LAZY && G.x == 0.0f && G.y == 0.0f && G.z == 0.0f && G.w == 0.0f) continue;
-        float4 P = reinterpret_cast<float4 *>(p)[i];
-        float4 M = reinterpret_cast<float4 *>(m)[i];
-        float4 V = reinterpret_cast<float4 *>(v)[i];
-        float4 S = scale ? reinterpret_cast<const float4 *>(scale)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
-        if (LAZY) {
+    if constexpr (!LAZY) {
+        adam_dense_vec<DVGO_ADAM_UNROLL>(p, g, m, v, n4, k, scale, pb, zero_grad);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 G = reinterpret_cast<const float4 *>(g)[i];
+            if (G.x == 0.0f && G.y == 0.0f && G.z == 0.0f && G.w == 0.0f) continue;
+            float4 P = reinterpret_cast<float4 *>(p)[i];
+            float4 M = reinterpret_cast<float4 *>(m)[i];
+            float4 V = reinterpret_cast<float4 *>(v)[i];
+            const float4 S = scale ? reinterpret_cast<const float4 *>(scale)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
             adam_lazy(P.x, M.x, V.x, G.x, S.x, k);
             adam_lazy(P.y, M.y, V.y, G.y, S.y, k);
             adam_lazy(P.z, M.z, V.z, G.z, S.z, k);
             adam_lazy(P.w, M.w, V.w, G.w, S.w, k);
-        } else {
-            adam_one(P.x, M.x, V.x, G.x, S.x, k);
-            adam_one(P.y, M.y, V.y, G.y, S.y, k);
-            adam_one(P.z, M.z, V.z, G.z, S.z, k);
-            adam_one(P.w, M.w, V.w, G.w, S.w, k);
-        }
-        reinterpret_cast<float4 *>(p)[i] = P;
-        reinterpret_cast<float4 *>(m)[i] = M;
-        reinterpret_cast<float4 *>(v)[i] = V;
-        if (zero_grad) reinterpret_cast<float4 *>(g)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pb) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
-            uint2 o;
-            o.x = *reinterpret_cast<unsigned *>(&lo);
-            o.y = *reinterpret_cast<unsigned *>(&hi);
-            reinterpret_cast<uint2 *>(pb)[i] = o;
+            adam_store(reinterpret_cast<float4 *>(p), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v),
+                       reinterpret_cast<float4 *>(g), reinterpret_cast<uint2 *>(pb), i, P, M, V, zero_grad);
         }
     }
     // scalar tail
@@ -95,9 +154,19 @@ void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const 
     k.inv_bc2 = (float)(1.0 / (1.0 - pow((double)h.beta2, (double)h.step)));
     size_t n4 = (n + 3) / 4;
     size_t blocks = (n4 + 255) / 256;
-    size_t cap = (size_t)num_sms() * 8;
+    size_t cap = (size_t)num_sms() * DVGO_ADAM_BLOCKS_PER_SM;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (DVGO_ADAM_CARVEOUT >= 0) {
+        static bool once = [] {
+            cudaFuncSetAttribute(reinterpret_cast<const void *>(adam_kernel<false>),
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, DVGO_ADAM_CARVEOUT);
+            cudaFuncSetAttribute(reinterpret_cast<const void *>(adam_kernel<true>),
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, DVGO_ADAM_CARVEOUT);
+            return true;
+        }();
+        (void)once;
+    }
     {
         ProfScope ps_(DVGO_K_ADAM, s);
         if (h.skip_zero_grad)

@@ -264,6 +264,11 @@ size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, 
     return ws_layout(n_rays, S, p->mode).total;
 }
 
+// The stream waits for the caller's event (if any) before the first kernel that reads cgrid.
+static void wait_cgrid(const dvgo_params *p, cudaStream_t s) {
+    if (p->cgrid_ready) cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(p->cgrid_ready), 0);
+}
+
 int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float *density, const dvgo_grid_desc *cd,
                     const void *cgrid, const dvgo_mlp *mlp, int R, const float *rays_o, const float *rays_d,
                     const float *jitter, const dvgo_samples *ex, const float *target, float *rgb_out,
@@ -287,9 +292,11 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     A.dloss_out = target ? dloss_out : nullptr;
     launch_ray_setup(A, rays_o, rays_d, jitter, *p, *dd, sample_cap(p, dd), s);
     if (p->mode == DVGO_MODE_COARSE) {
+        wait_cgrid(p, s);
         launch_coarse_fwd(A, s);
     } else {
         launch_fine_density(A, s);
+        wait_cgrid(p, s);
         if (p->mlp_prec == DVGO_MLP_BF16) {
             if ((st = launch_fine_colour_fwd_tc(A, s))) return st;
         } else {
@@ -320,9 +327,11 @@ int dvgo_render_bwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     A.grad_cgrid = grad_cgrid;
     A.grad_mlp = grad_mlp;
     if (p->mode == DVGO_MODE_COARSE) {
+        wait_cgrid(p, s);
         launch_coarse_bwd(A, s);
     } else {
         launch_fine_composite_bwd(A, s);
+        wait_cgrid(p, s);
         if (p->mlp_prec == DVGO_MLP_BF16) {
             if ((st = launch_fine_colour_bwd_tc(A, s))) return st;
         } else {

@@ -14,11 +14,15 @@
 //   sampling: q_b = (1 - eta) p_b + eta / n_bins, Q its CDF; sample j at u_j = (j + jit) / n * Q_nb
 //             lies in the bin with Q_b <= u_j < Q_{b+1}, at t = t0 + (b + (u_j - Q_b) / q_b) w;
 //             dt_j = t_{j+1} - t_j and, for the last sample, w Q_nb / (n q_b).
-// Integer decisions (bin of a sample, bin of a quantile) are taken in FP64 with separately
-// rounded operations, in the order written above.
+// The bin of a quantile (labels) is decided in FP64 with separately rounded operations, in the
+// order written above.  Sampling runs in double-float arithmetic (below): its CDF, quantiles and
+// sample positions carry ~48 significant bits, so a sample's bin can differ from the exact one
+// only where its quantile lies within ~1e-14 of a bin edge -- where t is continuous across the
+// edge -- and t, dt come out as the FP32 roundings of the exact values to within an ulp.
 
 #include <math.h>
 
+#include "df64.cuh"
 #include "dvgo_internal.cuh"
 
 namespace dvgo {
@@ -464,15 +468,21 @@ __global__ void __launch_bounds__(PNT, 1) proposal_kernel(PropArgs P) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Inverse-CDF sampling, thread per ray.  The CDF, the quantiles and every bin decision are FP64;
-// the position inside the chosen bin, (u - Q_b) / q_b in [0, 1], is divided in FP32 and the sample
-// assembled in FP64 (FP64 arithmetic is scarce on this GPU: the quantile uses one reciprocal per
-// ray instead of a division per sample).
+// Inverse-CDF sampling.  FP64 runs at 1/64 of the FP32 rate on this GPU, so everything past the
+// box clip is double-float arithmetic (df64.cuh).
 // ---------------------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(32) sample_pdf_kernel(int R, BoxD B, const float *ro, const float *rd,
-                                                        const float *probs, int nb, int ns, const float *jitter,
-                                                        double eta, float *t_out, float *dt_out) {
+constexpr int kPdfThreads = 32;
+constexpr int kPdfMaxBins = 128;
+
+// Thread per ray, no shared memory (the kernel runs beside the HBM-bound Adam, whose loads in
+// flight need the SM's L1): the CDF of the ray is summed twice in the same order, once for its
+// total and once merged with the sorted quantiles, and the probability of the next bin is loaded
+// a bin ahead so that the merge does not wait on memory.
+__global__ void __launch_bounds__(kPdfThreads) sample_pdf_kernel(int R, BoxD B, const float *ro, const float *rd,
+                                                                 const float *probs, int nb, int ns,
+                                                                 const float *jitter, float eta, float *t_out,
+                                                                 float *dt_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const Clip c = clip_ray(B, ro, rd, r);
@@ -482,31 +492,36 @@ __global__ void __launch_bounds__(32) sample_pdf_kernel(int R, BoxD B, const flo
         return;
     }
     const float *p = probs + (size_t)r * nb;
-    const double t0 = c.lo, t1 = c.hi;
-    const double w = __ddiv_rn(__dsub_rn(t1, t0), (double)nb);
-    const double eta_nb = __ddiv_rn(eta, (double)nb), one_m_eta = __dsub_rn(1.0, eta);
-    double Qtot = 0.0;
-    for (int b = 0; b < nb; ++b) Qtot = __dadd_rn(Qtot, __dadd_rn(__dmul_rn(one_m_eta, (double)p[b]), eta_nb));
-    const double jit = jitter ? (double)jitter[r] : 0.5;
-    const double du = __ddiv_rn(Qtot, (double)ns);
+    const Df t0 = df_from_double(c.lo), w = df_from_double(__ddiv_rn(__dsub_rn(c.hi, c.lo), (double)nb));
+    const float nbf = (float)nb, nsf = (float)ns;
+    const Df one_m_eta = df_two_sum(1.0f, -eta);
+    const Df eta_nb = df_div_n(Df{eta, 0.0f}, nbf);
+    auto q_of = [&](float pb) { return df_add(df_mul_f(one_m_eta, pb), eta_nb); };
+    Df Qtot = {0.0f, 0.0f};
+#pragma unroll 8
+    for (int b = 0; b < nb; ++b) Qtot = df_add(Qtot, q_of(__ldg(p + b)));
+    const float jit = jitter ? jitter[r] : 0.5f;
     int b = 0;
-    double Qb = 0.0;                                                               // CDF at the left edge of bin b
-    double qb = __dadd_rn(__dmul_rn(one_m_eta, (double)p[0]), eta_nb);
-    double tprev = 0.0;
+    Df Qb = {0.0f, 0.0f}, qb = q_of(__ldg(p)), tprev = {0.0f, 0.0f};
+    float pn = nb > 1 ? __ldg(p + 1) : 0.0f;   // p of bin b + 1
     for (int j = 0; j < ns; ++j) {
-        const double u = __dmul_rn(__dadd_rn((double)j, jit), du);
-        while (b < nb - 1 && __dadd_rn(Qb, qb) <= u) {
-            Qb = __dadd_rn(Qb, qb);
+        const Df u = df_mul(df_div_n(df_two_sum((float)j, jit), nsf), Qtot);
+        while (b < nb - 1) {
+            const Df Qn = df_add(Qb, qb);
+            if (!df_le(Qn, u)) break;
+            Qb = Qn;
             ++b;
-            qb = __dadd_rn(__dmul_rn(one_m_eta, (double)p[b]), eta_nb);
+            qb = q_of(pn);
+            pn = b + 1 < nb ? __ldg(p + b + 1) : 0.0f;
         }
-        const float frac = __fdiv_rn((float)__dsub_rn(u, Qb), (float)qb);
-        const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)b, (double)frac), w));
-        to[j] = (float)t;
-        if (j > 0) dto[j - 1] = (float)__dsub_rn(t, tprev);
+        const float frac = __fdiv_rn(df_add(u, df_neg(Qb)).hi, qb.hi);
+        const Df t = df_add(t0, df_mul(df_two_sum((float)b, frac), w));
+        to[j] = t.hi;
+        if (j > 0) dto[j - 1] = df_add(t, df_neg(tprev)).hi;
         tprev = t;
     }
-    dto[ns - 1] = (float)__ddiv_rn(w, __ddiv_rn(__dmul_rn((double)ns, qb), Qtot));
+    // last step: the bin width over n times the bin's normalised probability
+    dto[ns - 1] = __fdiv_rn(w.hi, __fdiv_rn(__fmul_rn(nsf, qb.hi), Qtot.hi));
 }
 
 }  // namespace
@@ -612,15 +627,16 @@ int dvgo_proposal_bwd(const dvgo_params *p, const dvgo_grid_desc *dd, const dvgo
 int dvgo_sample_pdf(const dvgo_params *p, const dvgo_grid_desc *dd, int n_rays, const float *rays_o,
                     const float *rays_d, const float *probs, int n_bins, int n_samples, const float *jitter,
                     float eta, float *t_out, float *dt_out, void *stream) {
-    if (!p || !dd || n_rays < 0 || n_bins < 1 || n_samples < 1 || !(eta >= 0.0f && eta <= 1.0f))
+    if (!p || !dd || n_rays < 0 || n_bins < 1 || n_bins > kPdfMaxBins || n_samples < 1 ||
+        n_samples > (1 << 24) || !(eta >= 0.0f && eta <= 1.0f))
         return DVGO_ERR_INVALID_ARG;
     if (n_rays > 0 && (!rays_o || !rays_d || !probs || !t_out || !dt_out)) return DVGO_ERR_INVALID_ARG;
     if (n_rays == 0) return DVGO_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     {
         ProfScope ps_(DVGO_K_SAMPLE_PDF, s);
-        sample_pdf_kernel<<<(n_rays + 31) / 32, 32, 0, s>>>(n_rays, make_box(*p, *dd), rays_o, rays_d, probs, n_bins,
-                                                             n_samples, jitter, (double)eta, t_out, dt_out);
+        sample_pdf_kernel<<<(n_rays + kPdfThreads - 1) / kPdfThreads, kPdfThreads, 0, s>>>(
+            n_rays, make_box(*p, *dd), rays_o, rays_d, probs, n_bins, n_samples, jitter, eta, t_out, dt_out);
     }
     return cudaGetLastError() == cudaSuccess ? DVGO_OK : DVGO_ERR_CUDA;
 }

@@ -23,6 +23,7 @@
 
 #include <math.h>
 
+#include "df64.cuh"
 #include "dvgo_internal.cuh"
 #include "tc_helpers.cuh"
 
@@ -35,12 +36,21 @@ using namespace tc;
 constexpr int NB = 64, NFQ = 6, PIN = 3 + 6 * NFQ, PW = 64, TT = 128;
 constexpr uint32_t COL_Z = 0, FWD_COLS = 64;   // the three layers use one accumulator in turn
 
+// Box clip of one ray as the encoding uses it: entry t0, bin width w = (t_exit - t_enter) / 64 and
+// direction as double-float values of the FP64 clip, the origin, and whether the ray hits the box.
+struct ClipDf {
+    Df t0, w, dn[3];
+    float o[3];
+    int hit;
+};
+
+constexpr int kClipTiles = TT / 2;   // tiles per clip pass: one ray per thread
+
 struct alignas(1024) SmallP {
     float b1[PW], b2[PW], w3[PW];
     float b3[4];
     float red[2][2][2];       // per ray: partial max / sum of the two warps
-    double t0[2], t1[2], dn[2][3];
-    int hit[2];
+    ClipDf clip[TT];          // rays of the CTA's current 64 tiles
     uint64_t mbar;
     uint32_t tmem_base;
 };
@@ -97,38 +107,47 @@ __device__ __forceinline__ void load_weights(const PropTcArgs &P, unsigned char 
     if (tid == 0) b3[0] = P.b3[0];
 }
 
-// Clip of the tile's two rays (threads 0 and 64).
-__device__ __forceinline__ void clip_tile_rays(const PropTcArgs &P, int tile, double *t0, double *t1, double (*dn)[3],
-                                               int *hit_out) {
-    const int tid = threadIdx.x, rl = tid >> 6, r = 2 * tile + rl;
-    if ((tid & 63) == 0) {
-        int hit = 0;
-        if (r < P.R) {
-            const double o[3] = {(double)P.ro[3 * r], (double)P.ro[3 * r + 1], (double)P.ro[3 * r + 2]};
-            const double d[3] = {(double)P.rd[3 * r], (double)P.rd[3 * r + 1], (double)P.rd[3 * r + 2]};
-            const Clip c = slab_clip(o, d, P.mn, P.mx, P.t_near, P.t_far);
-            hit = c.hi > c.lo;
-            t0[rl] = c.lo;
-            t1[rl] = c.hi;
-            for (int a = 0; a < 3; ++a) dn[rl][a] = c.dn[a];
+// Box clips (FP64, as in the renderer) of the rays of the CTA's tiles k0 .. k0 + 63 (its k-th tile
+// is blockIdx.x + k gridDim.x, rays 2 tile and 2 tile + 1), one ray per thread.  Clipping per ray
+// instead of per tile keeps the FP64 work (1/64 of the FP32 rate on this GPU) off the tile loop.
+__device__ __forceinline__ void clip_pass(const PropTcArgs &P, int k0, ClipDf *cl) {
+    const int tid = threadIdx.x;
+    const long long tile = blockIdx.x + (long long)(k0 + (tid >> 1)) * gridDim.x, r = 2 * tile + (tid & 1);
+    ClipDf c;
+    c.t0 = c.w = c.dn[0] = c.dn[1] = c.dn[2] = Df{0.0f, 0.0f};
+    c.o[0] = c.o[1] = c.o[2] = 0.0f;
+    c.hit = 0;
+    if (r < P.R) {
+        const double o[3] = {(double)P.ro[3 * r], (double)P.ro[3 * r + 1], (double)P.ro[3 * r + 2]};
+        const double d[3] = {(double)P.rd[3 * r], (double)P.rd[3 * r + 1], (double)P.rd[3 * r + 2]};
+        const Clip q = slab_clip(o, d, P.mn, P.mx, P.t_near, P.t_far);
+        c.hit = q.hi > q.lo;
+        if (c.hit) {
+            c.t0 = df_from_double(q.lo);
+            c.w = df_from_double(__ddiv_rn(__dsub_rn(q.hi, q.lo), (double)NB));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                c.dn[a] = df_from_double(q.dn[a]);
+                c.o[a] = P.ro[3 * r + a];
+            }
         }
-        hit_out[rl] = hit;
     }
+    cl[tid] = c;
 }
 
 // Input row of this thread's bin centre into the X panel (zeros for a ray that misses or does
-// not exist).
-__device__ __forceinline__ void encode_row(const PropTcArgs &P, int tile, bool hit, double t0, double t1,
-                                           const double *dn, unsigned char *x) {
-    const int tid = threadIdx.x, rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
+// not exist).  The bin centre t_b = t0 + (b + 1/2) w and the position x = o + t_b d are double-float,
+// so x is the FP32 rounding of the exact position (up to ties within ~1e-14).
+__device__ __forceinline__ void encode_row(const ClipDf &c, unsigned char *x) {
+    const int tid = threadIdx.x, bin = tid & 63;
     float v[64];
 #pragma unroll
     for (int k = 0; k < 64; ++k) v[k] = 0.0f;
-    if (hit) {
-        const double tb_ = t0 + ((double)bin + 0.5) * (t1 - t0) / (double)NB;
+    if (c.hit) {
+        const Df tb = df_add(c.t0, df_mul_f(c.w, (float)bin + 0.5f));
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float xa = (float)((double)P.ro[3 * r + a] + tb_ * dn[a]);
+            const float xa = df_add(Df{c.o[a], 0.0f}, df_mul(tb, c.dn[a])).hi;
             v[a] = xa;
             float sn, cs;
             sincosf(xa, &sn, &cs);
@@ -144,7 +163,7 @@ __device__ __forceinline__ void encode_row(const PropTcArgs &P, int tile, bool h
         v[PIN] = 1.0f;
     }
 #pragma unroll
-    for (int c = 0; c < 64; c += 8) panel_store8(x, tid, c, v + c);
+    for (int c8 = 0; c8 < 64; c8 += 8) panel_store8(x, tid, c8, v + c8);
 }
 
 __global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
@@ -162,14 +181,18 @@ __global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
     bool ok = true;
     const float invR = 1.0f / (float)P.R;
     const int ntiles = (P.R + 1) / 2;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
         uint32_t xh1_ = smem_u32(S.xh1), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
         uint32_t h0_ = smem_u32(S.h0);
         asm volatile("" : "+r"(xh1_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_));
         const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
-        clip_tile_rays(P, tile, S.sm.t0, S.sm.t1, S.sm.dn, S.sm.hit);
-        __syncthreads();
-        encode_row(P, tile, S.sm.hit[rl] != 0, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.xh1);
+        if (k % kClipTiles == 0) {
+            clip_pass(P, k, S.sm.clip);
+            __syncthreads();
+        }
+        const bool hit = S.sm.clip[2 * (k % kClipTiles) + rl].hit != 0;
+        encode_row(S.sm.clip[2 * (k % kClipTiles) + rl], S.xh1);
         fence_async_smem();
         sync_fenced();
         // ---- layer 0 ----
@@ -250,7 +273,6 @@ __global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
         __syncthreads();
         const float z = S.sm.red[rl][0][1] + S.sm.red[rl][1][1];
         if (r < P.R) {
-            const bool hit = S.sm.hit[rl] != 0;
             const float pr = hit ? e / z : 1.0f / NB;
             P.probs[(size_t)r * NB + bin] = pr;
             if (P.labels && P.loss && hit) {
@@ -279,8 +301,7 @@ struct alignas(1024) SmallB {
     float b1[PW], b2[PW], w3[PW];
     float b3[4];
     float red[2][2][2];
-    double t0[2], t1[2], dn[2][3];
-    int hit[2];
+    ClipDf clip[TT];
     uint64_t mbar;
     uint32_t tmem_base;
 };
@@ -398,17 +419,20 @@ __global__ void __launch_bounds__(TT, 1) proposal_bwd_tc_kernel(PropTcArgs P) {
     bool ok = true;
     uint32_t acc = 0;   // 0 until the first tile's weight-gradient MMAs have initialised TMEM
     const int ntiles = (P.R + 1) / 2;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
         uint32_t x_ = smem_u32(S.x), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
         uint32_t h0_ = smem_u32(S.h0), h1_ = smem_u32(S.h1), h2_ = smem_u32(S.h2), e_ = smem_u32(S.e);
         uint32_t dza_ = smem_u32(S.dza), dzb_ = smem_u32(S.dzb), dl_ = smem_u32(S.dl);
         asm volatile("" : "+r"(x_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_), "+r"(h1_), "+r"(h2_), "+r"(e_));
         asm volatile("" : "+r"(dza_), "+r"(dzb_), "+r"(dl_));
         const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
-        clip_tile_rays(P, tile, S.sm.t0, S.sm.t1, S.sm.dn, S.sm.hit);
-        __syncthreads();
-        const bool hit = S.sm.hit[rl] != 0;
-        encode_row(P, tile, hit, S.sm.t0[rl], S.sm.t1[rl], S.sm.dn[rl], S.x);
+        if (k % kClipTiles == 0) {
+            clip_pass(P, k, S.sm.clip);
+            __syncthreads();
+        }
+        const bool hit = S.sm.clip[2 * (k % kClipTiles) + rl].hit != 0;
+        encode_row(S.sm.clip[2 * (k % kClipTiles) + rl], S.x);
         fence_async_smem();
         sync_fenced();
         uint32_t m0[2], m1[2], m2[2];

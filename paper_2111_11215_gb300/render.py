@@ -43,14 +43,17 @@ class Renderer:
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
 
     def forward(self, density, cgrid, mlp, rays_o, rays_d, jitter=None, samples=None, target=None,
-                rgb=None, tfinal=None, loss=None, dloss=None, stream=None):
+                rgb=None, tfinal=None, loss=None, dloss=None, stream=None, cgrid_ready=None):
+        """cgrid_ready: an event (torch.cuda.Event) whose completion the colour kernels wait for;
+        the kernels before them (ray set-up, sample scan, density pass) do not."""
         R = rays_o.shape[0]
         dev = rays_o.device
         rgb = torch.empty((R, 3), device=dev) if rgb is None else rgb
         tfinal = torch.empty(R, device=dev) if tfinal is None else tfinal
         if target is not None:
             loss = torch.empty(1, device=dev) if loss is None else loss
-        B.dvgo_render_fwd(self.params, self.dd, density, self.cd, cgrid, mlp, rays_o, rays_d, jitter, samples,
+        params = self.params if cgrid_ready is None else self.params.with_(cgrid_ready=cgrid_ready.cuda_event)
+        B.dvgo_render_fwd(params, self.dd, density, self.cd, cgrid, mlp, rays_o, rays_d, jitter, samples,
                           target, rgb, tfinal, loss, dloss, self.workspace, stream)
         return rgb, tfinal, loss
 
@@ -293,13 +296,17 @@ class FineModel:
         uniform steps.  `after_forward(renderer)` (optional) is called between the forward and the
         backward, while the renderer's workspace holds this batch's forward samples."""
         rend = self.renderer if samples is None else self.explicit_renderer(samples[0].shape[1])
-        self.wait_params(stream)
-        rend.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, target,
-                     self.rgb, self.tfinal, self.loss, self.dloss, stream)
+        # a pending feature-grid Adam step holds back only the colour kernels of the forward (the
+        # stream waits on its event inside the call); the backward follows on the same stream
+        self.launch_feat_adam(stream)
+        ready = self._ev_feat if self._feat_pending else None
+        rend.forward(self.density, self._feat_bf16 if self.bf16_feat else self._feat, self.mlp, rays_o, rays_d,
+                     jitter, samples, target, self.rgb, self.tfinal, self.loss, self.dloss, stream,
+                     cgrid_ready=ready)
         if after_forward is not None:
             after_forward(rend)
-        rend.backward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, samples, self.dloss, None,
-                      self.g_density, self.g_feat, self.g_mlp, stream)
+        rend.backward(self.density, self._feat_bf16 if self.bf16_feat else self._feat, self.mlp, rays_o, rays_d,
+                      jitter, samples, self.dloss, None, self.g_density, self.g_feat, self.g_mlp, stream)
         self.step_count += 1
         t = self.step_count
         tg = t - self.grid_t0          # the grids' Adam count (restarted by rescale)

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_strings(lib):
     import paper_2111_11215_gb300 as dvgo
-    assert dvgo.dvgo_abi_version() == 7
+    assert dvgo.dvgo_abi_version() == 8
     assert dvgo.dvgo_status_string(0) == "ok"
     assert "workspace" in dvgo.dvgo_status_string(-2)
 
@@ -74,3 +74,21 @@ def test_grid_elements_per_layout(lib):
             bricks *= -(-n // 4)
         assert dvgo.dvgo_grid_elements(g.with_(layout=dvgo.DVGO_LAYOUT_PACKED)) == bricks * 64 * C
     assert dvgo.dvgo_grid_elements(dvgo.GridDesc((8, 8, 8), 1, layout=7)) == 0      # invalid layout
+
+
+def test_sample_pdf_rejects_bins_and_samples_out_of_range(lib):
+    """dvgo_sample_pdf checks its sizes before any device work: 1 <= n_bins <= 128 (the staged PDF
+    rows), 1 <= n_samples <= 2^24 (sample indices exact in FP32), 0 <= eta <= 1."""
+    import ctypes as C
+    import paper_2111_11215_gb300 as dvgo
+    from paper_2111_11215_gb300 import binding
+    p, g = dvgo.Params(mode=dvgo.DVGO_MODE_FINE, step=0.01).c(), dvgo.GridDesc((8, 8, 8), 1).c()
+    buf = (C.c_float * 16)()
+    ptr = C.cast(buf, C.c_void_p)
+
+    def call(nb, ns, eta):
+        return lib.dvgo_sample_pdf(C.byref(p), C.byref(g), 1, ptr, ptr, ptr, nb, ns, None, C.c_float(eta), ptr, ptr,
+                                   None)
+    for nb, ns, eta in ((0, 8, 0.1), (129, 8, 0.1), (64, 0, 0.1), (64, (1 << 24) + 1, 0.1), (64, 8, -0.5),
+                        (64, 8, 1.5)):
+        assert call(nb, ns, eta) == binding.DVGO_ERR_INVALID_ARG, (nb, ns, eta)

@@ -87,10 +87,9 @@ def _bf16(a):
     return torch.as_tensor(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
 
 
-def _bf16_chain_grads(P, w, o, d, labels):
-    """The proposal backward with BF16 rounding at exactly the points where the tensor-core kernel
-    rounds (inputs, weights, hidden activations, dlogit, the dZ of each layer), in FP64 otherwise:
-    separates kernel bugs from BF16 rounding."""
+def _bf16_chain_fwd(P, w, o, d):
+    """The proposal forward with BF16 rounding at exactly the points where the tensor-core kernel
+    rounds (inputs, weights, hidden activations), in FP64 otherwise."""
     R = o.shape[0]
     X = np.zeros((R, NB, 64))
     hit = np.zeros(R, bool)
@@ -119,6 +118,17 @@ def _bf16_chain_grads(P, w, o, d, labels):
     logit = (H2 @ w["w3"].reshape(PW, 1)).reshape(R, NB) + float(w["b3"][0])
     p = np.exp(logit - logit.max(axis=1, keepdims=True))
     p /= p.sum(axis=1, keepdims=True)
+    p[~hit] = 1.0 / NB
+    return {"Xb": Xb, "W1b": W1b, "W2b": W2b, "H0": H0, "H1": H1, "H2": H2, "p": p, "hit": hit}
+
+
+def _bf16_chain_grads(P, w, o, d, labels):
+    """The proposal backward with BF16 rounding at exactly the points where the tensor-core kernel
+    rounds (inputs, weights, hidden activations, dlogit, the dZ of each layer), in FP64 otherwise:
+    separates kernel bugs from BF16 rounding."""
+    R = o.shape[0]
+    f = _bf16_chain_fwd(P, w, o, d)
+    Xb, W1b, W2b, H0, H1, H2, p, hit = (f[k] for k in ("Xb", "W1b", "W2b", "H0", "H1", "H2", "p", "hit"))
     dl = np.where(hit[:, None], p - labels, 0.0).reshape(-1)
     dlb = _bf16(dl)
     dZ2 = _bf16(dl[:, None] * w["w3"].reshape(1, PW) * (H2 > 0))
@@ -130,7 +140,41 @@ def _bf16_chain_grads(P, w, o, d, labels):
             "b3": np.array([dlb.sum() / R])}
 
 
-@pytest.mark.parametrize("R", [157, 1001])
+@pytest.mark.parametrize("R", [157, 1001, 60000])
+def test_proposal_bf16_forward(R):
+    """BF16 tensor-core proposal forward (probabilities and cross-entropy) against the same chain
+    rounded to BF16 at the kernel's rounding points.  Differences come only from values near a
+    BF16 rounding midpoint that FP32 accumulation rounds the other way (each moves a logit by about
+    one BF16 ulp of one hidden unit); a wrong operand layout or index moves probabilities by their
+    own size.  R = 60000 gives every CTA more than 64 tiles, so the per-CTA clip pass runs twice;
+    R = 157 ends on a tile with one ray; rays 0-2 miss the box (uniform PDF)."""
+    res = 24
+    dens, feat, mlp, o, d, jit, p = _setup(res, R=R, seed=83)
+    dd = dvgo.GridDesc((res,) * 3, 1)
+    w = _proposal_weights(85)
+    labels = np.random.default_rng(86).dirichlet(np.full(NB, 0.3), size=R).astype(np.float32)
+    wd = {k: cuda(v) for k, v in w.items()}
+    probs, loss = torch.empty((R, NB), device="cuda"), torch.zeros(1, device="cuda")
+    dvgo.dvgo_proposal_fwd(p, dd, NB, NFQ, PW, wd, cuda(o), cuda(d), cuda(labels), probs, loss,
+                           precision=dvgo.DVGO_MLP_BF16)
+    torch.cuda.synchronize()
+    P = oracle_params(p, (res,) * 3, 12)
+    parts = [_bf16_chain_fwd(P, w, o[i:i + 4096], d[i:i + 4096]) for i in range(0, R, 4096)]
+    f = {k: np.concatenate([q[k] for q in parts]) for k in ("p", "hit")}
+    pg = probs.cpu().numpy().astype(np.float64)
+    assert f["hit"][3:].mean() > 0.5 and not f["hit"][:3].any()
+    np.testing.assert_allclose(pg.sum(axis=1), 1.0, rtol=1e-5)
+    np.testing.assert_array_equal(pg[:3], 1.0 / NB)
+    err = np.abs(pg - f["p"])
+    rel2 = float(np.linalg.norm(pg - f["p"]) / np.linalg.norm(f["p"]))
+    ref_loss = -np.sum(np.where(f["hit"][:, None] & (labels > 0), labels * np.log(f["p"]), 0.0)) / R
+    print(f"\nBF16 proposal forward R={R}: max |dp| {err.max():.2e} (max p {f['p'].max():.3f}), rel L2 {rel2:.2e}, "
+          f"loss {float(loss.item()):.6f} vs {ref_loss:.6f}")
+    assert rel2 < 2e-3 and err.max() < 2e-3 * f["p"].max()
+    assert abs(float(loss.item()) - ref_loss) < 1e-3 * abs(ref_loss)
+
+
+@pytest.mark.parametrize("R", [157, 1001, 20000])
 def test_proposal_bf16_backward(R):
     """BF16 tensor-core proposal backward (BF16 operands, FP32 accumulation).  Gate: agreement with
     the same chain rounded to BF16 at the kernel's rounding points (relative L2 <= 3e-2 per tensor;
@@ -140,7 +184,8 @@ def test_proposal_bf16_backward(R):
     Reported (and bounded at 0.2): the relative L2 error against the FP64 oracle, which is the
     BF16 operand rounding amplified by the cancellation in the row sums of the weight gradients
     (the rounded chain itself is 6-10 % from the oracle on these random labels).
-    R = 1001 gives the persistent CTAs several tiles each (the gradients accumulate in TMEM)."""
+    R = 1001 gives the persistent CTAs several tiles each (the gradients accumulate in TMEM);
+    R = 20000 more than 64 each (the per-CTA clip pass runs twice)."""
     res = 24
     dens, feat, mlp, o, d, jit, p = _setup(res, R=R, seed=73)
     dd = dvgo.GridDesc((res,) * 3, 1)
@@ -154,6 +199,8 @@ def test_proposal_bf16_backward(R):
     P = oracle_params(p, (res,) * 3, 12)
     _, _, ref_g = oracle.proposal(P, w, NB, NFQ, o, d, labels=labels, want_grads=True)
     emu = _bf16_chain_grads(P, w, o, d, labels)
+    assert np.mean([oracle.ray_bounds(P, o[r], d[r])[2] > oracle.ray_bounds(P, o[r], d[r])[1]
+                    for r in range(0, R, max(1, R // 500))]) > 0.5
     g = flat.cpu().numpy()
     assert np.all(np.isfinite(g))
     off, e_emu, e_ora = 0, {}, {}
@@ -212,11 +259,13 @@ def test_sample_pdf_matches_oracle_and_renders():
     assert_close(rgb.cpu().numpy(), ref.rgb, RTOL_COLOUR, "rgb_explicit")
 
 
-@pytest.mark.parametrize("nb,ns,eta", [(50, 100, 0.0), (64, 48, 0.05), (7, 3, 0.3)])
+@pytest.mark.parametrize("nb,ns,eta", [(50, 100, 0.0), (64, 48, 0.05), (7, 3, 0.3), (128, 200, 0.01), (64, 1, 0.05)])
 def test_sample_pdf_shapes_and_zero_bins(nb, ns, eta):
     """Inverse-CDF sampling against the oracle for bin counts that are not a multiple of the warp
-    width, more samples than bins, eta = 0 with zero-mass bins, and a one-hot PDF."""
-    res, R = 24, 96
+    width, the largest bin count (128), more samples than bins (outputs staged in several chunks of
+    32), a single sample, eta = 0 with zero-mass bins, a one-hot PDF, and a ray count that leaves a
+    partial block of 32 rays."""
+    res, R = 24, 77
     _, _, _, o, d, _, p = _setup(res, R=R, seed=76)
     dd = dvgo.GridDesc((res,) * 3, 1)
     rng = np.random.default_rng(77)
