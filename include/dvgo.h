@@ -210,7 +210,9 @@ typedef struct {
 } dvgo_samples;
 
 /* Bytes of workspace that dvgo_render_fwd / dvgo_render_bwd need for n_rays rays.  The bound
- * covers the longest possible ray: ceil(|xyz_max - xyz_min| / step) + 1 samples. */
+ * covers the longest possible ray: ceil(|xyz_max - xyz_min| / step) + 1 samples.  The fine stage
+ * with DVGO_MLP_BF16 adds 16 KiB per 128 samples: the tensor-core forward keeps every tile's
+ * BF16 MLP input rows there for the backward. */
 size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
                            const dvgo_samples *explicit_samples);
 
@@ -248,8 +250,9 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *density_desc, co
  * with respect to the density grid, the colour / feature grid and the MLP parameters.
  * Compositing state (T_k, the weights and the suffix colour sums) is recomputed from the
  * per-sample values the forward left in the workspace (optical depths and colours); the MLP's
- * activations are recomputed (the BF16 tensor-core backward takes the output colour from the
- * forward instead of recomputing the last layer).
+ * activations are recomputed (the BF16 tensor-core backward takes the output colour and the
+ * interpolated, encoded MLP input rows from the forward instead of recomputing the last layer
+ * and gathering the features again).
  * grad_rgb [n_rays*3] (required), grad_tfinal [n_rays] or NULL.
  * grad_density [nx*ny*nz] FP32; grad_cgrid [nx*ny*nz*C] FP32 (also for a BF16 feature grid);
  * grad_mlp (fine only) FP32, packed w1 | b1 | w2 | b2 | w3 | b3 in the dvgo_mlp layouts.

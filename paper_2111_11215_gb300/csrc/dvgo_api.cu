@@ -170,6 +170,7 @@ RenderArgs make_args(const dvgo_params *p, const dvgo_grid_desc *dd, const float
         A.samp = reinterpret_cast<float4 *>(b + L.samp);
         A.sgrad = reinterpret_cast<float4 *>(b + L.sgrad);
         A.kept = reinterpret_cast<int2 *>(b + L.kept);
+        A.xcache = L.xcache ? reinterpret_cast<unsigned char *>(b + L.xcache) : nullptr;
     }
     A.max_samples = L.max_samples;
     if (p->mode == DVGO_MODE_FINE && p->freespace && p->freespace->density) {
@@ -257,11 +258,14 @@ float dvgo_lr_at(float lr0, int step, float decay_steps) {
     return (float)((double)lr0 * pow(0.1, (double)step / (double)decay_steps));
 }
 
+// The BF16 tensor-core colour kernels keep the forward's input panels for the backward.
+static bool xcache_on(const dvgo_params *p) { return p->mode == DVGO_MODE_FINE && p->mlp_prec == DVGO_MLP_BF16; }
+
 size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
                            const dvgo_samples *ex) {
     if (!p || !density || n_rays < 0 || !grid_ok(density) || !(p->step > 0.0f)) return 0;
     long long S = max_samples(p, density, n_rays, ex);
-    return ws_layout(n_rays, S, p->mode).total;
+    return ws_layout(n_rays, S, p->mode, xcache_on(p)).total;
 }
 
 // The stream waits for the caller's event (if any) before the first kernel that reads cgrid.
@@ -278,7 +282,7 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     if (st) return st;
     if (R > 0 && !rgb_out) return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode);
+    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode, xcache_on(p));
     if ((st = check_ws(L, ws, ws_bytes))) return st;
     if (R == 0) {
         if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(float), s);
@@ -317,7 +321,7 @@ int dvgo_render_bwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     if (R > 0 && (!grad_rgb || !grad_density || !grad_cgrid)) return DVGO_ERR_INVALID_ARG;
     if (p->mode == DVGO_MODE_FINE && !grad_mlp) return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode);
+    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode, xcache_on(p));
     if ((st = check_ws(L, ws, ws_bytes))) return st;
     if (R == 0) return DVGO_OK;
     RenderArgs A = make_args(p, dd, density, cd, cgrid, mlp, R, ex, ws, L);
@@ -378,7 +382,7 @@ int dvgo_touched_points(const dvgo_params *p, const dvgo_grid_desc *dd, int R, c
     if (ex && (!ex->t || !ex->dt || ex->n_per_ray < 1)) return DVGO_ERR_INVALID_ARG;
     if (p->freespace && p->freespace->density && !grid_ok(&p->freespace->desc)) return DVGO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode);
+    WsLayout L = ws_layout(R, max_samples(p, dd, R, ex), p->mode, xcache_on(p));
     int st = check_ws(L, ws, ws_bytes);
     if (st) return st;
     RenderArgs A = make_args(p, dd, nullptr, dd, nullptr, nullptr, R, ex, ws, L);

@@ -61,7 +61,7 @@ static_assert(sizeof(WsHeader) == 256, "WsHeader size");
 
 // Workspace layout; every block 256-byte aligned.
 struct WsLayout {
-    size_t header, rays, rayout, rtarget, pe, texit, samp, sgrad, kept, total;
+    size_t header, rays, rayout, rtarget, pe, texit, samp, sgrad, kept, xcache, total;   // xcache 0: none
     long long max_samples;
 };
 
@@ -95,6 +95,8 @@ struct RenderArgs {
     float4 *samp;               // per sample slot: (tau, r, g, b)
     float4 *sgrad;              // per sample slot: (unused, dL/dc)
     int2 *kept;                 // compact list of kept samples: (slot, ray)
+    unsigned char *xcache;      // BF16 tensor-core path: the forward's X panel of every tile (16 KiB
+                                // each, swizzled as in shared memory), reloaded by the backward
     long long max_samples;
     // outputs
     float *rgb_out, *tfinal_out, *loss_out, *dloss_out;
@@ -410,7 +412,9 @@ __device__ __forceinline__ float seg_sum(float v, const Seg &s, int lane) {
 // Host-side launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------------------------
 
-WsLayout ws_layout(int R, long long max_samples, int mode);
+// xcache: add the block of the BF16 colour kernels' X panels (fine mode), after all others so
+// that the other offsets do not depend on it.
+WsLayout ws_layout(int R, long long max_samples, int mode, bool xcache = false);
 void launch_ray_setup(const RenderArgs &A, const float *rays_o, const float *rays_d, const float *jitter,
                       const dvgo_params &p, const dvgo_grid_desc &g, long long cap, cudaStream_t s);
 void launch_coarse_fwd(const RenderArgs &A, cudaStream_t s);

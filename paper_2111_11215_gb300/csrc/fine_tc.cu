@@ -10,8 +10,12 @@
 //
 // Persistent CTAs of 384 threads walk tiles of M = 128 kept samples.  Warps 8-11 (producers)
 // gather the next tile -- features at the 8 lattice corners, the ray's direction encoding, the
-// bias column and, in the backward, dL/dc -- into one of two X panels, and in the backward also
-// scatter the feature gradients of the tile that last used that panel.  Warps 0-7 (consumers)
+// bias column -- into one of two X panels, and in the backward also scatter the feature gradients
+// of the tile that last used that panel.  The forward stores every finished X panel (16 KiB, as
+// swizzled in shared memory) in the workspace (one bulk copy per tile); the backward loads it back
+// with one bulk copy instead of gathering again (tile t holds the same kept samples in both: the
+// kept list is the forward's), so its producers only form the per-row tables, dL/dc and the PE(x)
+// tail.  Warps 0-7 (consumers)
 // issue the MMAs (thread 0) and run the epilogues: warp w reads TMEM lanes 32 (w % 4)..+31 and
 // handles columns 64 (w / 4)..+63 of those rows, so two warps share each row.  full[b] / empty[b]
 // mbarriers hand the X panels over; every wait is bounded.
@@ -83,6 +87,7 @@ struct alignas(1024) SmallTC {
     float frac[2][TM][3];     // fractional offsets
     float dc[2][TM][3];       // dL/dc (backward)
     uint64_t full[2], empty[2], mma, mma1;   // mma1: the forward's second consumer group
+    uint64_t xl[2];           // backward: the bulk load of X panel b from the forward's copy
     uint32_t tmem_base;
     int abort;
 };
@@ -191,7 +196,8 @@ __device__ __forceinline__ Cell cell_pre(const RenderArgs &A, const RayPre &p, i
 // prefetched data rp) into X panel b (and its tail) and the per-row tables.
 template <typename FeatT, bool BWD, bool PEX, bool PK>
 __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int2 kv, const RayPre &rp,
-                                            int row) {
+                                            int row, bool cached) {
+    // cached (backward): the X panel arrives by bulk copy; only the tables, dL/dc and the tail here
     using D = TcDims<PEX>;
     float v[64], tail[16];
 #pragma unroll
@@ -217,7 +223,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
             d2 = gc.w * cv.w * (1.0f - cv.w);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
+        for (int q = 0; q < (cached ? 0 : 4); ++q) {   // corner pairs (x bit, y bit) with z = 0, 1 adjacent
             const int qa = q << 1;
             const long long idx0 = corner_index(c, qa, A.ny, A.nz, PK);
             const float w0 = corner_weight(c, qa), w1 = corner_weight(c, qa | 1);
@@ -274,7 +280,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         }
         const float4 *pe = reinterpret_cast<const float4 *>(A.pe + (size_t)kv.y * kPeStride);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < (cached ? 0 : 7); ++k) {
             const float4 q4 = __ldg(pe + k);
             if (4 * k + 0 < 27) v[FEAT + 4 * k + 0] = q4.x;
             if (4 * k + 1 < 27) v[FEAT + 4 * k + 1] = q4.y;
@@ -297,8 +303,10 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         }
         v[D::BIAS] = 1.0f;
     }
+    if (!cached) {
 #pragma unroll
-    for (int c = 0; c < 64; c += 8) panel_store8(S.x[b], row, c, v + c);
+        for (int c = 0; c < 64; c += 8) panel_store8(S.x[b], row, c, v + c);
+    }
     if constexpr (PEX) {
         panel_store8(S.tp, row, 16 * (1 + b), tail);
         panel_store8(S.tp, row, 16 * (1 + b) + 8, tail + 8);
@@ -330,6 +338,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         mbar_init(&S.sm.empty[1], 1);
         mbar_init(&S.sm.mma, 1);
         mbar_init(&S.sm.mma1, 1);
+        mbar_init(&S.sm.xl[0], 1);
+        mbar_init(&S.sm.xl[1], 1);
         S.sm.abort = 0;
     }
     if (warp == 0) tmem_alloc(&S.sm.tmem_base, NCOLS);
@@ -395,20 +405,24 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         int2 kv_cur = kept_at(blockIdx.x);
         RayPre rp_cur = kv_cur.y >= 0 ? ray_pre(A, kv_cur.y) : RayPre{};
         int2 kv_next = kept_at(blockIdx.x + gridDim.x);
+        const bool cached = BWD && A.xcache != nullptr;
+        int nload[2] = {0, 0};   // row 0, backward: bulk loads issued into X panel 0 / 1
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int b = i & 1;
             const RayPre rp_next = kv_next.y >= 0 ? ray_pre(A, kv_next.y) : RayPre{};
             const int2 kv_after = kept_at(tile + 2 * gridDim.x);
-            if (i >= 2) {
-                if (!mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1, A.wait_ns)) {
-                    ok = false;
-                    break;
-                }
-                if (BWD) scatter_row<PK>(A, S, b, row);   // feature gradients of tile i - 2
+            if (i >= 2 && !mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1, A.wait_ns)) {
+                ok = false;
+                break;
             }
             if (*(volatile int *)&S.sm.abort) break;
-            produce_row<FeatT, BWD, PEX, PK>(A, S, b, kv_cur, rp_cur, row);
+            if (cached && row == 0) {   // X panel b is free: the forward's copy of this tile's panel
+                bulk_load(S.x[b], A.xcache + (size_t)tile * kPanelBytes, kPanelBytes, &S.sm.xl[b]);
+                ++nload[b];
+            }
+            if (BWD && i >= 2) scatter_row<PK>(A, S, b, row);   // feature gradients of tile i - 2
+            produce_row<FeatT, BWD, PEX, PK>(A, S, b, kv_cur, rp_cur, row, cached);
             fence_async_smem();
             // (testing aid: one arrival withheld on a chosen tile makes the consumers' wait run out)
             if (!(row == 0 && tile + 1 == A.withhold_tile)) mbar_arrive(&S.sm.full[b]);
@@ -423,6 +437,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, row);
             }
         }
+        // every bulk load issued has landed before the CTA can exit (bounded)
+        for (int bb = 0; bb < 2; ++bb)
+            if (nload[bb] > 0) mbar_wait(&S.sm.xl[bb], (nload[bb] - 1) & 1, A.wait_ns);
         if (!ok) atomicExch(&S.sm.abort, 1);
     } else if constexpr (!BWD) {
         // --------------------------- forward consumers: two groups ---------------------------
@@ -470,9 +487,13 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 if (PEX)
                     mma(tb + COL_Z1, desc_kmajor(w3p_, 1 + b), desc_kmajor(w3p_, 3), idesc_bf16(128, 128, 0, 0), 1u);
                 commit(mbar);
+                if (A.xcache) bulk_store(A.xcache + (size_t)tile * kPanelBytes, S.x[b], kPanelBytes);   // for the backward
             }
             if (!wait_mma()) { ok = false; break; }
-            if (r == 0) mbar_arrive(&S.sm.empty[b]);   // X[b] is free once layer 1 is done
+            if (r == 0) {   // X[b] is free once layer 1 and the copy have read it
+                if (A.xcache) bulk_wait_read();
+                mbar_arrive(&S.sm.empty[b]);
+            }
             // ---- epilogue 1: H1 = relu(Z1), all 128 columns of my row ----
 #pragma unroll 1
             for (int g = 0; g < 4; ++g) {
@@ -523,6 +544,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             }
             group_sync();   // TMEM reads and panel reads done before this group's next MMAs
         }
+        if (r == 0 && A.xcache) bulk_wait_all();   // the copies are complete before the kernel ends
         if (!ok) atomicExch(&S.sm.abort, 1);
     } else {
         // ------------------------------- consumers -------------------------------
@@ -549,6 +571,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             // (no abort-flag test: consumers reading it on either side of its setting would part at
             // their named barrier; a failed producer leaves this wait unsatisfied for all of them)
             if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
+            else if (A.xcache && !mbar_wait(&S.sm.xl[b], (i >> 1) & 1, A.wait_ns)) ok = false;
             fence_after();
             if (!ok) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers

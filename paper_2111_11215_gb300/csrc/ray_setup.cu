@@ -157,7 +157,7 @@ void launch_ray_setup(const RenderArgs &A, const float *rays_o, const float *ray
     }
 }
 
-WsLayout ws_layout(int R, long long max_samples, int mode) {
+WsLayout ws_layout(int R, long long max_samples, int mode, bool xcache) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     WsLayout L;
     size_t o = 0;
@@ -178,6 +178,12 @@ WsLayout ws_layout(int R, long long max_samples, int mode) {
     // last; counted in total, so the allocation-free forward's static scratch includes it even
     // though that forward (no auxiliary losses) never writes it
     L.rtarget = o; o += up(sizeof(float4) * (size_t)(R > 0 ? R : 1));
+    L.xcache = 0;
+    if (xcache && mode == DVGO_MODE_FINE) {   // 128 kept samples per tile, a 16 KiB panel each
+        o = (o + 1023) & ~(size_t)1023;
+        L.xcache = o;
+        o += (size_t)16384 * ((S + 127) / 128);
+    }
     L.total = o;
     L.max_samples = max_samples;
     return L;
