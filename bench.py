@@ -369,14 +369,15 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
         n_dense = sum(form.trainer.is_uniform(i) for i in range(t_first, t_first + prof_steps))
         fwd_units = bwd_units = ((prof_steps - n_dense) * expl + n_dense * dense_samples) / prof_steps
     # algorithmic bytes of every Adam launch of the profiled pass: per step the density, feature and
-    # MLP sweeps (32 B per parameter, + the 2-byte BF16 feature copy), plus one proposal Adam per
-    # proposal training step (chosen form)
+    # MLP sweeps (adam_step_bytes with the touched points' gradients to clear), plus one proposal
+    # Adam per proposal training step (chosen form; its gradients are all nonzero: 32 B per parameter)
     prop_params = int(form.trainer.proposal.flat.numel()) if form.trainer is not None else 0
-    adam_bytes = prof_steps * adam_step_bytes(name == "chosen") + n_prop_train * 32 * prop_params
+    step_roof = step_hbm_minimum(form, dbatches[0], ms / args.steps, dvgo, torch, peaks)
+    nz = step_roof["grad_nonzero_per_step"]
+    adam_bytes = prof_steps * adam_step_bytes(name == "chosen", nz) + n_prop_train * 32 * prop_params
     dom_name, (dom_ms, dom_n) = max(per_kind.items(), key=lambda kv: kv[1][0])
     roof = roofline(dom_name, dom_ms, dom_n, fwd_units, bwd_units, name == "chosen", peaks, adam_bytes,
-                    (prof_steps, adam_step_bytes(name == "chosen")))
-    step_roof = step_hbm_minimum(form, dbatches[0], ms / args.steps, dvgo, torch, peaks)
+                    (prof_steps, adam_step_bytes(name == "chosen", nz)))
     return {"value": value, "ms_per_step": ms / args.steps, "dtype": "bf16" if name == "chosen" else "f32",
             "config": workload_config(args, name) | {"dense_samples_per_batch": dense_samples,
                                                      "hit_rays_per_batch": hit_rays,
@@ -393,10 +394,10 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
 def step_hbm_minimum(form, batch, ms_per_step, dvgo, torch, peaks):
     """The whole step against the HBM roofline: the minimum DRAM bytes of one step -- every touched
     lattice point's density (4 B) and features (48 B FP32 / 24 B BF16) read once and its FP32
-    gradients read and written once, the dense Adam sweep (32 B per parameter, plus the 2-byte BF16
-    feature copy), 48 B of ray input per ray -- with the touched points counted exactly
-    (dvgo_touched_points) on one batch; the chosen form weights a uniform step and a proposal step
-    by how often each runs."""
+    gradients read and written once, the dense Adam sweep (adam_step_bytes: 28 B per parameter, the
+    clearing of the touched points' gradients, the 2-byte BF16 feature copy), 48 B of ray input per
+    ray -- with the touched points counted exactly (dvgo_touched_points) on one batch; the chosen
+    form weights a uniform step and a proposal step by how often each runs."""
     m = form.model
     o, d, jit, _ = batch
     counts = {}
@@ -414,19 +415,26 @@ def step_hbm_minimum(form, batch, ms_per_step, dvgo, torch, peaks):
     counts = {k: [int(x) for x in v.cpu()] for k, v in counts.items()}
     feat_b = 24 if m.bf16_feat else 48
     render = sum(w * (counts[k][0] * 4 * 3 + counts[k][1] * (feat_b + 2 * 48)) for k, w in mix.items())
-    adam = n_params() * 32 + (RES ** 3 * FEAT * 2 if m.bf16_feat else 0)
+    # gradient elements the backward leaves nonzero: the touched points' density and features, the MLP
+    mlp_params = n_params() - RES ** 3 * (1 + FEAT)
+    nz = sum(w * (counts[k][0] + counts[k][1] * FEAT) for k, w in mix.items()) + mlp_params
+    adam = adam_step_bytes(m.bf16_feat, nz)
     byts = render + adam + 48 * NRAYS
     hbm = peaks.get("hbm_gbs") or 6800.0
     achieved = byts / (ms_per_step * 1e-3) / 1e9
     return {"bound": "hbm", "hbm_min_bytes_per_step": int(byts), "render_bytes": int(render), "adam_bytes": int(adam),
-            "touched_points": counts, "achieved": achieved, "unit": "GB/s", "peak": hbm, "frac": achieved / hbm,
+            "touched_points": counts, "grad_nonzero_per_step": int(nz), "achieved": achieved, "unit": "GB/s",
+            "peak": hbm, "frac": achieved / hbm,
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
 
 
-def adam_step_bytes(chosen):
-    """Algorithmic bytes of one step's Adam sweeps: 32 B per parameter (read p, g, m, v; write p, m,
-    v and the zeroed g) and, in the chosen form, the 2-byte BF16 copy of each feature."""
-    return n_params() * 32 + (RES ** 3 * FEAT * 2 if chosen else 0)
+def adam_step_bytes(chosen, grad_nonzero=None):
+    """Algorithmic bytes of one step's Adam sweeps: 28 B per parameter (read p, g, m, v; write p, m,
+    v), 4 B per gradient element the backward left nonzero (cleared for the next step; the kernel
+    does not rewrite an element that is already zero; every element when grad_nonzero is None) and,
+    in the chosen form, the 2-byte BF16 copy of each feature."""
+    nz = n_params() if grad_nonzero is None else grad_nonzero
+    return n_params() * 28 + 4 * nz + (RES ** 3 * FEAT * 2 if chosen else 0)
 
 
 def roofline(kind, total_ms, launches, fwd_units, bwd_units, chosen, peaks, adam_bytes=None,

@@ -2,8 +2,8 @@
 // Supp. A: Adam, base learning rates 0.1 for the voxel grids and 1e-3 for the MLP, decayed
 // exponentially by 0.1 over 20k iterations; Sec. 4.1 Prior 2: a per-voxel rate scale).
 //
-// HBM-bound: per element it reads p, g, m, v (16 B) and writes p, m, v and, with zero_grad, g
-// (12-16 B), plus 2 B for the optional BF16 copy.  16-byte vector loads/stores, grid-stride
+// HBM-bound: per element it reads p, g, m, v (16 B) and writes p, m, v and, with zero_grad, g where
+// it is not already zero (12-16 B), plus 2 B for the optional BF16 copy.  16-byte vector loads/stores, grid-stride
 // loop over a grid sized to fill every SM.  The lazy variant reads the gradient first and leaves
 // a 4-element vector whose gradients are all zero untouched (4 B of traffic per element there);
 // inside a vector it updates only the elements with a nonzero gradient.
@@ -46,12 +46,16 @@ __device__ __forceinline__ void adam_lazy(float &p, float &m, float &v, float g,
 #define DVGO_ADAM_CARVEOUT -1
 #endif
 
+// zero_grad: the gradient vector G read for this update is cleared; a vector that is already zero
+// (a lattice point no sample touched) is not written again.
 __device__ __forceinline__ void adam_store(float4 *p4, float4 *m4, float4 *v4, float4 *g4, uint2 *pb4, size_t i,
-                                           const float4 &P, const float4 &M, const float4 &V, int zero_grad) {
+                                           const float4 &P, const float4 &M, const float4 &V, const float4 &G,
+                                           int zero_grad) {
     p4[i] = P;
     m4[i] = M;
     v4[i] = V;
-    if (zero_grad) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zero_grad && (G.x != 0.0f || G.y != 0.0f || G.z != 0.0f || G.w != 0.0f))
+        g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pb4) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
         uint2 o;
@@ -94,7 +98,7 @@ __device__ __forceinline__ void adam_dense_vec(float *__restrict__ p, float *__r
                 adam_one(P[u].y, M[u].y, V[u].y, G[u].y, S[u].y, k);
                 adam_one(P[u].z, M[u].z, V[u].z, G[u].z, S[u].z, k);
                 adam_one(P[u].w, M[u].w, V[u].w, G[u].w, S[u].w, k);
-                adam_store(p4, m4, v4, g4, pb4, i, P[u], M[u], V[u], zero_grad);
+                adam_store(p4, m4, v4, g4, pb4, i, P[u], M[u], V[u], G[u], zero_grad);
             }
         }
     }
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
             adam_lazy(P.z, M.z, V.z, G.z, S.z, k);
             adam_lazy(P.w, M.w, V.w, G.w, S.w, k);
             adam_store(reinterpret_cast<float4 *>(p), reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v),
-                       reinterpret_cast<float4 *>(g), reinterpret_cast<uint2 *>(pb), i, P, M, V, zero_grad);
+                       reinterpret_cast<float4 *>(g), reinterpret_cast<uint2 *>(pb), i, P, M, V, G, zero_grad);
         }
     }
     // scalar tail
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
         p[i] = P;
         m[i] = M;
         v[i] = V;
-        if (zero_grad) g[i] = 0.0f;
+        if (zero_grad && g[i] != 0.0f) g[i] = 0.0f;
         if (pb) {
             __nv_bfloat16 b = __float2bfloat16_rn(P);
             pb[i] = *reinterpret_cast<uint16_t *>(&b);
