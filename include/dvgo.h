@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 8
+#define DVGO_ABI_VERSION 9
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -187,6 +187,11 @@ typedef struct {
      * the ray set-up, the sample scan and the density pass before it are not held back.  Not
      * validated; an event that was never recorded is complete.  Other calls ignore it. */
     void *cgrid_ready;
+    /* forward_only: non-zero when no dvgo_render_bwd follows the forward (test-time rendering).
+     * The forward then keeps nothing for a backward -- with DVGO_MLP_BF16 in the fine stage, the
+     * colour kernels' input panels (16 KiB per 128 samples) -- and dvgo_workspace_size leaves that
+     * block out.  A backward on such a workspace gathers its inputs again (same results). */
+    int forward_only;
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:
@@ -211,8 +216,8 @@ typedef struct {
 
 /* Bytes of workspace that dvgo_render_fwd / dvgo_render_bwd need for n_rays rays.  The bound
  * covers the longest possible ray: ceil(|xyz_max - xyz_min| / step) + 1 samples.  The fine stage
- * with DVGO_MLP_BF16 adds 16 KiB per 128 samples: the tensor-core forward keeps every tile's
- * BF16 MLP input rows there for the backward. */
+ * with DVGO_MLP_BF16 adds 16 KiB per 128 samples unless p->forward_only: the tensor-core forward
+ * keeps every tile's BF16 MLP input rows there for the backward. */
 size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
                            const dvgo_samples *explicit_samples);
 

@@ -66,7 +66,7 @@ class _Params(C.Structure):
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
                 ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
                 ("act_order", C.c_int), ("n_freq_pos", C.c_int), ("wait_limit_us", C.c_int),
-                ("test_withhold_tile", C.c_int), ("cgrid_ready", C.c_void_p)]
+                ("test_withhold_tile", C.c_int), ("cgrid_ready", C.c_void_p), ("forward_only", C.c_int)]
 
 
 class _Fit2d(C.Structure):
@@ -223,6 +223,7 @@ class Params:
     test_withhold_tile: int = 0  # testing aid: k > 0 withholds one producer arrival on tile k - 1
     cgrid_ready: int = 0         # cudaEvent_t handle (torch.cuda.Event.cuda_event) the render calls
                                  # wait on before their first kernel that reads the colour grid; 0: none
+    forward_only: int = 0        # no backward follows the forward: keep nothing for one
 
     def mlp_in_dim(self, channels: int = 12) -> int:
         """Width of the fine MLP's input row (Sec. 4.2 Eq. fine_queries_rgb): 39, or 72 with PE(x)."""
@@ -244,6 +245,7 @@ class Params:
         p.wait_limit_us = int(self.wait_limit_us)
         p.test_withhold_tile = int(self.test_withhold_tile)
         p.cgrid_ready = int(self.cgrid_ready) or None
+        p.forward_only = int(self.forward_only)
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)

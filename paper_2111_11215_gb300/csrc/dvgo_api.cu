@@ -258,8 +258,11 @@ float dvgo_lr_at(float lr0, int step, float decay_steps) {
     return (float)((double)lr0 * pow(0.1, (double)step / (double)decay_steps));
 }
 
-// The BF16 tensor-core colour kernels keep the forward's input panels for the backward.
-static bool xcache_on(const dvgo_params *p) { return p->mode == DVGO_MODE_FINE && p->mlp_prec == DVGO_MLP_BF16; }
+// The BF16 tensor-core colour kernels keep the forward's input panels for the backward (not when
+// no backward follows).
+static bool xcache_on(const dvgo_params *p) {
+    return p->mode == DVGO_MODE_FINE && p->mlp_prec == DVGO_MLP_BF16 && !p->forward_only;
+}
 
 size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, int n_rays,
                            const dvgo_samples *ex) {

@@ -55,7 +55,8 @@ struct WsHeader {
     unsigned done;       // block-completion counter of the loss reduction
     float loss_acc;      // sum over rays of ||C_hat - C||^2
     int aux;             // 1: the last forward had a target and auxiliary loss weights (rtarget valid)
-    int pad[58];
+    int xcache;          // 1: the last forward stored the colour kernels' input panels (xcache valid)
+    int pad[57];
 };
 static_assert(sizeof(WsHeader) == 256, "WsHeader size");
 

@@ -389,6 +389,9 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 
     const int n_kept = A.hdr->n_kept;
     const int ntiles = (n_kept + TM - 1) / TM;
+    // backward: reload the X panels the forward stored (the workspace has room and the forward that
+    // filled it stored them); otherwise gather them again
+    const bool cached = BWD && A.xcache != nullptr && A.hdr->xcache != 0;
     bool ok = true;
     int ntile_mine = 0;
 
@@ -405,7 +408,6 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         int2 kv_cur = kept_at(blockIdx.x);
         RayPre rp_cur = kv_cur.y >= 0 ? ray_pre(A, kv_cur.y) : RayPre{};
         int2 kv_next = kept_at(blockIdx.x + gridDim.x);
-        const bool cached = BWD && A.xcache != nullptr;
         int nload[2] = {0, 0};   // row 0, backward: bulk loads issued into X panel 0 / 1
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             // (no abort-flag test: consumers reading it on either side of its setting would part at
             // their named barrier; a failed producer leaves this wait unsatisfied for all of them)
             if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
-            else if (A.xcache && !mbar_wait(&S.sm.xl[b], (i >> 1) & 1, A.wait_ns)) ok = false;
+            else if (cached && !mbar_wait(&S.sm.xl[b], (i >> 1) & 1, A.wait_ns)) ok = false;
             fence_after();
             if (!ok) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
         A.hdr->done = 0u;
         A.hdr->loss_acc = 0.0f;
         A.hdr->aux = (A.target && (A.w_pt != 0.0f || A.w_bg != 0.0f)) ? 1 : 0;
+        A.hdr->xcache = A.xcache != nullptr ? 1 : 0;
     }
     if (r >= A.R) return;
     double o[3] = {(double)rays_o[3 * r], (double)rays_o[3 * r + 1], (double)rays_o[3 * r + 2]};

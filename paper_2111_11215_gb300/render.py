@@ -71,7 +71,7 @@ class FrameRenderer:
     def __init__(self, params: B.Params, density_desc: B.GridDesc, cgrid_desc: B.GridDesc, chunk: int = 65536,
                  device="cuda"):
         self.chunk = int(chunk)
-        self.renderer = Renderer(params, density_desc, cgrid_desc, self.chunk, device=device)
+        self.renderer = Renderer(params.with_(forward_only=1), density_desc, cgrid_desc, self.chunk, device=device)
 
     def render(self, density, cgrid, mlp, rays_o, rays_d, rgb=None, tfinal=None, stream=None):
         R, dev = rays_o.shape[0], rays_o.device

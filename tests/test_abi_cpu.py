@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_strings(lib):
     import paper_2111_11215_gb300 as dvgo
-    assert dvgo.dvgo_abi_version() == 8
+    assert dvgo.dvgo_abi_version() == 9
     assert dvgo.dvgo_status_string(0) == "ok"
     assert "workspace" in dvgo.dvgo_status_string(-2)
 
