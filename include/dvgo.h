@@ -473,6 +473,14 @@ enum {
 int dvgo_profile_enable(int on);
 int dvgo_profile_read(int kind, double *total_ms, long long *launches);
 
+/* Tracing: the launches recorded while profiling was enabled, in the order they were launched
+ * (on any stream): kind, and start / end times in ms relative to the start of the first one
+ * (CUDA events of different streams on one device are comparable).  Writes up to max_records
+ * entries to the host arrays kinds, start_ms, end_ms (each of max_records elements), the number
+ * written to *n_out, waits for the events, and forgets every record (also those beyond
+ * max_records).  DVGO_ERR_INVALID_ARG for a negative max_records or null arrays. */
+int dvgo_profile_trace(int max_records, int *kinds, double *start_ms, double *end_ms, int *n_out);
+
 /* Number of kernels this library has launched in this process (all devices, all streams). */
 long long dvgo_launch_counter(void);
 

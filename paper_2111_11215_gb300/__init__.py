@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     DVGOError, GridDesc, Params, dvgo_abi_version, dvgo_adam_step, dvgo_lr_at, dvgo_render_bwd,
     dvgo_render_fwd, dvgo_sample_counts, dvgo_shift_from_alpha_init, dvgo_status_string, dvgo_workspace_size,
     dvgo_workspace_status, lib, library_path, EXPORTED_SYMBOLS, KERNEL_KINDS, dvgo_profile_enable,
-    dvgo_profile_read, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
+    dvgo_profile_read, dvgo_profile_trace, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,
     dvgo_proposal_bwd, dvgo_sample_pdf, PROP_KEYS, FreeSpace, dvgo_unknown_bbox, DVGO_ACT_POST, DVGO_ACT_PRE,
     DVGO_ACT_IN, DVGO_LAYOUT_CANONICAL, DVGO_LAYOUT_PACKED, dvgo_grid_elements, dvgo_pack_grid, dvgo_resize_grid,
     dvgo_fit2d, dvgo_touched_points, dvgo_view_counts,

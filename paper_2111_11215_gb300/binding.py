@@ -22,7 +22,7 @@ DVGO_MLP_FP32, DVGO_MLP_BF16 = 0, 1
 EXPORTED_SYMBOLS = (
     "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_lr_at",
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
-    "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_launch_counter",
+    "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_profile_trace", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
     "dvgo_unknown_bbox", "dvgo_grid_elements", "dvgo_pack_grid", "dvgo_resize_grid", "dvgo_fit2d",
     "dvgo_touched_points", "dvgo_view_counts",
@@ -144,6 +144,9 @@ def lib():
         L.dvgo_profile_enable.argtypes = [i]
         L.dvgo_profile_read.restype = i
         L.dvgo_profile_read.argtypes = [i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.dvgo_profile_trace.restype = i
+        L.dvgo_profile_trace.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int)]
         L.dvgo_launch_counter.restype = C.c_longlong
         L.dvgo_launch_counter.argtypes = []
         L.dvgo_shift_from_alpha_init.restype = f
@@ -436,6 +439,16 @@ def dvgo_profile_read(kind) -> tuple:
     ms, n = C.c_double(0.0), C.c_longlong(0)
     _check(lib().dvgo_profile_read(k, C.byref(ms), C.byref(n)), "dvgo_profile_read")
     return ms.value, n.value
+
+
+def dvgo_profile_trace(max_records: int = 65536) -> list:
+    """The launches recorded while profiling was enabled, in launch order: (kind name, start ms,
+    end ms) relative to the first one's start; forgets every record."""
+    n = int(max_records)
+    kinds, a, b = (C.c_int * max(n, 1))(), (C.c_double * max(n, 1))(), (C.c_double * max(n, 1))()
+    got = C.c_int(0)
+    _check(lib().dvgo_profile_trace(n, kinds, a, b, C.byref(got)), "dvgo_profile_trace")
+    return [(KERNEL_KINDS[kinds[i]], a[i], b[i]) for i in range(got.value)]
 
 
 def dvgo_launch_counter() -> int:

@@ -84,6 +84,36 @@ int dvgo_profile_read(int kind, double *total_ms, long long *launches) {
     return DVGO_OK;
 }
 
+int dvgo_profile_trace(int max_records, int *kinds, double *start_ms, double *end_ms, int *n_out) {
+    using namespace dvgo;
+    if (max_records < 0 || !n_out || (max_records > 0 && (!kinds || !start_ms || !end_ms)))
+        return DVGO_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int n = (int)g_recs.size() < max_records ? (int)g_recs.size() : max_records;
+    int st = DVGO_OK;
+    if (!g_recs.empty() && cudaEventSynchronize(g_recs.back().b) != cudaSuccess) st = DVGO_ERR_CUDA;
+    for (int i = 0; i < n && st == DVGO_OK; ++i) {
+        const Rec &r = g_recs[i];
+        float a = 0.0f, b = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess ||
+            cudaEventElapsedTime(&a, g_recs[0].a, r.a) != cudaSuccess ||
+            cudaEventElapsedTime(&b, g_recs[0].a, r.b) != cudaSuccess) {
+            st = DVGO_ERR_CUDA;
+            break;
+        }
+        kinds[i] = r.kind;
+        start_ms[i] = a;
+        end_ms[i] = b;
+    }
+    for (const Rec &r : g_recs) {
+        g_free.push_back(r.a);
+        g_free.push_back(r.b);
+    }
+    g_recs.clear();
+    *n_out = st == DVGO_OK ? n : 0;
+    return st;
+}
+
 long long dvgo_launch_counter(void) { return dvgo::g_launches.load(); }
 
 }  // extern "C"

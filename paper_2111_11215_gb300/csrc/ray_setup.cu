@@ -95,10 +95,16 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
 // Exclusive scan of RayRec::n into RayRec::off by one CTA of 1024 threads; the total and the
 // flag word (a ray with a zero / non-finite direction) go to the header.  Each thread scans a contiguous chunk serially, then the chunk sums are scanned
 // across the block with warp shuffles.
-__global__ void __launch_bounds__(1024) scan_counts_kernel(RenderArgs A) {
-    __shared__ int warp_tot[32];
+// One block of kScanThreads threads: thread t takes a contiguous run of rays.  The block is small
+// (8 K registers) so that it fits on an SM beside the HBM-bound Adam step of another stream; a
+// 1024-thread block does not, and would wait for the whole Adam.
+constexpr int kScanThreads = 256;
+
+__global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(RenderArgs A) {
+    constexpr int NW = kScanThreads / 32;
+    __shared__ int warp_tot[NW];
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    int per = (A.R + 1023) / 1024;
+    int per = (A.R + kScanThreads - 1) / kScanThreads;
     int beg = tid * per, end = min(beg + per, A.R);
     int local = 0, bad = 0;
     for (int i = beg; i < end; ++i) {
@@ -116,13 +122,13 @@ __global__ void __launch_bounds__(1024) scan_counts_kernel(RenderArgs A) {
     if (lane == 31) warp_tot[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        int w = warp_tot[lane];
+        int w = lane < NW ? warp_tot[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int n = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += n;
         }
-        warp_tot[lane] = w;   // inclusive over warps
+        if (lane < NW) warp_tot[lane] = w;   // inclusive over warps
     }
     __syncthreads();
     int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
@@ -130,8 +136,8 @@ __global__ void __launch_bounds__(1024) scan_counts_kernel(RenderArgs A) {
         A.rays[i].off = run;
         run += A.rays[i].n;
     }
-    if (tid == 1023) {
-        A.hdr->total = warp_tot[31];
+    if (tid == kScanThreads - 1) {
+        A.hdr->total = warp_tot[NW - 1];
         A.hdr->flags = bad ? 1 : 0;
     }
 }
@@ -154,7 +160,7 @@ void launch_ray_setup(const RenderArgs &A, const float *rays_o, const float *ray
     }
     {
         ProfScope ps_(DVGO_K_SCAN, s);
-        scan_counts_kernel<<<1, 1024, 0, s>>>(A);
+        scan_counts_kernel<<<1, kScanThreads, 0, s>>>(A);
     }
 }
 

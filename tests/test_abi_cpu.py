@@ -92,3 +92,15 @@ def test_sample_pdf_rejects_bins_and_samples_out_of_range(lib):
     for nb, ns, eta in ((0, 8, 0.1), (129, 8, 0.1), (64, 0, 0.1), (64, (1 << 24) + 1, 0.1), (64, 8, -0.5),
                         (64, 8, 1.5)):
         assert call(nb, ns, eta) == binding.DVGO_ERR_INVALID_ARG, (nb, ns, eta)
+
+
+def test_profile_trace_without_records(lib):
+    """Tracing needs no GPU while nothing was recorded: no records, no error; bad arguments are
+    rejected."""
+    import ctypes as C
+    import paper_2111_11215_gb300 as dvgo
+    from paper_2111_11215_gb300 import binding
+    assert dvgo.binding.dvgo_profile_trace(16) == []
+    n = C.c_int(7)
+    assert lib.dvgo_profile_trace(-1, None, None, None, C.byref(n)) == binding.DVGO_ERR_INVALID_ARG
+    assert lib.dvgo_profile_trace(4, None, None, None, C.byref(n)) == binding.DVGO_ERR_INVALID_ARG
