@@ -22,6 +22,7 @@ GPU, the FP64 CPU oracle's rate on a bounded sample (`cpu_baseline`).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -117,6 +118,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_ready(self, timeout_s=5.0):
+        """Block until the first sample has arrived: nvidia-smi's start-up (NVML initialisation,
+        ~0.1-0.2 s of driver work) then lies before the timed region, not inside it."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -294,6 +302,10 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
         hits.append(int((cnt > 0).sum().item()))
     dense_samples = float(np.mean(totals))
     hit_rays = float(np.mean(hits))
+    # the clock sampler runs from before the warm-up through the timed region
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    clocks.wait_ready()
     for i in range(args.warmup):
         form.step(dbatches[i % N_BATCHES])
     form.finish()                      # the timed region starts with no deferred work pending
@@ -305,16 +317,17 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = dvgo.dvgo_launch_counter()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gc.collect()
+    gc.disable()                       # no collector pause while the host issues the timed steps
     e0.record(s)
     for i in range(args.steps):
         form.step(dbatches[i % N_BATCHES])
     form.finish()
     e1.record(s)
     torch.cuda.synchronize()
+    gc.enable()
     clk = clocks.stop()
     launches = dvgo.dvgo_launch_counter() - launches0
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
@@ -862,14 +875,15 @@ def run_stress(args):
     model.forward(*batches[0][:3])
     dvgo.dvgo_sample_counts(model.renderer.workspace, nr, cnt, tot)
     samples = int(tot.item())
+    clocks = ClockSampler(0)
+    clocks.start()
+    clocks.wait_ready()
     for i in range(args.warmup):
         model.train_step(*batches[i % 4])
     torch.cuda.synchronize()
     dvgo.dvgo_profile_enable(True)
     for k in dvgo.KERNEL_KINDS:
         dvgo.dvgo_profile_read(k)
-    clocks = ClockSampler(0)
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(args.steps):
@@ -899,6 +913,40 @@ def run_stress(args):
                       "adam_gbs": n_params * (32 + 0) / 1e9 / (adam_ms / 1e3) + rs ** 3 * FEAT * 2 / 1e9 / (adam_ms / 1e3),
                       "colour_bwd_samples_per_s": samples / (kernels.get("fine_colour_bwd", 1e9) / 1e3),
                       "clocks": clk, "cpu_baseline": cpu}), flush=True)
+
+
+def run_trace(args):
+    """Per-launch timeline of the chosen training step on the config-2 scene: both streams, one
+    cycle of PROPOSAL_EVERY steps (a uniform step, then proposal steps) after 3 warm-up cycles,
+    every launch of the library with its kernel kind, start and end in ms from the cycle's first
+    launch (dvgo_profile_trace: CUDA events around every launch, comparable across streams)."""
+    import torch
+    import paper_2111_11215_gb300 as dvgo
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dens, feat, mlp, batches = workload(seed=0)
+    form = Form("chosen", dev, dens, feat, mlp, dvgo, torch, args.layout, args.lazy_adam)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(dev)  # noqa: E731
+    dbatches = [tuple(t(x) for x in b) for b in batches]
+    for i in range(3 * PROPOSAL_EVERY):
+        form.step(dbatches[i % N_BATCHES])
+    form.finish()
+    torch.cuda.synchronize()
+    dvgo.dvgo_profile_trace()              # drop earlier records
+    dvgo.dvgo_profile_enable(True)
+    for i in range(PROPOSAL_EVERY):
+        form.step(dbatches[i % N_BATCHES])
+    form.finish()
+    torch.cuda.synchronize()
+    dvgo.dvgo_profile_enable(False)
+    tr = dvgo.dvgo_profile_trace()
+    line = {"metric": "per-launch timeline of the chosen training step", "workload": "trace", "unit": "ms",
+            "steps": PROPOSAL_EVERY, "cycle_ms": round(tr[-1][2], 4) if tr else None,
+            "data": "synthetic", "config": workload_config(args, "chosen"),
+            "launches": [[k, round(a, 4), round(b, 4)] for k, a, b in tr],
+            "note": "the feature-grid Adam (kind adam, ~0.25 ms) runs on a side stream beside the next step's "
+                    "sampling, ray set-up, scan and density pass; every other launch is on the main stream"}
+    print(json.dumps(line), flush=True)
 
 
 def run_render(args):
@@ -1160,7 +1208,7 @@ def main():
     ap.add_argument("--no-proposal-eval", action="store_true")
     ap.add_argument("--no-time-to-psnr", action="store_true",
                     help="step workload: leave out the time-to-PSNR run of both forms (paper recipe) from the line")
-    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d", "view-counts"],
+    ap.add_argument("--workload", choices=["step", "time-to-psnr", "stress", "render", "toy2d", "view-counts", "trace"],
                     default="step")
     ap.add_argument("--vc-res", type=int, default=100, help="view-counts: lattice points per axis")
     ap.add_argument("--vc-views", type=int, default=100, help="view-counts: number of views")
@@ -1235,6 +1283,10 @@ def main():
     if args.workload == "stress":
         if rank == 0:
             run_stress(args)
+        return
+    if args.workload == "trace":
+        if rank == 0:
+            run_trace(args)
         return
     if args.workload == "render":
         if rank == 0:
