@@ -930,9 +930,8 @@ def run_trace(args):
     dbatches = [tuple(t(x) for x in b) for b in batches]
     for i in range(3 * PROPOSAL_EVERY):
         form.step(dbatches[i % N_BATCHES])
-    form.finish()
-    torch.cuda.synchronize()
-    dvgo.dvgo_profile_trace()              # drop earlier records
+    torch.cuda.synchronize()               # the last warm-up step's feature-grid Adam stays deferred:
+    dvgo.dvgo_profile_trace()              # the traced cycle starts in the steady state; drop earlier records
     dvgo.dvgo_profile_enable(True)
     for i in range(PROPOSAL_EVERY):
         form.step(dbatches[i % N_BATCHES])
