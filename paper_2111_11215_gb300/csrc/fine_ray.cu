@@ -248,19 +248,35 @@ __global__ void __launch_bounds__(256) fine_comp_bwd_kernel(RenderArgs A) {
                                                   fmaf(kpt * w, cc[1] - tg.y, g[1] * w),
                                                   fmaf(kpt * w, cc[2] - tg.z, g[2] * w));
             }
+            // Runs of lanes in the same cell share all 8 corners (corner q of two samples is the
+            // same point exactly when their cells are), so one segmentation serves every corner;
+            // the 8 segmented sums run side by side and stop after the warp's longest run.
+            const Seg sg = make_seg(act ? cell_base(c, A.ny, A.nz, A.packed) : -1 - lane, lane);
+            int run = lane - sg.first + 1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) run = max(run, __shfl_xor_sync(FULL, run, o));
+            int idx[8];
+            float gq[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                int idx = (int)corner_index(c, q, A.ny, A.nz, A.packed);
-                Seg sg = make_seg(act ? idx : -1 - lane, lane);
-                float gq;
+                idx[q] = (int)corner_index(c, q, A.ny, A.nz, A.packed);
                 if (kOrder == DVGO_ACT_POST) {
-                    gq = dz * corner_weight(c, q);
+                    gq[q] = dz * corner_weight(c, q);
                 } else {
-                    gq = act ? dtau * dtau_dv_pre_in(kOrder, c, q, __ldg(A.density + idx), A.shift_b, dt, sv.x) : 0.0f;
+                    gq[q] = act ? dtau * dtau_dv_pre_in(kOrder, c, q, __ldg(A.density + idx[q]), A.shift_b, dt, sv.x)
+                                : 0.0f;
                 }
-                float v = seg_sum(gq, sg, lane);
-                if (act && sg.tail && v != 0.0f) atomicAdd(A.grad_density + idx, v);   // terminated samples add 0
             }
+            for (int o = 1; o < run; o <<= 1) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float n = __shfl_up_sync(FULL, gq[q], o);
+                    if (lane - o >= sg.first) gq[q] += n;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)   // the run's last lane adds its total; terminated samples add 0
+                if (act && sg.tail && gq[q] != 0.0f) atomicAdd(A.grad_density + idx[q], gq[q]);
         }
         __syncwarp();
     }
