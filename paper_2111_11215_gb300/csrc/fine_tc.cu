@@ -82,9 +82,11 @@ struct alignas(1024) SmallTC {
     float b2[HID];
     float b3[4];
     float db3[4];
-    int slot[2][TM];          // sample slot per row, -1 for padding rows
-    int cbase[2][TM];         // flat index of the base lattice corner
-    float frac[2][TM][3];     // fractional offsets
+    // per-row tables of a tile, a ring of 4 (tile i in entry i % 4): the scatter of tile i - 2 reads
+    // other rows' entries while a producer that is done with it already fills tile i or i + 1
+    int slot[4][TM];          // sample slot per row, -1 for padding rows
+    int cbase[4][TM];         // flat index of the base lattice corner
+    float frac[4][TM][3];     // fractional offsets
     float dc[2][TM][3];       // dL/dc (backward)
     uint64_t full[2], empty[2], mma, mma1;   // mma1: the forward's second consumer group
     uint64_t xl[2];           // backward: the bulk load of X panel b from the forward's copy
@@ -111,6 +113,7 @@ struct SmemTC {
 static_assert(offsetof(SmemTC, dout) == offsetof(SmemTC, h1) + 2 * kPanelBytes, "[H1 | dout] must be contiguous");
 
 constexpr size_t smem_bytes(bool bwd) { return (bwd ? sizeof(SmemTC) : offsetof(SmemTC, dz2)) + 1024; }
+static_assert(smem_bytes(true) <= 232448, "the backward must fit one CTA per SM (227 KB of shared memory)");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
@@ -134,23 +137,52 @@ __device__ __forceinline__ float4 *de_slot(unsigned char *dout, int b, int r, in
     return reinterpret_cast<float4 *>(dout + panel_offset(r, 8 * (2 + 3 * b + k)));
 }
 
-// Producer: add a tile's feature gradients (de rows staged in the dout panel) to the grid.
+// Producer: add a tile's feature gradients (de rows staged in the dout panel) to the grid.  Rows
+// are in kept order, so consecutive samples of a ray sit in consecutive rows; rows whose samples lie
+// in one lattice cell share all eight corners, and the last row of such a run adds the whole run's
+// weighted de with one set of reductions (the run's other rows add nothing).
 template <bool PK>
-__device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int b, int row) {
-    const int slot = S.sm.slot[b][row];
+__device__ __forceinline__ void scatter_row(const RenderArgs &A, SmemTC &S, int b, int t, int row) {
+    const int slot = S.sm.slot[t][row];
     if (slot < 0) return;
-    const float4 e0 = *de_slot(S.dout, b, row, 0), e1 = *de_slot(S.dout, b, row, 1), e2 = *de_slot(S.dout, b, row, 2);
-    const float fx = S.sm.frac[b][row][0], fy = S.sm.frac[b][row][1], fz = S.sm.frac[b][row][2];
-    const int cb = S.sm.cbase[b][row];
+    const int cb = S.sm.cbase[t][row];
+    if (row + 1 < TM && S.sm.slot[t][row + 1] >= 0 && S.sm.cbase[t][row + 1] == cb) return;
+    float4 acc[8][3];
+    {
+        const float4 e0 = *de_slot(S.dout, b, row, 0), e1 = *de_slot(S.dout, b, row, 1),
+                     e2 = *de_slot(S.dout, b, row, 2);
+        const float fx = S.sm.frac[t][row][0], fy = S.sm.frac[t][row][1], fz = S.sm.frac[t][row][2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float w = (((q >> 2) & 1) ? fx : 1.0f - fx) * (((q >> 1) & 1) ? fy : 1.0f - fy) *
+                            ((q & 1) ? fz : 1.0f - fz);
+            acc[q][0] = make_float4(w * e0.x, w * e0.y, w * e0.z, w * e0.w);
+            acc[q][1] = make_float4(w * e1.x, w * e1.y, w * e1.z, w * e1.w);
+            acc[q][2] = make_float4(w * e2.x, w * e2.y, w * e2.z, w * e2.w);
+        }
+    }
+    for (int j = row - 1; j >= 0 && S.sm.slot[t][j] >= 0 && S.sm.cbase[t][j] == cb; --j) {
+        const float4 e0 = *de_slot(S.dout, b, j, 0), e1 = *de_slot(S.dout, b, j, 1), e2 = *de_slot(S.dout, b, j, 2);
+        const float fx = S.sm.frac[t][j][0], fy = S.sm.frac[t][j][1], fz = S.sm.frac[t][j][2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float w = (((q >> 2) & 1) ? fx : 1.0f - fx) * (((q >> 1) & 1) ? fy : 1.0f - fy) *
+                            ((q & 1) ? fz : 1.0f - fz);
+            acc[q][0] = make_float4(fmaf(w, e0.x, acc[q][0].x), fmaf(w, e0.y, acc[q][0].y),
+                                    fmaf(w, e0.z, acc[q][0].z), fmaf(w, e0.w, acc[q][0].w));
+            acc[q][1] = make_float4(fmaf(w, e1.x, acc[q][1].x), fmaf(w, e1.y, acc[q][1].y),
+                                    fmaf(w, e1.z, acc[q][1].z), fmaf(w, e1.w, acc[q][1].w));
+            acc[q][2] = make_float4(fmaf(w, e2.x, acc[q][2].x), fmaf(w, e2.y, acc[q][2].y),
+                                    fmaf(w, e2.z, acc[q][2].z), fmaf(w, e2.w, acc[q][2].w));
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const int bx = (q >> 2) & 1, by = (q >> 1) & 1, bz = q & 1;
-        const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz);
-        const long long idx = corner_from_base(cb, bx, by, bz, A.ny, A.nz, PK);
+        const long long idx = corner_from_base(cb, (q >> 2) & 1, (q >> 1) & 1, q & 1, A.ny, A.nz, PK);
         float4 *g = reinterpret_cast<float4 *>(A.grad_cgrid + idx * FEAT);
-        atomicAdd(g + 0, make_float4(w * e0.x, w * e0.y, w * e0.z, w * e0.w));
-        atomicAdd(g + 1, make_float4(w * e1.x, w * e1.y, w * e1.z, w * e1.w));
-        atomicAdd(g + 2, make_float4(w * e2.x, w * e2.y, w * e2.z, w * e2.w));
+        atomicAdd(g + 0, acc[q][0]);
+        atomicAdd(g + 1, acc[q][1]);
+        atomicAdd(g + 2, acc[q][2]);
     }
 }
 
@@ -195,8 +227,8 @@ __device__ __forceinline__ Cell cell_pre(const RenderArgs &A, const RayPre &p, i
 // Producer: gather sample row `row` of a tile (kept entry kv, kv.y < 0 for a padding row; its ray's
 // prefetched data rp) into X panel b (and its tail) and the per-row tables.
 template <typename FeatT, bool BWD, bool PEX, bool PK>
-__device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int2 kv, const RayPre &rp,
-                                            int row, bool cached) {
+__device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int b, int t, int2 kv,
+                                            const RayPre &rp, int row, bool cached) {
     // cached (backward): the X panel arrives by bulk copy; only the tables, dL/dc and the tail here
     using D = TcDims<PEX>;
     float v[64], tail[16];
@@ -311,11 +343,11 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
         panel_store8(S.tp, row, 16 * (1 + b), tail);
         panel_store8(S.tp, row, 16 * (1 + b) + 8, tail + 8);
     }
-    S.sm.slot[b][row] = slot;
-    S.sm.cbase[b][row] = cbase;
-    S.sm.frac[b][row][0] = fx;
-    S.sm.frac[b][row][1] = fy;
-    S.sm.frac[b][row][2] = fz;
+    S.sm.slot[t][row] = slot;
+    S.sm.cbase[t][row] = cbase;
+    S.sm.frac[t][row][0] = fx;
+    S.sm.frac[t][row][1] = fy;
+    S.sm.frac[t][row][2] = fz;
     if (BWD) {
         S.sm.dc[b][row][0] = d0;
         S.sm.dc[b][row][1] = d1;
@@ -423,8 +455,8 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 bulk_load(S.x[b], A.xcache + (size_t)tile * kPanelBytes, kPanelBytes, &S.sm.xl[b]);
                 ++nload[b];
             }
-            if (BWD && i >= 2) scatter_row<PK>(A, S, b, row);   // feature gradients of tile i - 2
-            produce_row<FeatT, BWD, PEX, PK>(A, S, b, kv_cur, rp_cur, row, cached);
+            if (BWD && i >= 2) scatter_row<PK>(A, S, b, (i - 2) & 3, row);   // feature gradients of tile i - 2
+            produce_row<FeatT, BWD, PEX, PK>(A, S, b, i & 3, kv_cur, rp_cur, row, cached);
             fence_async_smem();
             // (testing aid: one arrival withheld on a chosen tile makes the consumers' wait run out)
             if (!(row == 0 && tile + 1 == A.withhold_tile)) mbar_arrive(&S.sm.full[b]);
@@ -436,7 +468,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             // the last (up to) two tiles: wait until the consumers are done with them, then scatter
             for (int j = (i >= 2 ? i - 2 : 0); j < i && ok; ++j) {
                 if (!mbar_wait(&S.sm.empty[j & 1], (j >> 1) & 1, A.wait_ns)) ok = false;
-                else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, row);
+                else if (!*(volatile int *)&S.sm.abort) scatter_row<PK>(A, S, j & 1, j & 3, row);
             }
         }
         // every bulk load issued has landed before the CTA can exit (bounded)
@@ -480,7 +512,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             if (!mbar_wait(&S.sm.full[b], (i >> 1) & 1, A.wait_ns)) ok = false;
             fence_after();
             if (!ok) break;
-            const int slot = S.sm.slot[b][r];
+            const int slot = S.sm.slot[i & 3][r];
             // ---- layer 1: Z1 = X W1 ----
             if (r == 0) {
 #pragma unroll 1
@@ -577,7 +609,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             fence_after();
             if (!ok) break;
             // per-row tables of buffer b, read before the buffer is handed back to the producers
-            const int slot = S.sm.slot[b][r];
+            const int slot = S.sm.slot[i & 3][r];
             const float d0 = BWD ? S.sm.dc[b][r][0] : 0.0f, d1 = BWD ? S.sm.dc[b][r][1] : 0.0f,
                         d2 = BWD ? S.sm.dc[b][r][2] : 0.0f;
             // ---- layer 1: Z1 = X W1 ----
