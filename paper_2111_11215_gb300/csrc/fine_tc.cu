@@ -78,7 +78,6 @@ constexpr uint32_t COL_Z1 = 0, COL_O = 0, COL_Z2 = 128, COL_DW2T = 256, COL_DW1 
 // Small per-CTA state, padded to a multiple of 1024 bytes so that the panels after it stay
 // aligned to the 128-byte-swizzle atom.
 struct alignas(1024) SmallTC {
-    float4 w3[HID];           // W3 row per hidden unit (3 used), BF16-rounded: dH2 = dout W3^T on the CUDA cores
     float b2[HID];
     float b3[4];
     float db3[4];
@@ -412,8 +411,6 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
             for (int c = 0; c < 64; c += 8) panel_store8(S.dout, tid, c, v + c);
         }
         S.sm.b2[tid] = A.b2[tid];
-        S.sm.w3[tid] = make_float4(bf16_round(A.w3[3 * tid]), bf16_round(A.w3[3 * tid + 1]),
-                                   bf16_round(A.w3[3 * tid + 2]), 0.0f);
         if (tid < 3) S.sm.b3[tid] = A.b3[tid];
         if (tid < 4) S.sm.db3[tid] = 0.0f;
     }
@@ -554,7 +551,13 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 float z[32];
                 tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * g), z);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k] + S.sm.b2[32 * g + k], 0.0f);
+                for (int k = 0; k < 32; k += 4) {
+                    const float4 bb = *reinterpret_cast<const float4 *>(&S.sm.b2[32 * g + k]);
+                    z[k] = fmaxf(z[k] + bb.x, 0.0f);
+                    z[k + 1] = fmaxf(z[k + 1] + bb.y, 0.0f);
+                    z[k + 2] = fmaxf(z[k + 2] + bb.z, 0.0f);
+                    z[k + 3] = fmaxf(z[k + 3] + bb.w, 0.0f);
+                }
 #pragma unroll
                 for (int k = 0; k < 32; k += 8) panel_store8(hp + (g >> 1) * kPanelBytes, r, 32 * (g & 1) + k, z + k);
             }
@@ -640,32 +643,47 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 #pragma unroll
                 for (int k = 0; k < 32; k += 8) panel_store8(S.h1 + hc * kPanelBytes, r, 32 * g + k, z + k);
             }
+            // dout = dL/dc c (1 - c), formed by the producers, into the dout panel: the operand of
+            // dH2 (issued with layer 2), of dW3 and, through its constant-1 column, of db2
+            if (BWD && hc == 0) {
+                db3_part[0] += d0;
+                db3_part[1] += d1;
+                db3_part[2] += d2;
+                uint2 q;
+                q.x = pack_bf16(d0, d1);
+                q.y = pack_bf16(d2, 1.0f);
+                *reinterpret_cast<uint2 *>(S.dout + panel_offset(r, 0)) = q;
+            }
             consumer_publish();
-            // ---- layer 2: Z2 = H1 W2 ----
+            // ---- layer 2: Z2 = H1 W2; in the backward also dH2 = dout W3^T (K = 16: dout's columns
+            //      [dL/do, 1, 0 ...] against the tail panel's [W3, 0 ...]) into Z1's columns, which
+            //      epilogue 1 has read ----
             if (tid == 0) {
 #pragma unroll 1
                 for (int kk = 0; kk < 8; ++kk)
                     mma(tb + COL_Z2, desc_kmajor(h1_, kk), desc_kmajor(w2t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                if (BWD)
+                    mma(tb + COL_Z1, desc_kmajor(dout_, 0), desc_kmajor(w3p_, 0), idesc_bf16(128, 128, 0, 0), 0u);
                 commit(&S.sm.mma);
             }
             if (!wait_mma()) { ok = false; break; }
             // ---- epilogue 2: H2 = relu(Z2 + b2), my 64 columns; in the backward also
-            //      dZ2 = (dout W3^T) [Z2 + b2 > 0] on the CUDA cores, from the BF16 operands the MMA
-            //      would take (dout rounded, W3 rounded; the three products are exact in FP32) ----
-            const float e0 = BWD ? bf16_round(d0) : 0.0f, e1 = BWD ? bf16_round(d1) : 0.0f,
-                        e2 = BWD ? bf16_round(d2) : 0.0f;
+            //      dZ2 = dH2 [Z2 + b2 > 0] ----
 #pragma unroll 1
             for (int g = 0; g < 2; ++g) {
                 const int col = 64 * hc + 32 * g;
                 float z[32], dz[32];
                 tmem_ld32(taddr(tb, warp, COL_Z2 + col), z);
+                if (BWD) tmem_ld32(taddr(tb, warp, COL_Z1 + col), dz);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float h = z[k] + S.sm.b2[col + k];
-                    z[k] = fmaxf(h, 0.0f);
-                    if (BWD) {
-                        const float4 w = S.sm.w3[col + k];
-                        dz[k] = h > 0.0f ? fmaf(e0, w.x, fmaf(e1, w.y, e2 * w.z)) : 0.0f;
+                for (int k = 0; k < 32; k += 4) {
+                    const float4 bb = *reinterpret_cast<const float4 *>(&S.sm.b2[col + k]);
+                    const float hb[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float h = z[k + j] + hb[j];
+                        z[k + j] = fmaxf(h, 0.0f);
+                        if (BWD) dz[k + j] = h > 0.0f ? dz[k + j] : 0.0f;
                     }
                 }
 #pragma unroll
@@ -699,18 +717,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 consumer_sync();   // TMEM reads done before the next tile's MMAs
                 continue;
             }
-            // ---- backward: dout = dL/dc c (1 - c), formed by the producers, into the dout panel
-            //      (the operand of dW3 and, through its constant-1 column, of db2); the publish
-            //      covers H2, dZ2 and dout ----
-            if (hc == 0) {
-                db3_part[0] += d0;
-                db3_part[1] += d1;
-                db3_part[2] += d2;
-                uint2 q;
-                q.x = pack_bf16(d0, d1);
-                q.y = pack_bf16(d2, 1.0f);
-                *reinterpret_cast<uint2 *>(S.dout + panel_offset(r, 0)) = q;
-            }
+            // ---- backward: H2 and dZ2 published for batch A ----
             consumer_publish();
             if (tid == 0) {
 #pragma unroll 1
