@@ -53,9 +53,17 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;
-constexpr int NT = 384;        // 8 consumer + 4 producer warps
 constexpr int NC = 256;        // consumer threads: warp w owns TMEM lanes 32 (w % 4).., columns 64 (w / 4)..
-constexpr int NP = 128;        // producer threads (one sample row each)
+constexpr int NP = 128;        // producer threads of one set (one sample row each)
+// producer sets: the backward has one (its consumers are the bound); the forward two, set p filling
+// X buffer p for consumer group p, so that two tiles are gathered at once
+#ifndef DVGO_FWD_PROD_SETS
+#define DVGO_FWD_PROD_SETS 2
+#endif
+template <bool BWD>
+constexpr int kProdSets = BWD ? 1 : DVGO_FWD_PROD_SETS;
+template <bool BWD>
+constexpr int kThreads = NC + NP * kProdSets<BWD>;   // 384 / 512
 constexpr int HID = 128;
 constexpr int FEAT = 12;
 constexpr int NF = 4;
@@ -355,7 +363,7 @@ __device__ __forceinline__ void produce_row(const RenderArgs &A, SmemTC &S, int 
 }
 
 template <typename FeatT, bool BWD, bool PEX, bool PK>
-__global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
+__global__ void __launch_bounds__(kThreads<BWD>, 1) fine_colour_tc_kernel(RenderArgs A) {
     using D = TcDims<PEX>;
     extern __shared__ unsigned char smem_raw[];
     SmemTC &S = *reinterpret_cast<SmemTC *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -426,23 +434,27 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
 
     if (tid >= NC) {
         // ------------------------------- producers -------------------------------
-        // Software-pipelined a tile deep: while producing a tile, a producer already has the next
-        // tile's kept entry and fetches that tile's ray data and the kept entry of the tile after, so
-        // that only the corner-feature loads of a tile wait on memory when it is produced.
-        const int row = tid - NC;   // 0 .. NP-1
+        // Set pset takes the CTA's tiles i = pset, pset + nsets, ... (X buffer i & 1).  Software-
+        // pipelined a tile deep: while producing a tile, a producer already has its set's next tile's
+        // kept entry and fetches that tile's ray data and the kept entry of the tile after, so that
+        // only the corner-feature loads of a tile wait on memory when it is produced.
+        constexpr int nsets = kProdSets<BWD>;
+        const int row = (tid - NC) & (NP - 1), pset = (tid - NC) / NP;
+        const int stride = nsets * (int)gridDim.x;
         auto kept_at = [&](int t) -> int2 {
             const int e = t * TM + row;
             return (t < ntiles && e < n_kept) ? A.kept[e] : make_int2(-1, -1);
         };
-        int2 kv_cur = kept_at(blockIdx.x);
+        const int tile0 = (int)blockIdx.x + pset * (int)gridDim.x;
+        int2 kv_cur = kept_at(tile0);
         RayPre rp_cur = kv_cur.y >= 0 ? ray_pre(A, kv_cur.y) : RayPre{};
-        int2 kv_next = kept_at(blockIdx.x + gridDim.x);
+        int2 kv_next = kept_at(tile0 + stride);
         int nload[2] = {0, 0};   // row 0, backward: bulk loads issued into X panel 0 / 1
-        int i = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        int i = pset;
+        for (int tile = tile0; tile < ntiles; tile += stride, i += nsets) {
             const int b = i & 1;
             const RayPre rp_next = kv_next.y >= 0 ? ray_pre(A, kv_next.y) : RayPre{};
-            const int2 kv_after = kept_at(tile + 2 * gridDim.x);
+            const int2 kv_after = kept_at(tile + 2 * stride);
             if (i >= 2 && !mbar_wait(&S.sm.empty[b], ((i >> 1) - 1) & 1, A.wait_ns)) {
                 ok = false;
                 break;
@@ -477,13 +489,15 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         // Group grp = warp / 4 takes every other tile of this CTA (the CTA's tiles i = grp, grp + 2,
         // ..., so always X buffer grp), so that one group's epilogues run while the other group's
         // MMAs do.  Thread r = tid % 128 owns row r (its TMEM lane) and all 128 columns; the group
-        // has its own 256 TMEM columns (Z1 and O at +0, Z2 at +128), its own H panel pair (h1 for
-        // group 0, h2 for group 1; H2 overwrites H1 once layer 2 has read it), MMA barrier and
-        // named barrier (2 + grp, 128 threads).
+        // has its own 256 TMEM columns, MMA barrier and named barrier (2 + grp, 128 threads).  The
+        // hidden activations never go to shared memory: each epilogue writes them back to TMEM as
+        // BF16 (two per column) and the next layer reads its A operand from there.  Columns:
+        // Z1 at +0, then H1 at +0 (64 columns, over the Z1 values already read) and H2 at +64;
+        // Z2 at +128, then O at +128.
+        constexpr uint32_t F_H1 = 0, F_H2 = 64, F_Z2 = 128, F_O = 128;
         const int grp = warp >> 2, r = tid & (TM - 1);
         const uint32_t tb = S.sm.tmem_base + 256u * (uint32_t)grp;
         uint64_t *mbar = grp ? &S.sm.mma1 : &S.sm.mma;
-        unsigned char *hp = grp ? S.h2 : S.h1;
         uint32_t mphase = 0;
         auto wait_mma = [&]() -> bool {
             bool w = mbar_wait(mbar, mphase, A.wait_ns);
@@ -501,8 +515,7 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
         for (int tile = blockIdx.x + grp * gridDim.x; tile < ntiles; tile += 2 * gridDim.x, i += 2) {
             const int b = grp;
             uint32_t x_ = smem_u32(S.x[b]), w1t_ = smem_u32(S.w1t), w2t_ = smem_u32(S.w2t), w3p_ = smem_u32(S.tp);
-            uint32_t hp_ = smem_u32(hp);
-            asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_), "+r"(hp_));
+            asm volatile("" : "+r"(x_), "+r"(w1t_), "+r"(w2t_), "+r"(w3p_));
             // (no abort-flag test here: two warps of a group could read it on either side of its
             // setting and part at the group barrier; a failed producer instead leaves this wait
             // unsatisfied for every thread of the group alike)
@@ -525,54 +538,55 @@ __global__ void __launch_bounds__(NT, 1) fine_colour_tc_kernel(RenderArgs A) {
                 if (A.xcache) bulk_wait_read();
                 mbar_arrive(&S.sm.empty[b]);
             }
-            // ---- epilogue 1: H1 = relu(Z1), all 128 columns of my row ----
+            // ---- epilogue 1: H1 = relu(Z1), all 128 columns of my row, as BF16 into TMEM (32-column
+            //      chunk g of Z1 becomes columns 16 g .. 16 g + 15, which chunks before g held) ----
 #pragma unroll 1
             for (int g = 0; g < 4; ++g) {
                 float z[32];
                 tmem_ld32(taddr(tb, warp, COL_Z1 + 32 * g), z);
+                uint32_t h[16];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k], 0.0f);
-#pragma unroll
-                for (int k = 0; k < 32; k += 8) panel_store8(hp + (g >> 1) * kPanelBytes, r, 32 * (g & 1) + k, z + k);
+                for (int k = 0; k < 16; ++k) h[k] = pack_bf16(fmaxf(z[2 * k], 0.0f), fmaxf(z[2 * k + 1], 0.0f));
+                tmem_st16(taddr(tb, warp, F_H1 + 16 * g), h);
             }
-            fence_async_smem();
+            tmem_wait_st();
             group_sync();
-            // ---- layer 2: Z2 = H1 W2 ----
+            // ---- layer 2: Z2 = H1 W2, A = H1 from TMEM ----
             if (r == 0) {
 #pragma unroll 1
                 for (int kk = 0; kk < 8; ++kk)
-                    mma(tb + COL_Z2, desc_kmajor(hp_, kk), desc_kmajor(w2t_, kk), idesc_bf16(128, 128, 0, 0), kk > 0);
+                    mma_ts(tb + F_Z2, tb + F_H1 + 8u * (uint32_t)kk, desc_kmajor(w2t_, kk), idesc_bf16(128, 128, 0, 0),
+                           kk > 0);
                 commit(mbar);
             }
             if (!wait_mma()) { ok = false; break; }
-            // ---- epilogue 2: H2 = relu(Z2 + b2) over H1 ----
+            // ---- epilogue 2: H2 = relu(Z2 + b2), as BF16 into TMEM ----
 #pragma unroll 1
             for (int g = 0; g < 4; ++g) {
                 float z[32];
-                tmem_ld32(taddr(tb, warp, COL_Z2 + 32 * g), z);
+                tmem_ld32(taddr(tb, warp, F_Z2 + 32 * g), z);
+                uint32_t h[16];
 #pragma unroll
                 for (int k = 0; k < 32; k += 4) {
                     const float4 bb = *reinterpret_cast<const float4 *>(&S.sm.b2[32 * g + k]);
-                    z[k] = fmaxf(z[k] + bb.x, 0.0f);
-                    z[k + 1] = fmaxf(z[k + 1] + bb.y, 0.0f);
-                    z[k + 2] = fmaxf(z[k + 2] + bb.z, 0.0f);
-                    z[k + 3] = fmaxf(z[k + 3] + bb.w, 0.0f);
+                    h[k / 2] = pack_bf16(fmaxf(z[k] + bb.x, 0.0f), fmaxf(z[k + 1] + bb.y, 0.0f));
+                    h[k / 2 + 1] = pack_bf16(fmaxf(z[k + 2] + bb.z, 0.0f), fmaxf(z[k + 3] + bb.w, 0.0f));
                 }
-#pragma unroll
-                for (int k = 0; k < 32; k += 8) panel_store8(hp + (g >> 1) * kPanelBytes, r, 32 * (g & 1) + k, z + k);
+                tmem_st16(taddr(tb, warp, F_H2 + 16 * g), h);
             }
-            fence_async_smem();
+            tmem_wait_st();
             group_sync();
-            // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used) ----
+            // ---- layer 3: O = H2 W3 (N = 16, columns 0-2 used), A = H2 from TMEM ----
             if (r == 0) {
 #pragma unroll 1
                 for (int kk = 0; kk < 8; ++kk)
-                    mma(tb + COL_O, desc_kmajor(hp_, kk), desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1), kk > 0);
+                    mma_ts(tb + F_O, tb + F_H2 + 8u * (uint32_t)kk, desc_mnmajor(w3p_, kk), idesc_bf16(128, 16, 0, 1),
+                           kk > 0);
                 commit(mbar);
             }
             if (!wait_mma()) { ok = false; break; }
             float o[16];
-            tmem_ld16(taddr(tb, warp, COL_O), o);
+            tmem_ld16(taddr(tb, warp, F_O), o);
             if (slot >= 0) {
                 float *sp = reinterpret_cast<float *>(A.samp + slot);
                 sp[1] = sigmoidf_(o[0] + S.sm.b3[0]);
@@ -844,7 +858,7 @@ void launch_tc(const RenderArgs &A, int kind, cudaStream_t s) {
     const int bytes = (int)smem_bytes(BWD);
     ensure_smem(reinterpret_cast<const void *>(kern), bytes);
     ProfScope ps_(kind, s);
-    kern<<<num_sms(), NT, bytes, s>>>(A);
+    kern<<<num_sms(), kThreads<BWD>, bytes, s>>>(A);
 }
 
 template <bool BWD>
