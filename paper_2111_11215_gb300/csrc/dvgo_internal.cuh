@@ -15,6 +15,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "dvgo.h"
@@ -46,6 +47,7 @@ struct RayRec {
     int off;             // first sample slot (exclusive scan of n)
 };
 static_assert(sizeof(RayRec) == 128, "RayRec layout");
+static_assert(offsetof(RayRec, off) == offsetof(RayRec, n) + 4 && offsetof(RayRec, n) % 8 == 0, "RayRec (n, off) pair");
 
 // Workspace header (first 256 bytes of the workspace).
 struct WsHeader {

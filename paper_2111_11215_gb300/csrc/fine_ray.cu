@@ -34,66 +34,104 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 // Specialised on the known-free-space test and the activation order (uniform per launch), so the
-// default configuration carries neither.
-template <bool kFreeSpace, int kOrder>
-__global__ void __launch_bounds__(256) fine_density_kernel(RenderArgs A) {
+// default configuration carries neither.  A warp walks its ray two 32-sample chunks at a time: the
+// optical depths of both chunks are formed first (their density loads in flight together), then
+// the chunks are composited in order, and one atomic reserves the kept-list slots of both.
+template <bool kFreeSpace, int kOrder, bool kExpl>
+__device__ __forceinline__ float sample_tau(const RenderArgs &A, const RayRec &rr, int r, int k, bool &kept) {
+    float dt;
+    long long u[3];
+    if (kExpl) {   // sample_fx's explicit branch, without the run-time test
+        const double t = (double)A.ts[(long long)r * A.n_expl + k];
+        dt = A.dts[(long long)r * A.n_expl + k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = rr.uefx[a] + to_fx((t - rr.t_enter) * rr.e[a]);
+    } else {
+        dt = A.step;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = rr.u0fx[a] + (long long)k * rr.dfx[a];
+    }
+    kept = false;
+    if (kFreeSpace && known_free(A, u)) return 0.0f;   // known free space: no fine query
+    const Cell c = cell_from_fx(u, A.nx, A.ny, A.nz);
+    float tau;
+    if (kOrder == DVGO_ACT_POST) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed)), s);
+        tau = softplusf(s + A.shift_b) * dt;
+    } else {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed));
+        tau = tau_pre_in(kOrder, c, v, A.shift_b, dt);
+    }
+    kept = !(-expm1f(-tau) < A.tau_f);
+    return kept ? tau : 0.0f;
+}
+
+// 128-thread blocks: the pass runs beside the feature-grid Adam of the other stream (3 x 256
+// threads x 56 registers per SM), next to which three of them fit per SM where one 256-thread
+// block does.
+constexpr int kDensityThreads = 128;
+#ifndef DVGO_DENSITY_MIN_BLOCKS
+#define DVGO_DENSITY_MIN_BLOCKS 1
+#endif
+template <bool kFreeSpace, int kOrder, bool kExpl>
+__global__ void __launch_bounds__(kDensityThreads, DVGO_DENSITY_MIN_BLOCKS) fine_density_kernel(RenderArgs A) {
     int lane = threadIdx.x & 31;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp; r < A.R; r += nwarps) {
         const RayRec rr = A.rays[r];
         float carry = 0.0f;          // optical depth before this chunk, as the compositing pass forms it
-        for (int base = 0; base < rr.n; base += 32) {
-            int k = base + lane;
-            bool valid = k < rr.n;
-            float tau = 0.0f;
-            bool kept = false;
+        for (int base = 0; base < rr.n; base += 64) {
             if (isinf(carry)) {      // terminated: T = 0 from here on
-                if (valid) A.samp[rr.off + k] = make_float4(INFINITY, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (base + 32 * h + lane < rr.n)
+                        A.samp[rr.off + base + 32 * h + lane] = make_float4(INFINITY, 0.0f, 0.0f, 0.0f);
                 continue;
             }
-            if (valid) {
-                float dt;
-                long long u[3];
-                sample_fx(A, rr, r, k, dt, u);
-                if (!(kFreeSpace && known_free(A, u))) {   // known free space: no fine query
-                    const Cell c = cell_from_fx(u, A.nx, A.ny, A.nz);
-                    if (kOrder == DVGO_ACT_POST) {
-                        float s = 0.0f;
+            float tau[2];
+            bool kept[2];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            s = fmaf(corner_weight(c, q), __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed)), s);
-                        tau = softplusf(s + A.shift_b) * dt;
-                    } else {
-                        float v[8];
+            for (int h = 0; h < 2; ++h) {
+                const int k = base + 32 * h + lane;
+                tau[h] = 0.0f;
+                kept[h] = false;
+                if (k < rr.n) tau[h] = sample_tau<kFreeSpace, kOrder, kExpl>(A, rr, r, k, kept[h]);
+            }
+            unsigned m[2];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] = __ldg(A.density + corner_index(c, q, A.ny, A.nz, A.packed));
-                        tau = tau_pre_in(kOrder, c, v, A.shift_b, dt);
+            for (int h = 0; h < 2; ++h) {
+                const int k = base + 32 * h + lane;
+                if (isinf(carry)) {  // the first chunk terminated the ray
+                    kept[h] = false;
+                    tau[h] = INFINITY;
+                } else {
+                    // T_k of the compositing pass; exactly 0 -> terminated (the scan sees tau of lanes below only)
+                    const float incl = warp_incl_scan(tau[h], lane);
+                    float excl = __shfl_up_sync(FULL, incl, 1);
+                    if (lane == 0) excl = 0.0f;
+                    if (expf(-(carry + excl)) == 0.0f) {
+                        kept[h] = false;
+                        tau[h] = INFINITY;
                     }
-                    kept = !(-expm1f(-tau) < A.tau_f);
-                    if (!kept) tau = 0.0f;
+                    const bool any_dead = __any_sync(FULL, isinf(tau[h]));
+                    carry = any_dead ? INFINITY : carry + __shfl_sync(FULL, incl, 31);
                 }
+                if (k < rr.n) A.samp[rr.off + k] = make_float4(tau[h], 0.0f, 0.0f, 0.0f);
+                m[h] = __ballot_sync(FULL, kept[h]);
             }
-            // T_k of the compositing pass; exactly 0 -> terminated (the scan sees tau of lanes below only)
-            const float incl = warp_incl_scan(tau, lane);
-            float excl = __shfl_up_sync(FULL, incl, 1);
-            if (lane == 0) excl = 0.0f;
-            if (expf(-(carry + excl)) == 0.0f) {
-                kept = false;
-                tau = INFINITY;
-            }
-            const bool any_dead = __any_sync(FULL, isinf(tau));
-            carry = any_dead ? INFINITY : carry + __shfl_sync(FULL, incl, 31);
-            if (valid) A.samp[rr.off + k] = make_float4(tau, 0.0f, 0.0f, 0.0f);
-            unsigned m = __ballot_sync(FULL, kept);
-            int cnt = __popc(m);
+            const int cnt0 = __popc(m[0]), cnt = cnt0 + __popc(m[1]);
             int base_slot = 0;
             if (lane == 0 && cnt) base_slot = atomicAdd(&A.hdr->n_kept, cnt);
             base_slot = __shfl_sync(FULL, base_slot, 0);
-            if (kept) {
-                int rank = __popc(m & ((1u << lane) - 1u));
-                A.kept[base_slot + rank] = make_int2(rr.off + k, r);
-            }
+            const unsigned below = (1u << lane) - 1u;
+            if (kept[0]) A.kept[base_slot + __popc(m[0] & below)] = make_int2(rr.off + base + lane, r);
+            if (kept[1]) A.kept[base_slot + cnt0 + __popc(m[1] & below)] = make_int2(rr.off + base + 32 + lane, r);
         }
     }
 }
@@ -294,15 +332,22 @@ int warp_grid(int R, int warps_per_block) {
 void launch_fine_density(const RenderArgs &A, cudaStream_t s) {
     {
         ProfScope ps_(DVGO_K_FINE_DENSITY, s);
-        const dim3 g(warp_grid(A.R, 8));
+        const dim3 g(warp_grid(A.R, kDensityThreads / 32));
         const bool fs = A.fs_density != nullptr;
-        switch (A.act_order * 2 + (fs ? 1 : 0)) {
-            case 0: fine_density_kernel<false, DVGO_ACT_POST><<<g, 256, 0, s>>>(A); break;
-            case 1: fine_density_kernel<true, DVGO_ACT_POST><<<g, 256, 0, s>>>(A); break;
-            case 2: fine_density_kernel<false, DVGO_ACT_PRE><<<g, 256, 0, s>>>(A); break;
-            case 3: fine_density_kernel<true, DVGO_ACT_PRE><<<g, 256, 0, s>>>(A); break;
-            case 4: fine_density_kernel<false, DVGO_ACT_IN><<<g, 256, 0, s>>>(A); break;
-            default: fine_density_kernel<true, DVGO_ACT_IN><<<g, 256, 0, s>>>(A); break;
+        const bool ex = A.ts != nullptr;
+        switch (A.act_order * 4 + (fs ? 2 : 0) + (ex ? 1 : 0)) {
+            case 0: fine_density_kernel<false, DVGO_ACT_POST, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 1: fine_density_kernel<false, DVGO_ACT_POST, true><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 2: fine_density_kernel<true, DVGO_ACT_POST, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 3: fine_density_kernel<true, DVGO_ACT_POST, true><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 4: fine_density_kernel<false, DVGO_ACT_PRE, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 5: fine_density_kernel<false, DVGO_ACT_PRE, true><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 6: fine_density_kernel<true, DVGO_ACT_PRE, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 7: fine_density_kernel<true, DVGO_ACT_PRE, true><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 8: fine_density_kernel<false, DVGO_ACT_IN, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 9: fine_density_kernel<false, DVGO_ACT_IN, true><<<g, kDensityThreads, 0, s>>>(A); break;
+            case 10: fine_density_kernel<true, DVGO_ACT_IN, false><<<g, kDensityThreads, 0, s>>>(A); break;
+            default: fine_density_kernel<true, DVGO_ACT_IN, true><<<g, kDensityThreads, 0, s>>>(A); break;
         }
     }
 }

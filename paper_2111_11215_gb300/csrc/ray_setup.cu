@@ -92,52 +92,62 @@ __global__ void __launch_bounds__(64) ray_setup_kernel(RenderArgs A, const float
     A.rays[r] = rec;
 }
 
-// Exclusive scan of RayRec::n into RayRec::off by one CTA of 1024 threads; the total and the
-// flag word (a ray with a zero / non-finite direction) go to the header.  Each thread scans a contiguous chunk serially, then the chunk sums are scanned
-// across the block with warp shuffles.
-// One block of kScanThreads threads: thread t takes a contiguous run of rays.  The block is small
-// (8 K registers) so that it fits on an SM beside the HBM-bound Adam step of another stream; a
-// 1024-thread block does not, and would wait for the whole Adam.
+// Exclusive scan of RayRec::n into RayRec::off by one block; the total and the flag word (a ray
+// with a zero / non-finite direction) go to the header.  The block is small (256 threads) so that
+// it fits on an SM beside the HBM-bound Adam step of another stream; a 1024-thread block does not,
+// and would wait for the whole Adam.  It works in rounds of 256 x kScanPer rays: thread t takes
+// the contiguous run of kScanPer rays at base + kScanPer t and issues all their (n, off) loads at
+// once (one load latency per round, not one per ray), the run sums are scanned across the block
+// with warp shuffles, and the offsets are written from registers.
 constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
 
 __global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(RenderArgs A) {
     constexpr int NW = kScanThreads / 32;
     __shared__ int warp_tot[NW];
-    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    int per = (A.R + kScanThreads - 1) / kScanThreads;
-    int beg = tid * per, end = min(beg + per, A.R);
-    int local = 0, bad = 0;
-    for (int i = beg; i < end; ++i) {
-        local += A.rays[i].n;
-        bad |= (A.rays[i].off < 0);
-    }
-    bad = __syncthreads_or(bad);
-    // inclusive warp scan of the chunk sums
-    int v = local;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int carry = 0, bad = 0;
+    for (int base = 0; base < A.R; base += kScanThreads * kScanPer) {
+        const int beg = base + tid * kScanPer;
+        int n[kScanPer], local = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < NW ? warp_tot[lane] : 0;
+        for (int k = 0; k < kScanPer; ++k) {
+            n[k] = 0;
+            if (beg + k < A.R) {
+                const int2 no = *reinterpret_cast<const int2 *>(&A.rays[beg + k].n);   // (n, off)
+                n[k] = no.x;
+                bad |= no.y < 0;
+            }
+            local += n[k];
+        }
+        // inclusive warp scan of the run sums, then the warp totals
+        int v = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int n = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += n;
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
         }
-        if (lane < NW) warp_tot[lane] = w;   // inclusive over warps
+        if (lane == 31) warp_tot[wid] = v;
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int t = warp_tot[w];
+            before += w < wid ? t : 0;
+            total += t;
+        }
+        __syncthreads();   // warp_tot is rewritten by the next round
+        int run = carry + before + v - local;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            if (beg + k < A.R) A.rays[beg + k].off = run;
+            run += n[k];
+        }
+        carry += total;
     }
-    __syncthreads();
-    int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int i = beg; i < end; ++i) {
-        A.rays[i].off = run;
-        run += A.rays[i].n;
-    }
-    if (tid == kScanThreads - 1) {
-        A.hdr->total = warp_tot[NW - 1];
+    bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        A.hdr->total = carry;
         A.hdr->flags = bad ? 1 : 0;
     }
 }
