@@ -34,7 +34,10 @@ namespace {
 using namespace tc;
 
 constexpr int NB = 64, NFQ = 6, PIN = 3 + 6 * NFQ, PW = 64, TT = 128;
-constexpr uint32_t COL_Z = 0, FWD_COLS = 64;   // the three layers use one accumulator in turn
+// Forward TMEM: the three layers use one accumulator (64 columns at COL_Z) in turn; their A operand
+// (X, then H0, then H1, BF16 packed two per column: 32 columns at COL_A) is written there too.
+constexpr uint32_t COL_Z = 0, COL_A = 64, FWD_COLS = 128;
+constexpr int kFwdCtasPerSm = 4;   // 4 x 128 TMEM columns
 
 // Box clip of one ray as the encoding uses it: entry t0, bin width w = (t_exit - t_enter) / 64 and
 // direction as double-float values of the FP64 clip, the origin, and whether the ray hits the box.
@@ -47,7 +50,9 @@ struct ClipDf {
 constexpr int kClipTiles = TT / 2;   // tiles per clip pass: one ray per thread
 
 struct alignas(1024) SmallP {
-    float b1[PW], b2[PW], w3[PW];
+    alignas(16) float b1[PW];
+    alignas(16) float b2[PW];
+    alignas(16) float w3[PW];
     float b3[4];
     float red[2][2][2];       // per ray: partial max / sum of the two warps
     ClipDf clip[TT];          // rays of the CTA's current 64 tiles
@@ -57,14 +62,20 @@ struct alignas(1024) SmallP {
 
 constexpr uint32_t kHalfPanelBytes = kPanelBytes / 2;   // 64 rows: a K-major operand of N = 64
 
+// The forward's shared memory: the weights and the small state (the activations stay in TMEM).
 struct SmemP {
     unsigned char w0t[kHalfPanelBytes];   // rows = 64 outputs, 64 input columns (bias in column 39)
     unsigned char w1t[kHalfPanelBytes];
     unsigned char w2t[kHalfPanelBytes];
-    unsigned char xh1[kPanelBytes];       // X, then H1 (X is dead once layer 0's MMAs complete)
-    unsigned char h0[kPanelBytes];
     SmallP sm;
 };
+// Dynamic shared memory the forward requests: more than it uses, so that exactly kFwdCtasPerSm
+// CTAs fit on an SM (228 KB, 1 KB reserved per CTA) and their TMEM columns add up to 512.
+constexpr int kFwdSmemBytes = 50 * 1024;
+static_assert(sizeof(SmemP) + 1024 <= kFwdSmemBytes, "forward shared memory");
+static_assert(kFwdCtasPerSm * (kFwdSmemBytes + 1024) <= 233472 &&
+              (kFwdCtasPerSm + 1) * (kFwdSmemBytes + 1024) > 233472, "CTAs per SM");
+static_assert(kFwdCtasPerSm * FWD_COLS == 512, "TMEM columns per SM");
 
 struct PropTcArgs {
     int R;
@@ -135,12 +146,11 @@ __device__ __forceinline__ void clip_pass(const PropTcArgs &P, int k0, ClipDf *c
     cl[tid] = c;
 }
 
-// Input row of this thread's bin centre into the X panel (zeros for a ray that misses or does
-// not exist).  The bin centre t_b = t0 + (b + 1/2) w and the position x = o + t_b d are double-float,
-// so x is the FP32 rounding of the exact position (up to ties within ~1e-14).
-__device__ __forceinline__ void encode_row(const ClipDf &c, unsigned char *x) {
+// Input row of this thread's bin centre (zeros for a ray that misses or does not exist).  The bin
+// centre t_b = t0 + (b + 1/2) w and the position x = o + t_b d are double-float, so x is the FP32
+// rounding of the exact position (up to ties within ~1e-14).
+__device__ __forceinline__ void encode_values(const ClipDf &c, float (&v)[64]) {
     const int tid = threadIdx.x, bin = tid & 63;
-    float v[64];
 #pragma unroll
     for (int k = 0; k < 64; ++k) v[k] = 0.0f;
     if (c.hit) {
@@ -162,11 +172,50 @@ __device__ __forceinline__ void encode_row(const ClipDf &c, unsigned char *x) {
         }
         v[PIN] = 1.0f;
     }
-#pragma unroll
-    for (int c8 = 0; c8 < 64; c8 += 8) panel_store8(x, tid, c8, v + c8);
 }
 
-__global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
+// ... into the X panel (the backward, whose dW0 reads X as an MN-major operand)
+__device__ __forceinline__ void encode_row(const ClipDf &c, unsigned char *x) {
+    float v[64];
+    encode_values(c, v);
+#pragma unroll
+    for (int c8 = 0; c8 < 64; c8 += 8) panel_store8(x, threadIdx.x, c8, v + c8);
+}
+
+// ... as BF16 into this thread's TMEM lane at column ta (the forward)
+__device__ __forceinline__ void encode_row_tmem(const ClipDf &c, uint32_t ta) {
+    float v[64];
+    encode_values(c, v);
+    uint32_t w[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = pack_bf16(v[32 * h + 2 * k], v[32 * h + 2 * k + 1]);
+        tmem_st16(ta + 16u * (uint32_t)h, w);
+    }
+}
+
+// Epilogue: 32-column chunk g of the accumulator (+ bias), ReLU, as BF16 into the A-operand
+// columns 16 g .. 16 g + 15 of this thread's TMEM lane.
+__device__ __forceinline__ void relu_to_tmem(uint32_t tz, uint32_t ta, const float *bias) {
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+        float z[32];
+        tmem_ld32(tz + 32u * (uint32_t)g, z);
+        uint32_t h[16];
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+            float4 bb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (bias) bb = *reinterpret_cast<const float4 *>(bias + 32 * g + k);
+            h[k / 2] = pack_bf16(fmaxf(z[k] + bb.x, 0.0f), fmaxf(z[k + 1] + bb.y, 0.0f));
+            h[k / 2 + 1] = pack_bf16(fmaxf(z[k + 2] + bb.z, 0.0f), fmaxf(z[k + 3] + bb.w, 0.0f));
+        }
+        tmem_st16(ta + 16u * (uint32_t)g, h);
+    }
+    tmem_wait_st();
+}
+
+__global__ void __launch_bounds__(TT, kFwdCtasPerSm) proposal_fwd_tc_kernel(PropTcArgs P) {
     extern __shared__ unsigned char smem_raw[];
     SmemP &S = *reinterpret_cast<SmemP *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -176,87 +225,62 @@ __global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
     fence_async_smem();
     sync_fenced();
     const uint32_t tb = S.sm.tmem_base;
+    const uint32_t tz = taddr(tb, warp, COL_Z), ta = taddr(tb, warp, COL_A);   // this warp's lanes
     const uint32_t id64 = idesc_bf16(128, 64, 0, 0);
     uint32_t phase = 0;
     bool ok = true;
     const float invR = 1.0f / (float)P.R;
     const int ntiles = (P.R + 1) / 2;
     int k = 0;
+    // one layer: D (COL_Z) = A (COL_A, TMEM) x W^T (K = 64: four k-steps of 8 columns), then wait
+    auto layer = [&](unsigned char *wt) -> bool {
+        if (tid == 0) {
+            uint32_t w_ = smem_u32(wt);
+            asm volatile("" : "+r"(w_));
+#pragma unroll 1
+            for (int kk = 0; kk < 4; ++kk)
+                mma_ts(tb + COL_Z, tb + COL_A + 8u * (uint32_t)kk, desc_kmajor(w_, kk), id64, kk > 0);
+            commit(&S.sm.mbar);
+        }
+        const bool w = mbar_wait(&S.sm.mbar, phase);
+        phase ^= 1;
+        const bool all = !__syncthreads_or(!w);
+        fence_after();
+        return all;
+    };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
-        uint32_t xh1_ = smem_u32(S.xh1), w0_ = smem_u32(S.w0t), w1_ = smem_u32(S.w1t), w2_ = smem_u32(S.w2t);
-        uint32_t h0_ = smem_u32(S.h0);
-        asm volatile("" : "+r"(xh1_), "+r"(w0_), "+r"(w1_), "+r"(w2_), "+r"(h0_));
         const int rl = tid >> 6, bin = tid & 63, r = 2 * tile + rl;
         if (k % kClipTiles == 0) {
             clip_pass(P, k, S.sm.clip);
             __syncthreads();
         }
         const bool hit = S.sm.clip[2 * (k % kClipTiles) + rl].hit != 0;
-        encode_row(S.sm.clip[2 * (k % kClipTiles) + rl], S.xh1);
-        fence_async_smem();
+        encode_row_tmem(S.sm.clip[2 * (k % kClipTiles) + rl], ta);
+        tmem_wait_st();
         sync_fenced();
-        // ---- layer 0 ----
-        if (tid == 0) {
-#pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(xh1_, kk), desc_kmajor(w0_, kk), id64, kk > 0);
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-            float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k], 0.0f);
-#pragma unroll
-            for (int k = 0; k < 32; k += 8) panel_store8(S.h0, tid, 32 * g + k, z + k);
-        }
-        fence_async_smem();
+        // ---- layer 0, H0 = relu(Z) over X ----
+        if (!(ok = layer(S.w0t))) break;
+        relu_to_tmem(tz, ta, nullptr);
         sync_fenced();
-        // ---- layer 1 ----
-        if (tid == 0) {
-#pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(h0_, kk), desc_kmajor(w1_, kk), id64, kk > 0);
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-            float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) z[k] = fmaxf(z[k] + S.sm.b1[32 * g + k], 0.0f);
-#pragma unroll
-            for (int k = 0; k < 32; k += 8) panel_store8(S.xh1, tid, 32 * g + k, z + k);
-        }
-        fence_async_smem();
+        // ---- layer 1, H1 = relu(Z + b1) over H0 ----
+        if (!(ok = layer(S.w1t))) break;
+        relu_to_tmem(tz, ta, S.sm.b1);
         sync_fenced();
         // ---- layer 2 and the output logit ----
-        if (tid == 0) {
-#pragma unroll 1
-            for (int kk = 0; kk < 4; ++kk) mma(tb + COL_Z, desc_kmajor(xh1_, kk), desc_kmajor(w2_, kk), id64, kk > 0);
-            commit(&S.sm.mbar);
-        }
-        ok = mbar_wait(&S.sm.mbar, phase);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) break;
-        fence_after();
+        if (!(ok = layer(S.w2t))) break;
         float lo_a = S.sm.b3[0], lo_b = 0.0f;
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
             float z[32];
-            tmem_ld32(taddr(tb, warp, COL_Z + 32 * g), z);
+            tmem_ld32(tz + 32u * (uint32_t)g, z);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const float h = fmaxf(z[k] + S.sm.b2[32 * g + k], 0.0f);
-                if (k & 1) lo_b = fmaf(h, S.sm.w3[32 * g + k], lo_b);
-                else lo_a = fmaf(h, S.sm.w3[32 * g + k], lo_a);
+            for (int k4 = 0; k4 < 32; k4 += 4) {
+                const float4 bb = *reinterpret_cast<const float4 *>(S.sm.b2 + 32 * g + k4);
+                const float4 ww = *reinterpret_cast<const float4 *>(S.sm.w3 + 32 * g + k4);
+                lo_a = fmaf(fmaxf(z[k4] + bb.x, 0.0f), ww.x, lo_a);
+                lo_b = fmaf(fmaxf(z[k4 + 1] + bb.y, 0.0f), ww.y, lo_b);
+                lo_a = fmaf(fmaxf(z[k4 + 2] + bb.z, 0.0f), ww.z, lo_a);
+                lo_b = fmaf(fmaxf(z[k4 + 3] + bb.w, 0.0f), ww.w, lo_b);
             }
         }
         const float logit = lo_a + lo_b;
@@ -288,7 +312,6 @@ __global__ void __launch_bounds__(TT, 3) proposal_fwd_tc_kernel(PropTcArgs P) {
     sync_fenced();
     if (warp == 0) tmem_dealloc(S.sm.tmem_base, FWD_COLS);
 }
-
 
 // ---------------------------------------------------------------------------------------------
 // Backward
@@ -591,10 +614,10 @@ int launch_proposal_fwd_tc(const dvgo_params &p, const dvgo_grid_desc &g, const 
     P.w0 = m.w0; P.b0 = m.b0; P.w1 = m.w1; P.b1 = m.b1; P.w2 = m.w2; P.b2 = m.b2; P.w3 = m.w3; P.b3 = m.b3;
     P.probs = probs;
     P.loss = loss;
-    const int bytes = (int)sizeof(SmemP) + 1024;
+    const int bytes = kFwdSmemBytes;
     ensure_smem(reinterpret_cast<const void *>(proposal_fwd_tc_kernel), bytes);
     const int ntiles = (R + 1) / 2;
-    int blocks = 3 * num_sms();
+    int blocks = kFwdCtasPerSm * num_sms();
     if (blocks > ntiles) blocks = ntiles;
     {
         ProfScope ps_(DVGO_K_PROPOSAL_FWD, s);
