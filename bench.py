@@ -353,6 +353,18 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
     dvgo.dvgo_profile_enable(False)
     per_kind = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
     n_prop_train = (form.trainer.n_uniform - n_prop_train0) if form.trainer is not None else 0
+    # chosen form: the same number of steps again, each waiting for the previous step's feature-grid
+    # Adam before it starts, so that nothing runs beside any kernel: each kernel's own time (the
+    # sampling, ray set-up, scan and density pass otherwise share the GPU with that Adam)
+    per_kind_alone = None
+    if form.trainer is not None:
+        dvgo.dvgo_profile_enable(True)
+        for i in range(prof_steps):
+            form.step(dbatches[i % N_BATCHES])
+            form.finish()
+        torch.cuda.synchronize()
+        dvgo.dvgo_profile_enable(False)
+        per_kind_alone = {k: dvgo.dvgo_profile_read(k) for k in dvgo.KERNEL_KINDS}
 
     # end to end through the public API with host buffers: H2D of each step's rays / jitter /
     # targets from pinned memory, the step, and a D2H read of its loss
@@ -403,6 +415,11 @@ def measure_form(name, args, dev, dens, feat, mlp, batches, dvgo, torch, world, 
             "kernels_ms_per_step": {k: round(v[0] / prof_steps, 4) for k, v in per_kind.items() if v[1]},
             "kernels_timing": f"a separate pass of {prof_steps} steps with per-launch CUDA events; the timed region "
                               f"runs without them",
+            "kernels_alone_ms_per_step": (None if per_kind_alone is None else
+                                          {k: round(v[0] / prof_steps, 4) for k, v in per_kind_alone.items() if v[1]}),
+            "kernels_alone_timing": (None if per_kind_alone is None else
+                                     f"a third pass of {prof_steps} steps, each waiting for the previous step's "
+                                     f"feature-grid Adam: no kernel has another running beside it"),
             "e2e": {"value": whole_job_rate(NRAYS * args.steps, world, e2e_ms), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "clocks": clk}
@@ -1179,7 +1196,8 @@ def run_ours(args, rank, world, local_rank):
         line["time_to_psnr"] = None        # filled in below; placed early so that a cut tail keeps it
     line.update({
             "roofline": head["roofline"], "step_roofline": head["step_roofline"],
-            "kernels_ms_per_step": head["kernels_ms_per_step"], "e2e": head["e2e"],
+            "kernels_ms_per_step": head["kernels_ms_per_step"],
+            "kernels_alone_ms_per_step": head.get("kernels_alone_ms_per_step"), "e2e": head["e2e"],
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
             "forms": res})
     if not args.no_time_to_psnr and world == 1:

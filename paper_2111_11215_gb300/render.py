@@ -460,6 +460,12 @@ class ProposalTrainer:
         self.dt_buf = torch.empty((R, self.n_samples), device=dev)
         self.i = 0
         self.n_uniform = self.n_proposal = 0
+        # with the model's overlapped Adam, the proposal's training step of a uniform step runs on a
+        # stream of its own beside the backward (it reads only the forward's samples)
+        overlap = getattr(model, "_side", None) is not None
+        self._side = torch.cuda.Stream(device=dev) if overlap else None
+        self._ev_fwd = torch.cuda.Event() if overlap else None
+        self._ev_prop = torch.cuda.Event() if overlap else None
 
     def rescale(self, shape, step: float, stream=None, adam: str = "reset"):
         """Progressive scaling of the model (FineModel.rescale); the proposal renders and labels on
@@ -473,10 +479,23 @@ class ProposalTrainer:
     def step(self, rays_o, rays_d, jitter, target, stream=None):
         """One step; returns the model's loss (device tensor)."""
         if self.is_uniform(self.i):
+            cur = stream if stream is not None else torch.cuda.current_stream(rays_o.device)
+
             def label(rend):
-                self.proposal.train_step(rend.workspace, rays_o, rays_d, stream=stream, n_train=self.train_rays,
+                if self._side is None:
+                    self.proposal.train_step(rend.workspace, rays_o, rays_d, stream=stream, n_train=self.train_rays,
+                                             with_loss=False)
+                    return
+                self._ev_fwd.record(cur)
+                self._side.wait_event(self._ev_fwd)
+                self.proposal.train_step(rend.workspace, rays_o, rays_d, stream=self._side, n_train=self.train_rays,
                                          with_loss=False)
+                self._ev_prop.record(self._side)
             loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, after_forward=label)
+            if self._side is not None:
+                # the backward was queued before this wait, so it overlaps the proposal's step; all
+                # later work on the stream (the next sampling, the batch's buffers) is ordered after it
+                cur.wait_event(self._ev_prop)
             self.n_uniform += 1
         else:
             R = rays_o.shape[0]

@@ -96,13 +96,15 @@ def _train_chosen(overlap, steps=9, res=48, R=2048):
     torch.cuda.synchronize()
     return (np.array([float(x.item()) for x in losses]),
             {k: t.detach().float().cpu().numpy() for k, t in (("density", model.density), ("feat", model.feat),
-                                                                ("feat_bf16", model.feat_bf16), ("mlp", model.mlp_flat))})
+                                                                ("feat_bf16", model.feat_bf16), ("mlp", model.mlp_flat),
+                                                                ("proposal", prop.flat))})
 
 
 def test_overlapped_feature_adam_matches_serial():
-    """The feature-grid Adam on the side stream (overlap_adam) gives the same training as the
-    serial order: the differences stay within the run-to-run spread of two serial runs (the
-    atomic summation order), scaled by 10, plus 1e-6."""
+    """The feature-grid Adam on the side stream (overlap_adam), and with it the proposal's training
+    step of the uniform steps on a stream of its own, give the same training as the serial order:
+    the differences stay within the run-to-run spread of two serial runs (the atomic summation
+    order), scaled by 10, plus 1e-6; the proposal network's weights included."""
     l_ref, p_ref = _train_chosen(False)
     l_ref2, p_ref2 = _train_chosen(False)
     l_ov, p_ov = _train_chosen(True)
@@ -112,4 +114,9 @@ def test_overlapped_feature_adam_matches_serial():
     for k in p_ref:
         base = _rel_l2(p_ref2[k], p_ref[k])
         got = _rel_l2(p_ov[k], p_ref[k])
-        assert got <= 10 * base + 1e-6, (k, got, base)
+        # the proposal backward adds its weight gradients with per-CTA FP32 atomics; their order moves
+        # the trained weights between two outcomes 3.4e-5 apart (relative L2 after three proposal
+        # steps; two serial runs land on either), so its floor is 1e-4 -- a wrong label or a step
+        # missed would move them by orders of magnitude more
+        floor = 1e-4 if k == "proposal" else 1e-6
+        assert got <= 10 * base + floor, (k, got, base)
