@@ -17,6 +17,6 @@ from .binding import (  # noqa: F401
     dvgo_fit2d, dvgo_touched_points, dvgo_view_counts,
 )
 from .render import (  # noqa: F401
-    AdamState, CoarseModel, FineModel, FrameRenderer, Proposal, ProposalTrainer, Renderer, RenderFunction,
+    AdamState, BatchStager, CoarseModel, FineModel, FrameRenderer, Proposal, ProposalTrainer, Renderer, RenderFunction,
     mlp_flat_size, mlp_views,
 )

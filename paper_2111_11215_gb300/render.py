@@ -507,3 +507,58 @@ class ProposalTrainer:
             self.n_proposal += 1
         self.i += 1
         return loss
+
+
+class BatchStager:
+    """Double-buffered host-to-device staging of training batches: the next batch's copy from pinned
+    host tensors runs on a copy stream of its own while the current step computes.
+
+        st = BatchStager(example_device_batch)
+        st.stage(host_batch_0)
+        for k in range(n):
+            batch = st.take()                 # device tensors of batch k (the stream waits for its copy)
+            if k + 1 < n:
+                st.stage(host_batch_k_plus_1)  # copies into the other buffer set
+            loss = trainer.step(*batch)
+            st.done()                         # batch k's buffers are free once the step's work is done
+
+    A buffer set is refilled only after the stream has passed the done() of the step that used it."""
+
+    def __init__(self, like, device=None):
+        dev = like[0].device if device is None else device
+        self.bufs = [tuple(torch.empty_like(x) for x in like) for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+        self.used = [False, False]
+        self.n_staged = self.n_taken = 0
+
+    def stage(self, host_batch):
+        """Queue the copy of host_batch (pinned CPU tensors shaped like the example batch)."""
+        k = self.n_staged % 2
+        if self.n_staged - self.n_taken >= 2:
+            raise RuntimeError("BatchStager: both buffer sets hold batches not taken yet")
+        if self.used[k]:
+            self.copy_stream.wait_event(self.ev_used[k])
+        with torch.cuda.stream(self.copy_stream):
+            for dst, src in zip(self.bufs[k], host_batch):
+                dst.copy_(src, non_blocking=True)
+        self.ev_copied[k].record(self.copy_stream)
+        self.n_staged += 1
+
+    def take(self, stream=None):
+        """The device tensors of the oldest staged batch; `stream` (default: current) waits for its copy."""
+        if self.n_taken >= self.n_staged:
+            raise RuntimeError("BatchStager: no staged batch to take")
+        k = self.n_taken % 2
+        cur = stream if stream is not None else torch.cuda.current_stream(self.bufs[k][0].device)
+        cur.wait_event(self.ev_copied[k])
+        self.n_taken += 1
+        return self.bufs[k]
+
+    def done(self, stream=None):
+        """The step that used the last taken batch has been queued on `stream` (default: current)."""
+        k = (self.n_taken - 1) % 2
+        cur = stream if stream is not None else torch.cuda.current_stream(self.bufs[k][0].device)
+        self.ev_used[k].record(cur)
+        self.used[k] = True
