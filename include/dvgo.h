@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DVGO_ABI_VERSION 9
+#define DVGO_ABI_VERSION 10
 
 /* Grid memory layouts (dvgo_grid_desc.layout).
  *   CANONICAL: channel-last [nx][ny][nz][C], nx*ny*nz*C elements.
@@ -291,6 +291,28 @@ typedef struct {
 int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n,
                    const dvgo_adam_hparams *h, const float *lr_scale, uint16_t *param_bf16_out,
                    int zero_grad, void *stream);
+
+/* One tensor of dvgo_adam_step_multi: the arguments of dvgo_adam_step. */
+typedef struct {
+    float *param, *grad, *m, *v;   /* device, n elements each, 16-byte aligned                     */
+    size_t n;
+    dvgo_adam_hparams h;           /* this tensor's rate, betas, eps, step count, lazy flag          */
+    const float *lr_scale;         /* nullable, as in dvgo_adam_step                                 */
+    uint16_t *param_bf16_out;      /* nullable, 8-byte aligned, as in dvgo_adam_step                 */
+    int zero_grad;
+} dvgo_adam_tensor;
+
+#define DVGO_ADAM_MAX_TENSORS 4
+
+/*
+ * The Adam step of dvgo_adam_step on each of n_tensors (0 .. DVGO_ADAM_MAX_TENSORS) tensors, with
+ * their own hyper-parameters, in one launch (every element gets exactly the arithmetic of
+ * dvgo_adam_step: the results are the same bits).  For the small tensors a training step updates
+ * last, whose separate launches would each cost a launch's latency.  The tensors must not overlap.
+ * Every tensor is checked as dvgo_adam_step checks it before anything is enqueued
+ * (DVGO_ERR_INVALID_ARG).
+ */
+int dvgo_adam_step_multi(const dvgo_adam_tensor *tensors, int n_tensors, void *stream);
 
 /* Pinhole training views for the view counts below: image size, intrinsics and near distance
  * shared by all views. */

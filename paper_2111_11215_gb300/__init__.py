@@ -8,7 +8,7 @@ the library is missing or a tensor is not on a CUDA device.
 """
 from .binding import (  # noqa: F401
     DVGO_DTYPE_BF16, DVGO_DTYPE_F32, DVGO_MLP_BF16, DVGO_MLP_FP32, DVGO_MODE_COARSE, DVGO_MODE_FINE,
-    DVGOError, GridDesc, Params, dvgo_abi_version, dvgo_adam_step, dvgo_lr_at, dvgo_render_bwd,
+    DVGOError, GridDesc, Params, dvgo_abi_version, dvgo_adam_step, dvgo_adam_step_multi, dvgo_lr_at, dvgo_render_bwd,
     dvgo_render_fwd, dvgo_sample_counts, dvgo_shift_from_alpha_init, dvgo_status_string, dvgo_workspace_size,
     dvgo_workspace_status, lib, library_path, EXPORTED_SYMBOLS, KERNEL_KINDS, dvgo_profile_enable,
     dvgo_profile_read, dvgo_profile_trace, dvgo_launch_counter, dvgo_render_fwd_noalloc, dvgo_weight_bins, dvgo_proposal_fwd,

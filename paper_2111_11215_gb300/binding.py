@@ -20,7 +20,8 @@ DVGO_MODE_COARSE, DVGO_MODE_FINE = 0, 1
 DVGO_MLP_FP32, DVGO_MLP_BF16 = 0, 1
 
 EXPORTED_SYMBOLS = (
-    "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_lr_at",
+    "dvgo_workspace_size", "dvgo_render_fwd", "dvgo_render_bwd", "dvgo_adam_step", "dvgo_adam_step_multi",
+    "dvgo_lr_at",
     "dvgo_workspace_status", "dvgo_sample_counts", "dvgo_shift_from_alpha_init", "dvgo_status_string",
     "dvgo_abi_version", "dvgo_profile_enable", "dvgo_profile_read", "dvgo_profile_trace", "dvgo_launch_counter",
     "dvgo_render_fwd_noalloc", "dvgo_weight_bins", "dvgo_proposal_fwd", "dvgo_proposal_bwd", "dvgo_sample_pdf",
@@ -92,6 +93,15 @@ class _AdamH(C.Structure):
                 ("step", C.c_int), ("skip_zero_grad", C.c_int)]
 
 
+class _AdamTensor(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("n", C.c_size_t), ("h", _AdamH), ("lr_scale", C.c_void_p), ("param_bf16_out", C.c_void_p),
+                ("zero_grad", C.c_int)]
+
+
+DVGO_ADAM_MAX_TENSORS = 4
+
+
 def lib():
     """Load libdvgo.so; raise if it has not been built (there is no fallback path)."""
     global _lib
@@ -110,6 +120,8 @@ def lib():
         L.dvgo_render_bwd.argtypes = [vp, vp, vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.dvgo_adam_step.restype = i
         L.dvgo_adam_step.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp, i, vp]
+        L.dvgo_adam_step_multi.restype = i
+        L.dvgo_adam_step_multi.argtypes = [vp, i, vp]
         L.dvgo_lr_at.restype = f
         L.dvgo_lr_at.argtypes = [f, i, f]
         L.dvgo_workspace_status.restype = i
@@ -415,6 +427,27 @@ def dvgo_adam_step(param, grad, m, v, lr: float, step: int, beta1=0.9, beta2=0.9
         _dev(v, "v", torch.float32), param.numel(), C.byref(h), _dev(lr_scale, "lr_scale", torch.float32, True),
         _dev(param_bf16_out, "param_bf16_out", torch.bfloat16, True), int(bool(zero_grad)), _stream(stream))
     _check(st, "dvgo_adam_step")
+
+
+def dvgo_adam_step_multi(tensors, stream=None):
+    """dvgo_adam_step on several tensors in one launch.  tensors: sequence of dicts with the keys
+    of dvgo_adam_step (param, grad, m, v, lr, step; optional beta1, beta2, eps, lr_scale,
+    param_bf16_out, zero_grad, skip_zero_grad)."""
+    arr = (_AdamTensor * max(len(tensors), 1))()
+    keep = []
+    for j, t in enumerate(tensors):
+        x = arr[j]
+        x.param, x.grad = _dev(t["param"], "param", torch.float32), _dev(t["grad"], "grad", torch.float32)
+        x.m, x.v = _dev(t["m"], "m", torch.float32), _dev(t["v"], "v", torch.float32)
+        x.n = t["param"].numel()
+        x.h.lr, x.h.beta1, x.h.beta2 = float(t["lr"]), float(t.get("beta1", 0.9)), float(t.get("beta2", 0.999))
+        x.h.eps, x.h.step = float(t.get("eps", 1e-8)), int(t["step"])
+        x.h.skip_zero_grad = int(bool(t.get("skip_zero_grad", False)))
+        x.lr_scale = _dev(t.get("lr_scale"), "lr_scale", torch.float32, True)
+        x.param_bf16_out = _dev(t.get("param_bf16_out"), "param_bf16_out", torch.bfloat16, True)
+        x.zero_grad = int(bool(t.get("zero_grad", True)))
+        keep.append(t)
+    _check(lib().dvgo_adam_step_multi(arr, len(tensors), _stream(stream)), "dvgo_adam_step_multi")
 
 
 def dvgo_workspace_status(workspace, stream=None) -> int:

@@ -159,10 +159,72 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     }
 }
 
-}  // namespace
 
-void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
-                 const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s) {
+// Several tensors in one launch: the vectors of all tensors form one index range (tensor j owns
+// [off[j], off[j + 1])), swept grid-stride one vector per thread per iteration; then the scalar
+// tails.  Every element goes through adam_one / adam_lazy and adam_store as in adam_kernel.
+struct AdamTensorK {
+    float *p, *g, *m, *v;
+    const float *scale;
+    uint16_t *pb;
+    size_t n;
+    AdamK k;
+    int zero_grad, lazy;
+};
+struct AdamMultiK {
+    AdamTensorK t[DVGO_ADAM_MAX_TENSORS];
+    size_t off[DVGO_ADAM_MAX_TENSORS + 1];   // vector offsets
+    int nt;
+};
+
+__global__ void __launch_bounds__(256) adam_multi_kernel(AdamMultiK a) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t total = a.off[a.nt];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        int j = 0;
+#pragma unroll
+        for (int q = 1; q < DVGO_ADAM_MAX_TENSORS; ++q) j += (q < a.nt && i >= a.off[q]) ? 1 : 0;
+        const AdamTensorK &t = a.t[j];
+        const size_t li = i - a.off[j];
+        float4 *p4 = reinterpret_cast<float4 *>(t.p), *g4 = reinterpret_cast<float4 *>(t.g);
+        float4 *m4 = reinterpret_cast<float4 *>(t.m), *v4 = reinterpret_cast<float4 *>(t.v);
+        const float4 G = g4[li];
+        if (t.lazy && G.x == 0.0f && G.y == 0.0f && G.z == 0.0f && G.w == 0.0f) continue;
+        float4 P = p4[li], M = m4[li], V = v4[li];
+        const float4 S = t.scale ? reinterpret_cast<const float4 *>(t.scale)[li] : make_float4(1.f, 1.f, 1.f, 1.f);
+        if (t.lazy) {
+            adam_lazy(P.x, M.x, V.x, G.x, S.x, t.k);
+            adam_lazy(P.y, M.y, V.y, G.y, S.y, t.k);
+            adam_lazy(P.z, M.z, V.z, G.z, S.z, t.k);
+            adam_lazy(P.w, M.w, V.w, G.w, S.w, t.k);
+        } else {
+            adam_one(P.x, M.x, V.x, G.x, S.x, t.k);
+            adam_one(P.y, M.y, V.y, G.y, S.y, t.k);
+            adam_one(P.z, M.z, V.z, G.z, S.z, t.k);
+            adam_one(P.w, M.w, V.w, G.w, S.w, t.k);
+        }
+        adam_store(p4, m4, v4, g4, reinterpret_cast<uint2 *>(t.pb), li, P, M, V, G, t.zero_grad);
+    }
+    // scalar tails (n % 4 elements of each tensor)
+    for (int j = 0; j < a.nt; ++j) {
+        const AdamTensorK &t = a.t[j];
+        for (size_t i = (t.n / 4) * 4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < t.n; i += stride) {
+            if (t.lazy && t.g[i] == 0.0f) continue;
+            float P = t.p[i], M = t.m[i], V = t.v[i];
+            adam_one(P, M, V, t.g[i], t.scale ? t.scale[i] : 1.0f, t.k);
+            t.p[i] = P;
+            t.m[i] = M;
+            t.v[i] = V;
+            if (t.zero_grad && t.g[i] != 0.0f) t.g[i] = 0.0f;
+            if (t.pb) {
+                __nv_bfloat16 b = __float2bfloat16_rn(P);
+                t.pb[i] = *reinterpret_cast<uint16_t *>(&b);
+            }
+        }
+    }
+}
+
+AdamK adam_constants(const dvgo_adam_hparams &h) {
     AdamK k;
     k.lr = h.lr;
     k.b1 = h.beta1;
@@ -170,6 +232,14 @@ void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const 
     k.eps = h.eps;
     k.inv_bc1 = (float)(1.0 / (1.0 - pow((double)h.beta1, (double)h.step)));
     k.inv_bc2 = (float)(1.0 / (1.0 - pow((double)h.beta2, (double)h.step)));
+    return k;
+}
+
+}  // namespace
+
+void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
+                 const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s) {
+    const AdamK k = adam_constants(h);
     size_t n4 = (n + 3) / 4;
     const bool small = n4 <= (size_t)DVGO_ADAM_SMALL_VECS;
     size_t blocks = (n4 + 255) / 256;
@@ -197,6 +267,25 @@ void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const 
             adam_kernel<false, DVGO_ADAM_UNROLL><<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, k, lr_scale,
                                                                                   bf16_out, zero_grad);
     }
+}
+
+void launch_adam_multi(const dvgo_adam_tensor *t, int nt, cudaStream_t s) {
+    AdamMultiK a{};
+    a.nt = nt;
+    a.off[0] = 0;
+    for (int j = 0; j < nt; ++j) {
+        a.t[j] = AdamTensorK{t[j].param, t[j].grad, t[j].m, t[j].v, t[j].lr_scale, t[j].param_bf16_out,
+                             t[j].n, adam_constants(t[j].h), t[j].zero_grad, t[j].h.skip_zero_grad};
+        a.off[j + 1] = a.off[j] + t[j].n / 4;
+    }
+    const size_t total = a.off[nt];
+    const bool small = total <= (size_t)DVGO_ADAM_SMALL_VECS;
+    size_t blocks = (total + 255) / 256;
+    const size_t cap = (size_t)num_sms() * (small ? DVGO_ADAM_SMALL_BLOCKS_PER_SM : DVGO_ADAM_BLOCKS_PER_SM);
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    ProfScope ps_(DVGO_K_ADAM, s);
+    adam_multi_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
 }
 
 }  // namespace dvgo

@@ -348,8 +348,8 @@ int dvgo_render_bwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     return launch_status();
 }
 
-int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams *h,
-                   const float *lr_scale, uint16_t *param_bf16_out, int zero_grad, void *stream) {
+static int check_adam(const float *param, const float *grad, const float *m, const float *v, size_t n,
+                      const dvgo_adam_hparams *h, const float *lr_scale, const uint16_t *param_bf16_out) {
     if (!h || (n > 0 && (!param || !grad || !m || !v))) return DVGO_ERR_INVALID_ARG;
     if (h->step < 1 || !isfinite(h->lr) || !(h->beta1 >= 0.0f && h->beta1 < 1.0f) ||
         !(h->beta2 >= 0.0f && h->beta2 < 1.0f) || !(h->eps >= 0.0f) || (h->skip_zero_grad & ~1) != 0)
@@ -357,8 +357,28 @@ int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n, cons
     const void *ptrs[6] = {param, grad, m, v, lr_scale, param_bf16_out};
     for (int i = 0; i < 6; ++i)
         if (ptrs[i] && (reinterpret_cast<uintptr_t>(ptrs[i]) & (i == 5 ? 7u : 15u)) != 0) return DVGO_ERR_INVALID_ARG;
+    return DVGO_OK;
+}
+
+int dvgo_adam_step(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams *h,
+                   const float *lr_scale, uint16_t *param_bf16_out, int zero_grad, void *stream) {
+    if (int st = check_adam(param, grad, m, v, n, h, lr_scale, param_bf16_out)) return st;
     if (n == 0) return DVGO_OK;
     launch_adam(param, grad, m, v, n, *h, lr_scale, param_bf16_out, zero_grad, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+int dvgo_adam_step_multi(const dvgo_adam_tensor *tensors, int n_tensors, void *stream) {
+    if (n_tensors < 0 || n_tensors > DVGO_ADAM_MAX_TENSORS || (n_tensors > 0 && !tensors)) return DVGO_ERR_INVALID_ARG;
+    dvgo_adam_tensor t[DVGO_ADAM_MAX_TENSORS];
+    int nt = 0;
+    for (int j = 0; j < n_tensors; ++j) {
+        const dvgo_adam_tensor &x = tensors[j];
+        if (int st = check_adam(x.param, x.grad, x.m, x.v, x.n, &x.h, x.lr_scale, x.param_bf16_out)) return st;
+        if (x.n > 0) t[nt++] = x;
+    }
+    if (nt == 0) return DVGO_OK;
+    launch_adam_multi(t, nt, static_cast<cudaStream_t>(stream));
     return launch_status();
 }
 

@@ -429,6 +429,7 @@ void launch_fine_composite_bwd(const RenderArgs &A, cudaStream_t s);
 void launch_fine_colour_bwd(const RenderArgs &A, cudaStream_t s);
 void launch_adam(float *param, float *grad, float *m, float *v, size_t n, const dvgo_adam_hparams &h,
                  const float *lr_scale, uint16_t *bf16_out, int zero_grad, cudaStream_t s);
+void launch_adam_multi(const dvgo_adam_tensor *t, int nt, cudaStream_t s);
 
 void launch_touched(const RenderArgs &A, uint32_t *bitmaps, unsigned long long *counts, cudaStream_t s);
 void launch_view_counts(const dvgo_grid_desc &g, const dvgo_view_rig &rig, const double *c2w, uint32_t *counts,

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_strings(lib):
     import paper_2111_11215_gb300 as dvgo
-    assert dvgo.dvgo_abi_version() == 9
+    assert dvgo.dvgo_abi_version() == 10
     assert dvgo.dvgo_status_string(0) == "ok"
     assert "workspace" in dvgo.dvgo_status_string(-2)
 
@@ -104,3 +104,26 @@ def test_profile_trace_without_records(lib):
     n = C.c_int(7)
     assert lib.dvgo_profile_trace(-1, None, None, None, C.byref(n)) == binding.DVGO_ERR_INVALID_ARG
     assert lib.dvgo_profile_trace(4, None, None, None, C.byref(n)) == binding.DVGO_ERR_INVALID_ARG
+
+
+def test_adam_step_multi_checks_before_launching(lib):
+    """dvgo_adam_step_multi validates the tensor count and every tensor before enqueueing anything
+    (so these calls need no GPU): more than DVGO_ADAM_MAX_TENSORS, a null array with a count, and a
+    tensor with a null parameter or a step count of 0 are refused; an empty list is a no-op."""
+    import ctypes as C
+    from paper_2111_11215_gb300 import binding as B
+    L = lib
+    assert L.dvgo_adam_step_multi(None, 0, None) == 0
+    assert L.dvgo_adam_step_multi(None, 1, None) == -1
+    arr = (B._AdamTensor * 5)()
+    assert L.dvgo_adam_step_multi(arr, 5, None) == -1
+    assert L.dvgo_adam_step_multi(arr, -1, None) == -1
+    arr[0].n = 16
+    arr[0].h.step = 1
+    arr[0].h.beta1, arr[0].h.beta2, arr[0].h.lr = 0.9, 0.999, 0.1
+    assert L.dvgo_adam_step_multi(arr, 1, None) == -1      # null pointers with n > 0
+    arr[0].n = 0
+    arr[0].h.step = 0
+    assert L.dvgo_adam_step_multi(arr, 1, None) == -1      # step count 0
+    arr[0].h.step = 1
+    assert L.dvgo_adam_step_multi(arr, 1, None) == 0       # an empty tensor: nothing to do
