@@ -192,6 +192,12 @@ typedef struct {
      * colour kernels' input panels (16 KiB per 128 samples) -- and dvgo_workspace_size leaves that
      * block out.  A backward on such a workspace gathers its inputs again (same results). */
     int forward_only;
+    /* density_ready: NULL, or a cudaEvent_t (of the calling device) that dvgo_render_fwd and
+     * dvgo_render_bwd make their stream wait on right before their first kernel that reads the
+     * density grid -- for a producer of that grid on another stream: the ray set-up and the sample
+     * scan before it are not held back.  Not validated; an event that was never recorded is
+     * complete.  Other calls ignore it. */
+    void *density_ready;
 } dvgo_params;
 
 /* Colour MLP (fine stage), FP32 row-major [in][out]:

@@ -67,7 +67,8 @@ class _Params(C.Structure):
                 ("t_near", C.c_float), ("t_far", C.c_float), ("bg", C.c_float * 3),
                 ("freespace", C.POINTER(_FreeSpace)), ("w_pt_rgb", C.c_float), ("w_bg", C.c_float),
                 ("act_order", C.c_int), ("n_freq_pos", C.c_int), ("wait_limit_us", C.c_int),
-                ("test_withhold_tile", C.c_int), ("cgrid_ready", C.c_void_p), ("forward_only", C.c_int)]
+                ("test_withhold_tile", C.c_int), ("cgrid_ready", C.c_void_p), ("forward_only", C.c_int),
+                ("density_ready", C.c_void_p)]
 
 
 class _Fit2d(C.Structure):
@@ -239,6 +240,8 @@ class Params:
     cgrid_ready: int = 0         # cudaEvent_t handle (torch.cuda.Event.cuda_event) the render calls
                                  # wait on before their first kernel that reads the colour grid; 0: none
     forward_only: int = 0        # no backward follows the forward: keep nothing for one
+    density_ready: int = 0       # cudaEvent_t handle the render calls wait on before their first kernel
+                                 # that reads the density grid; 0: none
 
     def mlp_in_dim(self, channels: int = 12) -> int:
         """Width of the fine MLP's input row (Sec. 4.2 Eq. fine_queries_rgb): 39, or 72 with PE(x)."""
@@ -261,6 +264,7 @@ class Params:
         p.test_withhold_tile = int(self.test_withhold_tile)
         p.cgrid_ready = int(self.cgrid_ready) or None
         p.forward_only = int(self.forward_only)
+        p.density_ready = int(self.density_ready) or None
         if self.freespace is not None:
             p._fs = self.freespace.c()          # kept alive with the struct that points to it
             p.freespace = C.pointer(p._fs)

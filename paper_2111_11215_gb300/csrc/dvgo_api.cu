@@ -275,6 +275,10 @@ size_t dvgo_workspace_size(const dvgo_params *p, const dvgo_grid_desc *density, 
 static void wait_cgrid(const dvgo_params *p, cudaStream_t s) {
     if (p->cgrid_ready) cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(p->cgrid_ready), 0);
 }
+// ... and before the first kernel that reads the density grid.
+static void wait_density(const dvgo_params *p, cudaStream_t s) {
+    if (p->density_ready) cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(p->density_ready), 0);
+}
 
 int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float *density, const dvgo_grid_desc *cd,
                     const void *cgrid, const dvgo_mlp *mlp, int R, const float *rays_o, const float *rays_d,
@@ -298,6 +302,7 @@ int dvgo_render_fwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     A.loss_out = target ? loss_out : nullptr;
     A.dloss_out = target ? dloss_out : nullptr;
     launch_ray_setup(A, rays_o, rays_d, jitter, *p, *dd, sample_cap(p, dd), s);
+    wait_density(p, s);
     if (p->mode == DVGO_MODE_COARSE) {
         wait_cgrid(p, s);
         launch_coarse_fwd(A, s);
@@ -333,6 +338,7 @@ int dvgo_render_bwd(const dvgo_params *p, const dvgo_grid_desc *dd, const float 
     A.grad_density = grad_density;
     A.grad_cgrid = grad_cgrid;
     A.grad_mlp = grad_mlp;
+    wait_density(p, s);
     if (p->mode == DVGO_MODE_COARSE) {
         wait_cgrid(p, s);
         launch_coarse_bwd(A, s);
