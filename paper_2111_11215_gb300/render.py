@@ -185,10 +185,7 @@ class FineModel:
         self._ev_bwd = torch.cuda.Event() if overlap_adam else None
         self._ev_after = torch.cuda.Event() if overlap_adam else None
         self._ev_feat = torch.cuda.Event() if overlap_adam else None
-        self._ev_dens = torch.cuda.Event() if overlap_adam else None
-        self._small = torch.cuda.Stream(device=dev) if overlap_adam else None   # deferred density / MLP steps
         self._feat_pending = False     # an Adam step was launched on the side stream
-        self._dens_pending = False     # the density / MLP Adam step of the last train_step ran there
         self._feat_deferred = None     # (lr, t) of an Adam step not launched yet
 
     @property
@@ -229,14 +226,10 @@ class FineModel:
 
     def wait_params(self, stream=None):
         """Order `stream` (default: the current stream) after the feature-grid Adam step (launching
-        it first if it is still deferred) and a density / MLP Adam step on the side stream (the
-        side stream runs the latter first)."""
+        it first if it is still deferred)."""
         self.launch_feat_adam(stream)
         if self._feat_pending:
             self._cur(stream).wait_event(self._ev_feat)
-        if self._dens_pending:
-            self._cur(stream).wait_event(self._ev_dens)
-        self._dens_pending = False
 
     @property
     def shape(self):
@@ -302,27 +295,19 @@ class FineModel:
             self._expl = (n_per_ray, rend)
         return self._expl[1]
 
-    def train_step(self, rays_o, rays_d, jitter, target, stream=None, samples=None, after_forward=None,
-                   defer_small_adam=False):
+    def train_step(self, rays_o, rays_d, jitter, target, stream=None, samples=None, after_forward=None):
         """One optimisation step: render + MSE (Eq. photo_loss), backward, Adam on every parameter.
         `samples` = (t, dt) [R, n] renders with explicit samples (e.g. from a Proposal) instead of
         uniform steps.  `after_forward(renderer)` (optional) is called between the forward and the
-        backward, while the renderer's workspace holds this batch's forward samples.
-        defer_small_adam (with overlap_adam): the density and MLP Adam steps go to a stream of their
-        own, and the next train_step's forward waits for them only before its density pass, so that
-        they overlap its ray set-up, sample scan and the feature-grid Adam (for a next step without
-        a proposal forward: beside that kernel's shared-memory CTAs they would slow the feature-grid
-        Adam)."""
+        backward, while the renderer's workspace holds this batch's forward samples."""
         rend = self.renderer if samples is None else self.explicit_renderer(samples[0].shape[1])
         # a pending feature-grid Adam step holds back only the colour kernels of the forward (the
         # stream waits on its event inside the call); the backward follows on the same stream
         self.launch_feat_adam(stream)
         ready = self._ev_feat if self._feat_pending else None
-        dready = self._ev_dens if self._dens_pending else None
-        self._dens_pending = False     # from this forward's wait on, the stream is ordered after it
         rend.forward(self.density, self._feat_bf16 if self.bf16_feat else self._feat, self.mlp, rays_o, rays_d,
                      jitter, samples, target, self.rgb, self.tfinal, self.loss, self.dloss, stream,
-                     cgrid_ready=ready, density_ready=dready)
+                     cgrid_ready=ready)
         if after_forward is not None:
             after_forward(rend)
         rend.backward(self.density, self._feat_bf16 if self.bf16_feat else self._feat, self.mlp, rays_o, rays_d,
@@ -338,16 +323,9 @@ class FineModel:
         else:
             B.dvgo_adam_step(self._feat, self.g_feat, self.adam["feat"].m, self.adam["feat"].v, lr_g, tg,
                              param_bf16_out=self._feat_bf16, stream=stream, skip_zero_grad=self.lazy_grid_adam)
-        small = stream
-        if self._small is not None and defer_small_adam:
-            self._small.wait_event(self._ev_bwd)
-            small = self._small
         B.dvgo_adam_step(self.density, self.g_density, self.adam["density"].m, self.adam["density"].v, lr_g, tg,
-                         stream=small, skip_zero_grad=self.lazy_grid_adam)
-        B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=small)
-        if small is self._small and self._small is not None:
-            self._ev_dens.record(self._small)
-            self._dens_pending = True
+                         stream=stream, skip_zero_grad=self.lazy_grid_adam)
+        B.dvgo_adam_step(self.mlp_flat, self.g_mlp, self.adam["mlp"].m, self.adam["mlp"].v, lr_m, t, stream=stream)
         return self.loss
 
 
@@ -518,8 +496,7 @@ class ProposalTrainer:
                 self.proposal.train_step(rend.workspace, rays_o, rays_d, stream=self._side, n_train=self.train_rays,
                                          with_loss=False)
                 self._ev_prop.record(self._side)
-            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, after_forward=label,
-                                         defer_small_adam=self.is_uniform(self.i + 1))
+            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, after_forward=label)
             if self._side is not None:
                 # the backward was queued before this wait, so it overlaps the proposal's step; all
                 # later work on the stream (the next sampling, the batch's buffers) is ordered after it
@@ -531,8 +508,7 @@ class ProposalTrainer:
             ts, dts = self.proposal.sample(rays_o, rays_d, jitter, self.n_samples, eta=self.eta,
                                            t_out=self.t_buf[:R], dt_out=self.dt_buf[:R], stream=stream,
                                            after_forward=lambda: self.model.launch_feat_adam(stream))
-            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, samples=(ts, dts),
-                                         defer_small_adam=self.is_uniform(self.i + 1))
+            loss = self.model.train_step(rays_o, rays_d, jitter, target, stream, samples=(ts, dts))
             self.n_proposal += 1
         self.i += 1
         return loss
