@@ -300,8 +300,10 @@ def test_fine_fp32_many_tiles_per_cta():
 # Adam
 # ------------------------------------------------------------------------------------------
 
-def test_adam_parity_and_bf16_copy():
-    n = 100003      # ragged tail after the 4-wide vector part
+@pytest.mark.parametrize("n", [100003, 9000003])
+def test_adam_parity_and_bf16_copy(n):
+    # ragged tail after the 4-wide vector part; the launch takes the small-tensor grid up to 2^21
+    # vectors (100,003 elements) and the one-wave grid of the large sweeps above (9,000,003)
     g = np.random.default_rng(30)
     p0 = g.normal(size=n)
     scale = g.uniform(size=n)
