@@ -1,7 +1,7 @@
 // tc_helpers.cuh -- 5th-generation tensor core (tcgen05) building blocks for sm_103a, written as
 // inline PTX: shared-memory matrix descriptors for the 128-byte-swizzled canonical layouts, the
-// BF16 instruction descriptor, MMA issue / commit, TMEM allocation and loads, mbarriers with
-// bounded waits.
+// BF16 instruction descriptor, MMA issue (A from shared or from tensor memory) / commit, TMEM
+// allocation, loads and stores, mbarriers with bounded waits, bulk copies.
 //
 // Operand tiles live in "panels": 128 rows x 128 bytes (64 BF16 values per row), 1024-byte
 // aligned, with the 128-byte swizzle applied to every 8-row (1024-byte) group: the 16-byte chunk
