@@ -11,7 +11,7 @@ Forms (both are timed by default; `value` is the chosen form):
   plain  = uniform 0.5-voxel steps, FP32 feature grid, FP32 SIMT MLP;
   chosen = learned proposal (64-bin PDF from a BF16 tensor-core proposal MLP trained by its BF16
            tensor-core backward; 48 inverse-CDF samples per ray from the PDF mixed 0.05 with the
-           uniform one; every 4th step is a full uniform step whose forward also labels 2048 rays
+           uniform one; every 4th step is a full uniform step whose forward also labels 1024 rays
            for one proposal Adam step), BF16 feature storage with an FP32 master copy, BF16
            tensor-core MLP.
 The line also carries the sample-proposal evaluation on this scene (`proposal_eval`) and, at one
@@ -41,7 +41,7 @@ RES, FEAT, HID, NRAYS = 160, 12, 128, 8192
 N_BATCHES = 8
 N_PROP_SAMPLES = 48
 PROPOSAL_EVERY = 4
-PROPOSAL_TRAIN_RAYS = 2048
+PROPOSAL_TRAIN_RAYS = 1024
 PROPOSAL_ETA = 0.05
 # Colour-MLP input width: 39 (features + PE(d), the benchmark's model) or 72 (+ PE(x, 5), --pe-x)
 MLP_IN = 39

@@ -454,7 +454,7 @@ class ProposalTrainer:
     smooth field cannot resolve, so they are not left untouched."""
 
     def __init__(self, model: FineModel, proposal: "Proposal", n_samples: int = 48, uniform_every: int = 4,
-                 warmup: int = 0, train_rays: int = 2048, eta: float = 0.05):
+                 warmup: int = 0, train_rays: int = 1024, eta: float = 0.05):
         if uniform_every < 1 or n_samples < 1:
             raise ValueError("uniform_every and n_samples must be >= 1")
         self.model, self.proposal = model, proposal
