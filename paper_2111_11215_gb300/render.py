@@ -527,7 +527,11 @@ class BatchStager:
             loss = trainer.step(*batch)
             st.done()                         # batch k's buffers are free once the step's work is done
 
-    A buffer set is refilled only after the stream has passed the done() of the step that used it."""
+    A buffer set is refilled only after the stream has passed the done() of the step that used it;
+    staging into a set whose batch was taken but not marked done() raises, as does staging a third
+    batch before one is taken.  The copy reads the host tensors asynchronously: a host batch must
+    not be written again until its batch has been taken and the taking stream has passed that
+    point (e.g. at the next done() that is synchronised on)."""
 
     def __init__(self, like, device=None):
         dev = like[0].device if device is None else device
@@ -535,15 +539,18 @@ class BatchStager:
         self.copy_stream = torch.cuda.Stream(device=dev)
         self.ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
         self.ev_used = [torch.cuda.Event(), torch.cuda.Event()]
-        self.used = [False, False]
-        self.n_staged = self.n_taken = 0
+        # batches j < n_staged were staged into set j % 2, j < n_taken taken, j < n_done done
+        self.n_staged = self.n_taken = self.n_done = 0
 
     def stage(self, host_batch):
         """Queue the copy of host_batch (pinned CPU tensors shaped like the example batch)."""
         k = self.n_staged % 2
         if self.n_staged - self.n_taken >= 2:
             raise RuntimeError("BatchStager: both buffer sets hold batches not taken yet")
-        if self.used[k]:
+        if self.n_staged >= 2:
+            # set k last held batch n_staged - 2: its step must have been marked done
+            if self.n_done < self.n_staged - 1:
+                raise RuntimeError("BatchStager: the batch in this buffer set was taken but not marked done()")
             self.copy_stream.wait_event(self.ev_used[k])
         with torch.cuda.stream(self.copy_stream):
             for dst, src in zip(self.bufs[k], host_batch):
@@ -562,8 +569,11 @@ class BatchStager:
         return self.bufs[k]
 
     def done(self, stream=None):
-        """The step that used the last taken batch has been queued on `stream` (default: current)."""
-        k = (self.n_taken - 1) % 2
+        """The step that used the oldest taken batch not yet marked done has been queued on `stream`
+        (default: current)."""
+        if self.n_done >= self.n_taken:
+            raise RuntimeError("BatchStager: no taken batch to mark done")
+        k = self.n_done % 2
         cur = stream if stream is not None else torch.cuda.current_stream(self.bufs[k][0].device)
         self.ev_used[k].record(cur)
-        self.used[k] = True
+        self.n_done += 1
