@@ -134,6 +134,47 @@ class AdamState:
         self.v = torch.zeros_like(param)
 
 
+# Checkpoint / resume.  A state_dict() holds device tensors cloned on the caller's stream (so that
+# the snapshot is ordered after every step queued before it) and plain Python scalars; torch.save
+# writes it as it is and torch.load(..., map_location=...) reads it back.  The library draws no
+# random numbers (jitter and batches come from the caller), so the caller's own RNG state is the
+# only other thing a resumed run needs.
+STATE_VERSION = 1
+
+
+def _clone_on(t, stream):
+    if t is None:
+        return None
+    if stream is None:
+        return t.detach().clone()
+    with torch.cuda.stream(stream):
+        return t.detach().clone()
+
+
+def _copy_on(dst, src, stream):
+    if tuple(dst.shape) != tuple(src.shape) or dst.dtype != src.dtype:
+        raise ValueError(f"load_state_dict: tensor {tuple(src.shape)} {src.dtype} does not fit "
+                         f"{tuple(dst.shape)} {dst.dtype}")
+    if stream is None:
+        dst.copy_(src)
+    else:
+        with torch.cuda.stream(stream):
+            dst.copy_(src)
+
+
+def _zero_on(t, stream):
+    if stream is None:
+        t.zero_()
+    else:
+        with torch.cuda.stream(stream):
+            t.zero_()
+
+
+def _check_version(sd, what):
+    if not isinstance(sd, dict) or sd.get("version") != STATE_VERSION or sd.get("kind") != what:
+        raise ValueError(f"load_state_dict: not a {what} state of version {STATE_VERSION}")
+
+
 class FineModel:
     """Fine-stage parameters (Sec. 4.2): density grid, feature grid (FP32 master, optional BF16
     storage copy written by the Adam step), colour MLP in one flat buffer; their gradients and
@@ -280,6 +321,58 @@ class FineModel:
             for k, (m, v) in moments.items():
                 self.adam[k].m, self.adam[k].v = m, v
 
+    def state_dict(self, stream=None) -> dict:
+        """Snapshot for checkpoint / resume: the density grid, the feature grid (FP32 master and the
+        BF16 copy), the MLP, the Adam moments of all three, the step counts and the lattice (shape
+        and sampling step, which progressive scaling changes).  Taken on `stream` (default:
+        current) after any pending feature-grid Adam step.  Gradients are not part of it: every
+        Adam step leaves them zero."""
+        self.wait_params(stream)
+        c = lambda t: _clone_on(t, stream)  # noqa: E731
+        return {"kind": "FineModel", "version": STATE_VERSION, "shape": self.shape, "channels": self.cd.channels,
+                "layout": self.layout, "bf16_feat": self.bf16_feat, "step": float(self.params.step),
+                "density": c(self.density), "feat": c(self._feat), "feat_bf16": c(self._feat_bf16),
+                "mlp": c(self.mlp_flat), "adam": {k: {"m": c(a.m), "v": c(a.v)} for k, a in self.adam.items()},
+                "step_count": self.step_count, "grid_t0": self.grid_t0}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Restore a state_dict() snapshot (tensors on any device) on `stream` (default: current).
+        The model must have the snapshot's grid layout, channel count, MLP size and BF16 setting; a
+        snapshot on another lattice (taken after progressive scaling) replaces the grids and the
+        renderer with ones of its shape and sampling step.  Gradients are cleared."""
+        _check_version(sd, "FineModel")
+        if (sd["layout"] != self.layout or sd["channels"] != self.cd.channels
+                or bool(sd["bf16_feat"]) != self.bf16_feat or sd["mlp"].numel() != self.mlp_flat.numel()):
+            raise ValueError("load_state_dict: the snapshot's layout, channels, MLP size or BF16 setting differ")
+        self.wait_params(stream)
+        self._feat_deferred = None
+        dev = self.density.device
+        shape = tuple(int(v) for v in sd["shape"])
+        if shape != self.shape or tuple(sd["density"].shape) != tuple(self.density.shape):
+            self.dd, self.cd = self.dd.with_(shape=shape), self.cd.with_(shape=shape)
+            self.density = torch.empty(sd["density"].shape, device=dev)
+            self._feat = torch.empty(sd["feat"].shape, device=dev)
+            if self.bf16_feat:
+                self._feat_bf16 = torch.empty(sd["feat_bf16"].shape, dtype=torch.bfloat16, device=dev)
+            self.g_density = torch.zeros_like(self.density)
+            self.g_feat = torch.zeros_like(self._feat)
+            self.adam["density"], self.adam["feat"] = AdamState(self.density), AdamState(self._feat)
+        if shape != tuple(self.renderer.dd.shape) or float(sd["step"]) != float(self.params.step):
+            self.params = self.params.with_(step=float(sd["step"]))
+            self.renderer = Renderer(self.params, self.dd, self.cd, self.renderer.n_rays, device=dev)
+            self._expl = None
+        _copy_on(self.density, sd["density"], stream)
+        _copy_on(self._feat, sd["feat"], stream)
+        if self.bf16_feat:
+            _copy_on(self._feat_bf16, sd["feat_bf16"], stream)
+        _copy_on(self.mlp_flat, sd["mlp"], stream)
+        for k, a in self.adam.items():
+            _copy_on(a.m, sd["adam"][k]["m"], stream)
+            _copy_on(a.v, sd["adam"][k]["v"], stream)
+        for g in (self.g_density, self.g_feat, self.g_mlp):
+            _zero_on(g, stream)
+        self.step_count, self.grid_t0 = int(sd["step_count"]), int(sd["grid_t0"])
+
     def forward(self, rays_o, rays_d, jitter=None, target=None, stream=None):
         self.wait_params(stream)
         return self.renderer.forward(self.density, self.cgrid, self.mlp, rays_o, rays_d, jitter, None, target,
@@ -362,6 +455,34 @@ class CoarseModel:
         self.view_counts, self.lr_scale = counts.view(self.density.shape), scale.view(self.density.shape)
         return int(n_max.item())
 
+    def state_dict(self, stream=None) -> dict:
+        """Snapshot for checkpoint / resume: both grids, their Adam moments, the step count and the
+        Prior-2 view counts and learning-rate scale when set; taken on `stream` (default: current).
+        Gradients are not part of it: every Adam step leaves them zero."""
+        c = lambda t: _clone_on(t, stream)  # noqa: E731
+        return {"kind": "CoarseModel", "version": STATE_VERSION, "shape": tuple(self.dd.shape),
+                "density": c(self.density), "rgb": c(self.rgb_grid),
+                "adam": {k: {"m": c(a.m), "v": c(a.v)} for k, a in self.adam.items()},
+                "step_count": self.step_count, "view_counts": c(self.view_counts), "lr_scale": c(self.lr_scale)}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Restore a state_dict() snapshot of a model of the same grid shape on `stream` (default:
+        current); gradients are cleared."""
+        _check_version(sd, "CoarseModel")
+        if tuple(sd["shape"]) != tuple(self.dd.shape):
+            raise ValueError("load_state_dict: the snapshot's grid shape differs")
+        _copy_on(self.density, sd["density"], stream)
+        _copy_on(self.rgb_grid, sd["rgb"], stream)
+        for k, a in self.adam.items():
+            _copy_on(a.m, sd["adam"][k]["m"], stream)
+            _copy_on(a.v, sd["adam"][k]["v"], stream)
+        for g in (self.g_density, self.g_rgb):
+            _zero_on(g, stream)
+        dev = self.density.device
+        self.view_counts = None if sd["view_counts"] is None else _clone_on(sd["view_counts"].to(dev), stream)
+        self.lr_scale = None if sd["lr_scale"] is None else _clone_on(sd["lr_scale"].to(dev), stream)
+        self.step_count = int(sd["step_count"])
+
     def forward(self, rays_o, rays_d, jitter=None, stream=None):
         return self.renderer.forward(self.density, self.rgb_grid, None, rays_o, rays_d, jitter, None, None,
                                      self.rgb, self.tfinal, None, None, stream)
@@ -428,6 +549,22 @@ class Proposal:
         B.dvgo_adam_step(self.flat, self.grad, self.adam.m, self.adam.v, lr, self.step_count, stream=stream)
         return self.loss
 
+    def state_dict(self, stream=None) -> dict:
+        """Snapshot for checkpoint / resume: the network's weights, their Adam moments, the step count
+        and the learning-rate schedule; taken on `stream` (default: current)."""
+        c = lambda t: _clone_on(t, stream)  # noqa: E731
+        return {"kind": "Proposal", "version": STATE_VERSION, "flat": c(self.flat), "m": c(self.adam.m),
+                "v": c(self.adam.v), "step_count": self.step_count, "lr": self.lr, "decay_steps": self.decay_steps}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Restore a state_dict() snapshot on `stream` (default: current); the gradient is cleared."""
+        _check_version(sd, "Proposal")
+        _copy_on(self.flat, sd["flat"], stream)
+        _copy_on(self.adam.m, sd["m"], stream)
+        _copy_on(self.adam.v, sd["v"], stream)
+        _zero_on(self.grad, stream)
+        self.step_count, self.lr, self.decay_steps = int(sd["step_count"]), float(sd["lr"]), float(sd["decay_steps"])
+
     def sample(self, rays_o, rays_d, jitter=None, n_samples: int = 48, eta: float = 0.05, t_out=None, dt_out=None,
                stream=None, after_forward=None):
         """Explicit samples (t, dt) [R, n_samples] drawn from the predicted PDFs mixed with the
@@ -477,6 +614,22 @@ class ProposalTrainer:
         the new lattice and step from then on."""
         self.model.rescale(shape, step, stream, adam)
         self.proposal.params, self.proposal.dd = self.model.params, self.model.dd
+
+    def state_dict(self, stream=None) -> dict:
+        """Snapshot for checkpoint / resume: the model's and the proposal's states and the schedule's
+        position (which step comes next, uniform or proposal); taken on `stream` (default: current),
+        which the proposal's own training stream has already been joined to."""
+        return {"kind": "ProposalTrainer", "version": STATE_VERSION, "model": self.model.state_dict(stream),
+                "proposal": self.proposal.state_dict(stream), "i": self.i, "n_uniform": self.n_uniform,
+                "n_proposal": self.n_proposal}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Restore a state_dict() snapshot into this trainer's model and proposal on `stream`."""
+        _check_version(sd, "ProposalTrainer")
+        self.model.load_state_dict(sd["model"], stream)
+        self.proposal.load_state_dict(sd["proposal"], stream)
+        self.proposal.params, self.proposal.dd = self.model.params, self.model.dd
+        self.i, self.n_uniform, self.n_proposal = int(sd["i"]), int(sd["n_uniform"]), int(sd["n_proposal"])
 
     def is_uniform(self, i: int) -> bool:
         return i < self.warmup or i % self.uniform_every == 0
